@@ -1,0 +1,165 @@
+"""Decomposition layout for the oracle (test infrastructure only).
+
+Follows the point sets of Sec. 2.2.1 (x_I, x_B, x_Gamma per subdomain), the
+split Gamma = Pi u Delta of Sec. 3 (Pi = interior cross points of the grid of
+subdomains), the change of variables T^i of Sec. 3.2 (Fig. "change": the
+coarse variable of a cross point is the linear function along each incident
+edge, so a Delta point at arc fraction s from the edge start carries weight
+1-s on the start vertex and s on the end vertex, each only if that vertex is in
+Pi), and the modified flux A_m of Sec. 3.2 (the row of a cross point p is the
+mean flux over the points of an incident edge, opposite end excluded, summed
+over the edges of the subdomain that meet p).
+
+Geometry conventions (independent restatement of the problem format):
+subdomain (ix, iy) = index iy*nx+ix; horizontal edge (ix, vy) has id vy*nx+ix,
+vertical edge (vx, iy) has id nx*(ny+1)+vx*ny+iy; edge points at
+start + k/(e+1)(end-start), k=1..e; global Dirichlet list = boundary-edge
+points in edge order, then boundary vertices in order vy*(nx+1)+vx; global
+Gamma = Pi (cross points in order (vy-1)*(nx-1)+(vx-1)) then Delta (interface
+edges in id order, points k=1..e).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class SubLayout:
+    """Per-subdomain point sets and index maps."""
+
+    def __init__(self):
+        self.bnd_xy = None        # [nB, 2]
+        self.bnd_gidx = None      # [nB] index into the global Dirichlet list
+        self.pi_xy = None         # [nPi, 2] local cross points (BL, BR, TL, TR order)
+        self.pi_gidx = None       # [nPi] global Pi index
+        self.pi_vertex = None     # list of (vx, vy)
+        self.dl_xy = None         # [nDl, 2] local Delta points
+        self.dl_gidx = None       # [nDl] global Gamma index (>= n_Pi)
+        self.dl_normal = None     # [nDl, 2] outward normal of this subdomain
+        self.dl_alpha = None      # [nDl] T weight on the start vertex
+        self.dl_alpha_pi = None   # [nDl] local Pi index of the start vertex or -1
+        self.dl_beta = None       # [nDl] T weight on the end vertex
+        self.dl_beta_pi = None    # [nDl] local Pi index of the end vertex or -1
+        self.am_terms = None      # per local Pi: list of (weight, xy, normal)
+
+
+class Layout:
+    def __init__(self, nx, ny, box, edge_pts):
+        self.nx, self.ny, self.box = nx, ny, box
+        self.edge_pts = np.asarray(edge_pts, np.int64)
+        x0, x1, y0, y1 = box
+        self.hx, self.hy = (x1 - x0) / nx, (y1 - y0) / ny
+        H = nx * (ny + 1)
+        self.n_edges = H + (nx + 1) * ny
+        # global Dirichlet list
+        bnd_off = {}
+        nb = 0
+        for eid in range(self.n_edges):
+            if self.edge_on_boundary(eid):
+                bnd_off[eid] = nb
+                nb += int(self.edge_pts[eid])
+        vtx_bnd = {}
+        for vy in range(ny + 1):
+            for vx in range(nx + 1):
+                if vx in (0, nx) or vy in (0, ny):
+                    vtx_bnd[(vx, vy)] = nb
+                    nb += 1
+        self.n_bnd = nb
+        # global Gamma
+        self.n_pi = (nx - 1) * (ny - 1)
+        dl_off = {}
+        nd = 0
+        for eid in range(self.n_edges):
+            if not self.edge_on_boundary(eid):
+                dl_off[eid] = self.n_pi + nd
+                nd += int(self.edge_pts[eid])
+        self.n_delta = nd
+        self.n_gamma = self.n_pi + nd
+        self.subs = []
+        for i in range(nx * ny):
+            self.subs.append(self._sub(i, bnd_off, vtx_bnd, dl_off))
+
+    # ------------------------------------------------------------------
+    def edge_on_boundary(self, eid):
+        nx, ny = self.nx, self.ny
+        H = nx * (ny + 1)
+        if eid < H:
+            vy = eid // nx
+            return vy == 0 or vy == ny
+        vx = (eid - H) // ny
+        return vx == 0 or vx == nx
+
+    def is_cross(self, v):
+        return 0 < v[0] < self.nx and 0 < v[1] < self.ny
+
+    def pi_index(self, v):
+        return (v[1] - 1) * (self.nx - 1) + (v[0] - 1)
+
+    def vxy(self, v):
+        return np.array([self.box[0] + v[0] * self.hx, self.box[2] + v[1] * self.hy])
+
+    def _sub(self, i, bnd_off, vtx_bnd, dl_off):
+        nx, ny = self.nx, self.ny
+        H = nx * (ny + 1)
+        ix, iy = i % nx, i // nx
+        BL, BR, TL, TR = (ix, iy), (ix + 1, iy), (ix, iy + 1), (ix + 1, iy + 1)
+        # (edge id, start vertex, end vertex, outward normal)
+        edges = [(iy * nx + ix, BL, BR, (0.0, -1.0)),
+                 ((iy + 1) * nx + ix, TL, TR, (0.0, 1.0)),
+                 (H + ix * ny + iy, BL, TL, (-1.0, 0.0)),
+                 (H + (ix + 1) * ny + iy, BR, TR, (1.0, 0.0))]
+        s = SubLayout()
+        bxy, bg = [], []
+        for eid, a, b, _ in edges:
+            if self.edge_on_boundary(eid):
+                e = int(self.edge_pts[eid])
+                pa, pb = self.vxy(a), self.vxy(b)
+                for k in range(1, e + 1):
+                    bxy.append(pa + k / (e + 1) * (pb - pa))
+                    bg.append(bnd_off[eid] + k - 1)
+        for v in (BL, BR, TL, TR):
+            if not self.is_cross(v) and (v[0] in (0, nx) or v[1] in (0, ny)):
+                bxy.append(self.vxy(v))
+                bg.append(vtx_bnd[v])
+        s.bnd_xy = np.array(bxy).reshape(-1, 2)
+        s.bnd_gidx = np.array(bg, np.int64)
+        pis = [v for v in (BL, BR, TL, TR) if self.is_cross(v)]
+        s.pi_vertex = pis
+        s.pi_xy = np.array([self.vxy(v) for v in pis]).reshape(-1, 2)
+        s.pi_gidx = np.array([self.pi_index(v) for v in pis], np.int64)
+        loc_pi = {v: k for k, v in enumerate(pis)}
+        dxy, dg, dn, al, alp, be, bep = [], [], [], [], [], [], []
+        for eid, a, b, nrm in edges:
+            if self.edge_on_boundary(eid):
+                continue
+            e = int(self.edge_pts[eid])
+            pa, pb = self.vxy(a), self.vxy(b)
+            for k in range(1, e + 1):
+                frac = k / (e + 1)
+                dxy.append(pa + frac * (pb - pa))
+                dg.append(dl_off[eid] + k - 1)
+                dn.append(nrm)
+                al.append(1.0 - frac if a in loc_pi else 0.0)
+                alp.append(loc_pi.get(a, -1))
+                be.append(frac if b in loc_pi else 0.0)
+                bep.append(loc_pi.get(b, -1))
+        s.dl_xy = np.array(dxy).reshape(-1, 2)
+        s.dl_gidx = np.array(dg, np.int64)
+        s.dl_normal = np.array(dn).reshape(-1, 2)
+        s.dl_alpha, s.dl_alpha_pi = np.array(al), np.array(alp, np.int64)
+        s.dl_beta, s.dl_beta_pi = np.array(be), np.array(bep, np.int64)
+        # A_m rows of the cross points: mean flux over (p and the edge's e points)
+        terms = []
+        for v in pis:
+            t = []
+            for eid, a, b, nrm in edges:
+                if v not in (a, b):
+                    continue
+                e = int(self.edge_pts[eid])
+                wgt = 1.0 / (e + 1)
+                pa, pb = self.vxy(a), self.vxy(b)
+                t.append((wgt, self.vxy(v), nrm))
+                for k in range(1, e + 1):
+                    t.append((wgt, pa + k / (e + 1) * (pb - pa), nrm))
+            terms.append(t)
+        s.am_terms = terms
+        return s
