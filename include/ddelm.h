@@ -1,0 +1,174 @@
+/*
+ * ddelm.h -- C ABI of the GB300 DDELM-NN library (libddelm.so).
+ *
+ * The library solves the coarse-space, Neumann-Neumann accelerated domain
+ * decomposition of extreme learning machines of arXiv 2503.10032 for 2-D
+ * second-order problems on a rectangle split into nx x ny subdomains:
+ *
+ *   setup  (ddelm_setup):  assembly of the local ELM collocation matrices
+ *          K_c^i (Sec. 2.2.1 with the change of variables of Sec. 3.2),
+ *          the Neumann matrices K-bar^i (Sec. 3.1), the modified flux rows
+ *          A_m^i (Sec. 3.2); factorisation of every local least-squares
+ *          problem; the local operators from which D_ab = -A_a K^+ B_b
+ *          (Sec. 3), K K^+ and P = A-bar K-bar^+ B-bar (Sec. 3.1) are
+ *          applied; the coarse matrix S_Pi assembled in full and factored
+ *          (Sec. 3).
+ *   solve  (ddelm_solve): for given forcing / boundary data, the right-hand
+ *          side of Eq. (nn-mixed), CG on Eq. (nn-mixed) for mu_Delta, then
+ *          [c; mu_Pi] = K~^+ (f~ - B~ mu_Delta), Eq. (coarse_sol_2), and the
+ *          network values at caller-given points.
+ *   backward (ddelm_backward): the adjoint of solve with respect to the
+ *          right-hand-side values (gradients of a loss given dL/dc).
+ *
+ * Conventions shared by every entry point:
+ *   - All floating-point data are IEEE double.  Host pointers are read during
+ *     the call only; device pointers are owned by the caller and must stay
+ *     valid until the stream work of the call has completed.
+ *   - Subdomain (ix, iy) has index iy*nx + ix and covers
+ *     [x0 + ix*hx, x0 + (ix+1)*hx] x [y0 + iy*hy, y0 + (iy+1)*hy].
+ *   - Grid edges: horizontal edge (ix, vy) has id vy*nx + ix; vertical edge
+ *     (vx, iy) has id nx*(ny+1) + vx*ny + iy.  An edge with e points carries
+ *     them at start + k/(e+1) * (end - start), k = 1..e, start = the vertex
+ *     with the smaller coordinate.
+ *   - Dirichlet data g are given on the global boundary list: the points of
+ *     every edge on the outer boundary in edge-id order, then every grid
+ *     vertex on the outer boundary in order vy*(nx+1) + vx.
+ *   - Interface unknowns: Gamma = Pi (interior grid vertices, order
+ *     (vy-1)*(nx-1) + (vx-1)) followed by Delta (points of the interior edges,
+ *     edge-id order, k = 1..e).  With the change of variables on, mu_Pi are
+ *     the coefficients of the edge-linear coarse functions of Sec. 3.2 and
+ *     mu_Delta the remaining values (mu = T mu' of Sec. 3.2).
+ *   - Arrays with a right-hand-side dimension are row-major [rows x n_rhs].
+ *   - Return value: DDELM_OK or a negative status; no call aborts, traps or
+ *     exits.  After a CUDA error the handle must be destroyed.
+ *
+ * Numerical readings fixed by this library (the paper is silent on them):
+ *   - K^+ is the pseudo-inverse of K augmented by rows eps*I with zero data
+ *     (a ridge term eps^2 |c|^2 in every local least-squares loss), with
+ *     eps^2 = eps_rel^2 * |K|_F^2 / M, separately for K^i and K-bar^i;
+ *     eps_rel = 0 gives the Moore-Penrose pseudo-inverse.
+ *   - F phi = (w . n)(1 - tanh^2(w.x + b)), n the subdomain's outward normal.
+ *   - A-bar^i uses the Delta rows of K_c^i (the (T^i)^{-1} C phi rows).
+ *   - The corner row of A_m^i sums, over the two edges of subdomain i that
+ *     meet the corner, the mean flux over the corner and the edge's e points.
+ */
+#ifndef DDELM_H
+#define DDELM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDELM_OK 0
+#define DDELM_ERR_INVALID_ARG (-1)    /* bad sizes, null pointers, workspace too small */
+#define DDELM_ERR_RANK_DEFICIENT (-2) /* a local Cholesky pivot was not positive (info: subdomain) */
+#define DDELM_ERR_NOT_CONVERGED (-3)  /* CG reached max_iters; outputs are still written */
+#define DDELM_ERR_CUDA (-4)           /* a CUDA runtime call failed */
+#define DDELM_ERR_TIMEOUT (-5)        /* a device-side grid barrier gave up waiting */
+#define DDELM_ERR_UNSUPPORTED (-6)    /* an option or size this build does not support */
+
+#define DDELM_OP_POISSON 0   /* L = -Laplacian */
+#define DDELM_OP_DIFFUSION 1 /* L = -div(a grad), a and grad a given at x_int */
+
+#define DDELM_PREC_FP64 0  /* every step in FP64 */
+#define DDELM_PREC_MIXED 1 /* FP32 inner CG with FP64 true-residual refinement */
+
+typedef struct ddelm_options {
+  double theta;           /* Eq. (nn-mixed) mixing weight; the paper uses 0.999 */
+  double eps_rel;         /* ridge of the local least-squares problems (see above) */
+  double tol;             /* stop when the relative residual of Eq. (nn-mixed) < tol */
+  int max_iters;          /* CG iteration cap (per refinement sweep in MIXED) */
+  int use_change_of_vars; /* 1: K_c^i (Sec. 3.2); 0: plain C phi rows */
+  int precision;          /* DDELM_PREC_FP64 or DDELM_PREC_MIXED */
+  int max_refine;         /* MIXED: outer refinement sweeps */
+  int keep_matrices;      /* 1: keep the assembled K_c^i, K-bar^i, A_m^i for ddelm_inspect */
+} ddelm_options;
+
+typedef struct ddelm_problem {
+  int nx, ny;               /* subdomains per direction (>= 1 each) */
+  double x0, x1, y0, y1;    /* the rectangle */
+  int op;                   /* DDELM_OP_POISSON or DDELM_OP_DIFFUSION */
+  int n_rhs;                /* right-hand sides solved together (>= 1) */
+  const int *M;             /* [n_sub] neurons per subdomain (1..1024) */
+  const double *w_hat;      /* [sum M][2] hidden weights before scaling */
+  const double *b_hat;      /* [sum M] hidden biases before scaling */
+  double scale;             /* s: w = s*w_hat, b = s*b_hat */
+  const int *n_int;         /* [n_sub] interior collocation points per subdomain */
+  const double *x_int;      /* [sum n_int][2] interior points, subdomain by subdomain */
+  const double *a_int;      /* [sum n_int] coefficient a (DIFFUSION only, else NULL) */
+  const double *grad_a_int; /* [sum n_int][2] grad a (DIFFUSION only, else NULL) */
+  const int *edge_pts;      /* [n_edges] points strictly inside every grid edge */
+  const int *n_eval;        /* [n_sub] evaluation points per subdomain (NULL: none) */
+  const double *x_eval;     /* [sum n_eval][2] evaluation points */
+  ddelm_options opt;
+} ddelm_problem;
+
+typedef struct ddelm_sizes {
+  int n_sub, n_edges;
+  int n_bnd;           /* length of the global Dirichlet list */
+  int n_pi, n_delta;   /* |Pi|, |Delta| */
+  long long sum_M, sum_int, sum_eval;
+  size_t workspace_bytes; /* device workspace ddelm_setup needs */
+} ddelm_sizes;
+
+typedef struct ddelm_solve_info {
+  int iterations;        /* CG iterations (all sweeps) */
+  int refinements;       /* MIXED: outer sweeps taken */
+  double rel_residual;   /* max over right-hand sides of the true FP64
+                            |b_theta - S_theta mu| / |b_theta| at exit */
+  double ms_total;       /* device time of the call (stream events) */
+} ddelm_solve_info;
+
+typedef struct ddelm_handle ddelm_handle;
+
+/* Sizes derived from the problem (host only, no GPU work).
+ * Returns DDELM_ERR_INVALID_ARG on inconsistent input. */
+int ddelm_query(const ddelm_problem *prob, ddelm_sizes *out);
+
+/* Builds the handle and runs the whole setup on `stream` (a cudaStream_t;
+ * NULL = default stream): uploads the problem, assembles the local matrices,
+ * factorises them, forms the local and coarse operators.  d_workspace is a
+ * device buffer of at least ddelm_sizes.workspace_bytes bytes (256-byte
+ * aligned), owned by the caller and used by the handle until ddelm_destroy.
+ * The call returns after the setup work has completed on the stream.
+ * info_sub (nullable) receives the first rank-deficient subdomain. */
+int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_bytes,
+                void *stream, ddelm_handle **out, int *info_sub);
+
+/* One solve for new data.  Device inputs: d_f_int [sum n_int][n_rhs] forcing
+ * at the interior points, d_g_bnd [n_bnd][n_rhs] Dirichlet data.  Device
+ * outputs (nullable): d_c [sum M][n_rhs] network coefficients,
+ * d_mu [n_pi + n_delta][n_rhs] interface unknowns (Pi first),
+ * d_u_eval [sum n_eval][n_rhs] network values at the evaluation points.
+ * info (host, nullable) is filled after the stream work completed. */
+int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, double *d_c,
+                double *d_mu, double *d_u_eval, ddelm_solve_info *info, void *stream);
+
+/* Adjoint of the last-configured solve map (f, g) -> c, for a cotangent
+ * d_grad_c [sum M][n_rhs]: writes d_grad_f [sum n_int][n_rhs] and
+ * d_grad_g [n_bnd][n_rhs] (device).  The map is linear in (f, g), so the
+ * result is the transpose of ddelm_solve's linear map applied to grad_c. */
+int ddelm_backward(ddelm_handle *h, const double *d_grad_c, double *d_grad_f, double *d_grad_g,
+                   ddelm_solve_info *info, void *stream);
+
+/* Copies a local block of subdomain `sub` to host memory for inspection
+ * (synchronous).  which: 0 K_c^i [m x M], 1 K-bar^i [m x M], 2 A_m^i [nG x M],
+ * 3 Lambda^i = A_m^i K^+ E_Gamma [nG x nG], 4 Psi^i = E_Gamma^T K K^+ E_Gamma
+ * [nG x nG], 5 Phi^i = A-bar^i K-bar^+ E_Delta [nDl x nDl], 6 S_Pi [n_pi x n_pi]
+ * (sub ignored), 7 the four sizes {m, M, nG, nDl} as doubles.  Blocks 0-2 are
+ * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
+ * their size to the workspace).  out_len is the capacity of host_out in
+ * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */
+int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t out_len);
+
+void ddelm_destroy(ddelm_handle *h);
+
+const char *ddelm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDELM_H */

@@ -1,0 +1,307 @@
+// C ABI of libddelm (declared in include/ddelm.h): handle creation, the setup
+// sequence (assembly, shifted CholeskyQR3 of every local least-squares
+// matrix, local operators, coarse problem), the solve sequence and
+// inspection.  The library allocates no device memory: every buffer lives in
+// the caller's workspace.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ddelm_internal.h"
+
+using namespace ddelm;
+
+struct ddelm_handle {
+  Plan plan;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+#define CK(x)                                      \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) return DDELM_ERR_CUDA;  \
+  } while (0)
+
+double *dbase(ddelm_handle *h) { return reinterpret_cast<double *>(h->ws + h->plan.off_dbl); }
+
+template <class T>
+void put(std::vector<char> &buf, size_t off, const std::vector<T> &v) {
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+}
+
+int run_setup(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s, int *info_sub) {
+  Plan &p = h->plan;
+  // tables
+  std::vector<char> tab(p.bytes_tables, 0);
+  put(tab, p.off_subs, p.subs);
+  put(tab, p.off_rows, p.rows);
+  put(tab, p.off_gdesc, p.gdesc);
+  put(tab, p.off_gtile, p.gtile);
+  put(tab, p.off_cdesc, p.cdesc);
+  put(tab, p.off_ints, p.ints);
+  CK(cudaMemcpyAsync(h->ws, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+  // problem data: w = s*w_hat, b = s*b_hat, interior points, coefficient
+  double *db = dbase(h);
+  const long long sumM = p.sz.sum_M, sumI = p.sz.sum_int;
+  std::vector<double> w(2 * sumM), b(sumM);
+  for (long long j = 0; j < 2 * sumM; ++j) w[j] = prob->scale * prob->w_hat[j];
+  for (long long j = 0; j < sumM; ++j) b[j] = prob->scale * prob->b_hat[j];
+  CK(cudaMemcpyAsync(db + p.o_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_b, b.data(), b.size() * 8, cudaMemcpyHostToDevice, s));
+  if (sumI > 0) {
+    CK(cudaMemcpyAsync(db + p.o_xint, prob->x_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
+    if (p.op == DDELM_OP_DIFFUSION) {
+      CK(cudaMemcpyAsync(db + p.o_aint, prob->a_int, sumI * 8, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(db + p.o_gaint, prob->grad_a_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
+    }
+  }
+  CK(cudaMemsetAsync(db + p.o_status, 0, (4 * (size_t)p.n_sub + 64) * 8, s));
+  const long long np = p.n_pi > 0 ? p.n_pi : 1;
+  CK(cudaMemsetAsync(db + p.o_Dpp, 0, np * np * 8, s));
+  CK(cudaMemsetAsync(db + p.o_Spi, 0, np * np * 8, s));
+  // assembly
+  CK(launch_features(p, h->ws, s));
+  if (p.keep) {
+    long long off = p.o_keepX;
+    for (const auto &d : p.subs) {
+      const size_t mm = (size_t)d.m * d.M;
+      CK(cudaMemcpyAsync(db + off, db + d.oX, mm * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(db + off + mm, db + d.oKb, mm * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(db + off + 2 * mm, db + d.oA, (size_t)d.nG * d.M * 8, cudaMemcpyDeviceToDevice, s));
+      off += (2 * (long long)mm + (long long)d.nG * d.M + 31) / 32 * 32;
+    }
+  }
+  // shifted CholeskyQR3 of [K; eps I] and [K-bar; eps-bar I]
+  const auto &G = p.setup_gemm;
+  CK(launch_gemm_phase(p, G[0], h->ws, s));
+  CK(launch_chol_phase(p, p.chol_pass[0], h->ws, s));
+  CK(launch_gemm_phase(p, G[1], h->ws, s));
+  CK(launch_gemm_phase(p, G[2], h->ws, s));
+  CK(launch_gemm_phase(p, G[3], h->ws, s));
+  CK(launch_chol_phase(p, p.chol_pass[1], h->ws, s));
+  CK(launch_gemm_phase(p, G[4], h->ws, s));
+  CK(launch_gemm_phase(p, G[5], h->ws, s));
+  CK(launch_gemm_phase(p, G[6], h->ws, s));
+  CK(launch_chol_phase(p, p.chol_pass[2], h->ws, s));
+  CK(launch_gemm_phase(p, G[7], h->ws, s));
+  CK(launch_gemm_phase(p, G[8], h->ws, s));
+  // local operators
+  CK(launch_gemm_phase(p, G[9], h->ws, s));
+  CK(launch_gemm_phase(p, G[10], h->ws, s));
+  // coarse problem
+  if (p.n_pi > 0) {
+    CK(launch_coarse_assembly(p, h->ws, s));
+    CK(launch_gemm_phase(p, G[11], h->ws, s));
+    CK(cudaMemcpyAsync(db + p.o_SpiR, db + p.o_Spi, (size_t)np * np * 8, cudaMemcpyDeviceToDevice, s));
+    CK(launch_chol_phase(p, p.chol_coarse, h->ws, s));
+    CK(launch_gemm_phase(p, G[12], h->ws, s));
+    CK(launch_gemm_phase(p, G[13], h->ws, s));
+    CK(launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
+    CK(launch_gemm_phase(p, G[14], h->ws, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> st(2 * (size_t)p.n_sub + 1);
+  CK(cudaMemcpy(st.data(), db + p.o_status, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < st.size(); ++k)
+    if (st[k]) {
+      if (info_sub) *info_sub = int(k / 2);
+      return DDELM_ERR_RANK_DEFICIENT;
+    }
+  return DDELM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddelm_query(const ddelm_problem *prob, ddelm_sizes *out) {
+  if (!out) return DDELM_ERR_INVALID_ARG;
+  Plan p;
+  int rc = build_plan(prob, p);
+  if (rc != DDELM_OK) return rc;
+  *out = p.sz;
+  return DDELM_OK;
+}
+
+int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_bytes, void *stream,
+                ddelm_handle **out, int *info_sub) {
+  if (!out || !d_workspace) return DDELM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (info_sub) *info_sub = -1;
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return DDELM_ERR_INVALID_ARG;
+  ddelm_handle *h = new (std::nothrow) ddelm_handle();
+  if (!h) return DDELM_ERR_INVALID_ARG;
+  int rc = build_plan(prob, h->plan);
+  if (rc != DDELM_OK) {
+    delete h;
+    return rc;
+  }
+  if (workspace_bytes < h->plan.bytes_total) {
+    delete h;
+    return DDELM_ERR_INVALID_ARG;
+  }
+  h->ws = static_cast<char *>(d_workspace);
+  h->ws_bytes = workspace_bytes;
+  rc = run_setup(h, prob, static_cast<cudaStream_t>(stream), info_sub);
+  if (rc != DDELM_OK && rc != DDELM_ERR_RANK_DEFICIENT) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return rc;
+}
+
+int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, double *d_c, double *d_mu,
+                double *d_u_eval, ddelm_solve_info *info, void *stream) {
+  if (!h) return DDELM_ERR_INVALID_ARG;
+  Plan &p = h->plan;
+  if ((p.sz.sum_int > 0 && !d_f_int) || (p.sz.n_bnd > 0 && !d_g_bnd)) return DDELM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *db = dbase(h);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (info) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  CK(launch_gather_rhs(p, h->ws, d_f_int, d_g_bnd, s));
+  const auto &G = p.setup_gemm;
+  CK(launch_gemm_phase(p, G[15], h->ws, s));
+  CK(launch_gemm_phase(p, G[16], h->ws, s));
+  CK(launch_gemm_phase(p, G[17], h->ws, s));
+  CK(launch_gemm_phase(p, G[18], h->ws, s));
+  // barrier words and error flag
+  CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
+  CgArgs a;
+  a.mu_out = d_mu;
+  a.c_out = d_c;
+  a.max_iters = p.opt.max_iters;
+  a.tol = p.opt.tol;
+  a.theta = p.opt.theta;
+  CK(launch_cg(p, h->ws, a, s));
+  if (p.sz.sum_eval > 0) {
+    CK(launch_gemm_phase(p, G[19], h->ws, s));
+    if (d_u_eval) {
+      for (const auto &d : p.subs)
+        if (d.nE > 0)
+          CK(cudaMemcpyAsync(d_u_eval + d.eval_off * p.n_rhs, db + d.oU, (size_t)d.nE * p.n_rhs * 8,
+                             cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  int rc = DDELM_OK;
+  double hinfo[40];
+  int herr = 0;
+  if (info) CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  const long long nd = p.n_dl > 0 ? p.n_dl : 1, np = p.n_pi > 0 ? p.n_pi : 1;
+  const double *info_dev = db + p.o_cg + 12 * nd * p.n_rhs + 14 * np * p.n_rhs + 2048 * 32 - 64;
+  CK(cudaMemcpy(hinfo, info_dev, sizeof(hinfo), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&herr, db + p.o_status + 2 * p.n_sub + 16, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) rc = DDELM_ERR_TIMEOUT;
+  const int iters = int(hinfo[0]);
+  double resmax = 0.0;
+  for (int k = 0; k < p.n_rhs; ++k) resmax = hinfo[1 + k] > resmax ? hinfo[1 + k] : resmax;
+  if (rc == DDELM_OK && iters >= p.opt.max_iters && !(resmax < p.opt.tol)) rc = DDELM_ERR_NOT_CONVERGED;
+  if (info) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    info->iterations = iters;
+    info->refinements = 0;
+    info->rel_residual = resmax;
+    info->ms_total = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return rc;
+}
+
+int ddelm_backward(ddelm_handle *h, const double *, double *, double *, ddelm_solve_info *, void *) {
+  if (!h) return DDELM_ERR_INVALID_ARG;
+  return DDELM_ERR_UNSUPPORTED;
+}
+
+int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t out_len) {
+  if (!h || !host_out) return DDELM_ERR_INVALID_ARG;
+  Plan &p = h->plan;
+  double *db = dbase(h);
+  if (which == 6) {
+    const size_t n = (size_t)p.n_pi * p.n_pi;
+    if (n > out_len) return DDELM_ERR_INVALID_ARG;
+    if (n) CK(cudaMemcpy(host_out, db + p.o_Spi, n * 8, cudaMemcpyDeviceToHost));
+    return DDELM_OK;
+  }
+  if (sub < 0 || sub >= p.n_sub) return DDELM_ERR_INVALID_ARG;
+  const SubDev &d = p.subs[sub];
+  long long src = -1;
+  size_t n = 0;
+  switch (which) {
+    case 0:
+    case 1:
+    case 2: {
+      if (!p.keep) return DDELM_ERR_UNSUPPORTED;
+      long long off = p.o_keepX;
+      for (int i = 0; i < sub; ++i) {
+        const SubDev &e = p.subs[i];
+        off += (2LL * e.m * e.M + (long long)e.nG * e.M + 31) / 32 * 32;
+      }
+      const long long mm = (long long)d.m * d.M;
+      src = off + (which == 0 ? 0 : which == 1 ? mm : 2 * mm);
+      n = which == 2 ? (size_t)d.nG * d.M : (size_t)mm;
+      break;
+    }
+    case 3:
+      src = d.oLam;
+      n = (size_t)d.nG * d.nG;
+      break;
+    case 4:
+      src = d.oPsi;
+      n = (size_t)d.nG * d.nG;
+      break;
+    case 5:
+      src = d.oPhi;
+      n = (size_t)d.nDl * d.nDl;
+      break;
+    case 7: {
+      if (out_len < 4) return DDELM_ERR_INVALID_ARG;
+      host_out[0] = d.m;
+      host_out[1] = d.M;
+      host_out[2] = d.nG;
+      host_out[3] = d.nDl;
+      return DDELM_OK;
+    }
+    default:
+      return DDELM_ERR_INVALID_ARG;
+  }
+  if (n > out_len) return DDELM_ERR_INVALID_ARG;
+  if (n) CK(cudaMemcpy(host_out, db + src, n * 8, cudaMemcpyDeviceToHost));
+  return DDELM_OK;
+}
+
+void ddelm_destroy(ddelm_handle *h) { delete h; }
+
+const char *ddelm_status_string(int status) {
+  switch (status) {
+    case DDELM_OK:
+      return "ok";
+    case DDELM_ERR_INVALID_ARG:
+      return "invalid argument";
+    case DDELM_ERR_RANK_DEFICIENT:
+      return "a local factorisation met a non-positive pivot";
+    case DDELM_ERR_NOT_CONVERGED:
+      return "CG reached max_iters before the tolerance";
+    case DDELM_ERR_CUDA:
+      return "CUDA runtime error";
+    case DDELM_ERR_TIMEOUT:
+      return "a device grid barrier timed out";
+    case DDELM_ERR_UNSUPPORTED:
+      return "unsupported option or call";
+    default:
+      return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,654 @@
+// Persistent interface solve: right-hand side of Eq. (nn-mixed), CG on
+// Eq. (nn-mixed) (plain CG from mu = 0, stopped on the relative residual,
+// Sec. 4), and the reconstruction [c; mu_Pi] = K~^+ (f~ - B~ mu_Delta) of
+// Eq. (coarse_sol_2) -- one cooperative launch, one CTA per SM.
+//
+// The operator S_theta = B~^T (I - K~ K~^+) B~ + D~^T W D~ with
+// W = theta P^T P + (1 - theta) I is applied through the local operators
+//   Lambda^i = A_m^i K^+ E_Gamma   (D_ab = sum_i R_a^T Lambda^i R_b, Sec. 3),
+//   Psi^i    = E_Gamma^T K K^+ E_Gamma (B^T K K^+ B = sum_i R^T Psi^i R),
+//   Phi^i    = A-bar^i K-bar^+ E_Delta (P = -sum_i R_f^T Phi^i R_f, Sec. 3.1),
+// and the factored coarse matrix S_Pi (Sec. 3; the application of K~^+ and of
+// (K~^+)^T on [phi; 0] reduce to S_Pi^{-1} and the blocks above).  Interface
+// sums are gathers over the fixed owner lists of every Pi / Delta point, so
+// every run is bitwise reproducible.  All grid barriers are bounded: a barrier
+// that waits too long sets the error word and every CTA returns.
+#include <cooperative_groups.h>
+
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+
+constexpr int CG_THREADS = 512;
+constexpr int CG_WARPS = CG_THREADS / 32;
+
+// Δ vectors ([n_dl x R]) and Π vectors ([n_pi x R]) inside the CG region
+enum DlVec { V_MU = 0, V_RES, V_PD, V_Q, V_V, V_BKB, V_PV, V_W, V_B, V_TMP, N_DLVEC = 12 };
+enum PiVec { P_PSI = 0, P_RA, P_MPI, P_G, P_RNU, P_NU, P_DNU, P_DPI, P_PPI, P_MPF, P_GF, P_PSI2, P_S2, P_MPIF, N_PIVEC = 14 };
+enum Slab { S_H1 = 0, S_H2, S_VL, S_BL, S_TL, S_T2L, S_ZL, S_YL, N_SLAB = 9 };
+
+struct Ctx {
+  const SubDev *subs;
+  const int *ints;
+  double *db;
+  int n_sub, n_pi, n_dl, R;
+  int o_pi_own, o_dl_own;
+  int o_tpi, n_tpi, o_tdl, n_tdl, o_tg, n_tg, o_tc, n_tc;
+  long long o_Sinv, o_C1, o_C2, o_C3;
+  double *dl[N_DLVEC];
+  double *pv[N_PIVEC];
+  double *slab[N_SLAB];
+  double *red;  // [gridDim][2*16]
+  unsigned *bar;  // [count, generation]
+  int *err;
+  double theta, tol;
+  int max_iters;
+  double *mu_out, *c_out;
+  double *info;  // [0] iterations, [1..16] true residuals, [17..32] |b|
+};
+
+__device__ __forceinline__ double ldg_cg(const double *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Sense-counting grid barrier; gives up after 2 s of waiting (error word set).
+__device__ bool grid_sync(const Ctx &c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = c.bar + 1;
+    const unsigned my = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(c.bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(c.bar, 0u);
+      __threadfence();
+      atomicAdd(c.bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (*vgen == my) {
+        if ((++spins & 1023u) == 0u) {
+          if (*(volatile int *)c.err) break;
+          if (global_ns() - t0 > 2000000000ull) {
+            atomicExch(c.err, 1);
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)c.err == 0;
+}
+
+__device__ __forceinline__ int gwarp() { return blockIdx.x * CG_WARPS + (threadIdx.x >> 5); }
+__device__ __forceinline__ int nwarps() { return gridDim.x * CG_WARPS; }
+__device__ __forceinline__ int gthread() { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int nthreads() { return gridDim.x * blockDim.x; }
+
+template <int RC>
+__device__ __forceinline__ void warp_sum(double (&a)[RC]) {
+#pragma unroll
+  for (int c = 0; c < RC; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+}
+
+// local row index of subdomain s in a slab
+__device__ __forceinline__ double *slab_row(const Ctx &c, int sl, const SubDev &d, int a) {
+  return c.slab[sl] + (long long)(d.loc_off + a) * c.R;
+}
+
+// ---------------------------------------------------------------- phases
+// Π-row phase: H1 = Lambda_PiDelta x^, H2 = Psi_PiDelta x^ for a Δ vector x
+template <int RC>
+__device__ void ph_pi_rows(const Ctx &c, const double *x) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tpi; t += nwarps()) {
+    const int s = c.ints[c.o_tpi + 2 * t], a = c.ints[c.o_tpi + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const double *lam = c.db + d.oLam + (long long)a * d.nG;
+    const double *psi = c.db + d.oPsi + (long long)a * d.nG;
+    const int *gdl = c.ints + d.gdl_off;
+    double h1[RC], h2[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) h1[k] = h2[k] = 0.0;
+    for (int b = lane; b < d.nDl; b += 32) {
+      const double la = lam[d.nPi + b], ps = psi[d.nPi + b];
+      const double *xv = x + (long long)gdl[b] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) {
+          const double xx = ldg_cg(xv + k);
+          h1[k] = fma(la, xx, h1[k]);
+          h2[k] = fma(ps, xx, h2[k]);
+        }
+    }
+    warp_sum<RC>(h1);
+    warp_sum<RC>(h2);
+    if (lane == 0) {
+      double *o1 = slab_row(c, S_H1, d, a), *o2 = slab_row(c, S_H2, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) {
+          o1[k] = h1[k];
+          o2[k] = h2[k];
+        }
+    }
+  }
+}
+
+// Π gather: out1[π] = s1 * sum_owners slab1, out2[π] = s2 * sum_owners slab2
+__device__ void ph_pi_gather(const Ctx &c, int sl1, double s1, double *out1, int sl2, double s2,
+                             double *out2) {
+  for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
+    const int p = e / c.R, k = e % c.R;
+    double a1 = 0.0, a2 = 0.0;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      a1 += ldg_cg(slab_row(c, sl1, d, a) + k);
+      if (out2) a2 += ldg_cg(slab_row(c, sl2, d, a) + k);
+    }
+    out1[e] = s1 * a1;
+    if (out2) out2[e] = s2 * a2;
+  }
+}
+
+// coarse dense products: o1 = A1 x1 + B1 y1, o2 = A2 x2 + B2 y2 (B*, o2 optional)
+__device__ void ph_coarse(const Ctx &c, long long A1, const double *x1, long long B1, const double *y1,
+                          double b1s, double *o1, long long A2, const double *x2, long long B2,
+                          const double *y2, double b2s, double *o2) {
+  const int lane = threadIdx.x & 31;
+  const int n = c.n_pi;
+  for (int t = gwarp(); t < n * c.R; t += nwarps()) {
+    const int p = t / c.R, k = t % c.R;
+    double s1 = 0.0, s2 = 0.0;
+    for (int q = lane; q < n; q += 32) {
+      const long long e = (long long)p * n + q;
+      s1 = fma(c.db[A1 + e], ldg_cg(x1 + (long long)q * c.R + k), s1);
+      if (B1 >= 0) s1 = fma(b1s * c.db[B1 + e], ldg_cg(y1 + (long long)q * c.R + k), s1);
+      if (o2) {
+        s2 = fma(c.db[A2 + e], ldg_cg(x2 + (long long)q * c.R + k), s2);
+        if (B2 >= 0) s2 = fma(b2s * c.db[B2 + e], ldg_cg(y2 + (long long)q * c.R + k), s2);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      o1[t] = s1;
+      if (o2) o2[t] = s2;
+    }
+  }
+}
+
+// Δ-row phase of the first half of S_theta (and of b_theta):
+//   lambda = [R_Pi piv; lsign * R_Delta x]  (piv: Π vector, x: Δ vector or null)
+//   VL = -(Lambda lambda + addA)_Delta ; BL = bsign*(lambda - Psi lambda)_Delta + addP + Lambda_PiD^T g
+// RHS mode (rhs=1): VL = -(a + Lambda lambda)_Δ, BL = (p + Psi lambda)_Δ + Lambda_PiD^T g
+template <int RC>
+__device__ void ph_dl_first(const Ctx &c, const double *piv, const double *x, const double *g, int rhs) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tdl; t += nwarps()) {
+    const int s = c.ints[c.o_tdl + 2 * t], dd = c.ints[c.o_tdl + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const int a = d.nPi + dd;
+    const double *lam = c.db + d.oLam + (long long)a * d.nG;
+    const double *psi = c.db + d.oPsi + (long long)a * d.nG;
+    const double *lamT = c.db + d.oLamT + (long long)a * d.nG;
+    const int *gpi = c.ints + d.gpi_off;
+    const int *gdl = c.ints + d.gdl_off;
+    double sl[RC], sp[RC], sg[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) sl[k] = sp[k] = sg[k] = 0.0;
+    const int bmax = rhs ? d.nPi : d.nG;
+    for (int b = lane; b < bmax; b += 32) {
+      const double la = lam[b], ps = psi[b];
+      const double *src;
+      double sgn;
+      if (b < d.nPi) {
+        src = piv + (long long)gpi[b] * c.R;
+        sgn = 1.0;
+      } else {
+        src = x + (long long)gdl[b - d.nPi] * c.R;
+        sgn = -1.0;
+      }
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) {
+          const double v = sgn * ldg_cg(src + k);
+          sl[k] = fma(la, v, sl[k]);
+          sp[k] = fma(ps, v, sp[k]);
+        }
+    }
+    for (int b = lane; b < d.nPi; b += 32) {
+      const double lt = lamT[b];
+      const double *src = g + (long long)gpi[b] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) sg[k] = fma(lt, ldg_cg(src + k), sg[k]);
+    }
+    warp_sum<RC>(sl);
+    warp_sum<RC>(sp);
+    warp_sum<RC>(sg);
+    if (lane == 0) {
+      double *vo = slab_row(c, S_VL, d, a), *bo = slab_row(c, S_BL, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) {
+          if (rhs) {
+            const double av = c.db[d.oAy + (long long)a * c.R + k];
+            const double pv = c.db[d.oP + (long long)a * c.R + k];
+            vo[k] = -(av + sl[k]);
+            bo[k] = pv + sp[k] + sg[k];
+          } else {
+            const double lama = -ldg_cg(x + (long long)gdl[dd] * c.R + k);
+            vo[k] = -sl[k];
+            bo[k] = -(lama - sp[k]) + sg[k];
+          }
+        }
+    }
+  }
+}
+
+// Δ gather: out[δ] = s * (slab[A] + slab[B]) + t * add[δ]
+__device__ void ph_dl_gather(const Ctx &c, int sl, double s, double *out, const double *add, double t,
+                             int sl2, double *out2) {
+  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+    const int p = e / c.R, k = e % c.R;
+    const int sa = c.ints[c.o_dl_own + 4 * p], la = c.ints[c.o_dl_own + 4 * p + 1];
+    const int sb = c.ints[c.o_dl_own + 4 * p + 2], lb = c.ints[c.o_dl_own + 4 * p + 3];
+    const SubDev &da = c.subs[sa];
+    const SubDev &dB = c.subs[sb];
+    const double v = ldg_cg(slab_row(c, sl, da, da.nPi + la) + k) + ldg_cg(slab_row(c, sl, dB, dB.nPi + lb) + k);
+    double r = s * v;
+    if (add) r = fma(t, ldg_cg(add + e), r);
+    out[e] = r;
+    if (out2) out2[e] = ldg_cg(slab_row(c, sl2, da, da.nPi + la) + k) + ldg_cg(slab_row(c, sl2, dB, dB.nPi + lb) + k);
+  }
+}
+
+// Δ-row local products with Phi or Phi^T: slab[nPi + d] = -sum_e M[d][e] x[gdl[e]]
+template <int RC>
+__device__ void ph_dl_phi(const Ctx &c, bool transposed, const double *x, int sl) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tdl; t += nwarps()) {
+    const int s = c.ints[c.o_tdl + 2 * t], dd = c.ints[c.o_tdl + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const double *row = c.db + (transposed ? d.oPhiT : d.oPhi) + (long long)dd * d.nDl;
+    const int *gdl = c.ints + d.gdl_off;
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int e = lane; e < d.nDl; e += 32) {
+      const double m = row[e];
+      const double *src = x + (long long)gdl[e] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(m, ldg_cg(src + k), acc[k]);
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+      double *o = slab_row(c, sl, d, d.nPi + dd);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) o[k] = -acc[k];
+    }
+  }
+}
+
+// Γ-row phase: ZL = Lambda^T [0; w^]  (all nG rows)
+template <int RC>
+__device__ void ph_g_lamT(const Ctx &c, const double *w) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tg; t += nwarps()) {
+    const int s = c.ints[c.o_tg + 2 * t], a = c.ints[c.o_tg + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const double *row = c.db + d.oLamT + (long long)a * d.nG;
+    const int *gdl = c.ints + d.gdl_off;
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int e = lane; e < d.nDl; e += 32) {
+      const double m = row[d.nPi + e];
+      const double *src = w + (long long)gdl[e] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(m, ldg_cg(src + k), acc[k]);
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+      double *o = slab_row(c, S_ZL, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) o[k] = acc[k];
+    }
+  }
+}
+
+// Δ-row phase: YL = ZL_Delta + Psi_DeltaPi nu^ - Lambda_PiDelta^T Dnu^
+template <int RC>
+__device__ void ph_dl_last(const Ctx &c, const double *nu, const double *dnu) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tdl; t += nwarps()) {
+    const int s = c.ints[c.o_tdl + 2 * t], dd = c.ints[c.o_tdl + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const int a = d.nPi + dd;
+    const double *psi = c.db + d.oPsi + (long long)a * d.nG;
+    const double *lamT = c.db + d.oLamT + (long long)a * d.nG;
+    const int *gpi = c.ints + d.gpi_off;
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int b = lane; b < d.nPi; b += 32) {
+      const double ps = psi[b], lt = lamT[b];
+      const double *sn = nu + (long long)gpi[b] * c.R;
+      const double *sd = dnu + (long long)gpi[b] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(ps, ldg_cg(sn + k), fma(-lt, ldg_cg(sd + k), acc[k]));
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+      double *o = slab_row(c, S_YL, d, a);
+      const double *z = slab_row(c, S_ZL, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) o[k] = ldg_cg(z + k) + acc[k];
+    }
+  }
+}
+
+// block-level partial dot products of columns: red[block][k] = sum x[e][k] y[e][k]
+template <int RC>
+__device__ void partial_dot(const Ctx &c, const double *x, const double *y, int slot) {
+  __shared__ double sred[CG_WARPS][16];
+  double acc[RC];
+#pragma unroll
+  for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+  for (int p = gthread(); p < c.n_dl; p += nthreads()) {
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k < c.R) acc[k] = fma(ldg_cg(x + (long long)p * c.R + k), ldg_cg(y + (long long)p * c.R + k), acc[k]);
+  }
+  warp_sum<RC>(acc);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < RC; ++k) sred[threadIdx.x >> 5][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < RC) {
+    double s = 0.0;
+    for (int w = 0; w < CG_WARPS; ++w) s += sred[w][threadIdx.x];
+    c.red[(long long)blockIdx.x * 32 + slot * 16 + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// every CTA sums the partials in the same order: out[k] (shared)
+template <int RC>
+__device__ void finish_dot(const Ctx &c, int slot, double *out) {
+  if (threadIdx.x < RC) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += ldg_cg(c.red + (long long)b * 32 + slot * 16 + threadIdx.x);
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Second half of the operator: given VL/BL slabs (v = sum VL, bkb = sum BL),
+// computes out = bkb + D~^T W v.  Returns false on a barrier timeout.
+template <int RC>
+__device__ bool second_half(const Ctx &c, double *out) {
+  double *v = c.dl[V_V], *bkb = c.dl[V_BKB], *pvv = c.dl[V_PV], *w = c.dl[V_W];
+  ph_dl_gather(c, S_VL, 1.0, v, nullptr, 0.0, S_BL, bkb);  // v = D~ x, bkb
+  if (!grid_sync(c)) return false;
+  ph_dl_phi<RC>(c, false, v, S_TL);  // -Phi v^
+  if (!grid_sync(c)) return false;
+  ph_dl_gather(c, S_TL, 1.0, pvv, nullptr, 0.0, -1, nullptr);  // P v
+  if (!grid_sync(c)) return false;
+  ph_dl_phi<RC>(c, true, pvv, S_T2L);  // -Phi^T (P v)^
+  if (!grid_sync(c)) return false;
+  ph_dl_gather(c, S_T2L, c.theta, w, v, 1.0 - c.theta, -1, nullptr);  // W v
+  if (!grid_sync(c)) return false;
+  ph_g_lamT<RC>(c, w);  // z = Lambda^T [0; w^]
+  if (!grid_sync(c)) return false;
+  ph_pi_gather(c, S_ZL, 1.0, c.pv[P_RNU], -1, 0.0, nullptr);
+  if (!grid_sync(c)) return false;
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_RNU], -1, nullptr, 0.0, c.pv[P_NU], c.o_C3, c.pv[P_RNU], -1, nullptr,
+              0.0, c.pv[P_DNU]);
+  if (!grid_sync(c)) return false;
+  ph_dl_last<RC>(c, c.pv[P_NU], c.pv[P_DNU]);
+  if (!grid_sync(c)) return false;
+  ph_dl_gather(c, S_YL, 1.0, out, bkb, 1.0, -1, nullptr);
+  return grid_sync(c);
+}
+
+// q = S_theta x for a Δ vector x
+template <int RC>
+__device__ bool apply_S(const Ctx &c, const double *x, double *q) {
+  ph_pi_rows<RC>(c, x);
+  if (!grid_sync(c)) return false;
+  ph_pi_gather(c, S_H1, 1.0, c.pv[P_PSI], S_H2, -1.0, c.pv[P_RA]);
+  if (!grid_sync(c)) return false;
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_RA], c.o_C1, c.pv[P_PSI], 1.0, c.pv[P_MPI], c.o_C2, c.pv[P_PSI], c.o_C3,
+              c.pv[P_RA], -1.0, c.pv[P_G]);
+  if (!grid_sync(c)) return false;
+  ph_dl_first<RC>(c, c.pv[P_MPI], x, c.pv[P_G], 0);
+  if (!grid_sync(c)) return false;
+  return second_half<RC>(c, q);
+}
+
+template <int RC>
+__global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
+  __shared__ double s_rr[16], s_bn[16], s_pq[16], s_rn[16], s_alpha[16], s_beta[16];
+  __shared__ int s_done;
+  double *B = c.dl[V_B], *MU = c.dl[V_MU], *RES = c.dl[V_RES], *PD = c.dl[V_PD], *Q = c.dl[V_Q];
+  // ---------------- right-hand side b_theta
+  // dpi = -sum a_Pi ; ppi = sum p_Pi (a, p are the per-subdomain A_m y and Q_Gamma Q^T f)
+  for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
+    const int p = e / c.R, k = e % c.R;
+    double ad = 0.0, pp = 0.0;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      ad += c.db[d.oAy + (long long)a * c.R + k];
+      pp += c.db[d.oP + (long long)a * c.R + k];
+    }
+    c.pv[P_DPI][e] = -ad;
+    c.pv[P_PPI][e] = pp;
+  }
+  if (!grid_sync(c)) return;
+  // mpf = S_Pi^{-1}(ppi + D^T dpi) ; gf = dpi - D mpf
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_PPI], c.o_C1, c.pv[P_DPI], 1.0, c.pv[P_MPF], c.o_C2, c.pv[P_DPI], c.o_C3,
+              c.pv[P_PPI], -1.0, c.pv[P_GF]);
+  if (!grid_sync(c)) return;
+  ph_dl_first<RC>(c, c.pv[P_MPF], nullptr, c.pv[P_GF], 1);
+  if (!grid_sync(c)) return;
+  if (!second_half<RC>(c, B)) return;
+  // ---------------- CG from mu = 0
+  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+    const double b = B[e];
+    MU[e] = 0.0;
+    RES[e] = b;
+    PD[e] = b;
+  }
+  partial_dot<RC>(c, B, B, 0);
+  if (!grid_sync(c)) return;
+  finish_dot<RC>(c, 0, s_bn);
+  if (threadIdx.x < RC) {
+    s_rr[threadIdx.x] = s_bn[threadIdx.x];
+    s_bn[threadIdx.x] = sqrt(s_bn[threadIdx.x]);
+  }
+  if (threadIdx.x == 0) s_done = 0;
+  __syncthreads();
+  int it = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < c.R && k < RC; ++k)
+        if (s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k]) done = 0;
+      s_done = done || it >= c.max_iters;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (!apply_S<RC>(c, PD, Q)) return;
+    partial_dot<RC>(c, PD, Q, 0);
+    if (!grid_sync(c)) return;
+    finish_dot<RC>(c, 0, s_pq);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      const bool live = k < c.R && s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k] && s_pq[k] != 0.0;
+      s_alpha[k] = live ? s_rr[k] / s_pq[k] : 0.0;
+    }
+    __syncthreads();
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+      const double al = s_alpha[e % c.R];
+      MU[e] = fma(al, PD[e], MU[e]);
+      RES[e] = fma(-al, ldg_cg(Q + e), RES[e]);
+    }
+    partial_dot<RC>(c, RES, RES, 1);
+    if (!grid_sync(c)) return;
+    finish_dot<RC>(c, 1, s_rn);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      s_beta[k] = (s_alpha[k] != 0.0 && s_rr[k] > 0.0) ? s_rn[k] / s_rr[k] : 0.0;
+      if (s_alpha[k] != 0.0) s_rr[k] = s_rn[k];
+    }
+    __syncthreads();
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+      const double be = s_beta[e % c.R];
+      if (s_alpha[e % c.R] != 0.0) PD[e] = fma(be, PD[e], RES[e]);
+    }
+    ++it;
+    if (!grid_sync(c)) return;
+  }
+  // ---------------- true residual |b - S mu| / |b|
+  if (!apply_S<RC>(c, MU, Q)) return;
+  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) c.dl[V_TMP][e] = B[e] - ldg_cg(Q + e);
+  partial_dot<RC>(c, c.dl[V_TMP], c.dl[V_TMP], 0);
+  if (!grid_sync(c)) return;
+  finish_dot<RC>(c, 0, s_rn);
+  if (blockIdx.x == 0 && threadIdx.x < RC && threadIdx.x < c.R) {
+    c.info[1 + threadIdx.x] = s_bn[threadIdx.x] > 0.0 ? sqrt(s_rn[threadIdx.x]) / s_bn[threadIdx.x] : 0.0;
+    c.info[17 + threadIdx.x] = s_bn[threadIdx.x];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.info[0] = it;
+  // ---------------- reconstruction, Eq. (coarse_sol_2)
+  ph_pi_rows<RC>(c, MU);
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_H1, 1.0, c.pv[P_PSI2], S_H2, 1.0, c.pv[P_S2]);
+  if (!grid_sync(c)) return;
+  // mu_Pi = mpf + S_Pi^{-1} s2 - C1 psi2
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_S2], c.o_C1, c.pv[P_PSI2], -1.0, c.pv[P_MPIF], -1, nullptr, -1, nullptr,
+              0.0, nullptr);
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
+    const double v = c.pv[P_MPIF][e] + c.pv[P_MPF][e];
+    c.pv[P_MPIF][e] = v;
+    if (c.mu_out) c.mu_out[e] = v;
+  }
+  if (c.mu_out)
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) c.mu_out[(long long)c.n_pi * c.R + e] = MU[e];
+  if (!grid_sync(c)) return;
+  // c = y + K^+ E_Gamma [mu_Pi^; mu_Delta^]
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tc; t += nwarps()) {
+    const int s = c.ints[c.o_tc + 2 * t], j = c.ints[c.o_tc + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    const double *row = c.db + d.oKpE + (long long)j * d.nG;
+    const int *gpi = c.ints + d.gpi_off;
+    const int *gdl = c.ints + d.gdl_off;
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int b = lane; b < d.nG; b += 32) {
+      const double m = row[b];
+      const double *src = b < d.nPi ? c.pv[P_MPIF] + (long long)gpi[b] * c.R : MU + (long long)gdl[b - d.nPi] * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(m, ldg_cg(src + k), acc[k]);
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) {
+          const double v = c.db[d.oY + (long long)j * c.R + k] + acc[k];
+          c.db[d.oC + (long long)j * c.R + k] = v;
+          if (c.c_out) c.c_out[(d.w_off + j) * c.R + k] = v;
+        }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  Ctx c;
+  c.subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
+  c.ints = reinterpret_cast<const int *>(base + p.off_ints);
+  c.db = reinterpret_cast<double *>(base + p.off_dbl);
+  c.n_sub = p.n_sub;
+  c.n_pi = p.n_pi;
+  c.n_dl = p.n_dl;
+  c.R = p.n_rhs;
+  c.o_pi_own = p.o_pi_own;
+  c.o_dl_own = p.o_dl_own;
+  c.o_tpi = p.o_tasks_pi;
+  c.n_tpi = p.n_tasks_pi;
+  c.o_tdl = p.o_tasks_dl;
+  c.n_tdl = p.n_tasks_dl;
+  c.o_tg = p.o_tasks_g;
+  c.n_tg = p.n_tasks_g;
+  c.o_tc = p.o_tasks_c;
+  c.n_tc = p.n_tasks_c;
+  c.o_Sinv = p.o_Sinv;
+  c.o_C1 = p.o_C1;
+  c.o_C2 = p.o_C2;
+  c.o_C3 = p.o_C3;
+  const long long nd = p.n_dl > 0 ? p.n_dl : 1, np = p.n_pi > 0 ? p.n_pi : 1, R = p.n_rhs;
+  double *cg = c.db + p.o_cg;
+  for (int k = 0; k < N_DLVEC; ++k) c.dl[k] = cg + k * nd * R;
+  cg += N_DLVEC * nd * R;
+  for (int k = 0; k < N_PIVEC; ++k) c.pv[k] = cg + k * np * R;
+  cg += N_PIVEC * np * R;
+  c.red = cg;              // 2048 x 32 doubles reserved below
+  c.info = cg + 2048 * 32 - 64;
+  for (int k = 0; k < N_SLAB; ++k) c.slab[k] = c.db + p.o_loc + (long long)k * p.sum_nG * R;
+  c.bar = reinterpret_cast<unsigned *>(c.db + p.o_status + 2 * p.n_sub + 8);
+  c.err = reinterpret_cast<int *>(c.db + p.o_status + 2 * p.n_sub + 16);
+  c.theta = a.theta;
+  c.tol = a.tol;
+  c.max_iters = a.max_iters;
+  c.mu_out = a.mu_out;
+  c.c_out = a.c_out;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = nsm < 2048 ? nsm : 2048;
+  void *args[] = {&c};
+  if (p.n_rhs == 1)
+    return cudaLaunchCooperativeKernel((const void *)cg_kernel<1>, grid, CG_THREADS, args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)cg_kernel<16>, grid, CG_THREADS, args, 0, s);
+}
+
+}  // namespace ddelm

@@ -1,0 +1,181 @@
+// Batched FP64 Cholesky factorisation with explicit triangular inverse (one
+// CTA per matrix), the coarse-matrix assembly of Sec. 3 (S_Pi assembled in
+// full), and small helpers (identity fill, right-hand-side gather).
+//
+// Cholesky pass of the shifted CholeskyQR3 factorisation of [K; eps I]:
+//   mode 1 (first pass): eps^2 = eps_rel^2 tr(G)/M is the ridge of the local
+//     least-squares problem; the diagonal additionally gets the stabilising
+//     shift s = 11 ((m+M) M + M (M+1)) u tr(G + eps^2 I), u = 2^-53;
+//     Z = eps R^{-1} is the ridge block of the first Q.
+//   mode 0: plain factorisation.
+// A pivot that is not positive marks the matrix in the status array; the
+// factorisation continues with a unit pivot so that no NaN propagates.
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+
+constexpr int CT = 512;
+
+__global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict__ descs,
+                                                      double *__restrict__ db, int *__restrict__ status) {
+  extern __shared__ double sh[];  // row buffer [M] + reduction scratch
+  const CholDesc cd = descs[blockIdx.x];
+  const int M = cd.M;
+  double *G = db + cd.g;
+  double *V = db + cd.v;
+  double *row = sh;
+  __shared__ double red[CT / 32];
+  __shared__ double s_eps2, s_piv;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = CT / 32;
+  if (tid == 0) s_bad = 0;
+  if (cd.mode == 1) {
+    double t = 0.0;
+    for (int j = tid; j < M; j += CT) t += G[(long long)j * M + j];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[wid] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int k = 0; k < nw; ++k) tr += red[k];
+      const double eps2 = cd.eps_rel * cd.eps_rel * tr / double(M);
+      const double u = 1.1102230246251565e-16;
+      const double sh_ = 11.0 * (double(cd.m + M) * M + double(M) * (M + 1)) * u * (tr + M * eps2);
+      s_eps2 = eps2;
+      s_piv = eps2 + sh_;
+    }
+    __syncthreads();
+    for (int j = tid; j < M; j += CT) G[(long long)j * M + j] += s_piv;
+    __syncthreads();
+  }
+  // upper Cholesky in place: G = R^T R
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) {
+      double piv = G[(long long)k * M + k];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        s_bad = 1;
+        piv = 1.0;
+      }
+      const double r = sqrt(piv);
+      G[(long long)k * M + k] = r;
+      s_piv = r;
+    }
+    __syncthreads();
+    const double r = s_piv;
+    for (int j = k + 1 + tid; j < M; j += CT) {
+      const double v = G[(long long)k * M + j] / r;
+      G[(long long)k * M + j] = v;
+      row[j] = v;
+    }
+    __syncthreads();
+    for (int i = k + 1 + wid; i < M; i += nw) {
+      const double gki = row[i];
+      double *gi = G + (long long)i * M;
+      for (int j = i + lane; j < M; j += 32) gi[j] = fma(-gki, row[j], gi[j]);
+    }
+    __syncthreads();
+  }
+  // V = R^{-1} (upper; zeros below the diagonal), rows from the bottom
+  for (long long e = tid; e < (long long)M * M; e += CT) V[e] = 0.0;
+  __syncthreads();
+  for (int i = M - 1; i >= 0; --i) {
+    for (int j = i + tid; j < M; j += CT) row[j] = G[(long long)i * M + j];
+    __syncthreads();
+    const double rii = row[i];
+    for (int j = i + tid; j < M; j += CT) {
+      double acc = (j == i) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) acc = fma(-row[k], V[(long long)k * M + j], acc);
+      V[(long long)i * M + j] = acc / rii;
+    }
+    __syncthreads();
+  }
+  if (cd.mode == 1 && cd.z >= 0) {
+    double *Z = db + cd.z;
+    const double e = sqrt(s_eps2);
+    for (long long q = tid; q < (long long)M * M; q += CT) Z[q] = e * V[q];
+  }
+  if (tid == 0 && s_bad) status[cd.status] = 1;
+}
+
+// Sec. 3: D_PiPi = sum_i R_Pi^T Lambda_PiPi^i R_Pi and the first two terms of
+// S_Pi = sum_i R_Pi^T (I - Psi^i)_PiPi R_Pi (+ D_PiPi^T D_PiPi added by a GEMM).
+// One CTA walks the subdomains in order, so the sums are deterministic.
+__global__ void coarse_assembly_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
+                                       double *__restrict__ db, int n_sub, int n_pi, long long o_Dpp,
+                                       long long o_Spi) {
+  for (int i = 0; i < n_sub; ++i) {
+    const SubDev d = subs[i];
+    const int np = d.nPi;
+    if (threadIdx.x < np * np) {
+      const int a = threadIdx.x / np, b = threadIdx.x % np;
+      const int ga = ints[d.gpi_off + a], gb = ints[d.gpi_off + b];
+      db[o_Dpp + (long long)ga * n_pi + gb] += db[d.oLam + (long long)a * d.nG + b];
+      db[o_Spi + (long long)ga * n_pi + gb] += (a == b ? 1.0 : 0.0) - db[d.oPsi + (long long)a * d.nG + b];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void fill_identity_kernel(double *dst, int n, double diag) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (e / n == e % n) ? diag : 0.0;
+}
+
+// F^i = [f(x_I); g(x_B)] per subdomain ([nI + nB] x R)
+__global__ void gather_rhs_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
+                                  double *__restrict__ db, const double *__restrict__ f_int,
+                                  const double *__restrict__ g_bnd, int R) {
+  const SubDev d = subs[blockIdx.x];
+  const int rows = d.nI + d.nB;
+  double *F = db + d.oF;
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+    const int r = e / R, c = e % R;
+    F[e] = r < d.nI ? f_int[(d.int_off + r) * R + c] : g_bnd[(long long)ints[d.bnd_off + r - d.nI] * R + c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cudaStream_t s) {
+  if (ph.ndesc == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  const CholDesc *descs = reinterpret_cast<const CholDesc *>(base + p.off_cdesc) + ph.desc0;
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  int *status = reinterpret_cast<int *>(db + p.o_status);
+  int maxM = 0;
+  for (int k = 0; k < ph.ndesc; ++k) maxM = p.cdesc[ph.desc0 + k].M > maxM ? p.cdesc[ph.desc0 + k].M : maxM;
+  const size_t smem = sizeof(double) * (size_t)(maxM + 1);
+  chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s) {
+  if (p.n_pi == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
+  const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  coarse_assembly_kernel<<<1, 32, 0, s>>>(subs, ints, db, p.n_sub, p.n_pi, p.o_Dpp, p.o_Spi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fill_identity_kernel<<<64, 256, 0, s>>>(dst, n, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,
+                              cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
+  const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  gather_rhs_kernel<<<p.n_sub, 256, 0, s>>>(subs, ints, db, f_int, g_bnd, p.n_rhs);
+  return cudaGetLastError();
+}
+
+}  // namespace ddelm

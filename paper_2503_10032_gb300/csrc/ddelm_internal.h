@@ -1,0 +1,165 @@
+// Internal declarations of libddelm: the device-side tables the host plan
+// builds and the kernel launchers.  Every offset below is an element index
+// into the double region of the caller's workspace (dbase) or into the int
+// region (ibase); tables are position independent, so a plan is built once on
+// the host and uploaded with one copy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ddelm.h"
+
+namespace ddelm {
+
+// ---------------------------------------------------------------- rows
+// Rows of the local matrices other than the interior collocation rows.
+enum RowKind : int {
+  ROW_POINT = 0,  // C phi = B phi = phi(x)
+  ROW_TINV = 1,   // (T^i)^{-1} C phi: phi(x) - alpha phi(x_a) - beta phi(x_b)
+  ROW_FLUX = 2,   // F phi = (w . n)(1 - tanh^2)
+  ROW_AM = 3,     // A_m corner row: mean edge fluxes (Sec. 3.2)
+};
+
+struct SpecialRow {
+  int kind, sub;
+  long long out0, out1;  // row starts in dbase (out1 < 0: single output)
+  double x, y, nx, ny;
+  double alpha, xa, ya, beta, xb, yb;
+  // A_m: two edges (start x, start y, end x, end y, normal x, normal y) and e
+  double am[2][6];
+  int am_e[2];
+};
+
+// Interior collocation rows of subdomain `sub` go to rows [0, nI) of both
+// K_c^i and K-bar^i; the point data come from the problem arrays.
+struct SubDev {
+  int M, nI, nB, nPi, nDl, nG, m, nE;
+  long long w_off;    // first neuron of this subdomain in the packed w/b arrays
+  long long int_off;  // first interior point
+  long long eval_off; // first evaluation point
+  // setup buffers (dbase offsets)
+  long long oX, oKb;  // K_c^i and K-bar^i [m x M]; hold Q2 after the second pass
+  long long oY1, oY1b;  // first-pass Q [m x M]
+  long long oA;       // A_m^i [nG x M]
+  long long oAbar;    // A-bar^i [nDl x M]
+  long long oEval;    // phi at the evaluation points [nE x M]
+  // persistent operators
+  long long oV, oVb;       // R^{-1} of K and K-bar [M x M]
+  long long oV3;           // third-pass R3^{-1} of K [M x M]
+  long long oQG;           // Gamma rows of the final Q of K [nG x M]
+  long long oKpE;          // K^+ E_Gamma [M x nG]
+  long long oLam, oLamT;   // Lambda^i and its transpose [nG x nG]
+  long long oPsi;          // Psi^i [nG x nG]
+  long long oPhi, oPhiT;   // Phi^i and its transpose [nDl x nDl]
+  // solve-time vectors ([rows x R])
+  long long oF;     // [nI + nB] x R data rows
+  long long oT, oQtf, oY, oAy, oP;  // M x R, M x R, M x R, nG x R, nG x R
+  long long oC;     // coefficients M x R
+  long long oU;     // network values at the evaluation points nE x R
+  int gpi_off, gdl_off, bnd_off;  // ibase offsets of R_Pi, R_Delta, boundary index maps
+  int loc_off;      // first row of this subdomain in the local vector buffers (nG rows)
+};
+
+struct GemmDesc {
+  long long a, b, c;  // dbase offsets
+  int m, n, k;
+  int lda, ldb, ldc;
+  int ta, tb;  // 1: operand stored transposed
+  int flags;   // GEMM_B_UPPER / GEMM_A_UPPER
+  int pad;
+  double alpha, beta;
+};
+enum { GEMM_B_UPPER = 1, GEMM_A_UPPER = 2 };
+
+struct GemmTile {
+  int desc, tm, tn, pad;
+};
+
+struct CholDesc {
+  long long g;  // in: symmetric matrix (upper triangle read); out: R (upper)
+  long long v;  // out: R^{-1} (upper, full square written)
+  long long z;  // out (mode 1): sqrt(eps2) R^{-1}; < 0 for none
+  int M, m;     // order, rows of the matrix whose Gram g is (for the shift)
+  int mode;     // 0 plain, 1 ridge + shift (first pass), 2 plain + explicit I - ...
+  int status;   // index into the status array
+  double eps_rel;
+};
+
+// ---------------------------------------------------------------- plan
+struct GemmPhase {
+  int desc0, ndesc;  // into the descriptor table
+  int tile0, ntile;  // into the tile table
+};
+
+struct CholPhase {
+  int desc0, ndesc;
+};
+
+struct Plan {
+  ddelm_sizes sz{};
+  int n_sub = 0, n_rhs = 1, op = 0;
+  int max_M = 0;
+  // host copies of the tables
+  std::vector<SubDev> subs;
+  std::vector<SpecialRow> rows;
+  std::vector<GemmDesc> gdesc;
+  std::vector<GemmTile> gtile;
+  std::vector<CholDesc> cdesc;
+  std::vector<int> ints;  // gpi, gdl, bnd maps, owner maps, task lists
+  // phases (indices into the tables)
+  std::vector<GemmPhase> setup_gemm;  // filled in order; see api.cu for the sequence
+  // named ranges into ints
+  int o_pi_own = 0;   // per Pi point: 4 x (sub, local) pairs, -1 padded
+  int o_dl_own = 0;   // per Delta point: 2 x (sub, local)
+  int o_tasks_pi = 0, n_tasks_pi = 0;  // (sub, local Pi row)
+  int o_tasks_dl = 0, n_tasks_dl = 0;  // (sub, local Delta row)
+  int o_tasks_g = 0, n_tasks_g = 0;    // (sub, local Gamma row)
+  int o_tasks_c = 0, n_tasks_c = 0;    // (sub, coefficient row j < M)
+  int o_bnd_map = 0;                    // local boundary -> global Dirichlet index
+  // workspace layout
+  size_t bytes_tables = 0, bytes_total = 0;
+  size_t off_subs = 0, off_rows = 0, off_gdesc = 0, off_gtile = 0, off_cdesc = 0, off_ints = 0;
+  size_t off_dbl = 0;      // byte offset of the double region
+  long long n_dbl = 0;     // doubles in the region
+  long long o_w = 0, o_b = 0, o_xint = 0, o_aint = 0, o_gaint = 0;  // problem data
+  long long o_status = 0;  // int status slots (in ints region? kept as doubles)
+  // coarse
+  int n_pi = 0, n_dl = 0;
+  long long o_Dpp = 0, o_Spi = 0, o_Vpi = 0, o_Sinv = 0, o_C1 = 0, o_C2 = 0, o_C3 = 0, o_SpiR = 0;
+  // CG vectors / scratch
+  long long o_cg = 0, n_cg = 0;
+  long long o_loc = 0;  // local vector buffers: several [sum nG x R] slabs
+  int sum_nG = 0;
+  // inspection copies
+  long long o_keepX = -1;
+  bool keep = false;
+  ddelm_options opt{};
+  // chol phases
+  CholPhase chol_pass[3]{}, chol_coarse{};
+  std::string err;
+};
+
+int build_plan(const ddelm_problem *prob, Plan &plan);
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_features(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cudaStream_t s);
+cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cudaStream_t s);
+cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s);
+cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,
+                              cudaStream_t s);
+struct CgArgs {
+  double *mu_out;   // [n_pi + n_dl] x R or null
+  double *c_out;    // [sum M] x R or null
+  int max_iters;
+  double tol;
+  double theta;
+};
+cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s);
+
+}  // namespace ddelm

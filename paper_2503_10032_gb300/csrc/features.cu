@@ -1,0 +1,117 @@
+// Fused feature assembly (Sec. 2.2 and Sec. 2.2.1, Sec. 3.1, Sec. 3.2):
+// phi_j(x) = tanh(w_j . x + b_j) and the rows of K_c^i, K-bar^i, A_m^i,
+// A-bar^i and the evaluation matrix, written once in FP64 with coalesced
+// row-major stores (consecutive threads -> consecutive neurons j).
+//
+//   L phi (Poisson)   = 2 |w|^2 t (1 - t^2)
+//   L phi (diffusion) = 2 a |w|^2 t (1 - t^2) - (grad a . w)(1 - t^2)
+//   B phi = C phi = t,   F phi = (w . n)(1 - t^2)
+// with t = tanh(w . x + b).
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+
+__device__ __forceinline__ double feat_t(double wx, double wy, double b, double x, double y) {
+  return tanh(fma(wx, x, wy * y) + b);
+}
+
+// Interior collocation rows: rows [0, nI) of K_c^i and K-bar^i.
+__global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__restrict__ subs,
+                                                            double *__restrict__ db, long long o_w,
+                                                            long long o_b, long long o_xint,
+                                                            long long o_aint, long long o_gaint, int op) {
+  const SubDev d = subs[blockIdx.y];
+  const int r0 = blockIdx.x * 8;
+  if (r0 >= d.nI) return;
+  const double *w = db + o_w + 2 * d.w_off;
+  const double *b = db + o_b + d.w_off;
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = r0 + rr;
+    if (r >= d.nI) break;
+    const long long pi = d.int_off + r;
+    const double x = db[o_xint + 2 * pi], y = db[o_xint + 2 * pi + 1];
+    double a = 1.0, ax = 0.0, ay = 0.0;
+    if (op == DDELM_OP_DIFFUSION) {
+      a = db[o_aint + pi];
+      ax = db[o_gaint + 2 * pi];
+      ay = db[o_gaint + 2 * pi + 1];
+    }
+    double *o0 = db + d.oX + (long long)r * d.M;
+    double *o1 = db + d.oKb + (long long)r * d.M;
+    for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+      const double wx = w[2 * j], wy = w[2 * j + 1];
+      const double t = feat_t(wx, wy, b[j], x, y);
+      const double s1 = 1.0 - t * t;
+      const double w2 = wx * wx + wy * wy;
+      double v = 2.0 * w2 * t * s1;
+      if (op == DDELM_OP_DIFFUSION) v = a * v - (ax * wx + ay * wy) * s1;
+      o0[j] = v;
+      o1[j] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__restrict__ rows,
+                                                           const SubDev *__restrict__ subs,
+                                                           double *__restrict__ db, long long o_w,
+                                                           long long o_b) {
+  const SpecialRow rw = rows[blockIdx.x];
+  const SubDev d = subs[rw.sub];
+  const double *w = db + o_w + 2 * d.w_off;
+  const double *b = db + o_b + d.w_off;
+  double *o0 = db + rw.out0;
+  double *o1 = rw.out1 >= 0 ? db + rw.out1 : nullptr;
+  for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+    const double wx = w[2 * j], wy = w[2 * j + 1], bj = b[j];
+    double v;
+    if (rw.kind == ROW_POINT) {
+      v = feat_t(wx, wy, bj, rw.x, rw.y);
+    } else if (rw.kind == ROW_TINV) {
+      v = feat_t(wx, wy, bj, rw.x, rw.y);
+      if (rw.alpha != 0.0) v -= rw.alpha * feat_t(wx, wy, bj, rw.xa, rw.ya);
+      if (rw.beta != 0.0) v -= rw.beta * feat_t(wx, wy, bj, rw.xb, rw.yb);
+    } else if (rw.kind == ROW_FLUX) {
+      const double t = feat_t(wx, wy, bj, rw.x, rw.y);
+      v = (rw.nx * wx + rw.ny * wy) * (1.0 - t * t);
+    } else {  // ROW_AM: sum over the two edges of the mean flux over {corner, e edge points}
+      v = 0.0;
+      for (int e = 0; e < 2; ++e) {
+        const double sx = rw.am[e][0], sy = rw.am[e][1], ex = rw.am[e][2], ey = rw.am[e][3];
+        const double wn = rw.am[e][4] * wx + rw.am[e][5] * wy;
+        const int ne = rw.am_e[e];
+        double t = feat_t(wx, wy, bj, rw.x, rw.y);
+        double acc = 1.0 - t * t;
+        for (int k = 1; k <= ne; ++k) {
+          const double f = double(k) / double(ne + 1);
+          t = feat_t(wx, wy, bj, sx + f * (ex - sx), sy + f * (ey - sy));
+          acc += 1.0 - t * t;
+        }
+        v += wn * acc / double(ne + 1);
+      }
+    }
+    o0[j] = v;
+    if (o1) o1[j] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_features(const Plan &p, void *ws, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
+  const SpecialRow *rows = reinterpret_cast<const SpecialRow *>(base + p.off_rows);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  int max_nI = 0;
+  for (const auto &d : p.subs) max_nI = d.nI > max_nI ? d.nI : max_nI;
+  if (max_nI > 0) {
+    dim3 grid((max_nI + 7) / 8, p.n_sub);
+    interior_rows_kernel<<<grid, 256, 0, s>>>(subs, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint,
+                                              p.op);
+  }
+  if (!p.rows.empty()) special_rows_kernel<<<(unsigned)p.rows.size(), 256, 0, s>>>(rows, subs, db, p.o_w, p.o_b);
+  return cudaGetLastError();
+}
+
+}  // namespace ddelm

@@ -1,0 +1,122 @@
+// Batched FP64 GEMM engine: C = alpha op(A) op(B) + beta C over a flat list
+// of 64x64 output tiles drawn from any number of descriptors of any shapes
+// (uneven subdomains are just more descriptors).  Triangular operands are
+// flagged so that the k loop skips the zero blocks.  FP64 runs on the CUDA
+// cores (DFMA); each thread owns a 4x4 register tile, operands are staged in
+// shared memory in 16-deep k slices with a double buffer.
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ void load_tiles(const double *__restrict__ A, const double *__restrict__ B,
+                                           const GemmDesc &d, int m0, int n0, int k0, int kbeg, int kend,
+                                           double (*As)[BM + 1], double (*Bs)[BN + 1]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int t = 0; t < (BM * BK) / NT; ++t) {
+    const int e = tid + t * NT;
+    int i, kk;
+    if (!d.ta) {
+      i = e / BK;
+      kk = e % BK;
+    } else {
+      i = e % BM;
+      kk = e / BM;
+    }
+    const int gi = m0 + i, gk = k0 + kk;
+    double v = 0.0;
+    if (gi < d.m && gk >= kbeg && gk < kend) v = d.ta ? A[(long long)gk * d.lda + gi] : A[(long long)gi * d.lda + gk];
+    As[kk][i] = v;
+  }
+#pragma unroll
+  for (int t = 0; t < (BN * BK) / NT; ++t) {
+    const int e = tid + t * NT;
+    int j, kk;
+    if (!d.tb) {
+      j = e % BN;
+      kk = e / BN;
+    } else {
+      kk = e % BK;
+      j = e / BK;
+    }
+    const int gj = n0 + j, gk = k0 + kk;
+    double v = 0.0;
+    if (gj < d.n && gk >= kbeg && gk < kend) v = d.tb ? B[(long long)gj * d.ldb + gk] : B[(long long)gk * d.ldb + gj];
+    Bs[kk][j] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmDesc *__restrict__ descs,
+                                                      const GemmTile *__restrict__ tiles,
+                                                      double *__restrict__ db) {
+  __shared__ double As[2][BK][BM + 1];
+  __shared__ double Bs[2][BK][BN + 1];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmDesc d = descs[tl.desc];
+  const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+  int kbeg = 0, kend = d.k;
+  if (d.flags & GEMM_B_UPPER) kend = min(kend, n0 + BN);  // op(B)[k][j] = 0 for k > j
+  if (d.flags & GEMM_A_UPPER) kbeg = max(kbeg, m0);       // op(A)[i][k] = 0 for k < i
+  const double *A = db + d.a;
+  const double *B = db + d.b;
+  double *C = db + d.c;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  const int kstart = (kbeg / BK) * BK;
+  int buf = 0;
+  if (kstart < kend) load_tiles(A, B, d, m0, n0, kstart, kbeg, kend, As[0], Bs[0]);
+  __syncthreads();
+  for (int k0 = kstart; k0 < kend; k0 += BK) {
+    if (k0 + BK < kend) load_tiles(A, B, d, m0, n0, k0 + BK, kbeg, kend, As[buf ^ 1], Bs[buf ^ 1]);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gi = m0 + ty + 16 * r;
+    if (gi >= d.m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gj = n0 + tx + 16 * c;
+      if (gj >= d.n) continue;
+      double *cp = C + (long long)gi * d.ldc + gj;
+      double v = d.alpha * acc[r][c];
+      if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cudaStream_t s) {
+  if (ph.ntile == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  const GemmDesc *descs = reinterpret_cast<const GemmDesc *>(base + p.off_gdesc);
+  const GemmTile *tiles = reinterpret_cast<const GemmTile *>(base + p.off_gtile) + ph.tile0;
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db);
+  return cudaGetLastError();
+}
+
+}  // namespace ddelm

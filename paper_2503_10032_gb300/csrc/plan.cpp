@@ -1,0 +1,824 @@
+// Host-side plan of a DDELM-NN handle: the decomposition (points, the split
+// Gamma = Pi u Delta of Sec. 3, the change of variables T^i and the modified
+// flux rows A_m^i of Sec. 3.2), the index maps R^i, the workspace layout and
+// the tables of every batched GEMM / Cholesky phase of the setup.
+//
+// The geometry follows the conventions documented in include/ddelm.h.  Every
+// table is position independent (offsets, not pointers), so the whole plan is
+// uploaded into the caller's workspace with one copy.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+
+struct V2 {
+  double x, y;
+};
+
+struct EdgeRef {
+  int id;
+  int sv[2], ev[2];  // start / end vertex (vx, vy)
+  double n[2];       // outward normal of the subdomain
+};
+
+struct Geo {
+  int nx, ny;
+  double x0, x1, y0, y1, hx, hy;
+  const int *edge_pts;
+  int H() const { return nx * (ny + 1); }
+  int n_edges() const { return H() + (nx + 1) * ny; }
+  bool edge_on_boundary(int eid) const {
+    if (eid < H()) {
+      int vy = eid / nx;
+      return vy == 0 || vy == ny;
+    }
+    int vx = (eid - H()) / ny;
+    return vx == 0 || vx == nx;
+  }
+  bool is_cross(const int v[2]) const { return v[0] > 0 && v[0] < nx && v[1] > 0 && v[1] < ny; }
+  int pi_index(const int v[2]) const { return (v[1] - 1) * (nx - 1) + (v[0] - 1); }
+  V2 vxy(const int v[2]) const { return {x0 + v[0] * hx, y0 + v[1] * hy}; }
+  V2 edge_point(const EdgeRef &e, int k) const {  // k = 1..n
+    int n = edge_pts[e.id];
+    V2 a = vxy(e.sv), b = vxy(e.ev);
+    double f = double(k) / double(n + 1);
+    return {a.x + f * (b.x - a.x), a.y + f * (b.y - a.y)};
+  }
+};
+
+}  // namespace
+
+int build_plan(const ddelm_problem *prob, Plan &P) {
+  if (!prob) return DDELM_ERR_INVALID_ARG;
+  const ddelm_problem &pr = *prob;
+  auto fail = [&](const char *m) {
+    P.err = m;
+    return DDELM_ERR_INVALID_ARG;
+  };
+  if (pr.nx < 1 || pr.ny < 1 || (long long)pr.nx * pr.ny > 65535) return fail("bad nx/ny");
+  if (!(pr.x1 > pr.x0) || !(pr.y1 > pr.y0)) return fail("bad rectangle");
+  if (pr.n_rhs < 1 || pr.n_rhs > 16) return fail("n_rhs must be in 1..16");
+  if (pr.op != DDELM_OP_POISSON && pr.op != DDELM_OP_DIFFUSION) return fail("bad op");
+  if (!pr.M || !pr.w_hat || !pr.b_hat || !pr.n_int || !pr.edge_pts) return fail("null input");
+  if (pr.op == DDELM_OP_DIFFUSION && (!pr.a_int || !pr.grad_a_int)) return fail("diffusion needs a");
+  const ddelm_options &o = pr.opt;
+  if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail("theta must be in [0,1]");
+  if (!(o.eps_rel >= 0.0) || !(o.tol > 0.0) || o.max_iters < 1) return fail("bad options");
+  if (o.precision != DDELM_PREC_FP64 && o.precision != DDELM_PREC_MIXED) return fail("bad precision");
+  P.opt = o;
+  P.keep = o.keep_matrices != 0;
+  const int nx = pr.nx, ny = pr.ny, n_sub = nx * ny;
+  Geo g{nx, ny, pr.x0, pr.x1, pr.y0, pr.y1, (pr.x1 - pr.x0) / nx, (pr.y1 - pr.y0) / ny, pr.edge_pts};
+  const int n_edges = g.n_edges();
+  for (int e = 0; e < n_edges; ++e)
+    if (pr.edge_pts[e] < 0 || pr.edge_pts[e] > 100000) return fail("bad edge_pts");
+  long long sumM = 0, sumI = 0, sumE = 0;
+  for (int i = 0; i < n_sub; ++i) {
+    if (pr.M[i] < 1 || pr.M[i] > 1024) return fail("M must be in 1..1024");
+    if (pr.n_int[i] < 0) return fail("bad n_int");
+    if (pr.n_eval && pr.n_eval[i] < 0) return fail("bad n_eval");
+    sumM += pr.M[i];
+    sumI += pr.n_int[i];
+    sumE += pr.n_eval ? pr.n_eval[i] : 0;
+  }
+  if (sumI > 0 && !pr.x_int) return fail("null x_int");
+  if (sumE > 0 && !pr.x_eval) return fail("null x_eval");
+  const int R = pr.n_rhs;
+  P.n_sub = n_sub;
+  P.n_rhs = R;
+  P.op = pr.op;
+
+  // ---- global Dirichlet list and Gamma numbering
+  std::vector<int> bnd_off(n_edges, -1), dl_off(n_edges, -1);
+  int nb = 0;
+  for (int e = 0; e < n_edges; ++e)
+    if (g.edge_on_boundary(e)) {
+      bnd_off[e] = nb;
+      nb += pr.edge_pts[e];
+    }
+  std::vector<int> vtx_bnd((nx + 1) * (ny + 1), -1);
+  for (int vy = 0; vy <= ny; ++vy)
+    for (int vx = 0; vx <= nx; ++vx)
+      if (vx == 0 || vx == nx || vy == 0 || vy == ny) vtx_bnd[vy * (nx + 1) + vx] = nb++;
+  const int n_pi = (nx - 1) * (ny - 1);
+  int nd = 0;
+  for (int e = 0; e < n_edges; ++e)
+    if (!g.edge_on_boundary(e)) {
+      dl_off[e] = nd;
+      nd += pr.edge_pts[e];
+    }
+  P.n_pi = n_pi;
+  P.n_dl = nd;
+  P.sz.n_sub = n_sub;
+  P.sz.n_edges = n_edges;
+  P.sz.n_bnd = nb;
+  P.sz.n_pi = n_pi;
+  P.sz.n_delta = nd;
+  P.sz.sum_M = sumM;
+  P.sz.sum_int = sumI;
+  P.sz.sum_eval = sumE;
+
+  // ---- per-subdomain geometry
+  struct SubGeo {
+    std::vector<V2> bxy;
+    std::vector<int> bg;
+    std::vector<V2> pxy;
+    std::vector<int> pg;
+    std::vector<std::pair<int, int>> pv;  // vertices of the local Pi points
+    std::vector<V2> dxy, dnrm;
+    std::vector<int> dg;
+    std::vector<double> al, be;
+    std::vector<int> alp, bep;
+    std::vector<std::vector<EdgeRef>> am_edges;  // per local Pi: the two edges meeting it
+  };
+  std::vector<SubGeo> sg(n_sub);
+  const int H = g.H();
+  for (int i = 0; i < n_sub; ++i) {
+    const int ix = i % nx, iy = i / nx;
+    int BL[2] = {ix, iy}, BR[2] = {ix + 1, iy}, TL[2] = {ix, iy + 1}, TR[2] = {ix + 1, iy + 1};
+    EdgeRef edges[4] = {
+        {iy * nx + ix, {BL[0], BL[1]}, {BR[0], BR[1]}, {0.0, -1.0}},
+        {(iy + 1) * nx + ix, {TL[0], TL[1]}, {TR[0], TR[1]}, {0.0, 1.0}},
+        {H + ix * ny + iy, {BL[0], BL[1]}, {TL[0], TL[1]}, {-1.0, 0.0}},
+        {H + (ix + 1) * ny + iy, {BR[0], BR[1]}, {TR[0], TR[1]}, {1.0, 0.0}},
+    };
+    SubGeo &s = sg[i];
+    for (auto &e : edges)
+      if (g.edge_on_boundary(e.id))
+        for (int k = 1; k <= pr.edge_pts[e.id]; ++k) {
+          s.bxy.push_back(g.edge_point(e, k));
+          s.bg.push_back(bnd_off[e.id] + k - 1);
+        }
+    const int *verts[4] = {BL, BR, TL, TR};
+    for (auto v : verts)
+      if (!g.is_cross(v) && (v[0] == 0 || v[0] == nx || v[1] == 0 || v[1] == ny)) {
+        s.bxy.push_back(g.vxy(v));
+        s.bg.push_back(vtx_bnd[v[1] * (nx + 1) + v[0]]);
+      }
+    std::map<std::pair<int, int>, int> locpi;
+    for (auto v : verts)
+      if (g.is_cross(v)) {
+        locpi[{v[0], v[1]}] = int(s.pxy.size());
+        s.pxy.push_back(g.vxy(v));
+        s.pg.push_back(g.pi_index(v));
+        s.pv.push_back({v[0], v[1]});
+      }
+    for (auto &e : edges) {
+      if (g.edge_on_boundary(e.id)) continue;
+      const int n = pr.edge_pts[e.id];
+      auto a = locpi.find({e.sv[0], e.sv[1]});
+      auto b = locpi.find({e.ev[0], e.ev[1]});
+      for (int k = 1; k <= n; ++k) {
+        double f = double(k) / double(n + 1);
+        s.dxy.push_back(g.edge_point(e, k));
+        s.dnrm.push_back({e.n[0], e.n[1]});
+        s.dg.push_back(dl_off[e.id] + k - 1);
+        s.al.push_back(a != locpi.end() ? 1.0 - f : 0.0);
+        s.alp.push_back(a != locpi.end() ? a->second : -1);
+        s.be.push_back(b != locpi.end() ? f : 0.0);
+        s.bep.push_back(b != locpi.end() ? b->second : -1);
+      }
+    }
+    s.am_edges.resize(s.pv.size());
+    for (size_t k = 0; k < s.pv.size(); ++k)
+      for (auto &e : edges) {
+        bool at_s = e.sv[0] == s.pv[k].first && e.sv[1] == s.pv[k].second;
+        bool at_e = e.ev[0] == s.pv[k].first && e.ev[1] == s.pv[k].second;
+        if (at_s || at_e) s.am_edges[k].push_back(e);
+      }
+  }
+
+  // ---- workspace layout
+  P.subs.resize(n_sub);
+  long long cur = 0;
+  auto take = [&](long long n) {
+    long long off = cur;
+    cur += (std::max(n, 1LL) + 31) / 32 * 32;
+    return off;
+  };
+  P.o_w = take(2 * sumM);
+  P.o_b = take(sumM);
+  P.o_xint = take(2 * sumI);
+  P.o_aint = take(sumI);
+  P.o_gaint = take(2 * sumI);
+  long long wo = 0, io = 0, eo = 0;
+  int max_M = 0, sum_nG = 0;
+  long long setup_scratch_begin = 0;
+  // persistent per-subdomain operators first
+  for (int i = 0; i < n_sub; ++i) {
+    SubDev &d = P.subs[i];
+    const SubGeo &s = sg[i];
+    d.M = pr.M[i];
+    d.nI = pr.n_int[i];
+    d.nB = int(s.bxy.size());
+    d.nPi = int(s.pxy.size());
+    d.nDl = int(s.dxy.size());
+    d.nG = d.nPi + d.nDl;
+    d.m = d.nI + d.nB + d.nG;
+    d.nE = pr.n_eval ? pr.n_eval[i] : 0;
+    d.w_off = wo;
+    d.int_off = io;
+    d.eval_off = eo;
+    wo += d.M;
+    io += d.nI;
+    eo += d.nE;
+    max_M = std::max(max_M, d.M);
+    d.loc_off = sum_nG;
+    sum_nG += d.nG;
+    const long long M = d.M, m = d.m, nG = d.nG, nDl = d.nDl;
+    d.oX = take(m * M);  // holds Q2 of K_c after setup (needed by every solve)
+    d.oA = take(nG * M);
+    d.oEval = take(d.nE * M);
+    d.oV = take(M * M);
+    d.oV3 = take(M * M);
+    d.oQG = take(nG * M);
+    d.oKpE = take(M * nG);
+    d.oLam = take(nG * nG);
+    d.oLamT = take(nG * nG);
+    d.oPsi = take(nG * nG);
+    d.oPhi = take(nDl * nDl);
+    d.oPhiT = take(nDl * nDl);
+    d.oF = take((d.nI + d.nB) * R);
+    d.oT = take(M * R);
+    d.oQtf = take(M * R);
+    d.oY = take(M * R);
+    d.oAy = take(nG * R);
+    d.oP = take(nG * R);
+    d.oC = take(M * R);
+    d.oU = take((long long)d.nE * R);
+  }
+  P.max_M = max_M;
+  P.sum_nG = sum_nG;
+  // coarse matrices
+  const long long np = std::max(n_pi, 1);
+  P.o_Dpp = take(np * np);
+  P.o_Spi = take(np * np);
+  P.o_Vpi = take(np * np);
+  P.o_Sinv = take(np * np);
+  P.o_C1 = take(np * np);
+  P.o_C2 = take(np * np);
+  P.o_C3 = take(np * np);
+  P.o_SpiR = take(np * np);
+  // CG vectors: 12 Delta vectors, 14 Pi vectors, 9 local slabs, reductions
+  const long long nd_ = std::max(nd, 1), nR = R;
+  P.o_cg = take(12 * nd_ * nR + 14 * np * nR + 2048 * 32 + 128);
+  P.o_loc = take(9LL * sum_nG * nR);
+  P.o_status = take(4 * n_sub + 64);
+  // inspection copies
+  if (P.keep) {
+    P.o_keepX = cur;
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      take(2LL * d.m * d.M + (long long)d.nG * d.M);
+    }
+  }
+  // setup scratch (not needed after setup)
+  setup_scratch_begin = cur;
+  struct Scr {
+    long long Kb, Y1, Y1b, Abar, G, Gb, V1, V1b, V2, V2b, V3b, Z, Zb, Z2, Z2b, T1, T1b, Vb, QbD, AV, AbV;
+  };
+  std::vector<Scr> scr(n_sub);
+  for (int i = 0; i < n_sub; ++i) {
+    SubDev &d = P.subs[i];
+    const long long M = d.M, m = d.m, nG = d.nG, nDl = d.nDl;
+    Scr &c = scr[i];
+    c.Kb = take(m * M);
+    c.Y1 = take(m * M);
+    c.Y1b = take(m * M);
+    c.Abar = take(nDl * M);
+    c.G = take(M * M);
+    c.Gb = take(M * M);
+    c.V1 = take(M * M);
+    c.V1b = take(M * M);
+    c.V2 = take(M * M);
+    c.V2b = take(M * M);
+    c.V3b = take(M * M);
+    c.Z = take(M * M);
+    c.Zb = take(M * M);
+    c.Z2 = take(M * M);
+    c.Z2b = take(M * M);
+    c.T1 = take(M * M);
+    c.T1b = take(M * M);
+    c.Vb = take(M * M);
+    c.QbD = take(nDl * M);
+    c.AV = take(nG * M);
+    c.AbV = take(nDl * M);
+    d.oKb = c.Kb;
+    d.oY1 = c.Y1;
+    d.oY1b = c.Y1b;
+    d.oAbar = c.Abar;
+    d.oVb = c.Vb;
+  }
+  (void)setup_scratch_begin;
+  P.n_dbl = cur;
+
+  // ---- special rows
+  for (int i = 0; i < n_sub; ++i) {
+    const SubDev &d = P.subs[i];
+    const SubGeo &s = sg[i];
+    const long long M = d.M;
+    auto base = [&](int kind) {
+      SpecialRow r;
+      std::memset(&r, 0, sizeof(r));
+      r.kind = kind;
+      r.sub = i;
+      r.out1 = -1;
+      return r;
+    };
+    for (int k = 0; k < d.nB; ++k) {  // boundary rows of K_c and K-bar
+      SpecialRow r = base(ROW_POINT);
+      r.x = s.bxy[k].x;
+      r.y = s.bxy[k].y;
+      r.out0 = d.oX + (long long)(d.nI + k) * M;
+      r.out1 = d.oKb + (long long)(d.nI + k) * M;
+      P.rows.push_back(r);
+    }
+    const int g0 = d.nI + d.nB;
+    for (int k = 0; k < d.nPi; ++k) {  // Pi rows: point values in K_c and K-bar
+      SpecialRow r = base(ROW_POINT);
+      r.x = s.pxy[k].x;
+      r.y = s.pxy[k].y;
+      r.out0 = d.oX + (long long)(g0 + k) * M;
+      r.out1 = d.oKb + (long long)(g0 + k) * M;
+      P.rows.push_back(r);
+      SpecialRow a = base(ROW_AM);  // A_m corner row
+      a.x = s.pxy[k].x;
+      a.y = s.pxy[k].y;
+      a.out0 = d.oA + (long long)k * M;
+      for (int t = 0; t < 2; ++t) {
+        const EdgeRef &e = s.am_edges[k][t];
+        V2 sa = g.vxy(e.sv), sb = g.vxy(e.ev);
+        a.am[t][0] = sa.x;
+        a.am[t][1] = sa.y;
+        a.am[t][2] = sb.x;
+        a.am[t][3] = sb.y;
+        a.am[t][4] = e.n[0];
+        a.am[t][5] = e.n[1];
+        a.am_e[t] = pr.edge_pts[e.id];
+      }
+      P.rows.push_back(a);
+    }
+    for (int k = 0; k < d.nDl; ++k) {
+      // K_c Delta row (also A-bar row): (T^i)^{-1} C phi, or C phi without the change
+      SpecialRow r = base(o.use_change_of_vars ? ROW_TINV : ROW_POINT);
+      r.x = s.dxy[k].x;
+      r.y = s.dxy[k].y;
+      if (o.use_change_of_vars) {
+        r.alpha = s.al[k];
+        r.beta = s.be[k];
+        if (s.alp[k] >= 0) {
+          r.xa = s.pxy[s.alp[k]].x;
+          r.ya = s.pxy[s.alp[k]].y;
+        }
+        if (s.bep[k] >= 0) {
+          r.xb = s.pxy[s.bep[k]].x;
+          r.yb = s.pxy[s.bep[k]].y;
+        }
+      }
+      r.out0 = d.oX + (long long)(g0 + d.nPi + k) * M;
+      r.out1 = d.oAbar + (long long)k * M;
+      P.rows.push_back(r);
+      // flux row: K-bar Delta row and A_m Delta row
+      SpecialRow f = base(ROW_FLUX);
+      f.x = s.dxy[k].x;
+      f.y = s.dxy[k].y;
+      f.nx = s.dnrm[k].x;
+      f.ny = s.dnrm[k].y;
+      f.out0 = d.oKb + (long long)(g0 + d.nPi + k) * M;
+      f.out1 = d.oA + (long long)(d.nPi + k) * M;
+      P.rows.push_back(f);
+    }
+  }
+  // evaluation rows
+  if (sumE > 0) {
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      for (int k = 0; k < d.nE; ++k) {
+        SpecialRow r;
+        std::memset(&r, 0, sizeof(r));
+        r.kind = ROW_POINT;
+        r.sub = i;
+        r.out1 = -1;
+        r.x = pr.x_eval[2 * (d.eval_off + k)];
+        r.y = pr.x_eval[2 * (d.eval_off + k) + 1];
+        r.out0 = d.oEval + (long long)k * d.M;
+        P.rows.push_back(r);
+      }
+    }
+  }
+
+  // ---- int tables
+  auto &I = P.ints;
+  for (int i = 0; i < n_sub; ++i) {
+    SubDev &d = P.subs[i];
+    d.gpi_off = int(I.size());
+    for (int v : sg[i].pg) I.push_back(v);
+    d.gdl_off = int(I.size());
+    for (int v : sg[i].dg) I.push_back(v);
+    d.bnd_off = int(I.size());
+    for (int v : sg[i].bg) I.push_back(v);
+  }
+  P.o_pi_own = int(I.size());
+  I.resize(I.size() + 8 * (size_t)n_pi, -1);
+  P.o_dl_own = int(I.size());
+  I.resize(I.size() + 4 * (size_t)nd, -1);
+  {
+    std::vector<int> cnt(n_pi, 0), cntd(nd, 0);
+    for (int i = 0; i < n_sub; ++i) {
+      for (size_t k = 0; k < sg[i].pg.size(); ++k) {
+        int gi = sg[i].pg[k];
+        int c = cnt[gi]++;
+        if (c >= 4) return fail("internal: Pi point with more than four subdomains");
+        I[P.o_pi_own + 8 * gi + 2 * c] = i;
+        I[P.o_pi_own + 8 * gi + 2 * c + 1] = int(k);
+      }
+      for (size_t k = 0; k < sg[i].dg.size(); ++k) {
+        int gi = sg[i].dg[k];
+        int c = cntd[gi]++;
+        if (c >= 2) return fail("internal: Delta point with more than two subdomains");
+        I[P.o_dl_own + 4 * gi + 2 * c] = i;
+        I[P.o_dl_own + 4 * gi + 2 * c + 1] = int(k);
+      }
+    }
+    for (int v : cntd)
+      if (v != 2) return fail("internal: Delta point not shared by two subdomains");
+  }
+  P.o_tasks_pi = int(I.size());
+  for (int i = 0; i < n_sub; ++i)
+    for (int k = 0; k < P.subs[i].nPi; ++k) {
+      I.push_back(i);
+      I.push_back(k);
+    }
+  P.n_tasks_pi = (int(I.size()) - P.o_tasks_pi) / 2;
+  P.o_tasks_dl = int(I.size());
+  for (int i = 0; i < n_sub; ++i)
+    for (int k = 0; k < P.subs[i].nDl; ++k) {
+      I.push_back(i);
+      I.push_back(k);
+    }
+  P.n_tasks_dl = (int(I.size()) - P.o_tasks_dl) / 2;
+  P.o_tasks_g = int(I.size());
+  for (int i = 0; i < n_sub; ++i)
+    for (int k = 0; k < P.subs[i].nG; ++k) {
+      I.push_back(i);
+      I.push_back(k);
+    }
+  P.n_tasks_g = (int(I.size()) - P.o_tasks_g) / 2;
+  P.o_tasks_c = int(I.size());
+  for (int i = 0; i < n_sub; ++i)
+    for (int k = 0; k < P.subs[i].M; ++k) {
+      I.push_back(i);
+      I.push_back(k);
+    }
+  P.n_tasks_c = (int(I.size()) - P.o_tasks_c) / 2;
+
+  // ---- GEMM phases
+  auto phase_begin = [&]() {
+    GemmPhase ph;
+    ph.desc0 = int(P.gdesc.size());
+    ph.tile0 = int(P.gtile.size());
+    ph.ndesc = ph.ntile = 0;
+    return ph;
+  };
+  auto add = [&](GemmPhase &ph, long long a, long long b, long long c, int m, int n, int k, int lda,
+                 int ldb, int ldc, int ta, int tb, int flags, double alpha, double beta,
+                 bool upper_tiles = false) {
+    if (m <= 0 || n <= 0) return;
+    GemmDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.a = a;
+    d.b = b;
+    d.c = c;
+    d.m = m;
+    d.n = n;
+    d.k = k;
+    d.lda = lda;
+    d.ldb = ldb;
+    d.ldc = ldc;
+    d.ta = ta;
+    d.tb = tb;
+    d.flags = flags;
+    d.alpha = alpha;
+    d.beta = beta;
+    int di = int(P.gdesc.size());
+    P.gdesc.push_back(d);
+    ph.ndesc++;
+    const int tm = (m + 63) / 64, tn = (n + 63) / 64;
+    for (int x = 0; x < tm; ++x)
+      for (int y = 0; y < tn; ++y) {
+        if (upper_tiles && x > y) continue;
+        P.gtile.push_back({di, x, y, 0});
+        ph.ntile++;
+      }
+  };
+  auto push = [&](GemmPhase &ph) { P.setup_gemm.push_back(ph); };
+  // phase indices are fixed; api.cu runs them in this order around the Cholesky passes
+  // 0: G = Y^T Y for K and K-bar
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, d.oX, d.oX, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+      add(ph, d.oKb, d.oKb, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+    }
+    push(ph);
+  }
+  // 1: Q1 = Y V1
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, d.oX, scr[i].V1, d.oY1, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, d.oKb, scr[i].V1b, d.oY1b, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+    }
+    push(ph);
+  }
+  // 2: G = Q1^T Q1 ; 3: G += Z1^T Z1
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, d.oY1, d.oY1, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+      add(ph, d.oY1b, d.oY1b, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+    }
+    push(ph);
+    GemmPhase ph2 = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      // op(A) = Z^T is lower triangular, op(B) = Z upper: k <= min(row, col)
+      add(ph2, scr[i].Z, scr[i].Z, scr[i].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
+          GEMM_B_UPPER, 1.0, 1.0, true);
+      add(ph2, scr[i].Zb, scr[i].Zb, scr[i].Gb, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
+          GEMM_B_UPPER, 1.0, 1.0, true);
+    }
+    push(ph2);
+  }
+  // 4: Q2 = Q1 V2 (into the feature buffers), Z2 = Z1 V2
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, d.oY1, scr[i].V2, d.oX, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, d.oY1b, scr[i].V2b, d.oKb, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, scr[i].Z, scr[i].V2, scr[i].Z2, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_B_UPPER | GEMM_A_UPPER, 1.0, 0.0);
+      add(ph, scr[i].Zb, scr[i].V2b, scr[i].Z2b, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_B_UPPER | GEMM_A_UPPER, 1.0, 0.0);
+    }
+    push(ph);
+  }
+  // 5: G = Q2^T Q2 ; 6: G += Z2^T Z2
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, d.oX, d.oX, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+      add(ph, d.oKb, d.oKb, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+    }
+    push(ph);
+    GemmPhase ph2 = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph2, scr[i].Z2, scr[i].Z2, scr[i].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
+          GEMM_B_UPPER, 1.0, 1.0, true);
+      add(ph2, scr[i].Z2b, scr[i].Z2b, scr[i].Gb, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
+          GEMM_B_UPPER, 1.0, 1.0, true);
+    }
+    push(ph2);
+  }
+  // 7: T1 = V1 V2 ; 8: V = T1 V3
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, scr[i].V1, scr[i].V2, scr[i].T1, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, scr[i].V1b, scr[i].V2b, scr[i].T1b, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+    }
+    push(ph);
+    GemmPhase ph2 = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph2, scr[i].T1, d.oV3, d.oV, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+      add(ph2, scr[i].T1b, scr[i].V3b, scr[i].Vb, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+    }
+    push(ph2);
+  }
+  // 9: Q_Gamma = Q2[Gamma rows] V3 ; Q-bar_Delta = Q2-bar[Delta rows] V3-bar ;
+  //    A_m V ; A-bar V-bar
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      const long long M = d.M;
+      add(ph, d.oX + (long long)(d.nI + d.nB) * M, d.oV3, d.oQG, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0,
+          GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, d.oKb + (long long)(d.m - d.nDl) * M, scr[i].V3b, scr[i].QbD, d.nDl, d.M, d.M, d.M, d.M,
+          d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, d.oA, d.oV, scr[i].AV, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+      add(ph, d.oAbar, scr[i].Vb, scr[i].AbV, d.nDl, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0,
+          0.0);
+    }
+    push(ph);
+  }
+  // 10: Lambda, Lambda^T, Psi, K^+ E_Gamma, Phi, Phi^T
+  {
+    GemmPhase ph = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(ph, scr[i].AV, d.oQG, d.oLam, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+      add(ph, d.oQG, scr[i].AV, d.oLamT, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+      add(ph, d.oQG, d.oQG, d.oPsi, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+      add(ph, d.oV, d.oQG, d.oKpE, d.M, d.nG, d.M, d.M, d.M, d.nG, 0, 1, GEMM_A_UPPER, 1.0, 0.0);
+      add(ph, scr[i].AbV, scr[i].QbD, d.oPhi, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
+      add(ph, scr[i].QbD, scr[i].AbV, d.oPhiT, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
+    }
+    push(ph);
+  }
+  // coarse: 11: S_Pi += D^T D ; 12: Sinv = V_Pi V_Pi^T ; 13: C1 = Sinv D^T, C3 = D Sinv ;
+  //         14: C2 = I - D C1
+  if (n_pi > 0) {
+    GemmPhase a = phase_begin();
+    add(a, P.o_Dpp, P.o_Dpp, P.o_Spi, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 1, 0, 0, 1.0, 1.0);
+    push(a);
+    GemmPhase b = phase_begin();
+    add(b, P.o_Vpi, P.o_Vpi, P.o_Sinv, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 1, GEMM_A_UPPER, 1.0, 0.0);
+    push(b);
+    GemmPhase c = phase_begin();
+    add(c, P.o_Sinv, P.o_Dpp, P.o_C1, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 1, 0, 1.0, 0.0);
+    add(c, P.o_Dpp, P.o_Sinv, P.o_C3, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 0, 0, 1.0, 0.0);
+    push(c);
+    GemmPhase e = phase_begin();
+    add(e, P.o_Dpp, P.o_C1, P.o_C2, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 0, 0, -1.0, 1.0);
+    push(e);
+  } else {
+    for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0});
+  }
+  // solve phases: 15: T = Q2[IB rows]^T F ; 16: Qtf = V3^T T ; 17: y = V Qtf, p = Q_Gamma Qtf ;
+  //               18: a = A_m y ; 19: u_eval = Eval c
+  {
+    GemmPhase a = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(a, d.oX, d.oF, d.oT, d.M, R, d.nI + d.nB, d.M, R, R, 1, 0, 0, 1.0, 0.0);
+    }
+    push(a);
+    GemmPhase b = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(b, d.oV3, d.oT, d.oQtf, d.M, R, d.M, d.M, R, R, 1, 0, 0, 1.0, 0.0);
+    }
+    push(b);
+    GemmPhase c = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(c, d.oV, d.oQtf, d.oY, d.M, R, d.M, d.M, R, R, 0, 0, GEMM_A_UPPER, 1.0, 0.0);
+      add(c, d.oQG, d.oQtf, d.oP, d.nG, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
+    }
+    push(c);
+    GemmPhase e = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(e, d.oA, d.oY, d.oAy, d.nG, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
+    }
+    push(e);
+    GemmPhase f = phase_begin();
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(f, d.oEval, d.oC, d.oU, d.nE, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
+    }
+    push(f);
+  }
+
+  // ---- Cholesky phases
+  for (int pass = 0; pass < 3; ++pass) {
+    P.chol_pass[pass].desc0 = int(P.cdesc.size());
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      for (int t = 0; t < 2; ++t) {
+        CholDesc c;
+        std::memset(&c, 0, sizeof(c));
+        c.g = t == 0 ? scr[i].G : scr[i].Gb;
+        c.v = pass == 0 ? (t == 0 ? scr[i].V1 : scr[i].V1b)
+                        : pass == 1 ? (t == 0 ? scr[i].V2 : scr[i].V2b) : (t == 0 ? d.oV3 : scr[i].V3b);
+        c.z = pass == 0 ? (t == 0 ? scr[i].Z : scr[i].Zb) : -1;
+        c.M = d.M;
+        c.m = d.m;
+        c.mode = pass == 0 ? 1 : 0;
+        c.status = 2 * i + t;
+        c.eps_rel = o.eps_rel;
+        P.cdesc.push_back(c);
+      }
+    }
+    P.chol_pass[pass].ndesc = int(P.cdesc.size()) - P.chol_pass[pass].desc0;
+  }
+  P.chol_coarse.desc0 = int(P.cdesc.size());
+  if (n_pi > 0) {
+    CholDesc c;
+    std::memset(&c, 0, sizeof(c));
+    c.g = P.o_SpiR;  // a copy of S_Pi, factored in place
+    c.v = P.o_Vpi;
+    c.z = -1;
+    c.M = n_pi;
+    c.m = n_pi;
+    c.mode = 0;
+    c.status = 2 * n_sub;
+    P.cdesc.push_back(c);
+  }
+  P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
+
+  // ---- bounds of every access the kernels make (an error here, not a fault there)
+  {
+    const long long N = P.n_dbl;
+    auto in = [&](long long off, long long len) { return off >= 0 && len >= 0 && off + len <= N; };
+    for (const auto &d : P.gdesc) {
+      const long long alen = d.ta ? (long long)(d.k - 1) * d.lda + d.m : (long long)(d.m - 1) * d.lda + d.k;
+      const long long blen = d.tb ? (long long)(d.n - 1) * d.ldb + d.k : (long long)(d.k - 1) * d.ldb + d.n;
+      const long long clen = (long long)(d.m - 1) * d.ldc + d.n;
+      if (d.k > 0 && (!in(d.a, alen) || !in(d.b, blen))) return fail("internal: GEMM operand out of bounds");
+      if (!in(d.c, clen)) return fail("internal: GEMM output out of bounds");
+      if ((d.ta ? d.lda < d.m : d.lda < d.k) || (d.tb ? d.ldb < d.k : d.ldb < d.n) || d.ldc < d.n)
+        return fail("internal: GEMM leading dimension");
+    }
+    for (const auto &t : P.gtile)
+      if (t.desc < 0 || t.desc >= (int)P.gdesc.size()) return fail("internal: GEMM tile");
+    for (const auto &c : P.cdesc) {
+      const long long mm = (long long)c.M * c.M;
+      if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm))) return fail("internal: Cholesky bounds");
+      if (c.status < 0 || c.status > 2 * n_sub) return fail("internal: status slot");
+    }
+    for (const auto &r : P.rows) {
+      const long long M = P.subs[r.sub].M;
+      if (!in(r.out0, M) || (r.out1 >= 0 && !in(r.out1, M))) return fail("internal: row output bounds");
+    }
+    for (const auto &d : P.subs) {
+      const long long M = d.M, m = d.m;
+      if (!in(d.oX, m * M) || !in(d.oKb, m * M) || !in(d.oY1, m * M) || !in(d.oY1b, m * M) ||
+          !in(d.oA, d.nG * M) || !in(d.oAbar, d.nDl * M) || !in(d.oEval, d.nE * M) ||
+          !in(d.oLam, (long long)d.nG * d.nG) || !in(d.oLamT, (long long)d.nG * d.nG) ||
+          !in(d.oPsi, (long long)d.nG * d.nG) || !in(d.oPhi, (long long)d.nDl * d.nDl) ||
+          !in(d.oPhiT, (long long)d.nDl * d.nDl) || !in(d.oKpE, M * d.nG) || !in(d.oY, M * R) ||
+          !in(d.oAy, d.nG * (long long)R) || !in(d.oP, d.nG * (long long)R) || !in(d.oC, M * R) ||
+          !in(d.oU, (long long)d.nE * R) || !in(d.oF, (long long)(d.nI + d.nB) * R))
+        return fail("internal: subdomain buffer bounds");
+      if (d.w_off + d.M > sumM || d.int_off + d.nI > sumI || d.eval_off + d.nE > sumE)
+        return fail("internal: packed input bounds");
+      if (d.loc_off + d.nG > sum_nG) return fail("internal: local slab bounds");
+      for (int k = 0; k < d.nPi; ++k)
+        if (I[d.gpi_off + k] < 0 || I[d.gpi_off + k] >= n_pi) return fail("internal: R_Pi map");
+      for (int k = 0; k < d.nDl; ++k)
+        if (I[d.gdl_off + k] < 0 || I[d.gdl_off + k] >= nd) return fail("internal: R_Delta map");
+      for (int k = 0; k < d.nB; ++k)
+        if (I[d.bnd_off + k] < 0 || I[d.bnd_off + k] >= nb) return fail("internal: boundary map");
+    }
+    for (int p = 0; p < n_pi; ++p)
+      for (int o = 0; o < 4; ++o) {
+        const int s = I[P.o_pi_own + 8 * p + 2 * o], a = I[P.o_pi_own + 8 * p + 2 * o + 1];
+        if (s >= 0 && (s >= n_sub || a < 0 || a >= P.subs[s].nPi)) return fail("internal: Pi owner map");
+      }
+    for (int p = 0; p < nd; ++p)
+      for (int o = 0; o < 2; ++o) {
+        const int s = I[P.o_dl_own + 4 * p + 2 * o], a = I[P.o_dl_own + 4 * p + 2 * o + 1];
+        if (s < 0 || s >= n_sub || a < 0 || a >= P.subs[s].nDl) return fail("internal: Delta owner map");
+      }
+    const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;
+    if (!in(P.o_cg, cg_need) || !in(P.o_loc, 9LL * sum_nG * R) || !in(P.o_status, 4LL * n_sub + 64))
+      return fail("internal: CG region bounds");
+    const long long np2 = (long long)std::max(n_pi, 1) * std::max(n_pi, 1);
+    for (long long o : {P.o_Dpp, P.o_Spi, P.o_Vpi, P.o_Sinv, P.o_C1, P.o_C2, P.o_C3, P.o_SpiR})
+      if (!in(o, np2)) return fail("internal: coarse bounds");
+  }
+
+  // ---- table region (bytes), then the double region
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t off = 0;
+  P.off_subs = off;
+  off = al(off + P.subs.size() * sizeof(SubDev));
+  P.off_rows = off;
+  off = al(off + std::max<size_t>(P.rows.size(), 1) * sizeof(SpecialRow));
+  P.off_gdesc = off;
+  off = al(off + std::max<size_t>(P.gdesc.size(), 1) * sizeof(GemmDesc));
+  P.off_gtile = off;
+  off = al(off + std::max<size_t>(P.gtile.size(), 1) * sizeof(GemmTile));
+  P.off_cdesc = off;
+  off = al(off + std::max<size_t>(P.cdesc.size(), 1) * sizeof(CholDesc));
+  P.off_ints = off;
+  off = al(off + std::max<size_t>(P.ints.size(), 1) * sizeof(int));
+  P.bytes_tables = off;
+  P.off_dbl = off;
+  P.bytes_total = off + (size_t)P.n_dbl * sizeof(double);
+  P.sz.workspace_bytes = P.bytes_total;
+  return DDELM_OK;
+}
+
+}  // namespace ddelm

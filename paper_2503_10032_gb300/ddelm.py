@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libddelm (include/ddelm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device memory (the workspace and the
+input/output tensors) and the stream.  If the shared library is missing the
+import of this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libddelm.so")
+
+DDELM_OK = 0
+DDELM_ERR_INVALID_ARG = -1
+DDELM_ERR_RANK_DEFICIENT = -2
+DDELM_ERR_NOT_CONVERGED = -3
+DDELM_ERR_CUDA = -4
+DDELM_ERR_TIMEOUT = -5
+DDELM_ERR_UNSUPPORTED = -6
+DDELM_OP_POISSON = 0
+DDELM_OP_DIFFUSION = 1
+DDELM_PREC_FP64 = 0
+DDELM_PREC_MIXED = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class ddelm_options(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("eps_rel", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("use_change_of_vars", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("keep_matrices", ctypes.c_int)]
+
+
+class ddelm_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("op", ctypes.c_int), ("n_rhs", ctypes.c_int),
+                ("M", _ip), ("w_hat", _dp), ("b_hat", _dp), ("scale", ctypes.c_double),
+                ("n_int", _ip), ("x_int", _dp), ("a_int", _dp), ("grad_a_int", _dp),
+                ("edge_pts", _ip), ("n_eval", _ip), ("x_eval", _dp),
+                ("opt", ddelm_options)]
+
+
+class ddelm_sizes(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int), ("n_edges", ctypes.c_int), ("n_bnd", ctypes.c_int),
+                ("n_pi", ctypes.c_int), ("n_delta", ctypes.c_int),
+                ("sum_M", ctypes.c_longlong), ("sum_int", ctypes.c_longlong),
+                ("sum_eval", ctypes.c_longlong), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class ddelm_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
+EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_solve", "ddelm_backward", "ddelm_inspect",
+           "ddelm_destroy", "ddelm_status_string")
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libddelm.so not built ({path}); run paper_2503_10032_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.ddelm_query.argtypes = [ctypes.POINTER(ddelm_problem), ctypes.POINTER(ddelm_sizes)]
+    lib.ddelm_query.restype = ctypes.c_int
+    lib.ddelm_setup.argtypes = [ctypes.POINTER(ddelm_problem), ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), _ip]
+    lib.ddelm_setup.restype = ctypes.c_int
+    lib.ddelm_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ddelm_solve_info),
+                                ctypes.c_void_p]
+    lib.ddelm_solve.restype = ctypes.c_int
+    lib.ddelm_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
+    lib.ddelm_backward.restype = ctypes.c_int
+    lib.ddelm_inspect.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.ddelm_inspect.restype = ctypes.c_int
+    lib.ddelm_destroy.argtypes = [ctypes.c_void_p]
+    lib.ddelm_destroy.restype = None
+    lib.ddelm_status_string.argtypes = [ctypes.c_int]
+    lib.ddelm_status_string.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = load_library()
+
+
+class DDELMError(RuntimeError):
+    def __init__(self, status, what=""):
+        super().__init__(f"{what}: {ddelm_status_string(status)} ({status})")
+        self.status = status
+
+
+def ddelm_status_string(status: int) -> str:
+    return _lib.ddelm_status_string(status).decode()
+
+
+def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change_of_vars=True,
+                 precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False):
+    return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
+                         max_refine, int(keep_matrices))
+
+
+class ProblemArgs:
+    """Keeps the numpy arrays of a problem alive while a ddelm_problem points at them."""
+
+    def __init__(self, prob, opts: ddelm_options):
+        def d(a):
+            return np.ascontiguousarray(a, dtype=np.float64)
+
+        def i(a):
+            return np.ascontiguousarray(a, dtype=np.int32)
+        self.M, self.n_int, self.edge_pts, self.n_eval = i(prob.M), i(prob.n_int), i(prob.edge_pts), i(prob.n_eval)
+        self.w_hat, self.b_hat, self.x_int = d(prob.w_hat), d(prob.b_hat), d(prob.x_int)
+        self.a_int, self.grad_a_int, self.x_eval = d(prob.a_int), d(prob.grad_a_int), d(prob.x_eval)
+        c = ddelm_problem()
+        c.nx, c.ny = prob.nx, prob.ny
+        c.x0, c.x1, c.y0, c.y1 = prob.box
+        c.op = prob.op
+        c.n_rhs = prob.n_rhs
+        c.M = self.M.ctypes.data_as(_ip)
+        c.w_hat = self.w_hat.ctypes.data_as(_dp)
+        c.b_hat = self.b_hat.ctypes.data_as(_dp)
+        c.scale = prob.scale
+        c.n_int = self.n_int.ctypes.data_as(_ip)
+        c.x_int = self.x_int.ctypes.data_as(_dp)
+        c.a_int = self.a_int.ctypes.data_as(_dp) if prob.op == DDELM_OP_DIFFUSION else None
+        c.grad_a_int = self.grad_a_int.ctypes.data_as(_dp) if prob.op == DDELM_OP_DIFFUSION else None
+        c.edge_pts = self.edge_pts.ctypes.data_as(_ip)
+        c.n_eval = self.n_eval.ctypes.data_as(_ip)
+        c.x_eval = self.x_eval.ctypes.data_as(_dp)
+        c.opt = opts
+        self.c = c
+
+
+def ddelm_query(pa: ProblemArgs) -> ddelm_sizes:
+    sz = ddelm_sizes()
+    rc = _lib.ddelm_query(ctypes.byref(pa.c), ctypes.byref(sz))
+    if rc != DDELM_OK:
+        raise DDELMError(rc, "ddelm_query")
+    return sz
+
+
+def ddelm_setup(pa: ProblemArgs, ws_ptr: int, ws_bytes: int, stream: int):
+    h = ctypes.c_void_p()
+    info = ctypes.c_int(-1)
+    rc = _lib.ddelm_setup(ctypes.byref(pa.c), ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream),
+                          ctypes.byref(h), ctypes.byref(info))
+    return rc, h, info.value
+
+
+def ddelm_solve(h, f_ptr, g_ptr, c_ptr, mu_ptr, u_ptr, stream):
+    info = ddelm_solve_info()
+    rc = _lib.ddelm_solve(h, ctypes.c_void_p(f_ptr), ctypes.c_void_p(g_ptr), ctypes.c_void_p(c_ptr),
+                          ctypes.c_void_p(mu_ptr), ctypes.c_void_p(u_ptr), ctypes.byref(info),
+                          ctypes.c_void_p(stream))
+    return rc, info
+
+
+def ddelm_backward(h, grad_c_ptr, grad_f_ptr, grad_g_ptr, stream):
+    info = ddelm_solve_info()
+    rc = _lib.ddelm_backward(h, ctypes.c_void_p(grad_c_ptr), ctypes.c_void_p(grad_f_ptr),
+                             ctypes.c_void_p(grad_g_ptr), ctypes.byref(info), ctypes.c_void_p(stream))
+    return rc, info
+
+
+def ddelm_inspect(h, sub: int, which: int, n: int) -> np.ndarray:
+    out = np.zeros(max(n, 1), np.float64)
+    rc = _lib.ddelm_inspect(h, sub, which, out.ctypes.data_as(_dp), out.size)
+    if rc != DDELM_OK:
+        raise DDELMError(rc, "ddelm_inspect")
+    return out[:n]
+
+
+def ddelm_destroy(h):
+    _lib.ddelm_destroy(h)
+
+
+class Solver:
+    """A DDELM-NN handle with its torch-allocated workspace on one CUDA device."""
+
+    def __init__(self, prob, *, device="cuda:0", stream=None, **opt_kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.prob = prob
+        self.opts = make_options(**opt_kw)
+        self.pa = ProblemArgs(prob, self.opts)
+        self.sizes = ddelm_query(self.pa)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = int(self.sizes.workspace_bytes)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        rc, h, sub = ddelm_setup(self.pa, self.ws_ptr, nbytes, self.stream.cuda_stream)
+        if rc != DDELM_OK:
+            if h.value:
+                ddelm_destroy(h)
+            raise DDELMError(rc, f"ddelm_setup (subdomain {sub})")
+        self.h = h
+
+    def solve(self, f_int, g_bnd):
+        """f_int [sum n_int, R], g_bnd [n_bnd, R] float64 CUDA tensors -> (c, mu, u_eval, info)."""
+        torch = self.torch
+        R = self.prob.n_rhs
+        sz = self.sizes
+        c = torch.empty((sz.sum_M, R), dtype=torch.float64, device=self.device)
+        mu = torch.empty((sz.n_pi + sz.n_delta, R), dtype=torch.float64, device=self.device)
+        u = torch.empty((max(sz.sum_eval, 1), R), dtype=torch.float64, device=self.device)
+        f_int = f_int.contiguous()
+        g_bnd = g_bnd.contiguous()
+        rc, info = ddelm_solve(self.h, f_int.data_ptr(), g_bnd.data_ptr(), c.data_ptr(), mu.data_ptr(),
+                               u.data_ptr(), self.stream.cuda_stream)
+        if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
+            raise DDELMError(rc, "ddelm_solve")
+        return c, mu, u[:sz.sum_eval], info, rc
+
+    def inspect(self, sub, which):
+        sizes = ddelm_inspect(self.h, sub, 7, 4)
+        m, M, nG, nDl = (int(v) for v in sizes)
+        shapes = {0: (m, M), 1: (m, M), 2: (nG, M), 3: (nG, nG), 4: (nG, nG), 5: (nDl, nDl),
+                  6: (self.sizes.n_pi, self.sizes.n_pi)}
+        shp = shapes[which]
+        return ddelm_inspect(self.h, sub, which, shp[0] * shp[1]).reshape(shp)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            ddelm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
