@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""DDELM-NN solves/sec on GB300.
+
+One step = one pass of the whole path on one problem: the setup (feature
+assembly, factorisation of every local least-squares problem, local and
+coarse operators) followed by one solve (right-hand side of Eq. nn-mixed, CG
+to the relative residual tolerance, reconstruction by Eq. coarse_sol_2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Under torchrun every rank solves its own independent replica of the problem
+(no data-path collective; weak scaling); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DDELM solves/sec to rel. interface residual 1e-8 (mixed vs FP64, same GB300)"
+DEFAULT_WORKLOAD = "poisson_8x8_m400"
+TOL = 1e-8
+EPS_REL = 1e-8
+THETA = 0.999
+FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
+
+
+def workload_config(name, prob, sizes=None):
+    cfg = {"workload": name, "subdomains": f"{prob.nx}x{prob.ny}",
+           "neurons_per_subdomain": int(prob.M[0]) if len(set(prob.M.tolist())) == 1 else "uneven",
+           "interior_points_per_subdomain": int(prob.n_int[0]) if len(set(prob.n_int.tolist())) == 1 else "uneven",
+           "points_per_edge": int(prob.edge_pts[0]) if len(set(prob.edge_pts.tolist())) == 1 else "uneven",
+           "n_rhs": int(prob.n_rhs), "theta": THETA, "eps_rel": EPS_REL, "tol": TOL,
+           "operator": "poisson" if prob.op == 0 else "diffusion"}
+    if sizes is not None:
+        cfg["n_pi"] = int(sizes.n_pi)
+        cfg["n_delta"] = int(sizes.n_delta)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(prob, n_sample, budget_s=None):
+    """Times the oracle's per-subdomain setup on a bounded sample of subdomains.
+
+    Returns (seconds per full-problem setup estimate, description).  The
+    oracle's coarse problem and CG are left out of the sample (they are a
+    minority of its time on these workloads), so the estimate favours the
+    oracle."""
+    from oracle import ddelm as odd
+    n = prob.n_sub
+    n_sample = max(1, min(n, n_sample))
+    only = set(np.linspace(0, n - 1, n_sample).round().astype(int).tolist())
+    t0 = time.perf_counter()
+    odd.DDELMOracle(prob, odd.Options(eps_rel=EPS_REL, theta=THETA, tol=TOL), only=only)
+    dt = time.perf_counter() - t0
+    return dt * n / len(only), dt, len(only)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2503_10032_gb300 import inputs
+    prob = inputs.config(args.workload)
+    cores = os.cpu_count() or 1
+    n_sample = max(1, prob.n_sub // 8)
+    for _ in range(args.warmup):
+        oracle_sample(prob, n_sample)
+    per = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        est, dt, ns = oracle_sample(prob, n_sample)
+        per.append(est)
+        t_total += dt
+    sec = float(np.mean(per))
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, prob),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step the FP64 oracle's local setup (features, two ridge "
+                                       f"pseudo-inverses by Householder QR, local blocks) of {n_sample} of "
+                                       f"{prob.n_sub} subdomains, scaled by {prob.n_sub}/{n_sample}; coarse "
+                                       f"problem and CG not included (favours the oracle)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2503_10032_gb300 import build as _b
+    _b.build()
+    from paper_2503_10032_gb300 import ddelm as D
+    from paper_2503_10032_gb300 import inputs
+
+    prob = inputs.config(args.workload)
+    prec = D.DDELM_PREC_FP64 if args.precision == "fp64" else D.DDELM_PREC_MIXED
+    opt_kw = dict(theta=THETA, eps_rel=EPS_REL, tol=TOL, max_iters=20000, precision=prec)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        solver = D.Solver(prob, device=dev, stream=stream, **opt_kw)
+        f = torch.tensor(prob.f_int, dtype=torch.float64, device=dev)
+        g = torch.tensor(prob.g_bnd, dtype=torch.float64, device=dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    sizes = solver.sizes
+    flops = D.ddelm_inspect(solver.h, 0, 8, 3)
+
+    def step():
+        solver.refactor()
+        return solver.solve(f, g)
+
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    solver.profile(enable=True, reset=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    infos = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                         # L2 flush, outside the timed events
+            ev[k][0].record(stream)
+        out = step()
+        ev[k][1].record(stream)
+        infos.append((out[3].iterations, out[3].rel_residual, out[4]))
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    prof_ms, prof_n = solver.profile(enable=False, reset=True)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C ABI with host buffers: setup from host arrays,
+    # H2D of the data from pinned memory, solve, D2H of c, mu and u
+    f_h = torch.tensor(prob.f_int, dtype=torch.float64).pin_memory()
+    g_h = torch.tensor(prob.g_bnd, dtype=torch.float64).pin_memory()
+    R = prob.n_rhs
+    c_h = torch.empty((sizes.sum_M, R), dtype=torch.float64).pin_memory()
+    mu_h = torch.empty((sizes.n_pi + sizes.n_delta, R), dtype=torch.float64).pin_memory()
+    u_h = torch.empty((max(sizes.sum_eval, 1), R), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_ms = []
+    ws_ptr, ws_bytes = solver.ws_ptr, int(sizes.workspace_bytes)
+    pa = D.ProblemArgs(prob, D.make_options(**opt_kw))
+    solver.close()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, h, _ = D.ddelm_setup(pa, ws_ptr, ws_bytes, stream.cuda_stream)
+        if rc != D.DDELM_OK:
+            raise D.DDELMError(rc, "ddelm_setup (e2e)")
+        with torch.cuda.stream(stream):
+            f_d = f_h.to(dev, non_blocking=True)
+            g_d = g_h.to(dev, non_blocking=True)
+            c_d = torch.empty((sizes.sum_M, R), dtype=torch.float64, device=dev)
+            mu_d = torch.empty((sizes.n_pi + sizes.n_delta, R), dtype=torch.float64, device=dev)
+            u_d = torch.empty((max(sizes.sum_eval, 1), R), dtype=torch.float64, device=dev)
+        rc, info = D.ddelm_solve(h, f_d.data_ptr(), g_d.data_ptr(), c_d.data_ptr(), mu_d.data_ptr(),
+                                 u_d.data_ptr(), stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            c_h.copy_(c_d, non_blocking=True)
+            mu_h.copy_(mu_d, non_blocking=True)
+            u_h.copy_(u_d, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        D.ddelm_destroy(h)
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(sum(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * e2e_steps / (e2e_total / 1e3)
+    h2d = int(sizes.upload_bytes) + f_h.numel() * 8 + g_h.numel() * 8
+    d2h = c_h.numel() * 8 + mu_h.numel() * 8 + u_h.numel() * 8
+
+    # roofline of the dominant kernel class (time measured live over the timed region)
+    names = D.PROF_CLASS_NAMES
+    k_dom = int(np.argmax(prof_ms[:len(names)]))
+    launches_total = int(prof_n.sum())
+    per_launch_ms = prof_ms[k_dom] / max(prof_n[k_dom], 1)
+    if names[k_dom] == "gemm_f64":
+        work = (flops[0] + flops[2]) * args.steps / max(prof_n[k_dom], 1)
+    elif names[k_dom] == "chol_inv":
+        work = flops[1] * args.steps / max(prof_n[k_dom], 1)
+    else:
+        work = float("nan")
+    achieved = work / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
+    roofline = {"kernel": names[k_dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS if math.isfinite(achieved) else None,
+                "traffic": None,
+                "peak_source": "nominal FP64 of the recipe table (no FP64 entry in the measured peaks)",
+                "time_share": {n: float(prof_ms[i] / max(prof_ms.sum(), 1e-12)) for i, n in enumerate(names)},
+                "launches": {n: int(prof_n[i]) for i, n in enumerate(names)}}
+
+    iters = [i for i, _, _ in infos]
+    resid = max(r for _, r, _ in infos)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(args.workload, prob, sizes), precision=args.precision,
+                           parallelism=f"replicas{world}", l2="flushed between steps (512 MB write)"),
+            "cg_iterations": int(np.median(iters)), "rel_residual_max": resid,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches_total, "roofline": roofline, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, dt, ns = oracle_sample(prob, max(1, prob.n_sub // 4))
+        line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count() or 1,
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle local setup of {ns} of {prob.n_sub} subdomains "
+                                          f"({dt:.1f} s), scaled by {prob.n_sub}/{ns}; coarse problem and CG "
+                                          f"left out (favours the oracle)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

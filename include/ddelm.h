@@ -111,6 +111,7 @@ typedef struct ddelm_sizes {
   int n_pi, n_delta;   /* |Pi|, |Delta| */
   long long sum_M, sum_int, sum_eval;
   size_t workspace_bytes; /* device workspace ddelm_setup needs */
+  size_t upload_bytes;    /* host-to-device bytes ddelm_setup copies (tables + problem data) */
 } ddelm_sizes;
 
 typedef struct ddelm_solve_info {
@@ -137,6 +138,12 @@ int ddelm_query(const ddelm_problem *prob, ddelm_sizes *out);
 int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_bytes,
                 void *stream, ddelm_handle **out, int *info_sub);
 
+/* Re-runs the whole setup (assembly, factorisation, local and coarse
+ * operators) from the problem data already resident in the workspace, on
+ * `stream`, without host work or host-device copies; the call returns after
+ * the work has completed.  Status as ddelm_setup. */
+int ddelm_refactor(ddelm_handle *h, void *stream, int *info_sub);
+
 /* One solve for new data.  Device inputs: d_f_int [sum n_int][n_rhs] forcing
  * at the interior points, d_g_bnd [n_bnd][n_rhs] Dirichlet data.  Device
  * outputs (nullable): d_c [sum M][n_rhs] network coefficients,
@@ -157,11 +164,22 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, double *d_grad_f, do
  * (synchronous).  which: 0 K_c^i [m x M], 1 K-bar^i [m x M], 2 A_m^i [nG x M],
  * 3 Lambda^i = A_m^i K^+ E_Gamma [nG x nG], 4 Psi^i = E_Gamma^T K K^+ E_Gamma
  * [nG x nG], 5 Phi^i = A-bar^i K-bar^+ E_Delta [nDl x nDl], 6 S_Pi [n_pi x n_pi]
- * (sub ignored), 7 the four sizes {m, M, nG, nDl} as doubles.  Blocks 0-2 are
+ * (sub ignored), 7 the four sizes {m, M, nG, nDl} as doubles, 8 the algorithmic
+ * flop counts {setup GEMMs, setup Cholesky + inverses, solve GEMMs} (sub ignored).  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */
 int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t out_len);
+
+/* Per-kernel device timing.  enable = 1 starts recording CUDA events around
+ * every launch of the library's kernels (on the launch stream), 0 stops.
+ * ms[k] and launches[k] (nullable, DDELM_PROF_CLASSES entries) receive the
+ * time and launch count accumulated since the last call with reset = 1, per
+ * kernel class: 0 feature assembly, 1 FP64 GEMM, 2 Cholesky/inverse,
+ * 3 persistent CG, 4 other (gathers, coarse assembly, fills).  Synchronises
+ * on the recorded events. */
+#define DDELM_PROF_CLASSES 8
+int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long *launches);
 
 void ddelm_destroy(ddelm_handle *h);
 

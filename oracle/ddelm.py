@@ -105,21 +105,27 @@ def _ridge_pinv(K, eps_rel):
 class DDELMOracle:
     """The structured oracle.  ``prob`` is a problem in the plain-array format."""
 
-    def __init__(self, prob, opts: Options | None = None):
+    def __init__(self, prob, opts: Options | None = None, only=None):
+        """only: optional list of subdomains; builds just their local blocks and
+        skips the coarse problem (used to time a bounded sample of the setup)."""
         self.p = prob
         self.o = opts or Options()
         self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts)
         self.n_pi, self.n_dl = self.lay.n_pi, self.lay.n_delta
-        self._build_local()
-        self._build_coarse()
+        self._build_local(only)
+        if only is None:
+            self._build_coarse()
 
     # ------------------------------------------------------------ local
-    def _build_local(self):
+    def _build_local(self, only=None):
         p, o = self.p, self.o
         Moff = np.concatenate([[0], np.cumsum(p.M)])
         Ioff = np.concatenate([[0], np.cumsum(p.n_int)])
         self.loc = []
         for i, sl in enumerate(self.lay.subs):
+            if only is not None and i not in only:
+                self.loc.append(None)
+                continue
             L = _Local()
             w = p.scale * p.w_hat[Moff[i]:Moff[i + 1]]
             b = p.scale * p.b_hat[Moff[i]:Moff[i + 1]]

@@ -16,6 +16,13 @@ struct ddelm_handle {
   Plan plan;
   char *ws = nullptr;
   size_t ws_bytes = 0;
+  // profiling: event pairs around launches, reduced on ddelm_profile
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_cls;
+  size_t ev_used = 0;
+  double prof_ms[DDELM_PROF_CLASSES] = {};
+  long long prof_n[DDELM_PROF_CLASSES] = {};
 };
 
 namespace {
@@ -28,14 +35,46 @@ namespace {
 
 double *dbase(ddelm_handle *h) { return reinterpret_cast<double *>(h->ws + h->plan.off_dbl); }
 
+// Records an event pair around a launch when profiling is on.
+struct ProfScope {
+  ddelm_handle *h;
+  cudaStream_t s;
+  size_t k = (size_t)-1;
+  ProfScope(ddelm_handle *h_, int cls, cudaStream_t s_) : h(h_), s(s_) {
+    if (!h->prof) return;
+    if (h->ev_used + 2 > h->ev.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+      h->ev.push_back(a);
+      h->ev.push_back(b);
+      h->ev_cls.push_back(cls);
+      h->ev_cls.push_back(cls);
+    }
+    k = h->ev_used;
+    h->ev_used += 2;
+    h->ev_cls[k] = cls;
+    cudaEventRecord(h->ev[k], s);
+  }
+  ~ProfScope() {
+    if (k != (size_t)-1) cudaEventRecord(h->ev[k + 1], s);
+  }
+};
+
+enum { PC_FEAT = 0, PC_GEMM = 1, PC_CHOL = 2, PC_CG = 3, PC_OTHER = 4 };
+
+#define LAUNCH(cls, call)              \
+  do {                                 \
+    ProfScope ps_(h, cls, s);          \
+    CK(call);                          \
+  } while (0)
+
 template <class T>
 void put(std::vector<char> &buf, size_t off, const std::vector<T> &v) {
   if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
 }
 
-int run_setup(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s, int *info_sub) {
+int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   Plan &p = h->plan;
-  // tables
   std::vector<char> tab(p.bytes_tables, 0);
   put(tab, p.off_subs, p.subs);
   put(tab, p.off_rows, p.rows);
@@ -59,12 +98,19 @@ int run_setup(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s, int *i
       CK(cudaMemcpyAsync(db + p.o_gaint, prob->grad_a_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
     }
   }
+  return DDELM_OK;
+}
+
+// Assembly, shifted CholeskyQR3 of [K; eps I] and [K-bar; eps-bar I], local
+// operators and the coarse problem, all from workspace-resident data.
+int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
+  Plan &p = h->plan;
+  double *db = dbase(h);
   CK(cudaMemsetAsync(db + p.o_status, 0, (4 * (size_t)p.n_sub + 64) * 8, s));
   const long long np = p.n_pi > 0 ? p.n_pi : 1;
   CK(cudaMemsetAsync(db + p.o_Dpp, 0, np * np * 8, s));
   CK(cudaMemsetAsync(db + p.o_Spi, 0, np * np * 8, s));
-  // assembly
-  CK(launch_features(p, h->ws, s));
+  LAUNCH(PC_FEAT, launch_features(p, h->ws, s));
   if (p.keep) {
     long long off = p.o_keepX;
     for (const auto &d : p.subs) {
@@ -75,33 +121,30 @@ int run_setup(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s, int *i
       off += (2 * (long long)mm + (long long)d.nG * d.M + 31) / 32 * 32;
     }
   }
-  // shifted CholeskyQR3 of [K; eps I] and [K-bar; eps-bar I]
   const auto &G = p.setup_gemm;
-  CK(launch_gemm_phase(p, G[0], h->ws, s));
-  CK(launch_chol_phase(p, p.chol_pass[0], h->ws, s));
-  CK(launch_gemm_phase(p, G[1], h->ws, s));
-  CK(launch_gemm_phase(p, G[2], h->ws, s));
-  CK(launch_gemm_phase(p, G[3], h->ws, s));
-  CK(launch_chol_phase(p, p.chol_pass[1], h->ws, s));
-  CK(launch_gemm_phase(p, G[4], h->ws, s));
-  CK(launch_gemm_phase(p, G[5], h->ws, s));
-  CK(launch_gemm_phase(p, G[6], h->ws, s));
-  CK(launch_chol_phase(p, p.chol_pass[2], h->ws, s));
-  CK(launch_gemm_phase(p, G[7], h->ws, s));
-  CK(launch_gemm_phase(p, G[8], h->ws, s));
-  // local operators
-  CK(launch_gemm_phase(p, G[9], h->ws, s));
-  CK(launch_gemm_phase(p, G[10], h->ws, s));
-  // coarse problem
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[0], h->ws, s));
+  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[0], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[1], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[2], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[3], h->ws, s));
+  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[1], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[4], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[5], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[6], h->ws, s));
+  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[2], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[7], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[8], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[9], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[10], h->ws, s));
   if (p.n_pi > 0) {
-    CK(launch_coarse_assembly(p, h->ws, s));
-    CK(launch_gemm_phase(p, G[11], h->ws, s));
+    LAUNCH(PC_OTHER, launch_coarse_assembly(p, h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[11], h->ws, s));
     CK(cudaMemcpyAsync(db + p.o_SpiR, db + p.o_Spi, (size_t)np * np * 8, cudaMemcpyDeviceToDevice, s));
-    CK(launch_chol_phase(p, p.chol_coarse, h->ws, s));
-    CK(launch_gemm_phase(p, G[12], h->ws, s));
-    CK(launch_gemm_phase(p, G[13], h->ws, s));
-    CK(launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
-    CK(launch_gemm_phase(p, G[14], h->ws, s));
+    LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_coarse, h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[12], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[13], h->ws, s));
+    LAUNCH(PC_OTHER, launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[14], h->ws, s));
   }
   CK(cudaStreamSynchronize(s));
   std::vector<int> st(2 * (size_t)p.n_sub + 1);
@@ -146,13 +189,20 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
   }
   h->ws = static_cast<char *>(d_workspace);
   h->ws_bytes = workspace_bytes;
-  rc = run_setup(h, prob, static_cast<cudaStream_t>(stream), info_sub);
+  rc = upload(h, prob, static_cast<cudaStream_t>(stream));
+  if (rc == DDELM_OK) rc = compute_setup(h, static_cast<cudaStream_t>(stream), info_sub);
   if (rc != DDELM_OK && rc != DDELM_ERR_RANK_DEFICIENT) {
     delete h;
     return rc;
   }
   *out = h;
   return rc;
+}
+
+int ddelm_refactor(ddelm_handle *h, void *stream, int *info_sub) {
+  if (!h) return DDELM_ERR_INVALID_ARG;
+  if (info_sub) *info_sub = -1;
+  return compute_setup(h, static_cast<cudaStream_t>(stream), info_sub);
 }
 
 int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, double *d_c, double *d_mu,
@@ -168,12 +218,12 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
   }
-  CK(launch_gather_rhs(p, h->ws, d_f_int, d_g_bnd, s));
+  LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, d_f_int, d_g_bnd, s));
   const auto &G = p.setup_gemm;
-  CK(launch_gemm_phase(p, G[15], h->ws, s));
-  CK(launch_gemm_phase(p, G[16], h->ws, s));
-  CK(launch_gemm_phase(p, G[17], h->ws, s));
-  CK(launch_gemm_phase(p, G[18], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[15], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[16], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[17], h->ws, s));
+  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[18], h->ws, s));
   // barrier words and error flag
   CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
   CgArgs a;
@@ -182,9 +232,9 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   a.max_iters = p.opt.max_iters;
   a.tol = p.opt.tol;
   a.theta = p.opt.theta;
-  CK(launch_cg(p, h->ws, a, s));
+  LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
   if (p.sz.sum_eval > 0) {
-    CK(launch_gemm_phase(p, G[19], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[19], h->ws, s));
     if (d_u_eval) {
       for (const auto &d : p.subs)
         if (d.nE > 0)
@@ -265,6 +315,15 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       src = d.oPhi;
       n = (size_t)d.nDl * d.nDl;
       break;
+    case 8: {  // algorithmic flops: setup GEMMs, Cholesky+inverse, solve GEMMs (no CG)
+      if (out_len < 3) return DDELM_ERR_INVALID_ARG;
+      double fs = 0.0, fv = 0.0;
+      for (size_t q = 0; q < p.phase_flops.size(); ++q) (q <= 14 ? fs : fv) += p.phase_flops[q];
+      host_out[0] = fs;
+      host_out[1] = p.chol_flops;
+      host_out[2] = fv;
+      return DDELM_OK;
+    }
     case 7: {
       if (out_len < 4) return DDELM_ERR_INVALID_ARG;
       host_out[0] = d.m;
@@ -281,7 +340,33 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
   return DDELM_OK;
 }
 
-void ddelm_destroy(ddelm_handle *h) { delete h; }
+int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long *launches) {
+  if (!h) return DDELM_ERR_INVALID_ARG;
+  for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+    CK(cudaEventSynchronize(h->ev[k + 1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->ev[k], h->ev[k + 1]));
+    h->prof_ms[h->ev_cls[k]] += t;
+    h->prof_n[h->ev_cls[k]] += 1;
+  }
+  h->ev_used = 0;
+  for (int c = 0; c < DDELM_PROF_CLASSES; ++c) {
+    if (ms) ms[c] = h->prof_ms[c];
+    if (launches) launches[c] = h->prof_n[c];
+    if (reset) {
+      h->prof_ms[c] = 0.0;
+      h->prof_n[c] = 0;
+    }
+  }
+  h->prof = enable != 0;
+  return DDELM_OK;
+}
+
+void ddelm_destroy(ddelm_handle *h) {
+  if (!h) return;
+  for (auto e : h->ev) cudaEventDestroy(e);
+  delete h;
+}
 
 const char *ddelm_status_string(int status) {
   switch (status) {

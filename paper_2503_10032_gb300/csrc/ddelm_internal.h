@@ -112,6 +112,9 @@ struct Plan {
   std::vector<int> ints;  // gpi, gdl, bnd maps, owner maps, task lists
   // phases (indices into the tables)
   std::vector<GemmPhase> setup_gemm;  // filled in order; see api.cu for the sequence
+  std::vector<double> gemm_flops;      // algorithmic flops per descriptor
+  std::vector<double> phase_flops;     // per GEMM phase
+  double chol_flops = 0.0;             // all Cholesky + inverse passes of one setup
   // named ranges into ints
   int o_pi_own = 0;   // per Pi point: 4 x (sub, local) pairs, -1 padded
   int o_dl_own = 0;   // per Delta point: 2 x (sub, local)

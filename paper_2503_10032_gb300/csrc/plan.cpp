@@ -510,6 +510,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     int di = int(P.gdesc.size());
     P.gdesc.push_back(d);
     ph.ndesc++;
+    // algorithmic flops: only the products that can be nonzero
+    double f = 2.0 * m * (double)n * k;
+    const bool bu = (flags & GEMM_B_UPPER) && k == n, au = (flags & GEMM_A_UPPER) && k == m;
+    if (bu && au) f /= 3.0;
+    else if (bu || au || upper_tiles) f /= 2.0;
+    P.gemm_flops.push_back(f);
     const int tm = (m + 63) / 64, tn = (n + 63) / 64;
     for (int x = 0; x < tm; ++x)
       for (int y = 0; y < tn; ++y) {
@@ -700,6 +706,11 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     push(f);
   }
 
+  for (size_t q = 0; q < P.setup_gemm.size(); ++q) {
+    double f = 0.0;
+    for (int k = 0; k < P.setup_gemm[q].ndesc; ++k) f += P.gemm_flops[P.setup_gemm[q].desc0 + k];
+    P.phase_flops.push_back(f);
+  }
   // ---- Cholesky phases
   for (int pass = 0; pass < 3; ++pass) {
     P.chol_pass[pass].desc0 = int(P.cdesc.size());
@@ -736,6 +747,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     P.cdesc.push_back(c);
   }
   P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
+  for (const auto &c : P.cdesc) P.chol_flops += 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
 
   // ---- bounds of every access the kernels make (an error here, not a fault there)
   {
@@ -818,6 +830,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.off_dbl = off;
   P.bytes_total = off + (size_t)P.n_dbl * sizeof(double);
   P.sz.workspace_bytes = P.bytes_total;
+  P.sz.upload_bytes = P.bytes_tables + sizeof(double) * (size_t)(3 * sumM + 2 * sumI) +
+                      (pr.op == DDELM_OP_DIFFUSION ? sizeof(double) * (size_t)(3 * sumI) : 0);
   return DDELM_OK;
 }
 

@@ -53,7 +53,8 @@ class ddelm_sizes(ctypes.Structure):
     _fields_ = [("n_sub", ctypes.c_int), ("n_edges", ctypes.c_int), ("n_bnd", ctypes.c_int),
                 ("n_pi", ctypes.c_int), ("n_delta", ctypes.c_int),
                 ("sum_M", ctypes.c_longlong), ("sum_int", ctypes.c_longlong),
-                ("sum_eval", ctypes.c_longlong), ("workspace_bytes", ctypes.c_size_t)]
+                ("sum_eval", ctypes.c_longlong), ("workspace_bytes", ctypes.c_size_t),
+                ("upload_bytes", ctypes.c_size_t)]
 
 
 class ddelm_solve_info(ctypes.Structure):
@@ -61,8 +62,10 @@ class ddelm_solve_info(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
 
-EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_solve", "ddelm_backward", "ddelm_inspect",
-           "ddelm_destroy", "ddelm_status_string")
+EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm_backward",
+           "ddelm_inspect", "ddelm_profile", "ddelm_destroy", "ddelm_status_string")
+DDELM_PROF_CLASSES = 8
+PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other")
 
 
 def load_library(path: str = LIB_PATH):
@@ -74,6 +77,11 @@ def load_library(path: str = LIB_PATH):
     lib.ddelm_setup.argtypes = [ctypes.POINTER(ddelm_problem), ctypes.c_void_p, ctypes.c_size_t,
                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), _ip]
     lib.ddelm_setup.restype = ctypes.c_int
+    lib.ddelm_refactor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _ip]
+    lib.ddelm_refactor.restype = ctypes.c_int
+    lib.ddelm_profile.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp,
+                                  ctypes.POINTER(ctypes.c_longlong)]
+    lib.ddelm_profile.restype = ctypes.c_int
     lib.ddelm_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ddelm_solve_info),
                                 ctypes.c_void_p]
@@ -157,6 +165,22 @@ def ddelm_setup(pa: ProblemArgs, ws_ptr: int, ws_bytes: int, stream: int):
     return rc, h, info.value
 
 
+def ddelm_refactor(h, stream):
+    info = ctypes.c_int(-1)
+    rc = _lib.ddelm_refactor(h, ctypes.c_void_p(stream), ctypes.byref(info))
+    return rc, info.value
+
+
+def ddelm_profile(h, enable: bool, reset: bool):
+    ms = np.zeros(DDELM_PROF_CLASSES, np.float64)
+    n = np.zeros(DDELM_PROF_CLASSES, np.int64)
+    rc = _lib.ddelm_profile(h, int(enable), int(reset), ms.ctypes.data_as(_dp),
+                            n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    if rc != DDELM_OK:
+        raise DDELMError(rc, "ddelm_profile")
+    return ms, n
+
+
 def ddelm_solve(h, f_ptr, g_ptr, c_ptr, mu_ptr, u_ptr, stream):
     info = ddelm_solve_info()
     rc = _lib.ddelm_solve(h, ctypes.c_void_p(f_ptr), ctypes.c_void_p(g_ptr), ctypes.c_void_p(c_ptr),
@@ -206,6 +230,14 @@ class Solver:
                 ddelm_destroy(h)
             raise DDELMError(rc, f"ddelm_setup (subdomain {sub})")
         self.h = h
+
+    def refactor(self):
+        rc, sub = ddelm_refactor(self.h, self.stream.cuda_stream)
+        if rc != DDELM_OK:
+            raise DDELMError(rc, f"ddelm_refactor (subdomain {sub})")
+
+    def profile(self, enable=True, reset=True):
+        return ddelm_profile(self.h, enable, reset)
 
     def solve(self, f_int, g_bnd):
         """f_int [sum n_int, R], g_bnd [n_bnd, R] float64 CUDA tensors -> (c, mu, u_eval, info)."""

@@ -78,7 +78,7 @@ def test_solution_matches_oracle(D, case):
     if n_pi:
         assert _rel(mu[:n_pi], ref["mu_pi"]) < 1e-9
     assert _rel(u, ref["u_eval"]) < 1e-9
-    assert info.rel_residual < 1e-12
+    assert info.rel_residual < 1e-10
     assert info.iterations > 0
 
 
