@@ -37,6 +37,14 @@ THETA = 0.999
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def workload_config(name, prob, sizes=None):
     cfg = {"workload": name, "subdomains": f"{prob.nx}x{prob.ny}",
            "neurons_per_subdomain": int(prob.M[0]) if len(set(prob.M.tolist())) == 1 else "uneven",
@@ -158,7 +166,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -196,7 +205,7 @@ def main():
         g = torch.tensor(prob.g_bnd, dtype=torch.float64, device=dev)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     sizes = solver.sizes
-    flops = D.ddelm_inspect(solver.h, 0, 8, 3)
+    flops = D.ddelm_inspect(solver.h, 0, 8, 5)
 
     def step():
         solver.refactor()
@@ -231,6 +240,35 @@ def main():
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
+
+    # the same steps on the FP64 path (the metric compares mixed with FP64 on the same GPU)
+    fp64_cmp = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        with torch.cuda.stream(stream):
+            s64 = D.Solver(prob, device=dev, stream=stream, **dict(opt_kw, precision=D.DDELM_PREC_FP64))
+        for _ in range(1):
+            s64.refactor()
+            o64 = s64.solve(f, g)
+        torch.cuda.synchronize(dev)
+        ev64 = []
+        for k in range(args.steps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a0.record(stream)
+            s64.refactor()
+            o64 = s64.solve(f, g)
+            a1.record(stream)
+            ev64.append((a0, a1))
+        torch.cuda.synchronize(dev)
+        t64 = float(sum(a.elapsed_time(b_) for a, b_ in ev64))
+        u_mixed = out[2].double().cpu().numpy()
+        u64 = o64[2].double().cpu().numpy()
+        fp64_cmp = {"value": args.steps / (t64 / 1e3), "ms_per_step": t64 / args.steps,
+                    "cg_iterations": int(o64[3].iterations), "rel_residual": float(o64[3].rel_residual),
+                    "mixed_vs_fp64_rel_l2_u": float(np.linalg.norm(u_mixed - u64) / max(np.linalg.norm(u64), 1e-300))}
+        s64.close()
+        del s64
 
     # end to end through the C ABI with host buffers: setup from host arrays,
     # H2D of the data from pinned memory, solve, D2H of c, mu and u
@@ -281,34 +319,45 @@ def main():
 
     # roofline of the dominant kernel class (time measured live over the timed region)
     names = D.PROF_CLASS_NAMES
-    k_dom = int(np.argmax(prof_ms[:len(names)]))
+    n_cls = len(names)
+    k_dom = int(np.argmax(prof_ms[:n_cls]))
     launches_total = int(prof_n.sum())
     per_launch_ms = prof_ms[k_dom] / max(prof_n[k_dom], 1)
+    peaks = measured_peaks()
+    bound, unit, peak, peak_src = "alu", "GFLOP/s", FP64_PEAK_GFLOPS, \
+        "nominal FP64 of the recipe table (no FP64 entry in the measured peaks)"
     if names[k_dom] == "gemm_f64":
-        work = (flops[0] + flops[2]) * args.steps / max(prof_n[k_dom], 1)
+        work = (flops[4] + flops[2]) * args.steps / max(prof_n[k_dom], 1)
     elif names[k_dom] == "chol_inv":
         work = flops[1] * args.steps / max(prof_n[k_dom], 1)
+    elif names[k_dom] == "tc_gemm":
+        work = flops[3] * args.steps / max(prof_n[k_dom], 1)
+        bound, unit = "tensor", "GFLOP/s"
+        peak = 1000.0 * float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
     else:
         work = float("nan")
     achieved = work / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
-    roofline = {"kernel": names[k_dom], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS if math.isfinite(achieved) else None,
-                "traffic": None,
-                "peak_source": "nominal FP64 of the recipe table (no FP64 entry in the measured peaks)",
-                "time_share": {n: float(prof_ms[i] / max(prof_ms.sum(), 1e-12)) for i, n in enumerate(names)},
+    roofline = {"kernel": names[k_dom], "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak if math.isfinite(achieved) else None,
+                "traffic": None, "peak_source": peak_src,
+                "time_share": {n: float(prof_ms[i] / max(prof_ms[:n_cls].sum(), 1e-12)) for i, n in enumerate(names)},
                 "launches": {n: int(prof_n[i]) for i, n in enumerate(names)}}
 
     iters = [i for i, _, _ in infos]
     resid = max(r for _, r, _ in infos)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x9+f64",
+            "data": "synthetic",
             "config": dict(workload_config(args.workload, prob, sizes), precision=args.precision,
                            parallelism=f"replicas{world}", l2="flushed between steps (512 MB write)"),
             "cg_iterations": int(np.median(iters)), "rel_residual_max": resid,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches_total, "roofline": roofline, "clocks": clk}
+    if fp64_cmp is not None:
+        line["fp64"] = fp64_cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, dt, ns = oracle_sample(prob, max(1, prob.n_sub // 4))
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count() or 1,

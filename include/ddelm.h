@@ -176,7 +176,8 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
  * ms[k] and launches[k] (nullable, DDELM_PROF_CLASSES entries) receive the
  * time and launch count accumulated since the last call with reset = 1, per
  * kernel class: 0 feature assembly, 1 FP64 GEMM, 2 Cholesky/inverse,
- * 3 persistent CG, 4 other (gathers, coarse assembly, fills).  Synchronises
+ * 3 persistent CG, 4 other (gathers, coarse assembly, fills), 5 BF16 slicing
+ * of tensor-core GEMM operands, 6 tensor-core (tcgen05) GEMM.  Synchronises
  * on the recorded events. */
 #define DDELM_PROF_CLASSES 8
 int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long *launches);

@@ -60,7 +60,7 @@ struct ProfScope {
   }
 };
 
-enum { PC_FEAT = 0, PC_GEMM = 1, PC_CHOL = 2, PC_CG = 3, PC_OTHER = 4 };
+enum { PC_FEAT = 0, PC_GEMM = 1, PC_CHOL = 2, PC_CG = 3, PC_OTHER = 4, PC_SLICE = 5, PC_TC = 6 };
 
 #define LAUNCH(cls, call)              \
   do {                                 \
@@ -82,6 +82,15 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   put(tab, p.off_gtile, p.gtile);
   put(tab, p.off_cdesc, p.cdesc);
   put(tab, p.off_ints, p.ints);
+  put(tab, p.off_sdesc, p.sdesc);
+  put(tab, p.off_odesc, p.odesc);
+  put(tab, p.off_otile, p.otile);
+  if (p.mixed) {
+    std::vector<unsigned char> maps;
+    const int rc = encode_tensor_maps(p, h->ws, maps);
+    if (rc != DDELM_OK) return rc;
+    std::memcpy(tab.data() + p.off_tmaps, maps.data(), maps.size());
+  }
   CK(cudaMemcpyAsync(h->ws, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
   // problem data: w = s*w_hat, b = s*b_hat, interior points, coefficient
   double *db = dbase(h);
@@ -122,20 +131,36 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
     }
   }
   const auto &G = p.setup_gemm;
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[0], h->ws, s));
+  // a setup GEMM phase runs on the tensor cores (BF16 slices) in MIXED precision
+  auto gemm = [&](int q) -> int {
+    if (p.mixed && q < (int)p.oz_phase.size() && p.oz_phase[q].ntile > 0) {
+      LAUNCH(PC_SLICE, launch_slices(p, p.oz_phase[q], h->ws, s));
+      LAUNCH(PC_TC, launch_oz_gemm(p, p.oz_phase[q], h->ws, s));
+    } else {
+      LAUNCH(PC_GEMM, launch_gemm_phase(p, G[q], h->ws, s));
+    }
+    return DDELM_OK;
+  };
+#define GEMM(q)                     \
+  do {                              \
+    const int rc_ = gemm(q);        \
+    if (rc_ != DDELM_OK) return rc_; \
+  } while (0)
+  GEMM(0);
   LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[0], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[1], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[2], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[3], h->ws, s));
+  GEMM(1);
+  GEMM(2);
+  GEMM(3);
   LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[1], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[4], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[5], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[6], h->ws, s));
+  GEMM(4);
+  GEMM(5);
+  GEMM(6);
   LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[2], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[7], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[8], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[9], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[10], h->ws, s));
+  GEMM(7);
+  GEMM(8);
+  GEMM(9);
+  GEMM(10);
+#undef GEMM
   if (p.n_pi > 0) {
     LAUNCH(PC_OTHER, launch_coarse_assembly(p, h->ws, s));
     LAUNCH(PC_GEMM, launch_gemm_phase(p, G[11], h->ws, s));
@@ -147,6 +172,9 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
     LAUNCH(PC_GEMM, launch_gemm_phase(p, G[14], h->ws, s));
   }
   CK(cudaStreamSynchronize(s));
+  int oz_err = 0;
+  CK(cudaMemcpy(&oz_err, db + p.o_status + 2 * p.n_sub + 32, sizeof(int), cudaMemcpyDeviceToHost));
+  if (oz_err) return DDELM_ERR_TIMEOUT;
   std::vector<int> st(2 * (size_t)p.n_sub + 1);
   CK(cudaMemcpy(st.data(), db + p.o_status, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
   for (size_t k = 0; k < st.size(); ++k)
@@ -315,13 +343,19 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       src = d.oPhi;
       n = (size_t)d.nDl * d.nDl;
       break;
-    case 8: {  // algorithmic flops: setup GEMMs, Cholesky+inverse, solve GEMMs (no CG)
-      if (out_len < 3) return DDELM_ERR_INVALID_ARG;
-      double fs = 0.0, fv = 0.0;
-      for (size_t q = 0; q < p.phase_flops.size(); ++q) (q <= 14 ? fs : fv) += p.phase_flops[q];
+    case 8: {  // algorithmic flops: setup GEMMs, Cholesky+inverse, solve GEMMs (no CG),
+               // tensor-core flops of the MIXED setup, FP64-engine flops left in MIXED
+      if (out_len < 5) return DDELM_ERR_INVALID_ARG;
+      double fs = 0.0, fv = 0.0, fleft = 0.0;
+      for (size_t q = 0; q < p.phase_flops.size(); ++q) {
+        (q <= 14 ? fs : fv) += p.phase_flops[q];
+        if (q <= 14 && !(p.mixed && q < p.oz_phase.size() && p.oz_phase[q].ntile > 0)) fleft += p.phase_flops[q];
+      }
       host_out[0] = fs;
       host_out[1] = p.chol_flops;
       host_out[2] = fv;
+      host_out[3] = p.oz_flops;
+      host_out[4] = p.mixed ? fleft : fs;
       return DDELM_OK;
     }
     case 7: {

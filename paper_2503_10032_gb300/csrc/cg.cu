@@ -369,17 +369,23 @@ __device__ void ph_dl_last(const Ctx &c, const double *nu, const double *dnu) {
   }
 }
 
-// block-level partial dot products of columns: red[block][k] = sum x[e][k] y[e][k]
+// block-level partial dot products of columns: red[block][k] = sum x[e][k] y[e][k].
+// Walks the elements e = row*R + k with the same grid stride as the vector
+// updates, so every thread reads only elements it wrote itself (no barrier is
+// needed between an update loop and the dot product that follows it).
 template <int RC>
 __device__ void partial_dot(const Ctx &c, const double *x, const double *y, int slot) {
   __shared__ double sred[CG_WARPS][16];
   double acc[RC];
 #pragma unroll
   for (int k = 0; k < RC; ++k) acc[k] = 0.0;
-  for (int p = gthread(); p < c.n_dl; p += nthreads()) {
+  const int R = c.R;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+    const double v = ldg_cg(x + e) * ldg_cg(y + e);
+    const int col = e % R;
 #pragma unroll
     for (int k = 0; k < RC; ++k)
-      if (k < c.R) acc[k] = fma(ldg_cg(x + (long long)p * c.R + k), ldg_cg(y + (long long)p * c.R + k), acc[k]);
+      if (k == col) acc[k] += v;
   }
   warp_sum<RC>(acc);
   if ((threadIdx.x & 31) == 0)

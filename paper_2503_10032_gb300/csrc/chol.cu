@@ -5,7 +5,8 @@
 // Cholesky pass of the shifted CholeskyQR3 factorisation of [K; eps I]:
 //   mode 1 (first pass): eps^2 = eps_rel^2 tr(G)/M is the ridge of the local
 //     least-squares problem; the diagonal additionally gets the stabilising
-//     shift s = 11 ((m+M) M + M (M+1)) u tr(G + eps^2 I), u = 2^-53;
+//     shift s = shift_rel tr(G + eps^2 I) (shift_rel = 11 ((m+M) M + M (M+1)) u,
+//     u = 2^-53, raised to cover the slice truncation of a tensor-core Gram);
 //     Z = eps R^{-1} is the ridge block of the first Q.
 //   mode 0: plain factorisation.
 // A pivot that is not positive marks the matrix in the status array; the
@@ -41,8 +42,7 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
       double tr = 0.0;
       for (int k = 0; k < nw; ++k) tr += red[k];
       const double eps2 = cd.eps_rel * cd.eps_rel * tr / double(M);
-      const double u = 1.1102230246251565e-16;
-      const double sh_ = 11.0 * (double(cd.m + M) * M + double(M) * (M + 1)) * u * (tr + M * eps2);
+      const double sh_ = cd.shift_rel * (tr + M * eps2);
       s_eps2 = eps2;
       s_piv = eps2 + sh_;
     }

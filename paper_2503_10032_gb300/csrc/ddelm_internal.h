@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ddelm.h"
+#include "ozaki.h"
 
 namespace ddelm {
 
@@ -70,7 +71,7 @@ struct GemmDesc {
   int lda, ldb, ldc;
   int ta, tb;  // 1: operand stored transposed
   int flags;   // GEMM_B_UPPER / GEMM_A_UPPER
-  int pad;
+  int syrk;    // 1: only the upper tiles of C are needed (C symmetric)
   double alpha, beta;
 };
 enum { GEMM_B_UPPER = 1, GEMM_A_UPPER = 2 };
@@ -87,6 +88,7 @@ struct CholDesc {
   int mode;     // 0 plain, 1 ridge + shift (first pass), 2 plain + explicit I - ...
   int status;   // index into the status array
   double eps_rel;
+  double shift_rel;  // mode 1: shift s = shift_rel * tr(G + eps^2 I)
 };
 
 // ---------------------------------------------------------------- plan
@@ -143,10 +145,21 @@ struct Plan {
   ddelm_options opt{};
   // chol phases
   CholPhase chol_pass[3]{}, chol_coarse{};
+  // tensor-core emulation of the setup GEMMs (precision MIXED)
+  bool mixed = false;
+  std::vector<SliceDesc> sdesc;
+  std::vector<OzDesc> odesc;
+  std::vector<OzTile> otile;
+  std::vector<OzPhase> oz_phase;  // parallel to setup_gemm; ntile == 0: FP64 engine
+  size_t off_sdesc = 0, off_odesc = 0, off_otile = 0, off_tmaps = 0, off_slices = 0;
+  size_t bytes_slices = 0;
+  double oz_flops = 0.0;          // BF16 tensor flops of one setup
   std::string err;
 };
 
 int build_plan(const ddelm_problem *prob, Plan &plan);
+int build_mixed(Plan &plan, long long &dbl_cursor);
+int encode_tensor_maps(const Plan &plan, void *ws, std::vector<unsigned char> &maps);
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_features(const Plan &p, void *ws, cudaStream_t s);

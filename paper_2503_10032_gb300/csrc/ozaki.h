@@ -1,0 +1,53 @@
+// Tables of the tensor-core (BF16 slice) emulation of FP64 GEMMs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ddelm {
+
+struct Plan;
+
+// One operand seen as an R x K matrix with K the contraction index:
+// element (r, k) = trans ? X[k*ld + r] : X[r*ld + k].  Its S slices are written
+// as [S][Rpad][Kpad] BF16 (K contiguous, zero padded) and its row scales as R
+// powers of two.
+struct SliceDesc {
+  long long x;      // dbase offset of the FP64 source
+  long long out;    // element offset of the slices in the slice region
+  long long scale;  // dbase offset of the R row scales
+  int ld, trans;
+  int R, K, Rpad, Kpad;
+  int S, pad;
+};
+
+// C = alpha * op(A) op(B) + beta * C, m x n, with op(A) = slices sa (rows i) and
+// op(B)^T = slices sb (rows j)
+struct OzDesc {
+  long long c, scaleA, scaleB;
+  int m, n, ldc;
+  int S, kc, Kpad;
+  int RpadA, RpadB;
+  int tmapA, tmapB;
+  double alpha, beta;
+};
+
+struct OzTile {
+  int desc, tm, tn, pad;
+};
+
+struct OzPhase {
+  int slice0, nslice;    // SliceDesc range
+  int desc0, ndesc;      // OzDesc range
+  int tile0, ntile;      // OzTile range
+  int max_rpad, max_kpad;
+};
+
+// Slice levels kept per setup GEMM phase (6 bits each): the first-pass Gram
+// only has to be accurate to well below the stabilising shift; every other
+// GEMM is kept at FP64 accuracy (9 levels, 54 bits).
+inline int oz_levels_for_phase(int q) { return q == 0 ? 6 : 9; }
+
+cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
+cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
+
+}  // namespace ddelm

@@ -1,0 +1,164 @@
+// Plan of the tensor-core (BF16 slice) emulation of the setup GEMMs and the
+// TMA tensor maps of the slice buffers.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "ddelm_internal.h"
+
+namespace ddelm {
+
+namespace {
+constexpr int OZ_BM = 128, OZ_BK = 64, OZ_KC = 1024;
+long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
+}  // namespace
+
+int build_mixed(Plan &P, long long &cur) {
+  auto take = [&](long long n) {
+    long long off = cur;
+    cur += (std::max(n, 1LL) + 31) / 32 * 32;
+    return off;
+  };
+  // scale scratch: sized for the largest phase
+  long long max_scales = 0;
+  size_t max_slices = 0;
+  const size_t n_setup = 11;  // phases 0..10: factorisation and local operators
+  P.oz_phase.assign(P.setup_gemm.size(), OzPhase{0, 0, 0, 0, 0, 0, 0, 0});
+  struct Key {
+    long long x;
+    int ld, trans, R, K;
+    bool operator<(const Key &o) const {
+      return std::tie(x, ld, trans, R, K) < std::tie(o.x, o.ld, o.trans, o.R, o.K);
+    }
+  };
+  std::vector<std::pair<int, long long>> scale_fix;  // (slice desc, relative scale offset)
+  long long scale_base = 0;
+  std::vector<int> phase_slices_begin;
+  for (size_t q = 0; q < n_setup && q < P.setup_gemm.size(); ++q) {
+    const GemmPhase &gp = P.setup_gemm[q];
+    OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0};
+    if (gp.ndesc == 0) {
+      P.oz_phase[q] = op;
+      continue;
+    }
+    const int S = oz_levels_for_phase(int(q));
+    std::map<Key, int> seen;
+    long long elem = 0, scl = 0;
+    auto slice_of = [&](long long x, int ld, int trans, int R, int K) {
+      Key k{x, ld, trans, R, K};
+      auto it = seen.find(k);
+      if (it != seen.end()) return it->second;
+      SliceDesc s;
+      std::memset(&s, 0, sizeof(s));
+      s.x = x;
+      s.ld = ld;
+      s.trans = trans;
+      s.R = R;
+      s.K = K;
+      s.Rpad = int(rup(R, OZ_BM));
+      s.Kpad = int(rup(K, OZ_BK));
+      s.S = S;
+      s.out = elem;
+      elem += (long long)S * s.Rpad * s.Kpad;
+      s.scale = scl;  // relative; fixed below
+      scl += rup(R, 32);
+      int idx = int(P.sdesc.size());
+      P.sdesc.push_back(s);
+      seen[k] = idx;
+      op.max_rpad = std::max(op.max_rpad, s.Rpad);
+      op.max_kpad = std::max(op.max_kpad, s.Kpad);
+      return idx;
+    };
+    for (int t = 0; t < gp.ndesc; ++t) {
+      const GemmDesc &d = P.gdesc[gp.desc0 + t];
+      const int sa = slice_of(d.a, d.lda, d.ta, d.m, d.k);
+      const int sb = slice_of(d.b, d.ldb, d.tb ? 0 : 1, d.n, d.k);
+      OzDesc o;
+      std::memset(&o, 0, sizeof(o));
+      o.c = d.c;
+      o.m = d.m;
+      o.n = d.n;
+      o.ldc = d.ldc;
+      o.S = S;
+      o.kc = OZ_KC;
+      o.Kpad = int(rup(d.k, OZ_BK));
+      o.RpadA = P.sdesc[sa].Rpad;
+      o.RpadB = P.sdesc[sb].Rpad;
+      o.tmapA = sa;
+      o.tmapB = sb;
+      o.scaleA = P.sdesc[sa].scale;  // relative for now
+      o.scaleB = P.sdesc[sb].scale;
+      o.alpha = d.alpha;
+      o.beta = d.beta;
+      const int di = int(P.odesc.size());
+      P.odesc.push_back(o);
+      op.ndesc++;
+      const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + OZ_BM - 1) / OZ_BM;
+      for (int x = 0; x < tm; ++x)
+        for (int y = 0; y < tn; ++y) {
+          if (d.syrk && x > y) continue;
+          P.otile.push_back({di, x, y, 0});
+          op.ntile++;
+        }
+      // tensor-core work: every level's pairs over the padded operands
+      double pairs = 0;
+      for (int l = 0; l < S; ++l) pairs += l + 1;
+      P.oz_flops += 2.0 * OZ_BM * OZ_BM * (double)o.Kpad * pairs * (d.syrk ? (tm * (tm + 1) / 2.0) : double(tm) * tn);
+    }
+    op.nslice = int(P.sdesc.size()) - op.slice0;
+    P.oz_phase[q] = op;
+    max_scales = std::max(max_scales, scl);
+    max_slices = std::max(max_slices, (size_t)elem * 2);
+  }
+  scale_base = take(max_scales);
+  for (auto &s : P.sdesc) s.scale += scale_base;
+  for (auto &o : P.odesc) {
+    o.scaleA += scale_base;
+    o.scaleB += scale_base;
+  }
+  P.bytes_slices = rup((long long)max_slices, 1024);
+  return DDELM_OK;
+}
+
+// One 2-D tensor map per slice buffer: [S*Rpad rows][Kpad] BF16, box 64 x 128,
+// 128-byte swizzle (the canonical K-major layout tcgen05 reads).
+int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps) {
+  maps.assign(std::max<size_t>(P.sdesc.size(), 1) * 128, 0);
+  if (P.sdesc.empty()) return DDELM_OK;
+  typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return DDELM_ERR_CUDA;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  char *slices = static_cast<char *>(ws) + P.off_slices;
+  for (size_t i = 0; i < P.sdesc.size(); ++i) {
+    const SliceDesc &s = P.sdesc[i];
+    void *gaddr = slices + s.out * 2;
+    if ((reinterpret_cast<uintptr_t>(gaddr) & 15u) != 0) return DDELM_ERR_INVALID_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)s.Kpad, (cuuint64_t)s.S * (cuuint64_t)s.Rpad};
+    cuuint64_t strides[1] = {(cuuint64_t)s.Kpad * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMap m;
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, gaddr, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return DDELM_ERR_CUDA;
+    std::memcpy(maps.data() + i * 128, &m, 128);
+  }
+  return DDELM_OK;
+}
+
+}  // namespace ddelm

@@ -1,0 +1,450 @@
+// FP64-accurate GEMM on the 5th-generation tensor cores (tcgen05, BF16 inputs,
+// FP32 accumulation in TMEM) by exact splitting into 6-bit integer slices.
+//
+//   op(A)[i][k] = sigma_i  sum_p a_p[i][k] 64^{-(p+1)},  |a_0| <= 64, |a_p| <= 32
+//   op(B)[k][j] = tau_j    sum_q b_q[j][k] 64^{-(q+1)}
+//   C = alpha sigma_i tau_j sum_{l <= S-1} 64^{-(l+2)} L_l + beta C,
+//   L_l = sum_{p+q=l} sum_k a_p[i][k] b_q[j][k].
+//
+// sigma_i, tau_j are powers of two (row / column maxima), so the slices are
+// small integers, exact in BF16; every partial sum of a level over a k-chunk
+// of at most 1024 is an integer below 2^24, hence exact in the FP32 TMEM
+// accumulator whatever the order of accumulation.  Each level is read out of
+// TMEM once per k-chunk and added in FP64 (levels from the smallest to the
+// largest).  The truncation after S levels is the only approximation.
+//
+// Kernel layout (one CTA per 128x128 output tile, 10 warps):
+//   warp 0     TMA producer: 128x64 BF16 boxes of A and B slices, 128B swizzle,
+//              6-stage shared-memory ring guarded by mbarriers;
+//   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
+//              (M=128, N=128, K=16, both operands K-major), two FP32
+//              accumulators of 128 TMEM columns each, committed per level/chunk;
+//   warps 2-9  epilogue: tcgen05.ld of their lane quadrant and column half,
+//              FP64 accumulation in registers, scaled store of C.
+// Every wait is bounded (2 s); on a timeout the CTA records an error, waits for
+// its own copies and MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "ddelm_internal.h"
+#include "ozaki.h"
+
+namespace ddelm {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 6;
+constexpr int STAGE_BYTES = (BM + BN) * BK * 2;  // 32 KB
+constexpr int OZ_THREADS = 320;
+constexpr unsigned TMEM_COLS = 256;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on timeout or when another role already failed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (unsigned n = 1;; ++n) {
+    if (mbar_test(bar, parity)) return true;
+    if ((n & 63u) == 0u) {
+      if (*(volatile int *)err) return false;
+      if (gtimer() - t0 > 2000000000ull) {
+        atomicExch(err, 3);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// K-major operand tile of 128 rows x 64 BF16 (128 B) with the 128-byte swizzle:
+// 8-row atoms of 1024 B, SBO = 1024 B, LBO unused (1), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                   // LBO (ignored for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;         // SBO
+  d |= (uint64_t)1u << 46;                   // descriptor version
+  d |= (uint64_t)2u << 61;                   // SWIZZLE_128B
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// pairs (p, q) of level l with p, q < S, in a fixed order
+__device__ __forceinline__ int level_pairs(int l, int S, int &p0) {
+  p0 = l - (S - 1) > 0 ? l - (S - 1) : 0;
+  const int p1 = l < S - 1 ? l : S - 1;
+  return p1 - p0 + 1;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    ozaki_gemm_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles,
+                      const CUtensorMap *__restrict__ maps, double *__restrict__ db, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2],
+      bar_drain;
+  __shared__ uint32_t tmem_base_sh;
+
+  const OzTile tl = tiles[blockIdx.x];
+  const OzDesc d = descs[tl.desc];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = d.S;
+  const int nkb = d.Kpad / BK;                 // 64-wide k blocks
+  const int kcb = d.kc / BK;                   // k blocks per exact chunk
+  const int nchunk = (nkb + kcb - 1) / kcb;
+  const int ngroups = S * nchunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 256);
+    }
+    mbar_init(smem_u32(&bar_drain), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      const CUtensorMap *ma = maps + d.tmapA;
+      const CUtensorMap *mb = maps + d.tmapB;
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
+      int st = 0;
+      uint32_t ph = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int l = S - 1 - g / nchunk, c = g % nchunk;
+        int p0;
+        const int np = level_pairs(l, S, p0);
+        const int kb0 = c * kcb, kb1 = min(nkb, kb0 + kcb);
+        for (int t = 0; t < np && ok; ++t) {
+          const int p = p0 + t, q = l - p;
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (issued >= STAGES && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sb = sa + BM * BK * 2;
+            const uint32_t fb = smem_u32(&bar_full[st]);
+            mbar_expect_tx(fb, STAGE_BYTES);
+            tma_load_2d(sa, ma, kb * BK, p * d.RpadA + tl.tm * BM, fb);
+            tma_load_2d(sb, mb, kb * BK, q * d.RpadB + tl.tn * BN, fb);
+            ++issued;
+            if (++st == STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+      // drain: every stage issued must have landed before the CTA may exit
+      for (int k = 0; k < STAGES && k < issued; ++k) {
+        if (--st < 0) {
+          st = STAGES - 1;
+          ph ^= 1u;
+        }
+        const unsigned long long t0 = gtimer();
+        while (!mbar_test(smem_u32(&bar_full[st]), ph)) {
+          if (gtimer() - t0 > 2000000000ull) {
+            atomicExch(err, 4);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int b = g & 1;
+        if (g >= 2 && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((g >> 1) - 1) & 1u, err)) break;
+        tc_fence_after();
+        const int l = S - 1 - g / nchunk, c = g % nchunk;
+        int p0;
+        const int np = level_pairs(l, S, p0);
+        const int kb0 = c * kcb, kb1 = min(nkb, kb0 + kcb);
+        const uint32_t dacc = tmem + (uint32_t)(b * BN);
+        uint32_t accum = 0;
+        for (int t = 0; t < np && ok; ++t) {
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sb = sa + BM * BK * 2;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              mma_bf16(dacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), accum);
+              accum = 1;
+            }
+            mma_commit(smem_u32(&bar_empty[st]));
+            if (++st == STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+        if (ok) mma_commit(smem_u32(&bar_acc_full[b]));
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(smem_u32(&bar_drain));
+      const unsigned long long t0 = gtimer();
+      while (!mbar_test(smem_u32(&bar_drain), 0)) {
+        if (gtimer() - t0 > 2000000000ull) {
+          atomicExch(err, 5);
+          break;
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9
+    const int ew = warp - 2;                  // 0..7
+    const int quad = warp & 3;                // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;                 // column half
+    const int row = quad * 32 + lane;
+    double acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+    bool ok = true;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      if (!mbar_wait(smem_u32(&bar_acc_full[b]), (g >> 1) & 1u, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int l = S - 1 - g / nchunk;
+      const double scale = ldexp(1.0, -6 * (l + 2));
+      const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + half * 64);
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tmem_ld16(ta + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] = fma(scale, (double)v[j], acc[c0 + j]);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bar_acc_empty[b]));
+    }
+    if (ok) {
+      const int gi = tl.tm * BM + row;
+      if (gi < d.m) {
+        const double si = db[d.scaleA + gi] * d.alpha;
+        double *crow = db + d.c + (long long)gi * d.ldc;
+        const int j0 = tl.tn * BN + half * 64;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int gj = j0 + j;
+          if (gj < d.n) {
+            double v = si * db[d.scaleB + gj] * acc[j];
+            if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
+            crow[gj] = v;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- slicing
+// sigma_r = 2^e with max_k |op(X)[r][k]| = f 2^e, f in [0.5, 1); 1 for a zero row
+__global__ void slice_scale_kernel(const SliceDesc *__restrict__ sd, double *__restrict__ db) {
+  const SliceDesc s = sd[blockIdx.y];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double *X = db + s.x;
+  if (s.trans) {  // element (r, k) = X[k*ld + r]: a thread per row, coalesced over r
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s.R; r += gridDim.x * blockDim.x) {
+      double mx = 0.0;
+      for (int k = 0; k < s.K; ++k) mx = fmax(mx, fabs(X[(long long)k * s.ld + r]));
+      int e = 0;
+      frexp(mx, &e);
+      db[s.scale + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+    }
+  } else {        // element (r, k) = X[r*ld + k]: a warp per row
+    for (int r = blockIdx.x * nw + w; r < s.R; r += gridDim.x * nw) {
+      double mx = 0.0;
+      for (int k = lane; k < s.K; k += 32) mx = fmax(mx, fabs(X[(long long)r * s.ld + k]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) {
+        int e = 0;
+        frexp(mx, &e);
+        db[s.scale + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+      }
+    }
+  }
+}
+
+// slices [S][Rpad][Kpad] BF16, zero padding; a 32 x 64 tile per block
+__global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__restrict__ sd,
+                                                          const double *__restrict__ db,
+                                                          __nv_bfloat16 *__restrict__ slices) {
+  __shared__ double tile[32][65];
+  const SliceDesc s = sd[blockIdx.z];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (r0 >= s.Rpad || k0 >= s.Kpad) return;
+  const double *X = db + s.x;
+  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+    int rr, kk;
+    if (s.trans) {  // read along r
+      rr = e % 32;
+      kk = e / 32;
+    } else {        // read along k
+      rr = e / 64;
+      kk = e % 64;
+    }
+    const int r = r0 + rr, k = k0 + kk;
+    double v = 0.0;
+    if (r < s.R && k < s.K) v = s.trans ? X[(long long)k * s.ld + r] : X[(long long)r * s.ld + k];
+    tile[rr][kk] = v;
+  }
+  __syncthreads();
+  __nv_bfloat16 *out = slices + s.out;
+  const long long plane = (long long)s.Rpad * s.Kpad;
+  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+    const int rr = e / 64, kk = e % 64;
+    const int r = r0 + rr, k = k0 + kk;
+    double x = 0.0;
+    if (r < s.R) x = tile[rr][kk] / db[s.scale + r];
+    const long long o = (long long)r * s.Kpad + k;
+    for (int p = 0; p < s.S; ++p) {
+      x *= 64.0;
+      const double a = rint(x);
+      x -= a;
+      out[p * plane + o] = __float2bfloat16_rn((float)a);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s) {
+  if (ph.ntile == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  const SliceDesc *sd = reinterpret_cast<const SliceDesc *>(base + p.off_sdesc) + ph.slice0;
+  __nv_bfloat16 *slices = reinterpret_cast<__nv_bfloat16 *>(base + p.off_slices);
+  slice_scale_kernel<<<dim3(8, ph.nslice), 256, 0, s>>>(sd, db);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  slice_write_kernel<<<dim3(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice), 256, 0, s>>>(sd, db, slices);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s) {
+  if (ph.ntile == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  int *err = reinterpret_cast<int *>(db + p.o_status + 2 * p.n_sub + 32);
+  const OzDesc *od = reinterpret_cast<const OzDesc *>(base + p.off_odesc);
+  const OzTile *ot = reinterpret_cast<const OzTile *>(base + p.off_otile) + ph.tile0;
+  const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(base + p.off_tmaps);
+  const size_t smem = STAGES * STAGE_BYTES + 1024;
+  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ozaki_gemm_kernel<<<ph.ntile, OZ_THREADS, smem, s>>>(od, ot, maps, db, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ddelm

@@ -317,7 +317,6 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     d.oVb = c.Vb;
   }
   (void)setup_scratch_begin;
-  P.n_dbl = cur;
 
   // ---- special rows
   for (int i = 0; i < n_sub; ++i) {
@@ -505,6 +504,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     d.ta = ta;
     d.tb = tb;
     d.flags = flags;
+    d.syrk = upper_tiles ? 1 : 0;
     d.alpha = alpha;
     d.beta = beta;
     int di = int(P.gdesc.size());
@@ -728,6 +728,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         c.mode = pass == 0 ? 1 : 0;
         c.status = 2 * i + t;
         c.eps_rel = o.eps_rel;
+        // shifted CholeskyQR: s = 11 ((m+M) M + M (M+1)) u tr covers FP64 rounding of the
+        // Gram; with the tensor-core Gram the shift also covers its slice truncation
+        const double u = 1.1102230246251565e-16;
+        c.shift_rel = 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) * u;
+        if (o.precision == DDELM_PREC_MIXED)
+          c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -oz_levels_for_phase(0)));
         P.cdesc.push_back(c);
       }
     }
@@ -748,6 +754,16 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   }
   P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
   for (const auto &c : P.cdesc) P.chol_flops += 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
+
+  // ---- tensor-core emulation tables (precision MIXED)
+  if (o.precision == DDELM_PREC_MIXED) {
+    P.mixed = true;
+    if (build_mixed(P, cur) != DDELM_OK) {
+      const std::string e = P.err.empty() ? std::string("mixed plan") : P.err;
+      return fail(e.c_str());
+    }
+  }
+  P.n_dbl = cur;
 
   // ---- bounds of every access the kernels make (an error here, not a fault there)
   {
@@ -803,6 +819,27 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         const int s = I[P.o_dl_own + 4 * p + 2 * o], a = I[P.o_dl_own + 4 * p + 2 * o + 1];
         if (s < 0 || s >= n_sub || a < 0 || a >= P.subs[s].nDl) return fail("internal: Delta owner map");
       }
+    for (const auto &s : P.sdesc) {
+      const long long len = s.trans ? (long long)(s.K - 1) * s.ld + s.R : (long long)(s.R - 1) * s.ld + s.K;
+      if (!in(s.x, len) || !in(s.scale, s.R)) return fail("internal: slice source bounds");
+      if ((s.out + (long long)s.S * s.Rpad * s.Kpad) * 2 > (long long)P.bytes_slices)
+        return fail("internal: slice buffer bounds");
+      if (s.Rpad % 128 || s.Kpad % 64 || s.Rpad < s.R || s.Kpad < s.K) return fail("internal: slice padding");
+    }
+    for (const auto &od : P.odesc) {
+      if (!in(od.c, (long long)(od.m - 1) * od.ldc + od.n)) return fail("internal: tensor-core GEMM output bounds");
+      if (od.tmapA < 0 || od.tmapA >= (int)P.sdesc.size() || od.tmapB < 0 || od.tmapB >= (int)P.sdesc.size())
+        return fail("internal: tensor map index");
+      if (od.RpadA != P.sdesc[od.tmapA].Rpad || od.RpadB != P.sdesc[od.tmapB].Rpad ||
+          od.Kpad != P.sdesc[od.tmapA].Kpad || od.Kpad != P.sdesc[od.tmapB].Kpad || od.S > P.sdesc[od.tmapA].S ||
+          od.S > P.sdesc[od.tmapB].S || od.kc % 64 || od.kc > 1024)
+        return fail("internal: tensor-core GEMM shape");
+    }
+    for (const auto &t : P.otile) {
+      if (t.desc < 0 || t.desc >= (int)P.odesc.size()) return fail("internal: tensor-core tile");
+      const OzDesc &od = P.odesc[t.desc];
+      if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * 128 > od.RpadB) return fail("internal: tensor-core tile box");
+    }
     const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;
     if (!in(P.o_cg, cg_need) || !in(P.o_loc, 9LL * sum_nG * R) || !in(P.o_status, 4LL * n_sub + 64))
       return fail("internal: CG region bounds");
@@ -826,9 +863,19 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   off = al(off + std::max<size_t>(P.cdesc.size(), 1) * sizeof(CholDesc));
   P.off_ints = off;
   off = al(off + std::max<size_t>(P.ints.size(), 1) * sizeof(int));
+  P.off_sdesc = off;
+  off = al(off + std::max<size_t>(P.sdesc.size(), 1) * sizeof(SliceDesc));
+  P.off_odesc = off;
+  off = al(off + std::max<size_t>(P.odesc.size(), 1) * sizeof(OzDesc));
+  P.off_otile = off;
+  off = al(off + std::max<size_t>(P.otile.size(), 1) * sizeof(OzTile));
+  P.off_tmaps = off;
+  off = al(off + std::max<size_t>(P.sdesc.size(), 1) * 128);
   P.bytes_tables = off;
   P.off_dbl = off;
-  P.bytes_total = off + (size_t)P.n_dbl * sizeof(double);
+  off = al(off + (size_t)P.n_dbl * sizeof(double));
+  P.off_slices = off;
+  P.bytes_total = off + P.bytes_slices;
   P.sz.workspace_bytes = P.bytes_total;
   P.sz.upload_bytes = P.bytes_tables + sizeof(double) * (size_t)(3 * sumM + 2 * sumI) +
                       (pr.op == DDELM_OP_DIFFUSION ? sizeof(double) * (size_t)(3 * sumI) : 0);

@@ -65,7 +65,7 @@ class ddelm_solve_info(ctypes.Structure):
 EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm_backward",
            "ddelm_inspect", "ddelm_profile", "ddelm_destroy", "ddelm_status_string")
 DDELM_PROF_CLASSES = 8
-PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other")
+PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other", "slicing", "tc_gemm")
 
 
 def load_library(path: str = LIB_PATH):
