@@ -18,15 +18,19 @@ namespace ddelm {
 namespace {
 
 constexpr int CT = 512;
+constexpr int NB = 16;   // panel rows
 
+// Blocked right-looking upper Cholesky G = R^T R in place (upper triangle), then
+// V = R^{-1} by blocked back substitution.  The panel (NB rows of the trailing
+// matrix) lives in shared memory; the trailing update is a register-tiled
+// SYRK (4x4 tiles per thread), so G is read and written once per panel.
 __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict__ descs,
                                                       double *__restrict__ db, int *__restrict__ status) {
-  extern __shared__ double sh[];  // row buffer [M] + reduction scratch
+  extern __shared__ double P[];  // NB x M panel
   const CholDesc cd = descs[blockIdx.x];
   const int M = cd.M;
   double *G = db + cd.g;
   double *V = db + cd.v;
-  double *row = sh;
   __shared__ double red[CT / 32];
   __shared__ double s_eps2, s_piv;
   __shared__ int s_bad;
@@ -42,52 +46,128 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
       double tr = 0.0;
       for (int k = 0; k < nw; ++k) tr += red[k];
       const double eps2 = cd.eps_rel * cd.eps_rel * tr / double(M);
-      const double sh_ = cd.shift_rel * (tr + M * eps2);
       s_eps2 = eps2;
-      s_piv = eps2 + sh_;
+      s_piv = eps2 + cd.shift_rel * (tr + M * eps2);
     }
     __syncthreads();
     for (int j = tid; j < M; j += CT) G[(long long)j * M + j] += s_piv;
     __syncthreads();
   }
-  // upper Cholesky in place: G = R^T R
-  for (int k = 0; k < M; ++k) {
-    if (tid == 0) {
-      double piv = G[(long long)k * M + k];
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        s_bad = 1;
-        piv = 1.0;
+  // ---------------- factorisation
+  for (int k0 = 0; k0 < M; k0 += NB) {
+    const int nb = min(NB, M - k0), W = M - k0;  // panel: rows k0..k0+nb, columns k0..M
+    for (int e = tid; e < nb * W; e += CT) {
+      const int r = e / W, c = e % W;
+      P[r * W + c] = G[(long long)(k0 + r) * M + k0 + c];
+    }
+    __syncthreads();
+    for (int t = 0; t < nb; ++t) {  // unblocked elimination inside the panel
+      if (tid == 0) {
+        double piv = P[t * W + t];
+        if (!(piv > 0.0) || !isfinite(piv)) {
+          s_bad = 1;
+          piv = 1.0;
+        }
+        s_piv = sqrt(piv);
       }
-      const double r = sqrt(piv);
-      G[(long long)k * M + k] = r;
-      s_piv = r;
+      __syncthreads();
+      const double r = s_piv;
+      for (int c = t + tid; c < W; c += CT) P[t * W + c] = c == t ? r : P[t * W + c] / r;
+      __syncthreads();
+      for (int e = tid; e < (nb - t - 1) * W; e += CT) {
+        const int u = t + 1 + e / W, c = e % W;
+        if (c >= u) P[u * W + c] = fma(-P[t * W + u], P[t * W + c], P[u * W + c]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const double r = s_piv;
-    for (int j = k + 1 + tid; j < M; j += CT) {
-      const double v = G[(long long)k * M + j] / r;
-      G[(long long)k * M + j] = v;
-      row[j] = v;
+    for (int e = tid; e < nb * W; e += CT) {
+      const int r = e / W, c = e % W;
+      if (c >= r) G[(long long)(k0 + r) * M + k0 + c] = P[r * W + c];
     }
-    __syncthreads();
-    for (int i = k + 1 + wid; i < M; i += nw) {
-      const double gki = row[i];
-      double *gi = G + (long long)i * M;
-      for (int j = i + lane; j < M; j += 32) gi[j] = fma(-gki, row[j], gi[j]);
+    // trailing update of the upper triangle: G[i][j] -= sum_t P[t][i] P[t][j], i <= j, i, j >= k0 + nb
+    const int T0 = k0 + nb, nt = M - T0;
+    if (nt > 0) {
+      const int nbt = (nt + 3) / 4;                  // 4x4 tiles along each side
+      const int ntiles = nbt * (nbt + 1) / 2;        // upper-triangular tile pairs
+      for (int q = tid; q < ntiles; q += CT) {
+        // map q -> (bi, bj) with bi <= bj
+        int bi = 0, rem = q;
+        while (rem >= nbt - bi) {
+          rem -= nbt - bi;
+          ++bi;
+        }
+        const int bj = bi + rem;
+        const int i0 = T0 + 4 * bi, j0 = T0 + 4 * bj;
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int t = 0; t < nb; ++t) {
+          double pa[4], pb[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pa[a] = (i0 + a < M) ? P[t * W + (i0 + a - k0)] : 0.0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) pb[b] = (j0 + b < M) ? P[t * W + (j0 + b - k0)] : 0.0;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(pa[a], pb[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = i0 + a;
+          if (i >= M) continue;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int j = j0 + b;
+            if (j < M && j >= i) G[(long long)i * M + j] -= acc[a][b];
+          }
+        }
+      }
     }
     __syncthreads();
   }
-  // V = R^{-1} (upper; zeros below the diagonal), rows from the bottom
+  // ---------------- V = R^{-1}: block rows from the bottom
+  // rows i0..i1 of V: V[i][j] = (delta_ij - sum_{k>i} R[i][k] V[k][j]) / R[i][i], j >= i
   for (long long e = tid; e < (long long)M * M; e += CT) V[e] = 0.0;
   __syncthreads();
-  for (int i = M - 1; i >= 0; --i) {
-    for (int j = i + tid; j < M; j += CT) row[j] = G[(long long)i * M + j];
+  const int nblk = (M + NB - 1) / NB;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int i0 = b * NB, nb = min(NB, M - i0), i1 = i0 + nb, W = M - i0;
+    for (int e = tid; e < nb * W; e += CT) {  // R[i0..i1][i0..M] into the panel
+      const int r = e / W, c = e % W;
+      P[r * W + c] = G[(long long)(i0 + r) * M + i0 + c];
+    }
     __syncthreads();
-    const double rii = row[i];
-    for (int j = i + tid; j < M; j += CT) {
-      double acc = (j == i) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= j; ++k) acc = fma(-row[k], V[(long long)k * M + j], acc);
-      V[(long long)i * M + j] = acc / rii;
+    // contribution of the rows below the block: a thread per column j
+    for (int j = i0 + tid; j < M; j += CT) {
+      double acc[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) acc[r] = 0.0;
+      for (int k = i1; k <= j; ++k) {
+        const double vk = V[(long long)k * M + j];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k - i0)], vk, acc[r]);
+      }
+      // back substitution inside the block, rows i1-1 .. i0
+      double x[NB];
+#pragma unroll
+      for (int r = NB - 1; r >= 0; --r) {
+        if (r >= nb) {
+          x[r] = 0.0;
+          continue;
+        }
+        const int i = i0 + r;
+        double v = (j == i ? 1.0 : 0.0) - acc[r];
+#pragma unroll
+        for (int u = r + 1; u < NB; ++u)
+          if (u < nb) v = fma(-P[r * W + (u)], x[u], v);
+        x[r] = (j >= i) ? v / P[r * W + r] : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < nb && j >= i0 + r) V[(long long)(i0 + r) * M + j] = x[r];
     }
     __syncthreads();
   }
@@ -147,7 +227,11 @@ cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cuda
   int *status = reinterpret_cast<int *>(db + p.o_status);
   int maxM = 0;
   for (int k = 0; k < ph.ndesc; ++k) maxM = p.cdesc[ph.desc0 + k].M > maxM ? p.cdesc[ph.desc0 + k].M : maxM;
-  const size_t smem = sizeof(double) * (size_t)(maxM + 1);
+  const size_t smem = sizeof(double) * (size_t)NB * (size_t)maxM;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
   return cudaGetLastError();
 }

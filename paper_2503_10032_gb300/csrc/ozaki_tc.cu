@@ -349,34 +349,71 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- slicing
-// sigma_r = 2^e with max_k |op(X)[r][k]| = f 2^e, f in [0.5, 1); 1 for a zero row
-__global__ void slice_scale_kernel(const SliceDesc *__restrict__ sd, double *__restrict__ db) {
+// Integer arithmetic only (the FP64 pipe is the scarce unit of this GPU):
+// sigma_r = 2^(E_max - 1022) from the largest biased exponent E_max of the
+// row, so that |op(X)[r][k]| / sigma_r < 1; then X = round(x / sigma * 64^S)
+// is an exact shift of the 53-bit mantissa, and the balanced base-64 digits of
+// X are the slices (|a_0| <= 64, |a_p| <= 32).
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// sigma from the largest |x| bit pattern of the row (non-negative doubles
+// order like their bit patterns)
+__device__ __forceinline__ double scale_from_max(unsigned long long mb) {
+  if (mb == 0ull) return 1.0;
+  const int E = int(mb >> 52);                 // 0 for subnormal maxima
+  const int e = (E == 0 ? 1 : E) - 1022;       // sigma = 2^e > max
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__global__ void __launch_bounds__(256) slice_scale_kernel(const SliceDesc *__restrict__ sd,
+                                                          double *__restrict__ db) {
+  __shared__ unsigned long long red[8][33];
   const SliceDesc s = sd[blockIdx.y];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double *X = db + s.x;
-  if (s.trans) {  // element (r, k) = X[k*ld + r]: a thread per row, coalesced over r
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s.R; r += gridDim.x * blockDim.x) {
-      double mx = 0.0;
-      for (int k = 0; k < s.K; ++k) mx = fmax(mx, fabs(X[(long long)k * s.ld + r]));
-      int e = 0;
-      frexp(mx, &e);
-      db[s.scale + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (s.trans) {  // element (r, k) = X[k*ld + r]: 32 rows per block, 8 k-lanes
+    for (int r0 = blockIdx.x * 32; r0 < s.R; r0 += gridDim.x * 32) {
+      const int r = r0 + tx;
+      unsigned long long mb = 0ull;
+      if (r < s.R)
+        for (int k = ty; k < s.K; k += 8) mb = max(mb, abs_bits(X[(long long)k * s.ld + r]));
+      red[ty][tx] = mb;
+      __syncthreads();
+      if (ty == 0 && r < s.R) {
+        for (int j = 1; j < 8; ++j) mb = max(mb, red[j][tx]);
+        db[s.scale + r] = scale_from_max(mb);
+      }
+      __syncthreads();
     }
   } else {        // element (r, k) = X[r*ld + k]: a warp per row
-    for (int r = blockIdx.x * nw + w; r < s.R; r += gridDim.x * nw) {
-      double mx = 0.0;
-      for (int k = lane; k < s.K; k += 32) mx = fmax(mx, fabs(X[(long long)r * s.ld + k]));
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) {
-        int e = 0;
-        frexp(mx, &e);
-        db[s.scale + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
-      }
+    for (int r = blockIdx.x * 8 + ty; r < s.R; r += gridDim.x * 8) {
+      unsigned long long mb = 0ull;
+      for (int k = tx; k < s.K; k += 32) mb = max(mb, abs_bits(X[(long long)r * s.ld + k]));
+      for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+      if (tx == 0) db[s.scale + r] = scale_from_max(mb);
     }
   }
 }
 
-// slices [S][Rpad][Kpad] BF16, zero padding; a 32 x 64 tile per block
+// x / 2^e * 64^S rounded to an integer (|result| <= 64^S)
+__device__ __forceinline__ long long fixed_point(double x, int e, int S) {
+  const long long bits = __double_as_longlong(x);
+  const int E = int((bits >> 52) & 0x7FF);
+  if (E == 0) return 0;  // zero or subnormal: below every kept digit
+  const long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  const int sh = E - 1075 - e + 6 * S;
+  long long v;
+  if (sh >= 0) v = m << sh;
+  else if (sh > -63) v = (m + (1ll << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return bits < 0 ? -v : v;
+}
+
+// slices [S][Rpad][Kpad] BF16, zero padding; a 32 x 64 tile per block, eight
+// consecutive k per thread, one 16-byte store per slice
 __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__restrict__ sd,
                                                           const double *__restrict__ db,
                                                           __nv_bfloat16 *__restrict__ slices) {
@@ -385,35 +422,42 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   if (r0 >= s.Rpad || k0 >= s.Kpad) return;
   const double *X = db + s.x;
-  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-    int rr, kk;
-    if (s.trans) {  // read along r
-      rr = e % 32;
-      kk = e / 32;
-    } else {        // read along k
-      rr = e / 64;
-      kk = e % 64;
+  if (s.trans) {  // coalesced along r, transposed through shared memory
+    const int rr = threadIdx.x & 31;
+    for (int kk = threadIdx.x >> 5; kk < 64; kk += 8) {
+      const int r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < s.R && k < s.K) ? X[(long long)k * s.ld + r] : 0.0;
     }
-    const int r = r0 + rr, k = k0 + kk;
-    double v = 0.0;
-    if (r < s.R && k < s.K) v = s.trans ? X[(long long)k * s.ld + r] : X[(long long)r * s.ld + k];
-    tile[rr][kk] = v;
+  } else {
+    const int kk = threadIdx.x & 63;
+    for (int rr = threadIdx.x >> 6; rr < 32; rr += 4) {
+      const int r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < s.R && k < s.K) ? X[(long long)r * s.ld + k] : 0.0;
+    }
   }
   __syncthreads();
-  __nv_bfloat16 *out = slices + s.out;
+  const int rr = threadIdx.x >> 3, kq = (threadIdx.x & 7) * 8;
+  const int r = r0 + rr;
+  int e = 0;
+  if (r < s.R) {
+    const long long sb = __double_as_longlong(db[s.scale + r]);
+    e = int((sb >> 52) & 0x7FF) - 1023;
+  }
+  long long v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = (r < s.R) ? fixed_point(tile[rr][kq + j], e, s.S) : 0;
+  __nv_bfloat16 *out = slices + s.out + (long long)r * s.Kpad + k0 + kq;
   const long long plane = (long long)s.Rpad * s.Kpad;
-  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-    const int rr = e / 64, kk = e % 64;
-    const int r = r0 + rr, k = k0 + kk;
-    double x = 0.0;
-    if (r < s.R) x = tile[rr][kk] / db[s.scale + r];
-    const long long o = (long long)r * s.Kpad + k;
-    for (int p = 0; p < s.S; ++p) {
-      x *= 64.0;
-      const double a = rint(x);
-      x -= a;
-      out[p * plane + o] = __float2bfloat16_rn((float)a);
+  for (int p = 0; p < s.S; ++p) {
+    const int shift = 6 * (s.S - 1 - p);
+    __align__(16) __nv_bfloat16 dig[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long a = shift > 0 ? (v[j] + (1ll << (shift - 1))) >> shift : v[j];
+      v[j] -= a << shift;
+      dig[j] = __float2bfloat16_rn((float)a);
     }
+    *reinterpret_cast<uint4 *>(out + p * plane) = *reinterpret_cast<const uint4 *>(dig);
   }
 }
 
@@ -425,7 +469,7 @@ cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
   const SliceDesc *sd = reinterpret_cast<const SliceDesc *>(base + p.off_sdesc) + ph.slice0;
   __nv_bfloat16 *slices = reinterpret_cast<__nv_bfloat16 *>(base + p.off_slices);
-  slice_scale_kernel<<<dim3(8, ph.nslice), 256, 0, s>>>(sd, db);
+  slice_scale_kernel<<<dim3(16, ph.nslice), 256, 0, s>>>(sd, db);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   slice_write_kernel<<<dim3(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice), 256, 0, s>>>(sd, db, slices);
