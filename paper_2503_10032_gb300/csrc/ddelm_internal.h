@@ -95,6 +95,7 @@ struct CholDesc {
 struct GemmPhase {
   int desc0, ndesc;  // into the descriptor table
   int tile0, ntile;  // into the tile table
+  int skinny;        // 1: every n <= 16; tiles are 32-row blocks (tn = 0)
 };
 
 struct CholPhase {

@@ -107,6 +107,73 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmDesc *__restrict
   }
 }
 
+// n <= 16 columns (right-hand sides): a block per 32 output rows, the n
+// accumulators of a row in registers.  op(A) transposed: a thread per row and
+// 8 k-lanes (coalesced along the rows); otherwise a warp per row.
+__global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__restrict__ descs,
+                                                          const GemmTile *__restrict__ tiles,
+                                                          double *__restrict__ db) {
+  __shared__ double red[8][32][17];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmDesc d = descs[tl.desc];
+  const double *A = db + d.a;
+  const double *B = db + d.b;
+  double *C = db + d.c;
+  const int n = d.n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int m0 = tl.tm * 32;
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  if (d.ta) {
+    const int i = m0 + tx;
+    if (i < d.m)
+      for (int k = ty; k < d.k; k += 8) {
+        const double a = A[(long long)k * d.lda + i];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < n) acc[c] = fma(a, d.tb ? B[(long long)c * d.ldb + k] : B[(long long)k * d.ldb + c], acc[c]);
+      }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) red[ty][tx][c] = acc[c];
+    __syncthreads();
+    if (ty == 0 && i < d.m) {
+      for (int c = 0; c < n; ++c) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w][tx][c];
+        double *cp = C + (long long)i * d.ldc + c;
+        double v = d.alpha * s;
+        if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+        *cp = v;
+      }
+    }
+  } else {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = m0 + r;
+      if (i >= d.m) break;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+      const double *arow = A + (long long)i * d.lda;
+      for (int k = tx; k < d.k; k += 32) {
+        const double a = arow[k];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < n) acc[c] = fma(a, d.tb ? B[(long long)c * d.ldb + k] : B[(long long)k * d.ldb + c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+      if (tx == 0)
+        for (int c = 0; c < n; ++c) {
+          double *cp = C + (long long)i * d.ldc + c;
+          double v = d.alpha * acc[c];
+          if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+          *cp = v;
+        }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cudaStream_t s) {
@@ -115,7 +182,10 @@ cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cuda
   const GemmDesc *descs = reinterpret_cast<const GemmDesc *>(base + p.off_gdesc);
   const GemmTile *tiles = reinterpret_cast<const GemmTile *>(base + p.off_gtile) + ph.tile0;
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db);
+  if (ph.skinny)
+    gemm_skinny_kernel<<<ph.ntile, 256, 0, s>>>(descs, tiles, db);
+  else
+    gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db);
   return cudaGetLastError();
 }
 

@@ -479,11 +479,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.n_tasks_c = (int(I.size()) - P.o_tasks_c) / 2;
 
   // ---- GEMM phases
-  auto phase_begin = [&]() {
+  auto phase_begin = [&](int skinny = 0) {
     GemmPhase ph;
     ph.desc0 = int(P.gdesc.size());
     ph.tile0 = int(P.gtile.size());
     ph.ndesc = ph.ntile = 0;
+    ph.skinny = skinny;
     return ph;
   };
   auto add = [&](GemmPhase &ph, long long a, long long b, long long c, int m, int n, int k, int lda,
@@ -516,6 +517,13 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     if (bu && au) f /= 3.0;
     else if (bu || au || upper_tiles) f /= 2.0;
     P.gemm_flops.push_back(f);
+    if (ph.skinny) {
+      for (int x = 0; x < (m + 31) / 32; ++x) {
+        P.gtile.push_back({di, x, 0, 0});
+        ph.ntile++;
+      }
+      return;
+    }
     const int tm = (m + 63) / 64, tn = (n + 63) / 64;
     for (int x = 0; x < tm; ++x)
       for (int y = 0; y < tn; ++y) {
@@ -668,37 +676,37 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     add(e, P.o_Dpp, P.o_C1, P.o_C2, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 0, 0, -1.0, 1.0);
     push(e);
   } else {
-    for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0});
+    for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0, 0});
   }
   // solve phases: 15: T = Q2[IB rows]^T F ; 16: Qtf = V3^T T ; 17: y = V Qtf, p = Q_Gamma Qtf ;
   //               18: a = A_m y ; 19: u_eval = Eval c
   {
-    GemmPhase a = phase_begin();
+    GemmPhase a = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
       add(a, d.oX, d.oF, d.oT, d.M, R, d.nI + d.nB, d.M, R, R, 1, 0, 0, 1.0, 0.0);
     }
     push(a);
-    GemmPhase b = phase_begin();
+    GemmPhase b = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
       add(b, d.oV3, d.oT, d.oQtf, d.M, R, d.M, d.M, R, R, 1, 0, 0, 1.0, 0.0);
     }
     push(b);
-    GemmPhase c = phase_begin();
+    GemmPhase c = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
       add(c, d.oV, d.oQtf, d.oY, d.M, R, d.M, d.M, R, R, 0, 0, GEMM_A_UPPER, 1.0, 0.0);
       add(c, d.oQG, d.oQtf, d.oP, d.nG, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
     }
     push(c);
-    GemmPhase e = phase_begin();
+    GemmPhase e = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
       add(e, d.oA, d.oY, d.oAy, d.nG, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
     }
     push(e);
-    GemmPhase f = phase_begin();
+    GemmPhase f = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
       add(f, d.oEval, d.oC, d.oU, d.nE, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);

@@ -277,6 +277,19 @@ CONFIGS = ("poisson_2x2_m100", "poisson_8x8_m400", "poisson_16x16_uneven",
            "poisson_8x8_fourier", "diffusion_32x32_m1000_r16")
 
 
+def small_uneven_problem(nx=4, ny=3, M_range=(20, 90), seed=13, n_rhs=1, init="paper", scale=8.0):
+    """Small problem with uneven subdomains: neurons, interior points (1.5-3 x M)
+    and points per edge all drawn per subdomain / per edge."""
+    rng = np.random.default_rng(seed)
+    n_sub = nx * ny
+    M = rng.integers(M_range[0], M_range[1] + 1, size=n_sub)
+    nI = np.round(rng.uniform(1.5, 3.0, size=n_sub) * M).astype(np.int64)
+    e = rng.integers(2, 7, size=nx * (ny + 1) + (nx + 1) * ny)
+    sols = [_sin_sin(1, 1), _sin2pix_cos3piy(), _sin_sin(2, 1), _sin_sin(1, 3)][:n_rhs]
+    return make_problem(nx, ny, M, nI, e, scale=scale, init=init, seed=seed + 1, solutions=sols,
+                        n_eval=8, name="small_uneven")
+
+
 def small_problem(nx=2, ny=2, M=12, n_int=40, edge_pts=3, *, seed=7, scale=3.0,
                   init="uniform", n_rhs=1, op=OP_POISSON, n_eval=8):
     """Tiny problems for brute-force checks (any grid, any sizes)."""

@@ -56,3 +56,22 @@ def test_mixed_local_operators_and_solution(D, case):
     assert rc == D.DDELM_OK
     assert _rel(mu.cpu().numpy()[o.n_pi:], ref["mu_delta"]) < tol
     assert _rel(u.cpu().numpy(), ref["u_eval"]) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_subdomains(D, prec):
+    """Per-subdomain neuron counts, collocation counts and edge point counts all differ."""
+    import torch
+    p = inputs.small_uneven_problem(4, 3, n_rhs=2)
+    assert len(set(p.M.tolist())) > 3 and len(set(p.edge_pts.tolist())) > 2
+    ref = odd.solve(p, odd.Options(eps_rel=1e-6))
+    s = D.Solver(p, eps_rel=1e-6, tol=1e-11,
+                 precision=D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED)
+    f = torch.tensor(p.f_int, dtype=torch.float64, device="cuda")
+    g = torch.tensor(p.g_bnd, dtype=torch.float64, device="cuda")
+    c, mu, u, info, rc = s.solve(f, g)
+    torch.cuda.synchronize()
+    assert rc == D.DDELM_OK
+    n_pi = ref["oracle"].n_pi
+    assert _rel(mu.cpu().numpy()[n_pi:], ref["mu_delta"]) < 1e-8
+    assert _rel(u.cpu().numpy(), ref["u_eval"]) < 1e-8
