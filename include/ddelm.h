@@ -182,6 +182,25 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
 #define DDELM_PROF_CLASSES 8
 int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long *launches);
 
+/* Ridge least-squares solve of ONE local ELM system, C = K^+ F (K^+ as in the
+ * readings above, eps^2 = eps_rel^2 |K|_F^2 / M), by the library's shifted
+ * CholeskyQR3 in FP64, for callers that cannot allocate device memory: the
+ * scratch lives in a file-scope static device array of
+ * DDELM_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
+ * library keeps until the process exits.  Inputs d_K [m x M] and d_F [m x R]
+ * (row-major) and the output d_C [M x R] are device buffers owned by the
+ * caller.  Limits: 1 <= M <= 256, 1 <= R <= 16 and
+ * 2 m M + m R + 8 M^2 + 3 M R + 16384 (rounded up) <= DDELM_STATIC_SCRATCH_DOUBLES;
+ * larger sizes return DDELM_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on a device resolves
+ * the array's device address with that device current, so make it before any
+ * stream capture.  All calls share the array (it keeps the last call's
+ * contents): calls that overlap on the GPU race.  Returns after the stream
+ * work has completed.  The paper has no counterpart to this entry point. */
+#define DDELM_STATIC_SCRATCH_DOUBLES 1048576
+int ddelm_local_lstsq_static(const double *d_K, int m, int M, const double *d_F, int R, double eps_rel,
+                             double *d_C, void *stream);
+
 void ddelm_destroy(ddelm_handle *h);
 
 const char *ddelm_status_string(int status);

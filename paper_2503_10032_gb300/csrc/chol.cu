@@ -236,6 +236,17 @@ cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cuda
   return cudaGetLastError();
 }
 
+cudaError_t launch_chol_table(const CholDesc *descs, int n, int maxM, double *db, int *status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * (size_t)NB * (size_t)maxM;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  chol_inv_kernel<<<n, CT, smem, s>>>(descs, db, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s) {
   if (p.n_pi == 0) return cudaSuccess;
   char *base = static_cast<char *>(ws);

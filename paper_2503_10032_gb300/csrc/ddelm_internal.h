@@ -170,6 +170,9 @@ cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s);
 cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,
                               cudaStream_t s);
+cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int ntiles, double *db, int skinny,
+                              cudaStream_t s);
+cudaError_t launch_chol_table(const CholDesc *descs, int n, int maxM, double *db, int *status, cudaStream_t s);
 struct CgArgs {
   double *mu_out;   // [n_pi + n_dl] x R or null
   double *c_out;    // [sum M] x R or null

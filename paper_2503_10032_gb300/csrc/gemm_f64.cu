@@ -189,4 +189,15 @@ cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cuda
   return cudaGetLastError();
 }
 
+// Same kernels on caller-built tables (used by the static-scratch entry point).
+cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int ntiles, double *db, int skinny,
+                              cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (skinny)
+    gemm_skinny_kernel<<<ntiles, 256, 0, s>>>(descs, tiles, db);
+  else
+    gemm_f64_kernel<<<ntiles, NT, 0, s>>>(descs, tiles, db);
+  return cudaGetLastError();
+}
+
 }  // namespace ddelm

@@ -63,7 +63,9 @@ class ddelm_solve_info(ctypes.Structure):
 
 
 EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm_backward",
-           "ddelm_inspect", "ddelm_profile", "ddelm_destroy", "ddelm_status_string")
+           "ddelm_inspect", "ddelm_profile", "ddelm_local_lstsq_static", "ddelm_destroy",
+           "ddelm_status_string")
+DDELM_STATIC_SCRATCH_DOUBLES = 1048576
 DDELM_PROF_CLASSES = 8
 PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other", "slicing", "tc_gemm")
 
@@ -91,6 +93,9 @@ def load_library(path: str = LIB_PATH):
     lib.ddelm_backward.restype = ctypes.c_int
     lib.ddelm_inspect.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
     lib.ddelm_inspect.restype = ctypes.c_int
+    lib.ddelm_local_lstsq_static.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ddelm_local_lstsq_static.restype = ctypes.c_int
     lib.ddelm_destroy.argtypes = [ctypes.c_void_p]
     lib.ddelm_destroy.restype = None
     lib.ddelm_status_string.argtypes = [ctypes.c_int]
@@ -202,6 +207,12 @@ def ddelm_inspect(h, sub: int, which: int, n: int) -> np.ndarray:
     if rc != DDELM_OK:
         raise DDELMError(rc, "ddelm_inspect")
     return out[:n]
+
+
+def ddelm_local_lstsq_static(k_ptr, m, M, f_ptr, R, eps_rel, c_ptr, stream):
+    """C = K^+ F for one local system with scratch in a static device array (no allocation)."""
+    return _lib.ddelm_local_lstsq_static(ctypes.c_void_p(k_ptr), m, M, ctypes.c_void_p(f_ptr), R, eps_rel,
+                                         ctypes.c_void_p(c_ptr), ctypes.c_void_p(stream))
 
 
 def ddelm_destroy(h):
