@@ -18,7 +18,7 @@
  *          [c; mu_Pi] = K~^+ (f~ - B~ mu_Delta), Eq. (coarse_sol_2), and the
  *          network values at caller-given points.
  *   backward (ddelm_backward): the adjoint of solve with respect to the
- *          right-hand-side values (gradients of a loss given dL/dc).
+ *          right-hand-side values (gradients of a loss given dL/dc or dL/du).
  *
  * Conventions shared by every entry point:
  *   - All floating-point data are IEEE double.  Host pointers are read during
@@ -153,12 +153,17 @@ int ddelm_refactor(ddelm_handle *h, void *stream, int *info_sub);
 int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, double *d_c,
                 double *d_mu, double *d_u_eval, ddelm_solve_info *info, void *stream);
 
-/* Adjoint of the last-configured solve map (f, g) -> c, for a cotangent
- * d_grad_c [sum M][n_rhs]: writes d_grad_f [sum n_int][n_rhs] and
- * d_grad_g [n_bnd][n_rhs] (device).  The map is linear in (f, g), so the
- * result is the transpose of ddelm_solve's linear map applied to grad_c. */
-int ddelm_backward(ddelm_handle *h, const double *d_grad_c, double *d_grad_f, double *d_grad_g,
-                   ddelm_solve_info *info, void *stream);
+/* Adjoint of the solve: the map (f, g) -> c of ddelm_solve is linear, and this
+ * call applies its exact transpose.  Given device cotangents d_grad_c
+ * [sum M][n_rhs] (dL/dc, nullable) and d_grad_u [sum n_eval][n_rhs] (dL/du at
+ * the evaluation points, nullable, u = Phi_eval c), writes d_grad_f
+ * [sum n_int][n_rhs] = dL/df and d_grad_g [n_bnd][n_rhs] = dL/dg (device,
+ * nullable).  Reuses the setup's factors: the transposed local products with
+ * V, R3^{-1}, Q_Gamma, A_m and K^+ E_Gamma, the transposed coarse steps, and
+ * one CG on the symmetric S_theta.  info as in ddelm_solve (iterations of
+ * that CG; rel_residual is not computed and reads 0). */
+int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
+                   double *d_grad_g, ddelm_solve_info *info, void *stream);
 
 /* Copies a local block of subdomain `sub` to host memory for inspection
  * (synchronous).  which: 0 K_c^i [m x M], 1 K-bar^i [m x M], 2 A_m^i [nG x M],

@@ -297,9 +297,54 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   return rc;
 }
 
-int ddelm_backward(ddelm_handle *h, const double *, double *, double *, ddelm_solve_info *, void *) {
+int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
+                   double *d_grad_g, ddelm_solve_info *info, void *stream) {
   if (!h) return DDELM_ERR_INVALID_ARG;
-  return DDELM_ERR_UNSUPPORTED;
+  Plan &p = h->plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *db = dbase(h);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (info) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  const auto &G = p.setup_gemm;
+  LAUNCH(PC_OTHER, launch_adjoint_init(p, h->ws, d_grad_c, d_grad_u, s));
+  if (d_grad_u && p.sz.sum_eval > 0) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[20], h->ws, s));
+  LAUNCH(PC_OTHER, launch_copy_c_to_y(p, h->ws, s));
+  CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
+  CgArgs a;
+  a.mu_out = nullptr;
+  a.c_out = nullptr;
+  a.max_iters = p.opt.max_iters;
+  a.tol = p.opt.tol;
+  a.theta = p.opt.theta;
+  a.mode = 1;
+  LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
+  for (int q = 21; q <= 25; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[q], h->ws, s));
+  LAUNCH(PC_OTHER, launch_adjoint_scatter(p, h->ws, d_grad_f, d_grad_g, s));
+  if (info) CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  const long long nd = p.n_dl > 0 ? p.n_dl : 1, np = p.n_pi > 0 ? p.n_pi : 1;
+  double it = 0.0;
+  CK(cudaMemcpy(&it, db + p.o_cg + 12 * nd * p.n_rhs + 14 * np * p.n_rhs + 2048 * 32 - 64, sizeof(double),
+                cudaMemcpyDeviceToHost));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, db + p.o_status + 2 * p.n_sub + 16, sizeof(int), cudaMemcpyDeviceToHost));
+  int rc = herr ? DDELM_ERR_TIMEOUT : DDELM_OK;
+  if (rc == DDELM_OK && int(it) >= p.opt.max_iters) rc = DDELM_ERR_NOT_CONVERGED;
+  if (info) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    info->iterations = int(it);
+    info->refinements = 0;
+    info->rel_residual = 0.0;
+    info->ms_total = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return rc;
 }
 
 int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t out_len) {
@@ -348,7 +393,8 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       if (out_len < 5) return DDELM_ERR_INVALID_ARG;
       double fs = 0.0, fv = 0.0, fleft = 0.0;
       for (size_t q = 0; q < p.phase_flops.size(); ++q) {
-        (q <= 14 ? fs : fv) += p.phase_flops[q];
+        if (q <= 14) fs += p.phase_flops[q];
+        else if (q <= 19) fv += p.phase_flops[q];
         if (q <= 14 && !(p.mixed && q < p.oz_phase.size() && p.oz_phase[q].ntile > 0)) fleft += p.phase_flops[q];
       }
       host_out[0] = fs;

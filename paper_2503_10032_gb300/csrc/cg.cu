@@ -47,6 +47,7 @@ struct Ctx {
   int max_iters;
   double *mu_out, *c_out;
   double *info;  // [0] iterations, [1..16] true residuals, [17..32] |b|
+  int mode;      // 0 forward solve, 1 adjoint
 };
 
 __device__ __forceinline__ double ldg_cg(const double *p) { return __ldcg(p); }
@@ -338,7 +339,7 @@ __device__ void ph_g_lamT(const Ctx &c, const double *w) {
 
 // Δ-row phase: YL = ZL_Delta + Psi_DeltaPi nu^ - Lambda_PiDelta^T Dnu^
 template <int RC>
-__device__ void ph_dl_last(const Ctx &c, const double *nu, const double *dnu) {
+__device__ void ph_dl_last(const Ctx &c, const double *nu, const double *dnu, bool with_z) {
   const int lane = threadIdx.x & 31;
   for (int t = gwarp(); t < c.n_tdl; t += nwarps()) {
     const int s = c.ints[c.o_tdl + 2 * t], dd = c.ints[c.o_tdl + 2 * t + 1];
@@ -364,7 +365,7 @@ __device__ void ph_dl_last(const Ctx &c, const double *nu, const double *dnu) {
       const double *z = slab_row(c, S_ZL, d, a);
 #pragma unroll
       for (int k = 0; k < RC; ++k)
-        if (k < c.R) o[k] = ldg_cg(z + k) + acc[k];
+        if (k < c.R) o[k] = (with_z ? ldg_cg(z + k) : 0.0) + acc[k];
     }
   }
 }
@@ -411,10 +412,10 @@ __device__ void finish_dot(const Ctx &c, int slot, double *out) {
   __syncthreads();
 }
 
-// Second half of the operator: given VL/BL slabs (v = sum VL, bkb = sum BL),
-// computes out = bkb + D~^T W v.  Returns false on a barrier timeout.
+// From the VL/BL slabs: v = sum VL (= D~ x), bkb = sum BL, and w = W v with
+// W = theta P^T P + (1 - theta) I.
 template <int RC>
-__device__ bool second_half(const Ctx &c, double *out) {
+__device__ bool apply_W(const Ctx &c) {
   double *v = c.dl[V_V], *bkb = c.dl[V_BKB], *pvv = c.dl[V_PV], *w = c.dl[V_W];
   ph_dl_gather(c, S_VL, 1.0, v, nullptr, 0.0, S_BL, bkb);  // v = D~ x, bkb
   if (!grid_sync(c)) return false;
@@ -425,7 +426,15 @@ __device__ bool second_half(const Ctx &c, double *out) {
   ph_dl_phi<RC>(c, true, pvv, S_T2L);  // -Phi^T (P v)^
   if (!grid_sync(c)) return false;
   ph_dl_gather(c, S_T2L, c.theta, w, v, 1.0 - c.theta, -1, nullptr);  // W v
-  if (!grid_sync(c)) return false;
+  return grid_sync(c);
+}
+
+// Second half of the operator: given VL/BL slabs (v = sum VL, bkb = sum BL),
+// computes out = bkb + D~^T W v.  Returns false on a barrier timeout.
+template <int RC>
+__device__ bool second_half(const Ctx &c, double *out) {
+  double *bkb = c.dl[V_BKB], *w = c.dl[V_W];
+  if (!apply_W<RC>(c)) return false;
   ph_g_lamT<RC>(c, w);  // z = Lambda^T [0; w^]
   if (!grid_sync(c)) return false;
   ph_pi_gather(c, S_ZL, 1.0, c.pv[P_RNU], -1, 0.0, nullptr);
@@ -434,7 +443,7 @@ __device__ bool second_half(const Ctx &c, double *out) {
     ph_coarse(c, c.o_Sinv, c.pv[P_RNU], -1, nullptr, 0.0, c.pv[P_NU], c.o_C3, c.pv[P_RNU], -1, nullptr,
               0.0, c.pv[P_DNU]);
   if (!grid_sync(c)) return false;
-  ph_dl_last<RC>(c, c.pv[P_NU], c.pv[P_DNU]);
+  ph_dl_last<RC>(c, c.pv[P_NU], c.pv[P_DNU], true);
   if (!grid_sync(c)) return false;
   ph_dl_gather(c, S_YL, 1.0, out, bkb, 1.0, -1, nullptr);
   return grid_sync(c);
@@ -456,11 +465,77 @@ __device__ bool apply_S(const Ctx &c, const double *x, double *q) {
   return second_half<RC>(c, q);
 }
 
+// Plain CG on S_theta mu = B from mu = 0 (per right-hand side, converged
+// columns frozen); returns the iteration count or -1 on a barrier timeout.
+// s_bn receives |B| per column.
 template <int RC>
-__global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
-  __shared__ double s_rr[16], s_bn[16], s_pq[16], s_rn[16], s_alpha[16], s_beta[16];
+__device__ int cg_solve(const Ctx &c, double *s_bn) {
+  __shared__ double s_rr[16], s_pq[16], s_rn[16], s_alpha[16], s_beta[16];
   __shared__ int s_done;
   double *B = c.dl[V_B], *MU = c.dl[V_MU], *RES = c.dl[V_RES], *PD = c.dl[V_PD], *Q = c.dl[V_Q];
+  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+    const double b = B[e];
+    MU[e] = 0.0;
+    RES[e] = b;
+    PD[e] = b;
+  }
+  partial_dot<RC>(c, B, B, 0);
+  if (!grid_sync(c)) return -1;
+  finish_dot<RC>(c, 0, s_bn);
+  if (threadIdx.x < RC) {
+    s_rr[threadIdx.x] = s_bn[threadIdx.x];
+    s_bn[threadIdx.x] = sqrt(s_bn[threadIdx.x]);
+  }
+  if (threadIdx.x == 0) s_done = 0;
+  __syncthreads();
+  int it = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < c.R && k < RC; ++k)
+        if (s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k]) done = 0;
+      s_done = done || it >= c.max_iters;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (!apply_S<RC>(c, PD, Q)) return -1;
+    partial_dot<RC>(c, PD, Q, 0);
+    if (!grid_sync(c)) return -1;
+    finish_dot<RC>(c, 0, s_pq);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      const bool live = k < c.R && s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k] && s_pq[k] != 0.0;
+      s_alpha[k] = live ? s_rr[k] / s_pq[k] : 0.0;
+    }
+    __syncthreads();
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+      const double al = s_alpha[e % c.R];
+      MU[e] = fma(al, PD[e], MU[e]);
+      RES[e] = fma(-al, ldg_cg(Q + e), RES[e]);
+    }
+    partial_dot<RC>(c, RES, RES, 1);
+    if (!grid_sync(c)) return -1;
+    finish_dot<RC>(c, 1, s_rn);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      s_beta[k] = (s_alpha[k] != 0.0 && s_rr[k] > 0.0) ? s_rn[k] / s_rr[k] : 0.0;
+      if (s_alpha[k] != 0.0) s_rr[k] = s_rn[k];
+    }
+    __syncthreads();
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+      const double be = s_beta[e % c.R];
+      if (s_alpha[e % c.R] != 0.0) PD[e] = fma(be, PD[e], RES[e]);
+    }
+    ++it;
+    if (!grid_sync(c)) return -1;
+  }
+  return it;
+}
+
+template <int RC>
+__device__ void forward_program(const Ctx &c) {
+  __shared__ double s_bn[16], s_rn[16];
+  double *B = c.dl[V_B], *MU = c.dl[V_MU], *Q = c.dl[V_Q];
   // ---------------- right-hand side b_theta
   // dpi = -sum a_Pi ; ppi = sum p_Pi (a, p are the per-subdomain A_m y and Q_Gamma Q^T f)
   for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
@@ -486,63 +561,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
   ph_dl_first<RC>(c, c.pv[P_MPF], nullptr, c.pv[P_GF], 1);
   if (!grid_sync(c)) return;
   if (!second_half<RC>(c, B)) return;
-  // ---------------- CG from mu = 0
-  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
-    const double b = B[e];
-    MU[e] = 0.0;
-    RES[e] = b;
-    PD[e] = b;
-  }
-  partial_dot<RC>(c, B, B, 0);
-  if (!grid_sync(c)) return;
-  finish_dot<RC>(c, 0, s_bn);
-  if (threadIdx.x < RC) {
-    s_rr[threadIdx.x] = s_bn[threadIdx.x];
-    s_bn[threadIdx.x] = sqrt(s_bn[threadIdx.x]);
-  }
-  if (threadIdx.x == 0) s_done = 0;
-  __syncthreads();
-  int it = 0;
-  while (true) {
-    if (threadIdx.x == 0) {
-      int done = 1;
-      for (int k = 0; k < c.R && k < RC; ++k)
-        if (s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k]) done = 0;
-      s_done = done || it >= c.max_iters;
-    }
-    __syncthreads();
-    if (s_done) break;
-    if (!apply_S<RC>(c, PD, Q)) return;
-    partial_dot<RC>(c, PD, Q, 0);
-    if (!grid_sync(c)) return;
-    finish_dot<RC>(c, 0, s_pq);
-    if (threadIdx.x < RC) {
-      const int k = threadIdx.x;
-      const bool live = k < c.R && s_bn[k] > 0.0 && sqrt(s_rr[k]) >= c.tol * s_bn[k] && s_pq[k] != 0.0;
-      s_alpha[k] = live ? s_rr[k] / s_pq[k] : 0.0;
-    }
-    __syncthreads();
-    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
-      const double al = s_alpha[e % c.R];
-      MU[e] = fma(al, PD[e], MU[e]);
-      RES[e] = fma(-al, ldg_cg(Q + e), RES[e]);
-    }
-    partial_dot<RC>(c, RES, RES, 1);
-    if (!grid_sync(c)) return;
-    finish_dot<RC>(c, 1, s_rn);
-    if (threadIdx.x < RC) {
-      const int k = threadIdx.x;
-      s_beta[k] = (s_alpha[k] != 0.0 && s_rr[k] > 0.0) ? s_rn[k] / s_rr[k] : 0.0;
-      if (s_alpha[k] != 0.0) s_rr[k] = s_rn[k];
-    }
-    __syncthreads();
-    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
-      const double be = s_beta[e % c.R];
-      if (s_alpha[e % c.R] != 0.0) PD[e] = fma(be, PD[e], RES[e]);
-    }
-    ++it;
-    if (!grid_sync(c)) return;
-  }
+  const int it = cg_solve<RC>(c, s_bn);
+  if (it < 0) return;
   // ---------------- true residual |b - S mu| / |b|
   if (!apply_S<RC>(c, MU, Q)) return;
   for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) c.dl[V_TMP][e] = B[e] - ldg_cg(Q + e);
@@ -603,6 +623,124 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
   }
 }
 
+// Adjoint of the solve map (f, g) -> c for a cotangent c-bar held in the
+// per-subdomain C buffers (and copied into the y buffers): every step of the
+// forward program transposed in reverse order; S_theta, S_Pi^{-1} and
+// C2 = I - D S_Pi^{-1} D^T are symmetric, C1^T = C3.  Leaves a-bar in the
+// A_m y buffers and p-bar in the p buffers for the local products that follow.
+template <int RC>
+__device__ void adjoint_program(const Ctx &c) {
+  __shared__ double s_bn[16];
+  double *B = c.dl[V_B], *MU = c.dl[V_MU];
+  const int lane = threadIdx.x & 31;
+  // lambda-bar = (K^+ E)^T c-bar on every Gamma row
+  for (int t = gwarp(); t < c.n_tg; t += nwarps()) {
+    const int s = c.ints[c.o_tg + 2 * t], a = c.ints[c.o_tg + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int j = lane; j < d.M; j += 32) {
+      const double m = c.db[d.oKpE + (long long)j * d.nG + a];
+      const double *src = c.db + d.oC + (long long)j * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(m, src[k], acc[k]);
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+      double *o = slab_row(c, S_H1, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) o[k] = acc[k];
+    }
+  }
+  if (!grid_sync(c)) return;
+  // mu-bar_Pi (gathered), mu-bar_Delta direct part
+  ph_pi_gather(c, S_H1, 1.0, c.pv[P_MPIF], -1, 0.0, nullptr);
+  ph_dl_gather(c, S_H1, 1.0, c.dl[V_TMP], nullptr, 0.0, -1, nullptr);
+  if (!grid_sync(c)) return;
+  // s2-bar = S_Pi^{-1} mu-bar_Pi ; (C3 mu-bar_Pi) for psi2-bar = -C3 mu-bar_Pi
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_MPIF], -1, nullptr, 0.0, c.pv[P_S2], c.o_C3, c.pv[P_MPIF], -1, nullptr, 0.0,
+              c.pv[P_PSI2]);
+  if (!grid_sync(c)) return;
+  // mu-bar = direct + sum R_D^T (Psi_DPi s2-bar^ - Lambda_PiD^T (C3 mu-bar_Pi)^)
+  ph_dl_last<RC>(c, c.pv[P_S2], c.pv[P_PSI2], false);
+  if (!grid_sync(c)) return;
+  ph_dl_gather(c, S_YL, 1.0, B, c.dl[V_TMP], 1.0, -1, nullptr);
+  if (!grid_sync(c)) return;
+  // b-bar = S_theta^{-1} mu-bar
+  const int it = cg_solve<RC>(c, s_bn);
+  if (it < 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.info[0] = it;
+  // dt-bar = W D~ b-bar (first half of the operator applied to b-bar)
+  ph_pi_rows<RC>(c, MU);
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_H1, 1.0, c.pv[P_PSI], S_H2, -1.0, c.pv[P_RA]);
+  if (!grid_sync(c)) return;
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_RA], c.o_C1, c.pv[P_PSI], 1.0, c.pv[P_MPI], c.o_C2, c.pv[P_PSI], c.o_C3,
+              c.pv[P_RA], -1.0, c.pv[P_G]);
+  if (!grid_sync(c)) return;
+  ph_dl_first<RC>(c, c.pv[P_MPI], MU, c.pv[P_G], 0);
+  if (!grid_sync(c)) return;
+  if (!apply_W<RC>(c)) return;  // V_W = dt-bar
+  // H1 = Lambda_PiD b-bar^ , H2 = Psi_PiD b-bar^ , ZL = Lambda^T [0; dt-bar^]
+  ph_pi_rows<RC>(c, MU);
+  ph_g_lamT<RC>(c, c.dl[V_W]);
+  if (!grid_sync(c)) return;
+  // gf-bar = sum H1 ; mpf-bar = mu-bar_Pi + sum H2 - sum ZL_Pi
+  for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
+    const int p = e / c.R, k = e % c.R;
+    double g1 = 0.0, h2 = 0.0, z = 0.0;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      g1 += ldg_cg(slab_row(c, S_H1, d, a) + k);
+      h2 += ldg_cg(slab_row(c, S_H2, d, a) + k);
+      z += ldg_cg(slab_row(c, S_ZL, d, a) + k);
+    }
+    c.pv[P_GF][e] = g1;
+    c.pv[P_MPF][e] = ldg_cg(c.pv[P_MPIF] + e) + h2 - z;
+  }
+  if (!grid_sync(c)) return;
+  // ppi-bar = S_Pi^{-1} mpf-bar - C1 gf-bar ; dpi-bar = C3 mpf-bar + C2 gf-bar
+  if (c.n_pi > 0)
+    ph_coarse(c, c.o_Sinv, c.pv[P_MPF], c.o_C1, c.pv[P_GF], -1.0, c.pv[P_PPI], c.o_C3, c.pv[P_MPF], c.o_C2,
+              c.pv[P_GF], 1.0, c.pv[P_DPI]);
+  if (!grid_sync(c)) return;
+  // a-bar = [-R_Pi dpi-bar ; -R_D dt-bar], p-bar = [R_Pi ppi-bar ; R_D b-bar]
+  for (int e = gthread(); e < c.n_tg * c.R; e += nthreads()) {
+    const int t = e / c.R, k = e % c.R;
+    const int s = c.ints[c.o_tg + 2 * t], a = c.ints[c.o_tg + 2 * t + 1];
+    const SubDev &d = c.subs[s];
+    double ab, pb;
+    if (a < d.nPi) {
+      const int gp = c.ints[d.gpi_off + a];
+      ab = -ldg_cg(c.pv[P_DPI] + (long long)gp * c.R + k);
+      pb = ldg_cg(c.pv[P_PPI] + (long long)gp * c.R + k);
+    } else {
+      const int gd = c.ints[d.gdl_off + a - d.nPi];
+      ab = -ldg_cg(c.dl[V_W] + (long long)gd * c.R + k);
+      pb = ldg_cg(MU + (long long)gd * c.R + k);
+    }
+    c.db[d.oAy + (long long)a * c.R + k] = ab;
+    c.db[d.oP + (long long)a * c.R + k] = pb;
+  }
+  (void)B;
+}
+
+template <int RC>
+__global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
+  if (c.mode == 0)
+    forward_program<RC>(c);
+  else
+    adjoint_program<RC>(c);
+}
+
 }  // namespace
 
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) {
@@ -645,6 +783,7 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   c.max_iters = a.max_iters;
   c.mu_out = a.mu_out;
   c.c_out = a.c_out;
+  c.mode = a.mode;
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

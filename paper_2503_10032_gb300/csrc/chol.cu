@@ -217,7 +217,71 @@ __global__ void gather_rhs_kernel(const SubDev *__restrict__ subs, const int *__
   }
 }
 
+// adjoint inputs per subdomain: C = dL/dc rows, U = dL/du rows (zero if absent)
+__global__ void adjoint_init_kernel(const SubDev *__restrict__ subs, double *__restrict__ db,
+                                    const double *__restrict__ grad_c, const double *__restrict__ grad_u, int R) {
+  const SubDev d = subs[blockIdx.x];
+  for (int e = threadIdx.x; e < d.M * R; e += blockDim.x) db[d.oC + e] = grad_c ? grad_c[d.w_off * R + e] : 0.0;
+  for (int e = threadIdx.x; e < d.nE * R; e += blockDim.x) db[d.oU + e] = grad_u ? grad_u[d.eval_off * R + e] : 0.0;
+}
+
+__global__ void copy_c_to_y_kernel(const SubDev *__restrict__ subs, double *__restrict__ db, int R) {
+  const SubDev d = subs[blockIdx.x];
+  for (int e = threadIdx.x; e < d.M * R; e += blockDim.x) db[d.oY + e] = db[d.oC + e];
+}
+
+// dL/df = interior rows of F-bar; dL/dg = sum over the owners of each Dirichlet point
+__global__ void adjoint_scatter_f_kernel(const SubDev *__restrict__ subs, const double *__restrict__ db,
+                                         double *__restrict__ grad_f, int R) {
+  const SubDev d = subs[blockIdx.x];
+  for (int e = threadIdx.x; e < d.nI * R; e += blockDim.x) grad_f[d.int_off * R + e] = db[d.oF + e];
+}
+
+__global__ void adjoint_scatter_g_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
+                                         const double *__restrict__ db, double *__restrict__ grad_g, int n_bnd,
+                                         int o_own, int R) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_bnd * R; e += gridDim.x * blockDim.x) {
+    const int b = e / R, k = e % R;
+    double v = 0.0;
+    for (int o = 0; o < 2; ++o) {
+      const int s = ints[o_own + 4 * b + 2 * o];
+      if (s < 0) continue;
+      const int r = ints[o_own + 4 * b + 2 * o + 1];
+      const SubDev &d = subs[s];
+      v += db[d.oF + (long long)(d.nI + r) * R + k];
+    }
+    grad_g[e] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_adjoint_init(const Plan &p, void *ws, const double *grad_c, const double *grad_u, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  adjoint_init_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
+                                              reinterpret_cast<double *>(base + p.off_dbl), grad_c, grad_u, p.n_rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_c_to_y(const Plan &p, void *ws, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  copy_c_to_y_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
+                                             reinterpret_cast<double *>(base + p.off_dbl), p.n_rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_scatter(const Plan &p, void *ws, double *grad_f, double *grad_g, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
+  const double *db = reinterpret_cast<const double *>(base + p.off_dbl);
+  if (grad_f && p.sz.sum_int > 0) adjoint_scatter_f_kernel<<<p.n_sub, 256, 0, s>>>(subs, db, grad_f, p.n_rhs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (grad_g && p.sz.n_bnd > 0)
+    adjoint_scatter_g_kernel<<<64, 256, 0, s>>>(subs, reinterpret_cast<const int *>(base + p.off_ints), db, grad_g,
+                                                p.sz.n_bnd, p.o_bnd_own, p.n_rhs);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cudaStream_t s) {
   if (ph.ndesc == 0) return cudaSuccess;

@@ -126,6 +126,7 @@ struct Plan {
   int o_tasks_g = 0, n_tasks_g = 0;    // (sub, local Gamma row)
   int o_tasks_c = 0, n_tasks_c = 0;    // (sub, coefficient row j < M)
   int o_bnd_map = 0;                    // local boundary -> global Dirichlet index
+  int o_bnd_own = 0;                    // per global Dirichlet point: 2 x (sub, local row)
   // workspace layout
   size_t bytes_tables = 0, bytes_total = 0;
   size_t off_subs = 0, off_rows = 0, off_gdesc = 0, off_gtile = 0, off_cdesc = 0, off_ints = 0;
@@ -170,6 +171,9 @@ cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s);
 cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,
                               cudaStream_t s);
+cudaError_t launch_adjoint_init(const Plan &p, void *ws, const double *grad_c, const double *grad_u, cudaStream_t s);
+cudaError_t launch_copy_c_to_y(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_adjoint_scatter(const Plan &p, void *ws, double *grad_f, double *grad_g, cudaStream_t s);
 cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int ntiles, double *db, int skinny,
                               cudaStream_t s);
 cudaError_t launch_chol_table(const CholDesc *descs, int n, int maxM, double *db, int *status, cudaStream_t s);
@@ -179,6 +183,7 @@ struct CgArgs {
   int max_iters;
   double tol;
   double theta;
+  int mode = 0;  // 0 solve, 1 adjoint
 };
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s);
 

@@ -449,6 +449,20 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (int v : cntd)
       if (v != 2) return fail("internal: Delta point not shared by two subdomains");
   }
+  // per global Dirichlet point: up to 2 (sub, local boundary row) owners (adjoint scatter)
+  P.o_bnd_own = int(I.size());
+  I.resize(I.size() + 4 * (size_t)nb, -1);
+  {
+    std::vector<int> cnt(nb, 0);
+    for (int i = 0; i < n_sub; ++i)
+      for (size_t k = 0; k < sg[i].bg.size(); ++k) {
+        const int gb = sg[i].bg[k];
+        const int c = cnt[gb]++;
+        if (c >= 2) return fail("internal: boundary point with more than two subdomains");
+        I[P.o_bnd_own + 4 * gb + 2 * c] = i;
+        I[P.o_bnd_own + 4 * gb + 2 * c + 1] = int(k);
+      }
+  }
   P.o_tasks_pi = int(I.size());
   for (int i = 0; i < n_sub; ++i)
     for (int k = 0; k < P.subs[i].nPi; ++k) {
@@ -719,6 +733,47 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (int k = 0; k < P.setup_gemm[q].ndesc; ++k) f += P.gemm_flops[P.setup_gemm[q].desc0 + k];
     P.phase_flops.push_back(f);
   }
+  // adjoint phases: 20: c-bar += Eval^T u-bar ; 21: y-bar += A_m^T a-bar ; 22: Qtf-bar = Q_Gamma^T p-bar ;
+  //                 23: Qtf-bar += V^T y-bar ; 24: T-bar = V3 Qtf-bar ; 25: F-bar = Q2[IB rows] T-bar
+  {
+    GemmPhase a = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(a, d.oEval, d.oU, d.oC, d.M, R, d.nE, d.M, R, R, 1, 0, 0, 1.0, 1.0);
+    }
+    push(a);
+    GemmPhase b = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(b, d.oA, d.oAy, d.oY, d.M, R, d.nG, d.M, R, R, 1, 0, 0, 1.0, 1.0);
+    }
+    push(b);
+    GemmPhase c = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(c, d.oQG, d.oP, d.oQtf, d.M, R, d.nG, d.M, R, R, 1, 0, 0, 1.0, 0.0);
+    }
+    push(c);
+    GemmPhase e = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(e, d.oV, d.oY, d.oQtf, d.M, R, d.M, d.M, R, R, 1, 0, 0, 1.0, 1.0);
+    }
+    push(e);
+    GemmPhase f = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(f, d.oV3, d.oQtf, d.oT, d.M, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
+    }
+    push(f);
+    GemmPhase g2 = phase_begin(1);
+    for (int i = 0; i < n_sub; ++i) {
+      const SubDev &d = P.subs[i];
+      add(g2, d.oX, d.oT, d.oF, d.nI + d.nB, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
+    }
+    push(g2);
+  }
+
   // ---- Cholesky phases
   for (int pass = 0; pass < 3; ++pass) {
     P.chol_pass[pass].desc0 = int(P.cdesc.size());
@@ -827,6 +882,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         const int s = I[P.o_dl_own + 4 * p + 2 * o], a = I[P.o_dl_own + 4 * p + 2 * o + 1];
         if (s < 0 || s >= n_sub || a < 0 || a >= P.subs[s].nDl) return fail("internal: Delta owner map");
       }
+    for (int b = 0; b < nb; ++b) {
+      const int s0 = I[P.o_bnd_own + 4 * b];
+      if (s0 < 0) return fail("internal: boundary point without owner");
+      for (int o = 0; o < 2; ++o) {
+        const int s = I[P.o_bnd_own + 4 * b + 2 * o], a = I[P.o_bnd_own + 4 * b + 2 * o + 1];
+        if (s >= 0 && (s >= n_sub || a < 0 || a >= P.subs[s].nB)) return fail("internal: boundary owner map");
+      }
+    }
     for (const auto &s : P.sdesc) {
       const long long len = s.trans ? (long long)(s.K - 1) * s.ld + s.R : (long long)(s.R - 1) * s.ld + s.K;
       if (!in(s.x, len) || !in(s.scale, s.R)) return fail("internal: slice source bounds");

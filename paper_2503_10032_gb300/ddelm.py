@@ -89,7 +89,7 @@ def load_library(path: str = LIB_PATH):
                                 ctypes.c_void_p]
     lib.ddelm_solve.restype = ctypes.c_int
     lib.ddelm_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                   ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
+                                   ctypes.c_void_p, ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
     lib.ddelm_backward.restype = ctypes.c_int
     lib.ddelm_inspect.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
     lib.ddelm_inspect.restype = ctypes.c_int
@@ -194,10 +194,11 @@ def ddelm_solve(h, f_ptr, g_ptr, c_ptr, mu_ptr, u_ptr, stream):
     return rc, info
 
 
-def ddelm_backward(h, grad_c_ptr, grad_f_ptr, grad_g_ptr, stream):
+def ddelm_backward(h, grad_c_ptr, grad_u_ptr, grad_f_ptr, grad_g_ptr, stream):
     info = ddelm_solve_info()
-    rc = _lib.ddelm_backward(h, ctypes.c_void_p(grad_c_ptr), ctypes.c_void_p(grad_f_ptr),
-                             ctypes.c_void_p(grad_g_ptr), ctypes.byref(info), ctypes.c_void_p(stream))
+    rc = _lib.ddelm_backward(h, ctypes.c_void_p(grad_c_ptr), ctypes.c_void_p(grad_u_ptr),
+                             ctypes.c_void_p(grad_f_ptr), ctypes.c_void_p(grad_g_ptr), ctypes.byref(info),
+                             ctypes.c_void_p(stream))
     return rc, info
 
 
@@ -265,6 +266,22 @@ class Solver:
         if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
             raise DDELMError(rc, "ddelm_solve")
         return c, mu, u[:sz.sum_eval], info, rc
+
+    def backward(self, grad_c=None, grad_u=None):
+        """(dL/df [sum n_int, R], dL/dg [n_bnd, R], info) for cotangents of c and/or u."""
+        torch = self.torch
+        R = self.prob.n_rhs
+        sz = self.sizes
+        gf = torch.empty((max(sz.sum_int, 1), R), dtype=torch.float64, device=self.device)
+        gg = torch.empty((max(sz.n_bnd, 1), R), dtype=torch.float64, device=self.device)
+        gc = grad_c.contiguous() if grad_c is not None else None
+        gu = grad_u.contiguous() if grad_u is not None else None
+        rc, info = ddelm_backward(self.h, gc.data_ptr() if gc is not None else 0,
+                                  gu.data_ptr() if gu is not None else 0, gf.data_ptr(), gg.data_ptr(),
+                                  self.stream.cuda_stream)
+        if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
+            raise DDELMError(rc, "ddelm_backward")
+        return gf[:sz.sum_int], gg[:sz.n_bnd], info
 
     def inspect(self, sub, which):
         sizes = ddelm_inspect(self.h, sub, 7, 4)
