@@ -32,9 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = "DDELM solves/sec to rel. interface residual 1e-8 (mixed vs FP64, same GB300)"
 DEFAULT_WORKLOAD = "poisson_8x8_m400"
 TOL = 1e-8
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 EPS_REL = 1e-8
 THETA = 0.999
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
+SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2}
 
 
 def measured_peaks():
@@ -169,6 +171,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scheme", default="auto", choices=list(SCHEMES))
+    ap.add_argument("--passes", type=int, default=0, help="FP32 scheme: shifted passes (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -197,7 +201,8 @@ def main():
 
     prob = inputs.config(args.workload)
     prec = D.DDELM_PREC_FP64 if args.precision == "fp64" else D.DDELM_PREC_MIXED
-    opt_kw = dict(theta=THETA, eps_rel=EPS_REL, tol=TOL, max_iters=20000, precision=prec)
+    opt_kw = dict(theta=THETA, eps_rel=EPS_REL, tol=TOL, max_iters=20000, precision=prec,
+                  setup_scheme=SCHEMES[args.scheme], setup_passes=args.passes)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         solver = D.Solver(prob, device=dev, stream=stream, **opt_kw)
@@ -205,7 +210,10 @@ def main():
         g = torch.tensor(prob.g_bnd, dtype=torch.float64, device=dev)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     sizes = solver.sizes
-    flops = D.ddelm_inspect(solver.h, 0, 8, 5)
+    flops = D.ddelm_inspect(solver.h, 0, 8, 6)
+    plan = D.ddelm_inspect(solver.h, 0, 9, 4)
+    scheme_desc = ("fp64-cholesky-cqr3" if int(plan[0]) == 1 else
+                   f"fp32-cholesky x{int(plan[1])} shifted + 1 polished")
 
     def step():
         solver.refactor()
@@ -245,7 +253,8 @@ def main():
     fp64_cmp = None
     if args.precision == "mixed" and not args.no_fp64_compare:
         with torch.cuda.stream(stream):
-            s64 = D.Solver(prob, device=dev, stream=stream, **dict(opt_kw, precision=D.DDELM_PREC_FP64))
+            s64 = D.Solver(prob, device=dev, stream=stream,
+                           **dict(opt_kw, precision=D.DDELM_PREC_FP64, setup_scheme=0, setup_passes=0))
         for _ in range(1):
             s64.refactor()
             o64 = s64.solve(f, g)
@@ -330,6 +339,9 @@ def main():
         work = (flops[4] + flops[2]) * args.steps / max(prof_n[k_dom], 1)
     elif names[k_dom] == "chol_inv":
         work = flops[1] * args.steps / max(prof_n[k_dom], 1)
+        if flops[5] > 0.5 * flops[1]:
+            peak, peak_src = FP32_PEAK_GFLOPS, ("nominal FP32 CUDA-core rate (152 SMs x 128 lanes x 2 x 2.07 GHz); "
+                                                "the Cholesky passes run in FP32")
     elif names[k_dom] == "tc_gemm":
         work = flops[3] * args.steps / max(prof_n[k_dom], 1)
         bound, unit = "tensor", "GFLOP/s"
@@ -351,6 +363,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x9+f64",
             "data": "synthetic",
             "config": dict(workload_config(args.workload, prob, sizes), precision=args.precision,
+                           factorisation=scheme_desc, setup_waves=int(plan[2]),
                            parallelism=f"replicas{world}", l2="flushed between steps (512 MB write)"),
             "cg_iterations": int(np.median(iters)), "rel_residual_max": resid,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,

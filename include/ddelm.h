@@ -75,6 +75,18 @@ extern "C" {
 #define DDELM_PREC_FP64 0  /* every step in FP64 */
 #define DDELM_PREC_MIXED 1 /* FP32 inner CG with FP64 true-residual refinement */
 
+/* Factorisation schemes of the ridge problems [K; eps I] (Sec. 2.2 pseudo-inverses):
+ *  FP64CQR3: shifted CholeskyQR3, every Cholesky factor in FP64 (the FP64 path);
+ *  FP32:     shifted CholeskyQR with FP32 Cholesky factors used only as
+ *            preconditioners (every update of Q, the ridge block and R^{-1} stays
+ *            FP64-exact), then one unshifted FP32 pass whose residual
+ *            E = V^T G V - I is removed by V (I - E/2 + 3/8 E^2).
+ * Automatic: FP64CQR3 in FP64 precision; in MIXED, FP32 once some subdomain has
+ * M >= 512 (where the O(M^3) FP64 Cholesky of one SM per matrix dominates). */
+#define DDELM_SCHEME_AUTO 0
+#define DDELM_SCHEME_FP64CQR3 1
+#define DDELM_SCHEME_FP32 2
+
 typedef struct ddelm_options {
   double theta;           /* Eq. (nn-mixed) mixing weight; the paper uses 0.999 */
   double eps_rel;         /* ridge of the local least-squares problems (see above) */
@@ -84,6 +96,9 @@ typedef struct ddelm_options {
   int precision;          /* DDELM_PREC_FP64 or DDELM_PREC_MIXED */
   int max_refine;         /* MIXED: outer refinement sweeps */
   int keep_matrices;      /* 1: keep the assembled K_c^i, K-bar^i, A_m^i for ddelm_inspect */
+  int setup_wave;         /* subdomains whose setup scratch coexists (0: as many as fit 48 GiB) */
+  int setup_scheme;       /* factorisation of [K; eps I]: DDELM_SCHEME_* (0: automatic) */
+  int setup_passes;       /* DDELM_SCHEME_FP32: shifted FP32 passes before the last (0: automatic) */
 } ddelm_options;
 
 typedef struct ddelm_problem {
@@ -170,7 +185,11 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
  * 3 Lambda^i = A_m^i K^+ E_Gamma [nG x nG], 4 Psi^i = E_Gamma^T K K^+ E_Gamma
  * [nG x nG], 5 Phi^i = A-bar^i K-bar^+ E_Delta [nDl x nDl], 6 S_Pi [n_pi x n_pi]
  * (sub ignored), 7 the four sizes {m, M, nG, nDl} as doubles, 8 the algorithmic
- * flop counts {setup GEMMs, setup Cholesky + inverses, solve GEMMs} (sub ignored).  Blocks 0-2 are
+ * flop counts {setup GEMMs, setup Cholesky + inverses, solve GEMMs, tensor-core
+ * flops of the MIXED setup, FP64-engine setup flops left in MIXED, the FP32 part
+ * of the Cholesky flops} (sub ignored, out_len >= 5; the sixth is written when
+ * out_len >= 6), 9 the setup plan {scheme, Cholesky passes before the last,
+ * setup waves, subdomains per wave} (sub ignored).  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */

@@ -81,6 +81,7 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   put(tab, p.off_gdesc, p.gdesc);
   put(tab, p.off_gtile, p.gtile);
   put(tab, p.off_cdesc, p.cdesc);
+  put(tab, p.off_mdesc, p.mdesc);
   put(tab, p.off_ints, p.ints);
   put(tab, p.off_sdesc, p.sdesc);
   put(tab, p.off_odesc, p.odesc);
@@ -110,8 +111,9 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   return DDELM_OK;
 }
 
-// Assembly, shifted CholeskyQR3 of [K; eps I] and [K-bar; eps-bar I], local
-// operators and the coarse problem, all from workspace-resident data.
+// Assembly, shifted CholeskyQR of [K; eps I] and [K-bar; eps-bar I] (the
+// plan's step list, wave by wave), local operators and the coarse problem, all
+// from workspace-resident data.
 int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
   Plan &p = h->plan;
   double *db = dbase(h);
@@ -119,17 +121,6 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
   const long long np = p.n_pi > 0 ? p.n_pi : 1;
   CK(cudaMemsetAsync(db + p.o_Dpp, 0, np * np * 8, s));
   CK(cudaMemsetAsync(db + p.o_Spi, 0, np * np * 8, s));
-  LAUNCH(PC_FEAT, launch_features(p, h->ws, s));
-  if (p.keep) {
-    long long off = p.o_keepX;
-    for (const auto &d : p.subs) {
-      const size_t mm = (size_t)d.m * d.M;
-      CK(cudaMemcpyAsync(db + off, db + d.oX, mm * 8, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(db + off + mm, db + d.oKb, mm * 8, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(db + off + 2 * mm, db + d.oA, (size_t)d.nG * d.M * 8, cudaMemcpyDeviceToDevice, s));
-      off += (2 * (long long)mm + (long long)d.nG * d.M + 31) / 32 * 32;
-    }
-  }
   const auto &G = p.setup_gemm;
   // a setup GEMM phase runs on the tensor cores (BF16 slices) in MIXED precision
   auto gemm = [&](int q) -> int {
@@ -141,35 +132,50 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
     }
     return DDELM_OK;
   };
-#define GEMM(q)                     \
-  do {                              \
-    const int rc_ = gemm(q);        \
-    if (rc_ != DDELM_OK) return rc_; \
-  } while (0)
-  GEMM(0);
-  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[0], h->ws, s));
-  GEMM(1);
-  GEMM(2);
-  GEMM(3);
-  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[1], h->ws, s));
-  GEMM(4);
-  GEMM(5);
-  GEMM(6);
-  LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_pass[2], h->ws, s));
-  GEMM(7);
-  GEMM(8);
-  GEMM(9);
-  GEMM(10);
-#undef GEMM
+  for (const Step &st : p.steps) {
+    switch (st.kind) {
+      case STEP_FEAT: {
+        LAUNCH(PC_FEAT, launch_features(p, h->ws, st.idx, s));
+        if (p.keep) {  // copies of the assembled matrices of this wave
+          long long off = p.o_keepX;
+          for (int i = 0; i < p.n_sub; ++i) {
+            const SubDev &d = p.subs[i];
+            const size_t mm = (size_t)d.m * d.M;
+            if (i / p.wave == st.idx) {
+              CK(cudaMemcpyAsync(db + off, db + d.oK, mm * 8, cudaMemcpyDeviceToDevice, s));
+              CK(cudaMemcpyAsync(db + off + mm, db + d.oKb, mm * 8, cudaMemcpyDeviceToDevice, s));
+              CK(cudaMemcpyAsync(db + off + 2 * mm, db + d.oA, (size_t)d.nG * d.M * 8, cudaMemcpyDeviceToDevice,
+                                 s));
+            }
+            off += (2 * (long long)mm + (long long)d.nG * d.M + 31) / 32 * 32;
+          }
+        }
+        break;
+      }
+      case STEP_GEMM: {
+        const int rc = gemm(st.idx);
+        if (rc != DDELM_OK) return rc;
+        break;
+      }
+      case STEP_CHOL:
+        LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_passes[st.idx], h->ws, s));
+        break;
+      case STEP_MATOP:
+        LAUNCH(PC_OTHER, launch_matop_phase(p, p.matop_phases[st.idx], h->ws, s));
+        break;
+      default:
+        return DDELM_ERR_INVALID_ARG;
+    }
+  }
   if (p.n_pi > 0) {
     LAUNCH(PC_OTHER, launch_coarse_assembly(p, h->ws, s));
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[11], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 0], h->ws, s));
     CK(cudaMemcpyAsync(db + p.o_SpiR, db + p.o_Spi, (size_t)np * np * 8, cudaMemcpyDeviceToDevice, s));
     LAUNCH(PC_CHOL, launch_chol_phase(p, p.chol_coarse, h->ws, s));
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[12], h->ws, s));
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[13], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 1], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 2], h->ws, s));
     LAUNCH(PC_OTHER, launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[14], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 3], h->ws, s));
   }
   CK(cudaStreamSynchronize(s));
   int oz_err = 0;
@@ -248,10 +254,7 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   }
   LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, d_f_int, d_g_bnd, s));
   const auto &G = p.setup_gemm;
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[15], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[16], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[17], h->ws, s));
-  LAUNCH(PC_GEMM, launch_gemm_phase(p, G[18], h->ws, s));
+  for (int q = 0; q < 4; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + q], h->ws, s));
   // barrier words and error flag
   CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
   CgArgs a;
@@ -262,7 +265,7 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   a.theta = p.opt.theta;
   LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
   if (p.sz.sum_eval > 0) {
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[19], h->ws, s));
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + 4], h->ws, s));
     if (d_u_eval) {
       for (const auto &d : p.subs)
         if (d.nE > 0)
@@ -311,7 +314,7 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
   }
   const auto &G = p.setup_gemm;
   LAUNCH(PC_OTHER, launch_adjoint_init(p, h->ws, d_grad_c, d_grad_u, s));
-  if (d_grad_u && p.sz.sum_eval > 0) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[20], h->ws, s));
+  if (d_grad_u && p.sz.sum_eval > 0) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_adj + 0], h->ws, s));
   LAUNCH(PC_OTHER, launch_copy_c_to_y(p, h->ws, s));
   CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
   CgArgs a;
@@ -322,7 +325,7 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
   a.theta = p.opt.theta;
   a.mode = 1;
   LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
-  for (int q = 21; q <= 25; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[q], h->ws, s));
+  for (int q = 1; q <= 5; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_adj + q], h->ws, s));
   LAUNCH(PC_OTHER, launch_adjoint_scatter(p, h->ws, d_grad_f, d_grad_g, s));
   if (info) CK(cudaEventRecord(e1, s));
   CK(cudaStreamSynchronize(s));
@@ -393,15 +396,25 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       if (out_len < 5) return DDELM_ERR_INVALID_ARG;
       double fs = 0.0, fv = 0.0, fleft = 0.0;
       for (size_t q = 0; q < p.phase_flops.size(); ++q) {
-        if (q <= 14) fs += p.phase_flops[q];
-        else if (q <= 19) fv += p.phase_flops[q];
-        if (q <= 14 && !(p.mixed && q < p.oz_phase.size() && p.oz_phase[q].ntile > 0)) fleft += p.phase_flops[q];
+        if ((int)q < p.ph_solve) fs += p.phase_flops[q];
+        else if ((int)q < p.ph_adj) fv += p.phase_flops[q];
+        if ((int)q < p.ph_solve && !(p.mixed && q < p.oz_phase.size() && p.oz_phase[q].ntile > 0))
+          fleft += p.phase_flops[q];
       }
       host_out[0] = fs;
       host_out[1] = p.chol_flops;
       host_out[2] = fv;
       host_out[3] = p.oz_flops;
       host_out[4] = p.mixed ? fleft : fs;
+      if (out_len >= 6) host_out[5] = p.chol_flops32;
+      return DDELM_OK;
+    }
+    case 9: {
+      if (out_len < 4) return DDELM_ERR_INVALID_ARG;
+      host_out[0] = p.scheme;
+      host_out[1] = p.n_pass;
+      host_out[2] = p.n_waves;
+      host_out[3] = p.wave;
       return DDELM_OK;
     }
     case 7: {

@@ -1,14 +1,17 @@
-// Batched FP64 Cholesky factorisation with explicit triangular inverse (one
-// CTA per matrix), the coarse-matrix assembly of Sec. 3 (S_Pi assembled in
-// full), and small helpers (identity fill, right-hand-side gather).
+// Batched Cholesky factorisation with explicit triangular inverse (one CTA
+// per matrix) in FP64 or FP32, the small matrix operations of the polished
+// FP32 scheme, the coarse-matrix assembly of Sec. 3 (S_Pi assembled in full),
+// and small helpers (identity fill, right-hand-side gather).
 //
-// Cholesky pass of the shifted CholeskyQR3 factorisation of [K; eps I]:
-//   mode 1 (first pass): eps^2 = eps_rel^2 tr(G)/M is the ridge of the local
-//     least-squares problem; the diagonal additionally gets the stabilising
-//     shift s = shift_rel tr(G + eps^2 I) (shift_rel = 11 ((m+M) M + M (M+1)) u,
-//     u = 2^-53, raised to cover the slice truncation of a tensor-core Gram);
-//     Z = eps R^{-1} is the ridge block of the first Q.
-//   mode 0: plain factorisation.
+// A Cholesky pass of shifted CholeskyQR on [K; eps I] factors
+// G + (eps^2 + s) I:
+//   ridge passes (the first): eps^2 = eps_rel^2 tr(G)/M is the ridge of the
+//     local least-squares problem and Z = eps R^{-1} the ridge block of the
+//     first Q;
+//   shift kind 1 (FP64 first pass): s = shift_rel tr(G + eps^2 I) with
+//     shift_rel = 11 ((m+M) M + M (M+1)) u, u = 2^-53 (raised to cover the
+//     slice truncation of a tensor-core Gram);
+//   shift kind 2 (FP32 passes): s = shift_rel max diag(G + eps^2 I).
 // A pivot that is not positive marks the matrix in the status array; the
 // factorisation continues with a unit pivot so that no NaN propagates.
 #include "ddelm_internal.h"
@@ -20,58 +23,37 @@ namespace {
 constexpr int CT = 512;
 constexpr int NB = 16;   // panel rows
 
-// Blocked right-looking upper Cholesky G = R^T R in place (upper triangle), then
-// V = R^{-1} by blocked back substitution.  The panel (NB rows of the trailing
-// matrix) lives in shared memory; the trailing update is a register-tiled
-// SYRK (4x4 tiles per thread), so G is read and written once per panel.
-__global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict__ descs,
-                                                      double *__restrict__ db, int *__restrict__ status) {
-  extern __shared__ double P[];  // NB x M panel
-  const CholDesc cd = descs[blockIdx.x];
-  const int M = cd.M;
-  double *G = db + cd.g;
-  double *V = db + cd.v;
-  __shared__ double red[CT / 32];
-  __shared__ double s_eps2, s_piv;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = CT / 32;
-  if (tid == 0) s_bad = 0;
-  if (cd.mode == 1) {
-    double t = 0.0;
-    for (int j = tid; j < M; j += CT) t += G[(long long)j * M + j];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[wid] = t;
-    __syncthreads();
-    if (tid == 0) {
-      double tr = 0.0;
-      for (int k = 0; k < nw; ++k) tr += red[k];
-      const double eps2 = cd.eps_rel * cd.eps_rel * tr / double(M);
-      s_eps2 = eps2;
-      s_piv = eps2 + cd.shift_rel * (tr + M * eps2);
-    }
-    __syncthreads();
-    for (int j = tid; j < M; j += CT) G[(long long)j * M + j] += s_piv;
-    __syncthreads();
-  }
-  // ---------------- factorisation
+// Blocked right-looking upper Cholesky A = R^T R in place (upper triangle), then
+// V = R^{-1} by blocked back substitution, in precision T.  The panel (NB rows
+// of the trailing matrix) lives in shared memory; the trailing update is a
+// register-tiled SYRK (4x4 tiles per thread), so A is read and written once per
+// panel.  band > 0: A (and R) vanish beyond band superdiagonals, and only
+// in-band entries are touched.  A non-positive pivot sets *bad and continues
+// with a unit pivot.
+template <typename T>
+__device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
+  __shared__ T s_piv;
+  const int tid = threadIdx.x;
+  const int BW = band > 0 ? band : M;
   for (int k0 = 0; k0 < M; k0 += NB) {
-    const int nb = min(NB, M - k0), W = M - k0;  // panel: rows k0..k0+nb, columns k0..M
+    const int nb = min(NB, M - k0);
+    const int W = min(M, k0 + nb + BW) - k0;  // panel columns k0 .. k0+W
     for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      P[r * W + c] = G[(long long)(k0 + r) * M + k0 + c];
+      P[r * W + c] = A[(long long)(k0 + r) * M + k0 + c];
     }
     __syncthreads();
     for (int t = 0; t < nb; ++t) {  // unblocked elimination inside the panel
       if (tid == 0) {
-        double piv = P[t * W + t];
-        if (!(piv > 0.0) || !isfinite(piv)) {
-          s_bad = 1;
-          piv = 1.0;
+        T piv = P[t * W + t];
+        if (!(piv > T(0)) || !isfinite(piv)) {
+          *bad = 1;
+          piv = T(1);
         }
         s_piv = sqrt(piv);
       }
       __syncthreads();
-      const double r = s_piv;
+      const T r = s_piv;
       for (int c = t + tid; c < W; c += CT) P[t * W + c] = c == t ? r : P[t * W + c] / r;
       __syncthreads();
       for (int e = tid; e < (nb - t - 1) * W; e += CT) {
@@ -82,15 +64,14 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
     }
     for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      if (c >= r) G[(long long)(k0 + r) * M + k0 + c] = P[r * W + c];
+      if (c >= r) A[(long long)(k0 + r) * M + k0 + c] = P[r * W + c];
     }
-    // trailing update of the upper triangle: G[i][j] -= sum_t P[t][i] P[t][j], i <= j, i, j >= k0 + nb
-    const int T0 = k0 + nb, nt = M - T0;
+    // trailing update of the upper triangle: A[i][j] -= sum_t P[t][i] P[t][j], i <= j
+    const int T0 = k0 + nb, T1 = k0 + W, nt = T1 - T0;  // only columns the panel reaches
     if (nt > 0) {
-      const int nbt = (nt + 3) / 4;                  // 4x4 tiles along each side
-      const int ntiles = nbt * (nbt + 1) / 2;        // upper-triangular tile pairs
+      const int nbt = (nt + 3) / 4;
+      const int ntiles = nbt * (nbt + 1) / 2;
       for (int q = tid; q < ntiles; q += CT) {
-        // map q -> (bi, bj) with bi <= bj
         int bi = 0, rem = q;
         while (rem >= nbt - bi) {
           rem -= nbt - bi;
@@ -98,17 +79,17 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
         }
         const int bj = bi + rem;
         const int i0 = T0 + 4 * bi, j0 = T0 + 4 * bj;
-        double acc[4][4];
+        T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+          for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
         for (int t = 0; t < nb; ++t) {
-          double pa[4], pb[4];
+          T pa[4], pb[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) pa[a] = (i0 + a < M) ? P[t * W + (i0 + a - k0)] : 0.0;
+          for (int a = 0; a < 4; ++a) pa[a] = (i0 + a < T1) ? P[t * W + (i0 + a - k0)] : T(0);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) pb[b] = (j0 + b < M) ? P[t * W + (j0 + b - k0)] : 0.0;
+          for (int b = 0; b < 4; ++b) pb[b] = (j0 + b < T1) ? P[t * W + (j0 + b - k0)] : T(0);
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -117,53 +98,53 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int i = i0 + a;
-          if (i >= M) continue;
+          if (i >= T1) continue;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int j = j0 + b;
-            if (j < M && j >= i) G[(long long)i * M + j] -= acc[a][b];
+            if (j < T1 && j >= i) A[(long long)i * M + j] -= acc[a][b];
           }
         }
       }
     }
     __syncthreads();
   }
-  // ---------------- V = R^{-1}: block rows from the bottom
-  // rows i0..i1 of V: V[i][j] = (delta_ij - sum_{k>i} R[i][k] V[k][j]) / R[i][i], j >= i
-  for (long long e = tid; e < (long long)M * M; e += CT) V[e] = 0.0;
+  // V = R^{-1}: block rows from the bottom;
+  // V[i][j] = (delta_ij - sum_{k>i} R[i][k] V[k][j]) / R[i][i], j >= i
+  for (long long e = tid; e < (long long)M * M; e += CT) V[e] = T(0);
   __syncthreads();
   const int nblk = (M + NB - 1) / NB;
   for (int b = nblk - 1; b >= 0; --b) {
-    const int i0 = b * NB, nb = min(NB, M - i0), i1 = i0 + nb, W = M - i0;
-    for (int e = tid; e < nb * W; e += CT) {  // R[i0..i1][i0..M] into the panel
+    const int i0 = b * NB, nb = min(NB, M - i0), i1 = i0 + nb;
+    const int W = min(M, i0 + nb + BW) - i0;  // R[i0..i1][i0 .. i0+W] holds the block's nonzeros
+    for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      P[r * W + c] = G[(long long)(i0 + r) * M + i0 + c];
+      P[r * W + c] = A[(long long)(i0 + r) * M + i0 + c];
     }
     __syncthreads();
-    // contribution of the rows below the block: a thread per column j
     for (int j = i0 + tid; j < M; j += CT) {
-      double acc[NB];
+      T acc[NB];
 #pragma unroll
-      for (int r = 0; r < NB; ++r) acc[r] = 0.0;
-      for (int k = i1; k <= j; ++k) {
-        const double vk = V[(long long)k * M + j];
+      for (int r = 0; r < NB; ++r) acc[r] = T(0);
+      const int kend = min(j, i0 + W - 1);
+      for (int k = i1; k <= kend; ++k) {
+        const T vk = V[(long long)k * M + j];
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k - i0)], vk, acc[r]);
       }
-      // back substitution inside the block, rows i1-1 .. i0
-      double x[NB];
+      T x[NB];
 #pragma unroll
       for (int r = NB - 1; r >= 0; --r) {
         if (r >= nb) {
-          x[r] = 0.0;
+          x[r] = T(0);
           continue;
         }
         const int i = i0 + r;
-        double v = (j == i ? 1.0 : 0.0) - acc[r];
+        T v = (j == i ? T(1) : T(0)) - acc[r];
 #pragma unroll
         for (int u = r + 1; u < NB; ++u)
-          if (u < nb) v = fma(-P[r * W + (u)], x[u], v);
-        x[r] = (j >= i) ? v / P[r * W + r] : 0.0;
+          if (u < nb) v = fma(-P[r * W + u], x[u], v);
+        x[r] = (j >= i) ? v / P[r * W + r] : T(0);
       }
 #pragma unroll
       for (int r = 0; r < NB; ++r)
@@ -171,12 +152,134 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
     }
     __syncthreads();
   }
-  if (cd.mode == 1 && cd.z >= 0) {
-    double *Z = db + cd.z;
-    const double e = sqrt(s_eps2);
-    for (long long q = tid; q < (long long)M * M; q += CT) Z[q] = e * V[q];
+}
+
+// trace and maximum of the diagonal of an FP64 matrix (block reduction)
+__device__ void diag_stats(const double *G, int M, double *tr_out, double *mx_out) {
+  __shared__ double rt[CT / 32], rm[CT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double t = 0.0, mx = 0.0;
+  for (int j = tid; j < M; j += CT) {
+    const double g = G[(long long)j * M + j];
+    t += g;
+    mx = fmax(mx, g);
   }
-  if (tid == 0 && s_bad) status[cd.status] = 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    rt[wid] = t;
+    rm[wid] = mx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < CT / 32; ++k) {
+      a += rt[k];
+      b = fmax(b, rm[k]);
+    }
+    *tr_out = a;
+    *mx_out = b;
+  }
+  __syncthreads();
+}
+
+// The diagonal additions of a Cholesky pass: the ridge eps^2 = eps_rel^2 tr/M
+// (ridge passes) and the stabilising shift (shift_rel * tr(G + eps^2 I) for
+// shift kind 1, shift_rel * max diag(G + eps^2 I) for kind 2).
+__device__ void diag_additions(const CholDesc &cd, const double *G, double *eps2_out, double *add_out) {
+  __shared__ double s_tr, s_mx;
+  diag_stats(G, cd.M, &s_tr, &s_mx);
+  const double eps2 = cd.ridge ? cd.eps_rel * cd.eps_rel * s_tr / double(cd.M) : 0.0;
+  double shift = 0.0;
+  if (cd.shift_kind == 1) shift = cd.shift_rel * (s_tr + cd.M * eps2);
+  if (cd.shift_kind == 2) shift = cd.shift_rel * (s_mx + eps2);
+  *eps2_out = eps2;
+  *add_out = eps2 + shift;
+}
+
+// FP64 pass: factor in place in G, V = R^{-1}
+__global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict__ descs,
+                                                      double *__restrict__ db, int *__restrict__ status) {
+  extern __shared__ double P[];
+  const CholDesc cd = descs[blockIdx.x];
+  const int M = cd.M;
+  double *G = db + cd.g;
+  double *V = db + cd.v;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  double eps2 = 0.0, add = 0.0;
+  diag_additions(cd, G, &eps2, &add);
+  if (add != 0.0) {
+    for (int j = threadIdx.x; j < M; j += CT) G[(long long)j * M + j] += add;
+    __syncthreads();
+  }
+  chol_inv_core<double>(G, V, M, cd.band, P, &s_bad);
+  if (cd.z >= 0) {
+    double *Z = db + cd.z;
+    const double e = sqrt(eps2);
+    for (long long q = threadIdx.x; q < (long long)M * M; q += CT) Z[q] = e * V[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_bad) status[cd.status] = 1;
+}
+
+// FP32 pass (a preconditioning factor of shifted CholeskyQR: every product
+// with V is exact downstream, so V need only be well conditioned): G is read
+// in FP64, factored in FP32 in the work buffer w (2 M^2 floats), V written in
+// FP64.
+__global__ void __launch_bounds__(CT) chol_inv32_kernel(const CholDesc *__restrict__ descs,
+                                                        double *__restrict__ db, int *__restrict__ status) {
+  extern __shared__ float P32[];
+  const CholDesc cd = descs[blockIdx.x];
+  const int M = cd.M;
+  const double *G = db + cd.g;
+  double *V = db + cd.v;
+  float *A = reinterpret_cast<float *>(db + cd.w);
+  float *V32 = A + (long long)M * M;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  double eps2 = 0.0, add = 0.0;
+  diag_additions(cd, G, &eps2, &add);
+  for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
+    const int i = int(e / M), j = int(e % M);
+    A[e] = j >= i ? float(G[e] + (i == j ? add : 0.0)) : 0.0f;
+  }
+  __syncthreads();
+  chol_inv_core<float>(A, V32, M, 0, P32, &s_bad);
+  const double ez = sqrt(eps2);
+  for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
+    const double v = double(V32[e]);
+    V[e] = v;
+    if (cd.z >= 0) db[cd.z + e] = ez * v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_bad) status[cd.status] = 1;
+}
+
+// small batched matrix operations of the polishing step:
+//   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B  (two terms of (I + A)^{-1/2}, B = A A) ;
+//   op 2: C symmetric from its upper triangle.
+// op 1 flags the subdomain when max |A| > 1e-5: beyond that the neglected
+// third-order term could reach the FP64 level.
+__global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__restrict__ db, int *__restrict__ status) {
+  const MatopDesc md = descs[blockIdx.y];
+  const long long n = (long long)md.M * md.M;
+  bool big = false;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / md.M, j = e % md.M;
+    if (md.op == 0) {
+      db[md.c + e] = i == j ? -1.0 : 0.0;
+    } else if (md.op == 1) {
+      const double a = db[md.a + e];
+      big |= !(fabs(a) <= 1e-5);
+      db[md.c + e] = (i == j ? 1.0 : 0.0) - 0.5 * a + 0.375 * db[md.b + e];
+    } else if (i > j) {
+      db[md.c + e] = db[md.c + j * md.M + i];
+    }
+  }
+  if (big) status[md.status] = 1;
 }
 
 // Sec. 3: D_PiPi = sum_i R_Pi^T Lambda_PiPi^i R_Pi and the first two terms of
@@ -291,12 +394,26 @@ cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cuda
   int *status = reinterpret_cast<int *>(db + p.o_status);
   int maxM = 0;
   for (int k = 0; k < ph.ndesc; ++k) maxM = p.cdesc[ph.desc0 + k].M > maxM ? p.cdesc[ph.desc0 + k].M : maxM;
-  const size_t smem = sizeof(double) * (size_t)NB * (size_t)maxM;
+  const bool f32 = p.cdesc[ph.desc0].prec == 1;
+  const size_t smem = (f32 ? sizeof(float) : sizeof(double)) * (size_t)NB * (size_t)maxM;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = f32 ? cudaFuncSetAttribute(chol_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+  if (f32)
+    chol_inv32_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+  else
+    chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matop_phase(const Plan &p, const MatopPhase &ph, void *ws, cudaStream_t s) {
+  if (ph.ndesc == 0) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  const MatopDesc *descs = reinterpret_cast<const MatopDesc *>(base + p.off_mdesc) + ph.desc0;
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  matop_kernel<<<dim3(16, ph.ndesc), 256, 0, s>>>(descs, db, reinterpret_cast<int *>(db + p.o_status));
   return cudaGetLastError();
 }
 

@@ -43,8 +43,11 @@ struct SubDev {
   long long int_off;  // first interior point
   long long eval_off; // first evaluation point
   // setup buffers (dbase offsets)
-  long long oX, oKb;  // K_c^i and K-bar^i [m x M]; hold Q2 after the second pass
-  long long oY1, oY1b;  // first-pass Q [m x M]
+  long long oX;       // persistent [m x M]: the final Q of K_c^i after setup
+  long long oK;       // where the feature kernels write K_c^i (oX or oY1: the
+                      // Q updates alternate between the two so the last lands in oX)
+  long long oKb;      // K-bar^i [m x M] (setup scratch)
+  long long oY1, oY1b;  // the other Q buffers of K and K-bar [m x M] (setup scratch)
   long long oA;       // A_m^i [nG x M]
   long long oAbar;    // A-bar^i [nDl x M]
   long long oEval;    // phi at the evaluation points [nE x M]
@@ -81,14 +84,36 @@ struct GemmTile {
 };
 
 struct CholDesc {
-  long long g;  // in: symmetric matrix (upper triangle read); out: R (upper)
+  long long g;  // in: symmetric matrix (upper triangle read); FP64 passes factor it in place
   long long v;  // out: R^{-1} (upper, full square written)
-  long long z;  // out (mode 1): sqrt(eps2) R^{-1}; < 0 for none
+  long long z;  // out: sqrt(eps2) R^{-1} (ridge passes); < 0 for none
+  long long w;  // FP32 passes: work buffer of 2 M^2 floats
   int M, m;     // order, rows of the matrix whose Gram g is (for the shift)
-  int mode;     // 0 plain, 1 ridge + shift (first pass), 2 plain + explicit I - ...
+  int ridge;    // 1: add eps^2 = eps_rel^2 tr(G)/M (the ridge of the local problem)
+  int shift_kind;  // 0 none, 1 shift_rel * tr(G + eps^2 I), 2 shift_rel * max diag(G + eps^2 I)
+  int prec;     // 0 FP64, 1 FP32
+  int band;     // > 0: G and R vanish beyond this many superdiagonals
   int status;   // index into the status array
+  int pad;
   double eps_rel;
-  double shift_rel;  // mode 1: shift s = shift_rel * tr(G + eps^2 I)
+  double shift_rel;
+};
+
+struct MatopDesc {
+  long long a, b, c;
+  int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B ; op 2: lower(C) = upper(C)^T
+  int status;  // op 1: set when max |A| exceeds the range of the two-term series
+  int pad;
+};
+
+struct MatopPhase {
+  int desc0, ndesc;
+};
+
+// one step of the setup sequence
+enum StepKind : int { STEP_GEMM = 0, STEP_CHOL = 1, STEP_MATOP = 2, STEP_FEAT = 3 };
+struct Step {
+  int kind, idx;
 };
 
 // ---------------------------------------------------------------- plan
@@ -145,8 +170,25 @@ struct Plan {
   long long o_keepX = -1;
   bool keep = false;
   ddelm_options opt{};
-  // chol phases
-  CholPhase chol_pass[3]{}, chol_coarse{};
+  // setup waves: subdomains [w*wave, (w+1)*wave) share the scratch slots
+  int wave = 1, n_waves = 1;
+  // phase layout in setup_gemm: wave w phase q (0..10) at 11*w + q, then the
+  // coarse (4), solve (5) and adjoint (6) phases from these offsets
+  int ph_coarse = 0, ph_solve = 0, ph_adj = 0;
+  // chol phases (referenced by the step list), coarse chol
+  std::vector<CholPhase> chol_passes;
+  CholPhase chol_coarse{};
+  std::vector<MatopDesc> mdesc;
+  std::vector<MatopPhase> matop_phases;
+  std::vector<Step> steps;  // the per-subdomain part of the setup, in order
+  std::vector<int> setup_levels;  // per setup GEMM phase: BF16 slice levels (MIXED)
+  std::vector<int> wave_row0;     // special rows of wave w: [wave_row0[w], wave_row0[w+1]); then evaluation rows
+  int scheme = DDELM_SCHEME_FP64CQR3;
+  int n_pass = 2;        // Cholesky passes before the last one
+  bool polish = false;   // last factor corrected by the series (I + E)^{-1/2}
+  bool tri_v = true;     // V and the last factor are upper triangular
+  double chol_flops32 = 0.0;  // the part of chol_flops done in FP32
+  size_t off_mdesc = 0;
   // tensor-core emulation of the setup GEMMs (precision MIXED)
   bool mixed = false;
   std::vector<SliceDesc> sdesc;
@@ -164,9 +206,10 @@ int build_mixed(Plan &plan, long long &dbl_cursor);
 int encode_tensor_maps(const Plan &plan, void *ws, std::vector<unsigned char> &maps);
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_features(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s);
 cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cudaStream_t s);
+cudaError_t launch_matop_phase(const Plan &p, const MatopPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s);
 cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,

@@ -7,6 +7,8 @@
 //   L phi (diffusion) = 2 a |w|^2 t (1 - t^2) - (grad a . w)(1 - t^2)
 //   B phi = C phi = t,   F phi = (w . n)(1 - t^2)
 // with t = tanh(w . x + b).
+#include <algorithm>
+
 #include "ddelm_internal.h"
 
 namespace ddelm {
@@ -18,11 +20,11 @@ __device__ __forceinline__ double feat_t(double wx, double wy, double b, double 
 }
 
 // Interior collocation rows: rows [0, nI) of K_c^i and K-bar^i.
-__global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__restrict__ subs,
+__global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__restrict__ subs, int sub0,
                                                             double *__restrict__ db, long long o_w,
                                                             long long o_b, long long o_xint,
                                                             long long o_aint, long long o_gaint, int op) {
-  const SubDev d = subs[blockIdx.y];
+  const SubDev d = subs[sub0 + blockIdx.y];
   const int r0 = blockIdx.x * 8;
   if (r0 >= d.nI) return;
   const double *w = db + o_w + 2 * d.w_off;
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
       ax = db[o_gaint + 2 * pi];
       ay = db[o_gaint + 2 * pi + 1];
     }
-    double *o0 = db + d.oX + (long long)r * d.M;
+    double *o0 = db + d.oK + (long long)r * d.M;
     double *o1 = db + d.oKb + (long long)r * d.M;
     for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
       const double wx = w[2 * j], wy = w[2 * j + 1];
@@ -98,19 +100,24 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
 
 }  // namespace
 
-cudaError_t launch_features(const Plan &p, void *ws, cudaStream_t s) {
+// Features of the subdomains of one setup wave (their special rows included);
+// wave 0 also writes the evaluation rows.
+cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
   char *base = static_cast<char *>(ws);
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const SpecialRow *rows = reinterpret_cast<const SpecialRow *>(base + p.off_rows);
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  const int s0 = wave * p.wave, s1 = std::min(p.n_sub, s0 + p.wave);
   int max_nI = 0;
-  for (const auto &d : p.subs) max_nI = d.nI > max_nI ? d.nI : max_nI;
+  for (int i = s0; i < s1; ++i) max_nI = std::max(max_nI, p.subs[i].nI);
   if (max_nI > 0) {
-    dim3 grid((max_nI + 7) / 8, p.n_sub);
-    interior_rows_kernel<<<grid, 256, 0, s>>>(subs, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint,
-                                              p.op);
+    dim3 grid((max_nI + 7) / 8, s1 - s0);
+    interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint, p.op);
   }
-  if (!p.rows.empty()) special_rows_kernel<<<(unsigned)p.rows.size(), 256, 0, s>>>(rows, subs, db, p.o_w, p.o_b);
+  const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
+  if (r1 > r0) special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b);
+  const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
+  if (wave == 0 && e1 > e0) special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_b);
   return cudaGetLastError();
 }
 

@@ -31,8 +31,10 @@ struct OzDesc {
   double alpha, beta;
 };
 
+// one 128 x 128 output tile; only the 64-wide k blocks [kb0, kb1) can be
+// nonzero in op(A)[tile rows] op(B)[:, tile columns] (triangular operands)
 struct OzTile {
-  int desc, tm, tn, pad;
+  int desc, tm, tn, kb0, kb1, pad0, pad1, pad2;
 };
 
 struct OzPhase {
@@ -41,11 +43,6 @@ struct OzPhase {
   int tile0, ntile;      // OzTile range
   int max_rpad, max_kpad;
 };
-
-// Slice levels kept per setup GEMM phase (6 bits each): the first-pass Gram
-// only has to be accurate to well below the stabilising shift; every other
-// GEMM is kept at FP64 accuracy (9 levels, 54 bits).
-inline int oz_levels_for_phase(int q) { return q == 0 ? 6 : 9; }
 
 cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);

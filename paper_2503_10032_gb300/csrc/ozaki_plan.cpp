@@ -26,7 +26,7 @@ int build_mixed(Plan &P, long long &cur) {
   // scale scratch: sized for the largest phase
   long long max_scales = 0;
   size_t max_slices = 0;
-  const size_t n_setup = 11;  // phases 0..10: factorisation and local operators
+  const size_t n_setup = (size_t)P.ph_coarse;  // every wave's factorisation and local operator phases
   P.oz_phase.assign(P.setup_gemm.size(), OzPhase{0, 0, 0, 0, 0, 0, 0, 0});
   struct Key {
     long long x;
@@ -45,7 +45,8 @@ int build_mixed(Plan &P, long long &cur) {
       P.oz_phase[q] = op;
       continue;
     }
-    const int S = oz_levels_for_phase(int(q));
+    const int S = q < P.setup_levels.size() ? P.setup_levels[q] : 9;  // 6 bits per level
+    if (S < 1 || S > 10) return DDELM_ERR_INVALID_ARG;  // the fixed-point split holds 64^S in an int64
     std::map<Key, int> seen;
     long long elem = 0, scl = 0;
     auto slice_of = [&](long long x, int ld, int trans, int R, int K) {
@@ -98,16 +99,22 @@ int build_mixed(Plan &P, long long &cur) {
       P.odesc.push_back(o);
       op.ndesc++;
       const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + OZ_BM - 1) / OZ_BM;
+      const int nkb = o.Kpad / OZ_BK;
+      // tensor-core work: every level's pairs over the k blocks a tile needs
+      double pairs = 0;
+      for (int l = 0; l < S; ++l) pairs += l + 1;
       for (int x = 0; x < tm; ++x)
         for (int y = 0; y < tn; ++y) {
           if (d.syrk && x > y) continue;
-          P.otile.push_back({di, x, y, 0});
+          int kb0 = 0, kb1 = nkb;
+          // op(B)[k][j] = 0 for k > j ; op(A)[i][k] = 0 for k < i
+          if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (OZ_BM / OZ_BK));
+          if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / OZ_BK));
+          if (kb1 < kb0) kb1 = kb0;
+          P.otile.push_back({di, x, y, kb0, kb1, 0, 0, 0});
           op.ntile++;
+          P.oz_flops += 2.0 * OZ_BM * OZ_BM * (double)(kb1 - kb0) * OZ_BK * pairs;
         }
-      // tensor-core work: every level's pairs over the padded operands
-      double pairs = 0;
-      for (int l = 0; l < S; ++l) pairs += l + 1;
-      P.oz_flops += 2.0 * OZ_BM * OZ_BM * (double)o.Kpad * pairs * (d.syrk ? (tm * (tm + 1) / 2.0) : double(tm) * tn);
     }
     op.nslice = int(P.sdesc.size()) - op.slice0;
     P.oz_phase[q] = op;

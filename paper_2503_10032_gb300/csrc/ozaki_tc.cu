@@ -162,9 +162,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const OzDesc d = descs[tl.desc];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = d.S;
-  const int nkb = d.Kpad / BK;                 // 64-wide k blocks
+  const int kblo = tl.kb0, kbhi = tl.kb1;      // 64-wide k blocks this tile needs
   const int kcb = d.kc / BK;                   // k blocks per exact chunk
-  const int nchunk = (nkb + kcb - 1) / kcb;
+  const int nchunk = kbhi > kblo ? (kbhi - kblo + kcb - 1) / kcb : 0;
   const int ngroups = S * nchunk;
 
   if (threadIdx.x == 0) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int l = S - 1 - g / nchunk, c = g % nchunk;
         int p0;
         const int np = level_pairs(l, S, p0);
-        const int kb0 = c * kcb, kb1 = min(nkb, kb0 + kcb);
+        const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
         for (int t = 0; t < np && ok; ++t) {
           const int p = p0 + t, q = l - p;
           for (int kb = kb0; kb < kb1; ++kb) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int l = S - 1 - g / nchunk, c = g % nchunk;
         int p0;
         const int np = level_pairs(l, S, p0);
-        const int kb0 = c * kcb, kb1 = min(nkb, kb0 + kcb);
+        const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
         const uint32_t dacc = tmem + (uint32_t)(b * BN);
         uint32_t accum = 0;
         for (int t = 0; t < np && ok; ++t) {

@@ -72,6 +72,9 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail("theta must be in [0,1]");
   if (!(o.eps_rel >= 0.0) || !(o.tol > 0.0) || o.max_iters < 1) return fail("bad options");
   if (o.precision != DDELM_PREC_FP64 && o.precision != DDELM_PREC_MIXED) return fail("bad precision");
+  if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_FP32 || o.setup_passes < 0 ||
+      o.setup_passes > 8)
+    return fail("bad setup scheme");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
   const int nx = pr.nx, ny = pr.ny, n_sub = nx * ny;
@@ -233,7 +236,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     d.loc_off = sum_nG;
     sum_nG += d.nG;
     const long long M = d.M, m = d.m, nG = d.nG, nDl = d.nDl;
-    d.oX = take(m * M);  // holds Q2 of K_c after setup (needed by every solve)
+    d.oX = take(m * M);  // the final Q of K_c (needed by every solve)
     d.oA = take(nG * M);
     d.oEval = take(d.nE * M);
     d.oV = take(M * M);
@@ -281,45 +284,112 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   }
   // setup scratch (not needed after setup)
   setup_scratch_begin = cur;
-  struct Scr {
-    long long Kb, Y1, Y1b, Abar, G, Gb, V1, V1b, V2, V2b, V3b, Z, Zb, Z2, Z2b, T1, T1b, Vb, QbD, AV, AbV;
+  // factorisation scheme of [K; eps I] (shifted CholeskyQR, Sec. 2.2 pseudo-inverses)
+  {
+    int sch = o.setup_scheme;
+    if (sch == DDELM_SCHEME_AUTO)
+      sch = (o.precision == DDELM_PREC_MIXED && max_M >= 512) ? DDELM_SCHEME_FP32 : DDELM_SCHEME_FP64CQR3;
+    P.scheme = sch;
+    if (sch == DDELM_SCHEME_FP64CQR3) {
+      P.n_pass = 2;
+      P.polish = false;
+      P.tri_v = true;
+    } else {
+      // cond(G + eps^2 I) <= M / eps_rel^2 (tr G <= M lambda_max is attained when
+      // one direction dominates, as with tanh features); each shifted FP32 pass
+      // divides the condition number by about 1/shift_rel = 1e4, and the last,
+      // unshifted pass needs it near 1.
+      const double eps2 = std::max(o.eps_rel * o.eps_rel, 1e-300);
+      const int auto_pass = int(std::ceil(std::log10(std::max(10.0, max_M / eps2)) / 4.0));
+      P.n_pass = o.setup_passes > 0 ? o.setup_passes : std::min(8, std::max(2, auto_pass));
+      P.polish = true;
+      P.tri_v = false;
+    }
+  }
+  // per variant (K, K-bar): Gram, two pass factors, two ridge blocks, two
+  // accumulated products, FP32 Cholesky work, last factor and R^{-1}
+  struct VarScr {
+    long long G, Va, Vb, Za, Zb, Ta, Tb, W32, V3, V;
   };
-  std::vector<Scr> scr(n_sub);
-  for (int i = 0; i < n_sub; ++i) {
-    SubDev &d = P.subs[i];
-    const long long M = d.M, m = d.m, nG = d.nG, nDl = d.nDl;
-    Scr &c = scr[i];
+  struct Scr {
+    long long Kb, Y1, Y1b, Abar, QbD, AV, AbV;
+    VarScr v[2];
+  };
+  // Setup scratch is shared by the subdomains of different waves: subdomain i
+  // uses slot i % W, sized for the largest subdomain mapped to it.
+  {
+    const double per_sub_bytes = [&] {
+      double mx = 0;
+      for (const auto &d : P.subs) {
+        const double mM = double(d.m) * d.M, MM = double(d.M) * d.M;
+        double b = 8.0 * (3 * mM + 18 * MM + 4.0 * d.nG * d.M);
+        if (o.precision == DDELM_PREC_MIXED) b += 36.0 * mM + 36.0 * MM;  // BF16 slices of one phase
+        mx = std::max(mx, b);
+      }
+      return mx;
+    }();
+    const double budget = 48.0 * (1ull << 30);
+    int W = o.setup_wave > 0 ? o.setup_wave : n_sub;
+    if (o.setup_wave <= 0 && per_sub_bytes * n_sub > budget)
+      W = std::max(1, int(budget / std::max(per_sub_bytes, 1.0)));
+    W = std::min(W, n_sub);
+    P.wave = W;
+    P.n_waves = (n_sub + W - 1) / W;
+  }
+  const int W = P.wave;
+  std::vector<Scr> slot(W);
+  for (int k = 0; k < W; ++k) {
+    long long M = 1, m = 1, nG = 1, nDl = 1;
+    for (int i = k; i < n_sub; i += W) {
+      const SubDev &d = P.subs[i];
+      M = std::max<long long>(M, d.M);
+      m = std::max<long long>(m, d.m);
+      nG = std::max<long long>(nG, d.nG);
+      nDl = std::max<long long>(nDl, d.nDl);
+    }
+    Scr &c = slot[k];
     c.Kb = take(m * M);
     c.Y1 = take(m * M);
     c.Y1b = take(m * M);
     c.Abar = take(nDl * M);
-    c.G = take(M * M);
-    c.Gb = take(M * M);
-    c.V1 = take(M * M);
-    c.V1b = take(M * M);
-    c.V2 = take(M * M);
-    c.V2b = take(M * M);
-    c.V3b = take(M * M);
-    c.Z = take(M * M);
-    c.Zb = take(M * M);
-    c.Z2 = take(M * M);
-    c.Z2b = take(M * M);
-    c.T1 = take(M * M);
-    c.T1b = take(M * M);
-    c.Vb = take(M * M);
     c.QbD = take(nDl * M);
     c.AV = take(nG * M);
     c.AbV = take(nDl * M);
-    d.oKb = c.Kb;
-    d.oY1 = c.Y1;
-    d.oY1b = c.Y1b;
-    d.oAbar = c.Abar;
-    d.oVb = c.Vb;
+    for (int t = 0; t < 2; ++t) {
+      VarScr &v = c.v[t];
+      v.G = take(M * M);
+      v.Va = take(M * M);
+      v.Vb = take(M * M);
+      v.Za = take(M * M);
+      v.Zb = take(M * M);
+      v.Ta = take(M * M);
+      v.Tb = take(M * M);
+      v.W32 = take(M * M);  // 2 M^2 floats
+      v.V3 = t == 0 ? -1 : take(M * M);
+      v.V = t == 0 ? -1 : take(M * M);
+    }
+  }
+  std::vector<Scr> scr(n_sub);
+  for (int i = 0; i < n_sub; ++i) {
+    SubDev &d = P.subs[i];
+    scr[i] = slot[i % W];
+    scr[i].v[0].V3 = d.oV3;  // persistent for K
+    scr[i].v[0].V = d.oV;
+    d.oKb = scr[i].Kb;
+    d.oY1 = scr[i].Y1;
+    d.oY1b = scr[i].Y1b;
+    d.oAbar = scr[i].Abar;
+    d.oVb = scr[i].v[1].V;
+    // the Q updates alternate between the feature buffer and the other one;
+    // the features go where the last update lands in oX
+    d.oK = (P.n_pass % 2 == 0) ? d.oX : d.oY1;
   }
   (void)setup_scratch_begin;
 
   // ---- special rows
+  std::vector<int> sub_row0(n_sub + 1, 0);
   for (int i = 0; i < n_sub; ++i) {
+    sub_row0[i] = int(P.rows.size());
     const SubDev &d = P.subs[i];
     const SubGeo &s = sg[i];
     const long long M = d.M;
@@ -335,7 +405,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       SpecialRow r = base(ROW_POINT);
       r.x = s.bxy[k].x;
       r.y = s.bxy[k].y;
-      r.out0 = d.oX + (long long)(d.nI + k) * M;
+      r.out0 = d.oK + (long long)(d.nI + k) * M;
       r.out1 = d.oKb + (long long)(d.nI + k) * M;
       P.rows.push_back(r);
     }
@@ -344,7 +414,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       SpecialRow r = base(ROW_POINT);
       r.x = s.pxy[k].x;
       r.y = s.pxy[k].y;
-      r.out0 = d.oX + (long long)(g0 + k) * M;
+      r.out0 = d.oK + (long long)(g0 + k) * M;
       r.out1 = d.oKb + (long long)(g0 + k) * M;
       P.rows.push_back(r);
       SpecialRow a = base(ROW_AM);  // A_m corner row
@@ -381,7 +451,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           r.yb = s.pxy[s.bep[k]].y;
         }
       }
-      r.out0 = d.oX + (long long)(g0 + d.nPi + k) * M;
+      r.out0 = d.oK + (long long)(g0 + d.nPi + k) * M;
       r.out1 = d.oAbar + (long long)k * M;
       P.rows.push_back(r);
       // flux row: K-bar Delta row and A_m Delta row
@@ -395,6 +465,10 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       P.rows.push_back(f);
     }
   }
+  sub_row0[n_sub] = int(P.rows.size());
+  P.wave_row0.resize(P.n_waves + 1);
+  for (int w = 0; w < P.n_waves; ++w) P.wave_row0[w] = sub_row0[w * W];
+  P.wave_row0[P.n_waves] = sub_row0[n_sub];
   // evaluation rows
   if (sumE > 0) {
     for (int i = 0; i < n_sub; ++i) {
@@ -547,132 +621,230 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       }
   };
   auto push = [&](GemmPhase &ph) { P.setup_gemm.push_back(ph); };
-  // phase indices are fixed; api.cu runs them in this order around the Cholesky passes
-  // 0: G = Y^T Y for K and K-bar
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
+  // ---- the setup sequence: per wave the features, then the factorisation of
+  // [K; eps I] and [K-bar; eps-bar I] by shifted CholeskyQR with every O(m M^2)
+  // and O(M^3) product a GEMM phase, then the local operators.
+  const bool fp32 = P.scheme == DDELM_SCHEME_FP32;
+  const int N = P.n_pass;
+  // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
+  // accurate well below the shift; every other product keeps 54 bits.
+  // Products of the triangular factors (R^{-1} accumulated pass by pass) span
+  // many orders of magnitude inside a row, and the slice truncation is
+  // relative to the row maximum: they keep 60 bits.
+  const int lv_exact = 9, lv_factor = 10, lv_first64 = 6, lv_shifted32 = 5, lv_small = 4;
+  auto gemm_step = [&](GemmPhase &ph, int levels) {
+    P.steps.push_back({STEP_GEMM, int(P.setup_gemm.size())});
+    P.setup_gemm.push_back(ph);
+    P.setup_levels.push_back(levels);
+  };
+  auto chol_step = [&](int desc0) {
+    P.steps.push_back({STEP_CHOL, int(P.chol_passes.size())});
+    P.chol_passes.push_back(CholPhase{desc0, int(P.cdesc.size()) - desc0});
+  };
+  auto matop_step = [&](int desc0) {
+    P.steps.push_back({STEP_MATOP, int(P.matop_phases.size())});
+    P.matop_phases.push_back(MatopPhase{desc0, int(P.mdesc.size()) - desc0});
+  };
+  const int TU = P.tri_v ? GEMM_B_UPPER : 0;  // the last factor / R^{-1} as right operand
+  const int TA = P.tri_v ? GEMM_A_UPPER : 0;  // ... as left operand
+  for (int w = 0; w < P.n_waves; ++w) {
+    const int w0 = w * W, w1 = std::min(n_sub, w0 + W);
+    P.steps.push_back({STEP_FEAT, w});
+    // Q_k of variant t (0: K, 1: K-bar) lives in the feature buffer for even k
+    auto qk = [&](int i, int t, int k) -> long long {
       const SubDev &d = P.subs[i];
-      add(ph, d.oX, d.oX, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
-      add(ph, d.oKb, d.oKb, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+      const long long F = t == 0 ? d.oK : d.oKb;
+      const long long O = t == 0 ? (d.oK == d.oX ? d.oY1 : d.oX) : d.oY1b;
+      return (k % 2) ? O : F;
+    };
+    auto vk = [&](int i, int t, int k) { return (k % 2) ? scr[i].v[t].Vb : scr[i].v[t].Va; };  // pass-k factor
+    auto zk = [&](int i, int t, int k) { return (k % 2) ? scr[i].v[t].Zb : scr[i].v[t].Za; };  // ridge block after pass k
+    auto tk = [&](int i, int t, int k) { return k == 0 ? vk(i, t, 0) : (k % 2) ? scr[i].v[t].Ta : scr[i].v[t].Tb; };
+    // Gram of the features
+    {
+      GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph, qk(i, t, 0), qk(i, t, 0), scr[i].v[t].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+        }
+      gemm_step(ph, fp32 && N > 0 ? lv_shifted32 : lv_first64);
     }
-    push(ph);
+    for (int k = 0; k <= N; ++k) {
+      const bool last = k == N;
+      // Cholesky pass k: G = Q_k^T Q_k + Z_k^T Z_k (k = 0: Y^T Y and the ridge)
+      const int c0 = int(P.cdesc.size());
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          const VarScr &v = scr[i].v[t];
+          CholDesc c;
+          std::memset(&c, 0, sizeof(c));
+          c.g = v.G;
+          c.v = (last && !P.polish) ? v.V3 : vk(i, t, k);
+          c.z = k == 0 ? zk(i, t, 0) : -1;
+          c.w = v.W32;
+          c.M = d.M;
+          c.m = d.m;
+          c.ridge = k == 0;
+          c.band = 0;
+          c.status = 2 * i + t;
+          c.eps_rel = o.eps_rel;
+          if (!fp32) {
+            // s = 11 ((m+M) M + M (M+1)) u tr covers FP64 rounding of the Gram; with
+            // the tensor-core Gram the shift also covers its slice truncation
+            const double u = 1.1102230246251565e-16;
+            c.prec = 0;
+            c.shift_kind = k == 0 ? 1 : 0;
+            c.shift_rel = 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) * u;
+            if (o.precision == DDELM_PREC_MIXED)
+              c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -lv_first64));
+          } else {
+            // FP32 factor: the shift keeps the FP32 Cholesky away from breakdown and
+            // limits the condition number each pass removes to about 1/shift
+            c.prec = 1;
+            c.shift_kind = last ? 0 : 2;
+            c.shift_rel = std::max(1e-4, 2.0 * d.M * 5.9604644775390625e-8);
+          }
+          P.cdesc.push_back(c);
+        }
+      chol_step(c0);
+      if (last) break;
+      // Q_{k+1} = Q_k V_k, Z_{k+1} = Z_k V_k, T_k = T_{k-1} V_k (T_0 = V_0)
+      {
+        GemmPhase ph = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph, qk(i, t, k), vk(i, t, k), qk(i, t, k + 1), d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER,
+                1.0, 0.0);
+            if (k > 0)
+              add(ph, zk(i, t, k - 1), vk(i, t, k), zk(i, t, k), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+                  GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+          }
+        gemm_step(ph, lv_exact);
+      }
+      if (k > 0) {
+        GemmPhase ph = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph, tk(i, t, k - 1), vk(i, t, k), tk(i, t, k), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+                GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
+          }
+        gemm_step(ph, lv_factor);
+      }
+      // the Gram of pass k+1: G = Q^T Q, then G += Z^T Z (Z upper triangular)
+      const int lv = (fp32 && k + 1 < N) ? lv_shifted32 : lv_exact;
+      {
+        GemmPhase ph = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph, qk(i, t, k + 1), qk(i, t, k + 1), scr[i].v[t].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0,
+                0.0, true);
+          }
+        gemm_step(ph, lv);
+        GemmPhase ph2 = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph2, zk(i, t, k), zk(i, t, k), scr[i].v[t].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, GEMM_B_UPPER,
+                1.0, 1.0, true);
+          }
+        gemm_step(ph2, lv);
+      }
+    }
+    if (P.polish) {
+      // last factor V_l (FP32 Cholesky of G): E = V_l^T G V_l - I is small and
+      // V3 = V_l (I - E/2 + 3/8 E^2) makes [Q; Z] V3 orthonormal to O(|E|^3)
+      auto H = [&](int i, int t) { return zk(i, t, N - 1); };  // free after the last Gram
+      auto E = [&](int i, int t) { return zk(i, t, N); };
+      auto E2 = [&](int i, int t) { return vk(i, t, N - 1); };
+      int m0 = int(P.mdesc.size());
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t)
+          P.mdesc.push_back(MatopDesc{scr[i].v[t].G, 0, scr[i].v[t].G, P.subs[i].M, 2, 2 * i + t});
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) P.mdesc.push_back(MatopDesc{0, 0, E(i, t), P.subs[i].M, 0, 2 * i + t});
+      matop_step(m0);  // G lower = G upper ; E = -I
+      GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph, scr[i].v[t].G, vk(i, t, N), H(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+        }
+      gemm_step(ph, lv_exact);
+      GemmPhase ph2 = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph2, vk(i, t, N), H(i, t), E(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0);
+        }
+      gemm_step(ph2, lv_exact);
+      GemmPhase ph3 = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph3, E(i, t), E(i, t), E2(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, 0, 1.0, 0.0);
+        }
+      gemm_step(ph3, lv_small);
+      m0 = int(P.mdesc.size());
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t)
+          P.mdesc.push_back(MatopDesc{E(i, t), E2(i, t), E2(i, t), P.subs[i].M, 1, 2 * i + t});
+      matop_step(m0);  // W = I - E/2 + 3/8 E^2 (checks |E|)
+      GemmPhase ph4 = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph4, vk(i, t, N), E2(i, t), scr[i].v[t].V3, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_A_UPPER, 1.0,
+              0.0);
+        }
+      gemm_step(ph4, lv_exact);
+    }
+    // R^{-1} = T_{N-1} V3
+    {
+      GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t) {
+          const SubDev &d = P.subs[i];
+          add(ph, tk(i, t, N - 1), scr[i].v[t].V3, scr[i].v[t].V, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
+              GEMM_A_UPPER | TU, 1.0, 0.0);
+        }
+      gemm_step(ph, lv_factor);
+    }
+    // Q_Gamma = Q_N[Gamma rows] V3 ; Q-bar_Delta = Q-bar_N[Delta rows] V3-bar ; A_m V ; A-bar V-bar
+    {
+      GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i) {
+        const SubDev &d = P.subs[i];
+        const long long M = d.M;
+        add(ph, qk(i, 0, N) + (long long)(d.nI + d.nB) * M, scr[i].v[0].V3, d.oQG, d.nG, d.M, d.M, d.M, d.M, d.M,
+            0, 0, TU, 1.0, 0.0);
+        add(ph, qk(i, 1, N) + (long long)(d.m - d.nDl) * M, scr[i].v[1].V3, scr[i].QbD, d.nDl, d.M, d.M, d.M,
+            d.M, d.M, 0, 0, TU, 1.0, 0.0);
+        add(ph, d.oA, d.oV, scr[i].AV, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
+        add(ph, d.oAbar, scr[i].v[1].V, scr[i].AbV, d.nDl, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
+      }
+      gemm_step(ph, lv_exact);
+    }
+    // Lambda, Lambda^T, Psi, K^+ E_Gamma, Phi, Phi^T
+    {
+      GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i) {
+        const SubDev &d = P.subs[i];
+        add(ph, scr[i].AV, d.oQG, d.oLam, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+        add(ph, d.oQG, scr[i].AV, d.oLamT, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+        add(ph, d.oQG, d.oQG, d.oPsi, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
+        add(ph, d.oV, d.oQG, d.oKpE, d.M, d.nG, d.M, d.M, d.M, d.nG, 0, 1, TA, 1.0, 0.0);
+        add(ph, scr[i].AbV, scr[i].QbD, d.oPhi, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
+        add(ph, scr[i].QbD, scr[i].AbV, d.oPhiT, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
+      }
+      gemm_step(ph, lv_exact);
+    }
   }
-  // 1: Q1 = Y V1
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, d.oX, scr[i].V1, d.oY1, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, d.oKb, scr[i].V1b, d.oY1b, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-    }
-    push(ph);
-  }
-  // 2: G = Q1^T Q1 ; 3: G += Z1^T Z1
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, d.oY1, d.oY1, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
-      add(ph, d.oY1b, d.oY1b, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
-    }
-    push(ph);
-    GemmPhase ph2 = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      // op(A) = Z^T is lower triangular, op(B) = Z upper: k <= min(row, col)
-      add(ph2, scr[i].Z, scr[i].Z, scr[i].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
-          GEMM_B_UPPER, 1.0, 1.0, true);
-      add(ph2, scr[i].Zb, scr[i].Zb, scr[i].Gb, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
-          GEMM_B_UPPER, 1.0, 1.0, true);
-    }
-    push(ph2);
-  }
-  // 4: Q2 = Q1 V2 (into the feature buffers), Z2 = Z1 V2
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, d.oY1, scr[i].V2, d.oX, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, d.oY1b, scr[i].V2b, d.oKb, d.m, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, scr[i].Z, scr[i].V2, scr[i].Z2, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_B_UPPER | GEMM_A_UPPER, 1.0, 0.0);
-      add(ph, scr[i].Zb, scr[i].V2b, scr[i].Z2b, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_B_UPPER | GEMM_A_UPPER, 1.0, 0.0);
-    }
-    push(ph);
-  }
-  // 5: G = Q2^T Q2 ; 6: G += Z2^T Z2
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, d.oX, d.oX, scr[i].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
-      add(ph, d.oKb, d.oKb, scr[i].Gb, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
-    }
-    push(ph);
-    GemmPhase ph2 = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph2, scr[i].Z2, scr[i].Z2, scr[i].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
-          GEMM_B_UPPER, 1.0, 1.0, true);
-      add(ph2, scr[i].Z2b, scr[i].Z2b, scr[i].Gb, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0,
-          GEMM_B_UPPER, 1.0, 1.0, true);
-    }
-    push(ph2);
-  }
-  // 7: T1 = V1 V2 ; 8: V = T1 V3
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, scr[i].V1, scr[i].V2, scr[i].T1, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, scr[i].V1b, scr[i].V2b, scr[i].T1b, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
-    }
-    push(ph);
-    GemmPhase ph2 = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph2, scr[i].T1, d.oV3, d.oV, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
-      add(ph2, scr[i].T1b, scr[i].V3b, scr[i].Vb, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
-    }
-    push(ph2);
-  }
-  // 9: Q_Gamma = Q2[Gamma rows] V3 ; Q-bar_Delta = Q2-bar[Delta rows] V3-bar ;
-  //    A_m V ; A-bar V-bar
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      const long long M = d.M;
-      add(ph, d.oX + (long long)(d.nI + d.nB) * M, d.oV3, d.oQG, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0,
-          GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, d.oKb + (long long)(d.m - d.nDl) * M, scr[i].V3b, scr[i].QbD, d.nDl, d.M, d.M, d.M, d.M,
-          d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, d.oA, d.oV, scr[i].AV, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-      add(ph, d.oAbar, scr[i].Vb, scr[i].AbV, d.nDl, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0,
-          0.0);
-    }
-    push(ph);
-  }
-  // 10: Lambda, Lambda^T, Psi, K^+ E_Gamma, Phi, Phi^T
-  {
-    GemmPhase ph = phase_begin();
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      add(ph, scr[i].AV, d.oQG, d.oLam, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
-      add(ph, d.oQG, scr[i].AV, d.oLamT, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
-      add(ph, d.oQG, d.oQG, d.oPsi, d.nG, d.nG, d.M, d.M, d.M, d.nG, 0, 1, 0, 1.0, 0.0);
-      add(ph, d.oV, d.oQG, d.oKpE, d.M, d.nG, d.M, d.M, d.M, d.nG, 0, 1, GEMM_A_UPPER, 1.0, 0.0);
-      add(ph, scr[i].AbV, scr[i].QbD, d.oPhi, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
-      add(ph, scr[i].QbD, scr[i].AbV, d.oPhiT, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
-    }
-    push(ph);
-  }
+  P.ph_coarse = int(P.setup_gemm.size());
   // coarse: 11: S_Pi += D^T D ; 12: Sinv = V_Pi V_Pi^T ; 13: C1 = Sinv D^T, C3 = D Sinv ;
   //         14: C2 = I - D C1
   if (n_pi > 0) {
@@ -692,6 +864,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   } else {
     for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0, 0});
   }
+  P.ph_solve = int(P.setup_gemm.size());
   // solve phases: 15: T = Q2[IB rows]^T F ; 16: Qtf = V3^T T ; 17: y = V Qtf, p = Q_Gamma Qtf ;
   //               18: a = A_m y ; 19: u_eval = Eval c
   {
@@ -710,7 +883,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     GemmPhase c = phase_begin(1);
     for (int i = 0; i < n_sub; ++i) {
       const SubDev &d = P.subs[i];
-      add(c, d.oV, d.oQtf, d.oY, d.M, R, d.M, d.M, R, R, 0, 0, GEMM_A_UPPER, 1.0, 0.0);
+      add(c, d.oV, d.oQtf, d.oY, d.M, R, d.M, d.M, R, R, 0, 0, TA, 1.0, 0.0);
       add(c, d.oQG, d.oQtf, d.oP, d.nG, R, d.M, d.M, R, R, 0, 0, 0, 1.0, 0.0);
     }
     push(c);
@@ -733,6 +906,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (int k = 0; k < P.setup_gemm[q].ndesc; ++k) f += P.gemm_flops[P.setup_gemm[q].desc0 + k];
     P.phase_flops.push_back(f);
   }
+  P.ph_adj = int(P.setup_gemm.size());
   // adjoint phases: 20: c-bar += Eval^T u-bar ; 21: y-bar += A_m^T a-bar ; 22: Qtf-bar = Q_Gamma^T p-bar ;
   //                 23: Qtf-bar += V^T y-bar ; 24: T-bar = V3 Qtf-bar ; 25: F-bar = Q2[IB rows] T-bar
   {
@@ -774,34 +948,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     push(g2);
   }
 
-  // ---- Cholesky phases
-  for (int pass = 0; pass < 3; ++pass) {
-    P.chol_pass[pass].desc0 = int(P.cdesc.size());
-    for (int i = 0; i < n_sub; ++i) {
-      const SubDev &d = P.subs[i];
-      for (int t = 0; t < 2; ++t) {
-        CholDesc c;
-        std::memset(&c, 0, sizeof(c));
-        c.g = t == 0 ? scr[i].G : scr[i].Gb;
-        c.v = pass == 0 ? (t == 0 ? scr[i].V1 : scr[i].V1b)
-                        : pass == 1 ? (t == 0 ? scr[i].V2 : scr[i].V2b) : (t == 0 ? d.oV3 : scr[i].V3b);
-        c.z = pass == 0 ? (t == 0 ? scr[i].Z : scr[i].Zb) : -1;
-        c.M = d.M;
-        c.m = d.m;
-        c.mode = pass == 0 ? 1 : 0;
-        c.status = 2 * i + t;
-        c.eps_rel = o.eps_rel;
-        // shifted CholeskyQR: s = 11 ((m+M) M + M (M+1)) u tr covers FP64 rounding of the
-        // Gram; with the tensor-core Gram the shift also covers its slice truncation
-        const double u = 1.1102230246251565e-16;
-        c.shift_rel = 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) * u;
-        if (o.precision == DDELM_PREC_MIXED)
-          c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -oz_levels_for_phase(0)));
-        P.cdesc.push_back(c);
-      }
-    }
-    P.chol_pass[pass].ndesc = int(P.cdesc.size()) - P.chol_pass[pass].desc0;
-  }
+  // ---- coarse Cholesky
   P.chol_coarse.desc0 = int(P.cdesc.size());
   if (n_pi > 0) {
     CholDesc c;
@@ -809,14 +956,18 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     c.g = P.o_SpiR;  // a copy of S_Pi, factored in place
     c.v = P.o_Vpi;
     c.z = -1;
+    c.w = -1;
     c.M = n_pi;
     c.m = n_pi;
-    c.mode = 0;
     c.status = 2 * n_sub;
     P.cdesc.push_back(c);
   }
   P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
-  for (const auto &c : P.cdesc) P.chol_flops += 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
+  for (const auto &c : P.cdesc) {
+    const double f = 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
+    P.chol_flops += f;
+    if (c.prec == 1) P.chol_flops32 += f;
+  }
 
   // ---- tensor-core emulation tables (precision MIXED)
   if (o.precision == DDELM_PREC_MIXED) {
@@ -845,16 +996,26 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       if (t.desc < 0 || t.desc >= (int)P.gdesc.size()) return fail("internal: GEMM tile");
     for (const auto &c : P.cdesc) {
       const long long mm = (long long)c.M * c.M;
-      if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm))) return fail("internal: Cholesky bounds");
+      if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm)) || (c.prec == 1 && !in(c.w, mm)))
+        return fail("internal: Cholesky bounds");
+      if (c.prec == 1 && c.band != 0) return fail("internal: banded FP32 Cholesky");
       if (c.status < 0 || c.status > 2 * n_sub) return fail("internal: status slot");
     }
+    for (const auto &md : P.mdesc) {
+      const long long mm = (long long)md.M * md.M;
+      if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm))) || md.op < 0 || md.op > 2 ||
+          md.status < 0 || md.status >= 2 * n_sub)
+        return fail("internal: matrix operation bounds");
+    }
+    if ((int)P.wave_row0.size() != P.n_waves + 1 || P.wave_row0[P.n_waves] > (int)P.rows.size())
+      return fail("internal: wave rows");
     for (const auto &r : P.rows) {
       const long long M = P.subs[r.sub].M;
       if (!in(r.out0, M) || (r.out1 >= 0 && !in(r.out1, M))) return fail("internal: row output bounds");
     }
     for (const auto &d : P.subs) {
       const long long M = d.M, m = d.m;
-      if (!in(d.oX, m * M) || !in(d.oKb, m * M) || !in(d.oY1, m * M) || !in(d.oY1b, m * M) ||
+      if (!in(d.oX, m * M) || !in(d.oK, m * M) || !in(d.oKb, m * M) || !in(d.oY1, m * M) || !in(d.oY1b, m * M) ||
           !in(d.oA, d.nG * M) || !in(d.oAbar, d.nDl * M) || !in(d.oEval, d.nE * M) ||
           !in(d.oLam, (long long)d.nG * d.nG) || !in(d.oLamT, (long long)d.nG * d.nG) ||
           !in(d.oPsi, (long long)d.nG * d.nG) || !in(d.oPhi, (long long)d.nDl * d.nDl) ||
@@ -910,6 +1071,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       if (t.desc < 0 || t.desc >= (int)P.odesc.size()) return fail("internal: tensor-core tile");
       const OzDesc &od = P.odesc[t.desc];
       if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * 128 > od.RpadB) return fail("internal: tensor-core tile box");
+      if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
     }
     const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;
     if (!in(P.o_cg, cg_need) || !in(P.o_loc, 9LL * sum_nG * R) || !in(P.o_status, 4LL * n_sub + 64))
@@ -932,6 +1094,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   off = al(off + std::max<size_t>(P.gtile.size(), 1) * sizeof(GemmTile));
   P.off_cdesc = off;
   off = al(off + std::max<size_t>(P.cdesc.size(), 1) * sizeof(CholDesc));
+  P.off_mdesc = off;
+  off = al(off + std::max<size_t>(P.mdesc.size(), 1) * sizeof(MatopDesc));
   P.off_ints = off;
   off = al(off + std::max<size_t>(P.ints.size(), 1) * sizeof(int));
   P.off_sdesc = off;

@@ -137,7 +137,9 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
     cd[k].z = k == 0 ? oZ1 : -1;
     cd[k].M = M;
     cd[k].m = m;
-    cd[k].mode = k == 0 ? 1 : 0;
+    cd[k].w = -1;
+    cd[k].ridge = k == 0;
+    cd[k].shift_kind = k == 0 ? 1 : 0;
     cd[k].status = k;
     cd[k].eps_rel = eps_rel;
     cd[k].shift_rel = 11.0 * (double(m + M) * M + double(M) * (M + 1)) * u;

@@ -35,7 +35,8 @@ class ddelm_options(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("eps_rel", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("use_change_of_vars", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("keep_matrices", ctypes.c_int)]
+                ("keep_matrices", ctypes.c_int), ("setup_wave", ctypes.c_int),
+                ("setup_scheme", ctypes.c_int), ("setup_passes", ctypes.c_int)]
 
 
 class ddelm_problem(ctypes.Structure):
@@ -66,6 +67,7 @@ EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm
            "ddelm_inspect", "ddelm_profile", "ddelm_local_lstsq_static", "ddelm_destroy",
            "ddelm_status_string")
 DDELM_STATIC_SCRATCH_DOUBLES = 1048576
+DDELM_SCHEME_AUTO, DDELM_SCHEME_FP64CQR3, DDELM_SCHEME_FP32 = 0, 1, 2
 DDELM_PROF_CLASSES = 8
 PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other", "slicing", "tc_gemm")
 
@@ -117,9 +119,11 @@ def ddelm_status_string(status: int) -> str:
 
 
 def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change_of_vars=True,
-                 precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False):
+                 precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False, setup_wave=0,
+                 setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0):
     return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
-                         max_refine, int(keep_matrices))
+                         max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
+                         int(setup_passes))
 
 
 class ProblemArgs:

@@ -75,3 +75,22 @@ def test_uneven_subdomains(D, prec):
     n_pi = ref["oracle"].n_pi
     assert _rel(mu.cpu().numpy()[n_pi:], ref["mu_delta"]) < 1e-8
     assert _rel(u.cpu().numpy(), ref["u_eval"]) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_setup_waves_give_identical_results(D, prec):
+    """Subdomains set up in waves that share scratch slots give the same bits."""
+    import torch
+    p = inputs.small_uneven_problem(4, 3, n_rhs=1, seed=17)
+    pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
+    f = torch.tensor(p.f_int, dtype=torch.float64, device="cuda")
+    g = torch.tensor(p.g_bnd, dtype=torch.float64, device="cuda")
+    outs = []
+    for wave in (0, 5, 1):
+        s = D.Solver(p, eps_rel=1e-6, tol=1e-11, precision=pr, setup_wave=wave)
+        c, mu, u, info, rc = s.solve(f, g)
+        torch.cuda.synchronize()
+        assert rc == D.DDELM_OK
+        outs.append(mu.cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

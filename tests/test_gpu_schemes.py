@@ -1,0 +1,109 @@
+"""Factorisation schemes and the variable-coefficient operator against the FP64
+oracle: the FP32-Cholesky scheme (shifted FP32 passes, exact updates, series
+polish of the last factor) in both precisions, and -div(a grad u) problems."""
+import numpy as np
+import pytest
+
+from oracle import ddelm as odd
+from paper_2503_10032_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_10032_gb300 import build
+    build.build()
+    from paper_2503_10032_gb300 import ddelm
+    return ddelm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _solve(D, p, **kw):
+    import torch
+    s = D.Solver(p, **kw)
+    f = torch.tensor(p.f_int, dtype=torch.float64, device="cuda")
+    g = torch.tensor(p.g_bnd, dtype=torch.float64, device="cuda")
+    c, mu, u, info, rc = s.solve(f, g)
+    torch.cuda.synchronize()
+    return s, mu.cpu().numpy(), u.cpu().numpy(), info, rc
+
+
+SCHEME_CASES = [  # nx, ny, M, n_int, e, eps_rel, R, seed, passes
+    (2, 2, 12, 40, 3, 1e-6, 1, 1, 0),
+    (3, 3, 130, 300, 7, 1e-6, 2, 6, 0),
+    (2, 2, 200, 700, 20, 1e-8, 1, 9, 0),
+    (2, 2, 200, 700, 20, 1e-8, 1, 9, 6),
+    (3, 2, 90, 260, 9, 1e-7, 1, 4, 0),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", SCHEME_CASES)
+def test_fp32_cholesky_scheme(D, case, prec):
+    nx, ny, M, nI, e, eps, R, seed, passes = case
+    p = inputs.small_problem(nx, ny, M=M, n_int=nI, edge_pts=e, n_rhs=R, seed=seed)
+    o = odd.DDELMOracle(p, odd.Options(eps_rel=eps))
+    pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
+    s, mu, u, info, rc = _solve(D, p, eps_rel=eps, tol=1e-11, precision=pr,
+                                setup_scheme=D.DDELM_SCHEME_FP32, setup_passes=passes)
+    assert rc == D.DDELM_OK
+    tol_op = 1e-9 if eps >= 1e-6 else 1e-6
+    for i in range(p.n_sub):
+        L = o.loc[i]
+        G = slice(L.m - L.nG, L.m)
+        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < tol_op
+        assert _rel(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G]) < tol_op
+        if L.nDl:
+            assert _rel(s.inspect(i, 5), L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]) < tol_op
+    ref = odd.solve(p, odd.Options(eps_rel=eps))
+    tol = 1e-8 if eps >= 1e-6 else 1e-7
+    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < tol
+    assert _rel(u, ref["u_eval"]) < tol
+
+
+def test_too_few_fp32_passes_is_reported(D):
+    """One shifted FP32 pass cannot bring a Gram of condition 1e16 near the identity:
+    the setup must fail with a status (the series check or a pivot), never return."""
+    p = inputs.small_problem(2, 2, M=200, n_int=700, edge_pts=20, n_rhs=1, seed=9)
+    with pytest.raises(D.DDELMError):
+        D.Solver(p, eps_rel=1e-8, tol=1e-11, precision=D.DDELM_PREC_MIXED,
+                 setup_scheme=D.DDELM_SCHEME_FP32, setup_passes=1)
+
+
+def test_fp32_scheme_uneven(D):
+    p = inputs.small_uneven_problem(4, 3, n_rhs=2)
+    ref = odd.solve(p, odd.Options(eps_rel=1e-6))
+    s, mu, u, info, rc = _solve(D, p, eps_rel=1e-6, tol=1e-11, precision=D.DDELM_PREC_MIXED,
+                                setup_scheme=D.DDELM_SCHEME_FP32)
+    assert rc == D.DDELM_OK
+    n_pi = ref["oracle"].n_pi
+    assert _rel(mu[n_pi:], ref["mu_delta"]) < 1e-8
+    assert _rel(u, ref["u_eval"]) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_variable_coefficient_operator(D, prec, scheme):
+    """-div(a grad u) = f with a = 1 + 0.5 sin(2 pi x) sin(2 pi y): local operators and solution."""
+    p = inputs.small_problem(3, 3, M=80, n_int=200, edge_pts=6, n_rhs=2, seed=21, op=inputs.OP_DIFFUSION)
+    assert p.op == inputs.OP_DIFFUSION and np.ptp(p.a_int) > 0.5
+    o = odd.DDELMOracle(p, odd.Options(eps_rel=1e-6))
+    pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
+    s, mu, u, info, rc = _solve(D, p, eps_rel=1e-6, tol=1e-11, precision=pr, setup_scheme=scheme,
+                                keep_matrices=True)
+    assert rc == D.DDELM_OK
+    for i in range(p.n_sub):
+        L = o.loc[i]
+        assert _rel(s.inspect(i, 0), L.K) < 1e-13  # assembled K_c with the variable-coefficient rows
+        G = slice(L.m - L.nG, L.m)
+        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < 1e-9
+    ref = odd.solve(p, odd.Options(eps_rel=1e-6))
+    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < 1e-8
+    assert _rel(u, ref["u_eval"]) < 1e-8
