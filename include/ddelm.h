@@ -63,7 +63,7 @@ extern "C" {
 
 #define DDELM_OK 0
 #define DDELM_ERR_INVALID_ARG (-1)    /* bad sizes, null pointers, workspace too small */
-#define DDELM_ERR_RANK_DEFICIENT (-2) /* a local Cholesky pivot was not positive (info: subdomain) */
+#define DDELM_ERR_RANK_DEFICIENT (-2) /* a local factorisation failed: a Cholesky pivot was not positive, or (FP32 scheme) the last factor left max |V^T G V - I| > 1e-5 (info: subdomain) */
 #define DDELM_ERR_NOT_CONVERGED (-3)  /* CG reached max_iters; outputs are still written */
 #define DDELM_ERR_CUDA (-4)           /* a CUDA runtime call failed */
 #define DDELM_ERR_TIMEOUT (-5)        /* a device-side grid barrier gave up waiting */
@@ -198,7 +198,8 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
 /* Per-kernel device timing.  enable = 1 starts recording CUDA events around
  * every launch of the library's kernels (on the launch stream), 0 stops.
  * ms[k] and launches[k] (nullable, DDELM_PROF_CLASSES entries) receive the
- * time and launch count accumulated since the last call with reset = 1, per
+ * time and the number of kernel launches accumulated since the last call with
+ * reset = 1, per
  * kernel class: 0 feature assembly, 1 FP64 GEMM, 2 Cholesky/inverse,
  * 3 persistent CG, 4 other (gathers, coarse assembly, fills), 5 BF16 slicing
  * of tensor-core GEMM operands, 6 tensor-core (tcgen05) GEMM.  Synchronises
@@ -228,6 +229,11 @@ int ddelm_local_lstsq_static(const double *d_K, int m, int M, const double *d_F,
 void ddelm_destroy(ddelm_handle *h);
 
 const char *ddelm_status_string(int status);
+
+/* The CUDA error behind the last DDELM_ERR_CUDA returned on the calling host
+ * thread: error name, message, the failing call and its source location
+ * ("" if none).  The string stays valid until the next failing call. */
+const char *ddelm_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,18 @@
 
 using namespace ddelm;
 
+namespace ddelm {
+std::atomic<long long> g_kernel_launches{0};
+namespace {
+thread_local char g_last_error[512] = "";
+}
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  const char *f = std::strrchr(file, '/');
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) in %s at %s:%d", cudaGetErrorName(e),
+                cudaGetErrorString(e), what, f ? f + 1 : file, line);
+}
+}  // namespace ddelm
+
 struct ddelm_handle {
   Plan plan;
   char *ws = nullptr;
@@ -23,14 +35,18 @@ struct ddelm_handle {
   size_t ev_used = 0;
   double prof_ms[DDELM_PROF_CLASSES] = {};
   long long prof_n[DDELM_PROF_CLASSES] = {};
+  std::vector<long long> ev_kernels;  // kernels launched inside each recorded pair
 };
 
 namespace {
 
-#define CK(x)                                      \
-  do {                                             \
-    cudaError_t e_ = (x);                          \
-    if (e_ != cudaSuccess) return DDELM_ERR_CUDA;  \
+#define CK(x)                                                 \
+  do {                                                        \
+    cudaError_t e_ = (x);                                     \
+    if (e_ != cudaSuccess) {                                  \
+      ::ddelm::record_cuda_error(e_, #x, __FILE__, __LINE__); \
+      return DDELM_ERR_CUDA;                                  \
+    }                                                         \
   } while (0)
 
 double *dbase(ddelm_handle *h) { return reinterpret_cast<double *>(h->ws + h->plan.off_dbl); }
@@ -40,6 +56,7 @@ struct ProfScope {
   ddelm_handle *h;
   cudaStream_t s;
   size_t k = (size_t)-1;
+  long long n0 = 0;
   ProfScope(ddelm_handle *h_, int cls, cudaStream_t s_) : h(h_), s(s_) {
     if (!h->prof) return;
     if (h->ev_used + 2 > h->ev.size()) {
@@ -49,14 +66,19 @@ struct ProfScope {
       h->ev.push_back(b);
       h->ev_cls.push_back(cls);
       h->ev_cls.push_back(cls);
+      h->ev_kernels.push_back(0);
+      h->ev_kernels.push_back(0);
     }
     k = h->ev_used;
     h->ev_used += 2;
     h->ev_cls[k] = cls;
+    n0 = ddelm::g_kernel_launches.load(std::memory_order_relaxed);
     cudaEventRecord(h->ev[k], s);
   }
   ~ProfScope() {
-    if (k != (size_t)-1) cudaEventRecord(h->ev[k + 1], s);
+    if (k == (size_t)-1) return;
+    cudaEventRecord(h->ev[k + 1], s);
+    h->ev_kernels[k] = ddelm::g_kernel_launches.load(std::memory_order_relaxed) - n0;
   }
 };
 
@@ -440,7 +462,7 @@ int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long 
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, h->ev[k], h->ev[k + 1]));
     h->prof_ms[h->ev_cls[k]] += t;
-    h->prof_n[h->ev_cls[k]] += 1;
+    h->prof_n[h->ev_cls[k]] += h->ev_kernels[k];
   }
   h->ev_used = 0;
   for (int c = 0; c < DDELM_PROF_CLASSES; ++c) {
@@ -461,6 +483,8 @@ void ddelm_destroy(ddelm_handle *h) {
   delete h;
 }
 
+const char *ddelm_last_error(void) { return ddelm::g_last_error; }
+
 const char *ddelm_status_string(int status) {
   switch (status) {
     case DDELM_OK:
@@ -468,7 +492,7 @@ const char *ddelm_status_string(int status) {
     case DDELM_ERR_INVALID_ARG:
       return "invalid argument";
     case DDELM_ERR_RANK_DEFICIENT:
-      return "a local factorisation met a non-positive pivot";
+      return "a local factorisation failed (a non-positive pivot, or an FP32 factor too far from V^T G V = I)";
     case DDELM_ERR_NOT_CONVERGED:
       return "CG reached max_iters before the tolerance";
     case DDELM_ERR_CUDA:

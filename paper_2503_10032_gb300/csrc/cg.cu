@@ -791,8 +791,8 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   const int grid = nsm < 2048 ? nsm : 2048;
   void *args[] = {&c};
-  if (p.n_rhs == 1)
-    return cudaLaunchCooperativeKernel((const void *)cg_kernel<1>, grid, CG_THREADS, args, 0, s);
+  DDELM_COUNT_LAUNCH();
+  if (p.n_rhs == 1) return cudaLaunchCooperativeKernel((const void *)cg_kernel<1>, grid, CG_THREADS, args, 0, s);
   return cudaLaunchCooperativeKernel((const void *)cg_kernel<16>, grid, CG_THREADS, args, 0, s);
 }
 

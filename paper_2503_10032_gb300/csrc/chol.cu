@@ -361,15 +361,15 @@ __global__ void adjoint_scatter_g_kernel(const SubDev *__restrict__ subs, const 
 
 cudaError_t launch_adjoint_init(const Plan &p, void *ws, const double *grad_c, const double *grad_u, cudaStream_t s) {
   char *base = static_cast<char *>(ws);
-  adjoint_init_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
-                                              reinterpret_cast<double *>(base + p.off_dbl), grad_c, grad_u, p.n_rhs);
+  { adjoint_init_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
+                                              reinterpret_cast<double *>(base + p.off_dbl), grad_c, grad_u, p.n_rhs); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_c_to_y(const Plan &p, void *ws, cudaStream_t s) {
   char *base = static_cast<char *>(ws);
-  copy_c_to_y_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
-                                             reinterpret_cast<double *>(base + p.off_dbl), p.n_rhs);
+  { copy_c_to_y_kernel<<<p.n_sub, 256, 0, s>>>(reinterpret_cast<const SubDev *>(base + p.off_subs),
+                                             reinterpret_cast<double *>(base + p.off_dbl), p.n_rhs); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -377,12 +377,12 @@ cudaError_t launch_adjoint_scatter(const Plan &p, void *ws, double *grad_f, doub
   char *base = static_cast<char *>(ws);
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const double *db = reinterpret_cast<const double *>(base + p.off_dbl);
-  if (grad_f && p.sz.sum_int > 0) adjoint_scatter_f_kernel<<<p.n_sub, 256, 0, s>>>(subs, db, grad_f, p.n_rhs);
+  if (grad_f && p.sz.sum_int > 0) { adjoint_scatter_f_kernel<<<p.n_sub, 256, 0, s>>>(subs, db, grad_f, p.n_rhs); DDELM_COUNT_LAUNCH(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (grad_g && p.sz.n_bnd > 0)
-    adjoint_scatter_g_kernel<<<64, 256, 0, s>>>(subs, reinterpret_cast<const int *>(base + p.off_ints), db, grad_g,
-                                                p.sz.n_bnd, p.o_bnd_own, p.n_rhs);
+    { adjoint_scatter_g_kernel<<<64, 256, 0, s>>>(subs, reinterpret_cast<const int *>(base + p.off_ints), db, grad_g,
+                                                p.sz.n_bnd, p.o_bnd_own, p.n_rhs); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -402,9 +402,9 @@ cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cuda
     if (e != cudaSuccess) return e;
   }
   if (f32)
-    chol_inv32_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+    { chol_inv32_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
   else
-    chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status);
+    { chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -413,7 +413,7 @@ cudaError_t launch_matop_phase(const Plan &p, const MatopPhase &ph, void *ws, cu
   char *base = static_cast<char *>(ws);
   const MatopDesc *descs = reinterpret_cast<const MatopDesc *>(base + p.off_mdesc) + ph.desc0;
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  matop_kernel<<<dim3(16, ph.ndesc), 256, 0, s>>>(descs, db, reinterpret_cast<int *>(db + p.o_status));
+  { matop_kernel<<<dim3(16, ph.ndesc), 256, 0, s>>>(descs, db, reinterpret_cast<int *>(db + p.o_status)); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -424,7 +424,7 @@ cudaError_t launch_chol_table(const CholDesc *descs, int n, int maxM, double *db
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  chol_inv_kernel<<<n, CT, smem, s>>>(descs, db, status);
+  { chol_inv_kernel<<<n, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -434,13 +434,13 @@ cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s) {
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  coarse_assembly_kernel<<<1, 32, 0, s>>>(subs, ints, db, p.n_sub, p.n_pi, p.o_Dpp, p.o_Spi);
+  { coarse_assembly_kernel<<<1, 32, 0, s>>>(subs, ints, db, p.n_sub, p.n_pi, p.o_Dpp, p.o_Spi); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  fill_identity_kernel<<<64, 256, 0, s>>>(dst, n, diag);
+  { fill_identity_kernel<<<64, 256, 0, s>>>(dst, n, diag); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -450,7 +450,7 @@ cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, cons
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  gather_rhs_kernel<<<p.n_sub, 256, 0, s>>>(subs, ints, db, f_int, g_bnd, p.n_rhs);
+  { gather_rhs_kernel<<<p.n_sub, 256, 0, s>>>(subs, ints, db, f_int, g_bnd, p.n_rhs); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -15,6 +16,12 @@
 #include "ozaki.h"
 
 namespace ddelm {
+
+// every kernel launch of the library (the profiler attributes them to classes)
+extern std::atomic<long long> g_kernel_launches;
+#define DDELM_COUNT_LAUNCH() ::ddelm::g_kernel_launches.fetch_add(1, std::memory_order_relaxed)
+// keeps the message ddelm_last_error() returns (per host thread)
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
 // ---------------------------------------------------------------- rows
 // Rows of the local matrices other than the interior collocation rows.

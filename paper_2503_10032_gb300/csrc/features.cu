@@ -112,12 +112,12 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
   for (int i = s0; i < s1; ++i) max_nI = std::max(max_nI, p.subs[i].nI);
   if (max_nI > 0) {
     dim3 grid((max_nI + 7) / 8, s1 - s0);
-    interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint, p.op);
+    { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
   }
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
-  if (r1 > r0) special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b);
+  if (r1 > r0) { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
   const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
-  if (wave == 0 && e1 > e0) special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_b);
+  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -183,9 +183,9 @@ cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cuda
   const GemmTile *tiles = reinterpret_cast<const GemmTile *>(base + p.off_gtile) + ph.tile0;
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
   if (ph.skinny)
-    gemm_skinny_kernel<<<ph.ntile, 256, 0, s>>>(descs, tiles, db);
+    { gemm_skinny_kernel<<<ph.ntile, 256, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
-    gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db);
+    { gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -194,9 +194,9 @@ cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int 
                               cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (skinny)
-    gemm_skinny_kernel<<<ntiles, 256, 0, s>>>(descs, tiles, db);
+    { gemm_skinny_kernel<<<ntiles, 256, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
-    gemm_f64_kernel<<<ntiles, NT, 0, s>>>(descs, tiles, db);
+    { gemm_f64_kernel<<<ntiles, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -17,10 +17,11 @@
 //   warp 0     TMA producer: 128x64 BF16 boxes of A and B slices, 128B swizzle,
 //              6-stage shared-memory ring guarded by mbarriers;
 //   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
-//              (M=128, N=128, K=16, both operands K-major), two FP32
+//              (M=128, N=128, K=16, both operands K-major), four FP32
 //              accumulators of 128 TMEM columns each, committed per level/chunk;
 //   warps 2-9  epilogue: tcgen05.ld of their lane quadrant and column half,
-//              FP64 accumulation in registers, scaled store of C.
+//              two level sums at a time combined exactly in int32, FP64
+//              accumulation in registers, scaled store of C.
 // Every wait is bounded (2 s); on a timeout the CTA records an error, waits for
 // its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -39,7 +40,8 @@ constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int STAGES = 6;
 constexpr int STAGE_BYTES = (BM + BN) * BK * 2;  // 32 KB
 constexpr int OZ_THREADS = 320;
-constexpr unsigned TMEM_COLS = 256;
+constexpr int NACC = 4;                // FP32 level accumulators of 128 TMEM columns
+constexpr unsigned TMEM_COLS = 512;
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -125,6 +127,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -154,7 +167,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2],
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[NACC], bar_acc_empty[NACC],
       bar_drain;
   __shared__ uint32_t tmem_base_sh;
 
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NACC; ++b) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 256);
     }
@@ -249,8 +262,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int g = 0; g < ngroups && ok; ++g) {
-        const int b = g & 1;
-        if (g >= 2 && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((g >> 1) - 1) & 1u, err)) break;
+        const int b = g % NACC;
+        if (g >= NACC && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((g / NACC) - 1) & 1u, err)) break;
         tc_fence_after();
         const int l = S - 1 - g / nchunk, c = g % nchunk;
         int p0;
@@ -293,6 +306,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: warps 2..9
+    // Groups are taken in pairs (two TMEM accumulators; the MMA issuer fills
+    // the other two meanwhile).  A pair is either two k-chunks of one level or
+    // level l+1 followed by level l; in both cases x = L_a + (1 or 64) L_b is an
+    // exact int32 (|L| < 2^23.6), so one FP64 FMA per pair combines the levels
+    // (the FP64 pipe of this GPU does 4 flop/clk/SM).
     const int ew = warp - 2;                  // 0..7
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
     const int half = ew >> 2;                 // column half
@@ -301,25 +319,39 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0.0;
     bool ok = true;
-    for (int g = 0; g < ngroups; ++g) {
-      const int b = g & 1;
-      if (!mbar_wait(smem_u32(&bar_acc_full[b]), (g >> 1) & 1u, err)) {
+    for (int g = 0; g < ngroups && ok; g += 2) {
+      const bool two = g + 1 < ngroups;
+      const int b0 = g % NACC, b1 = (g + 1) % NACC;
+      if (!mbar_wait(smem_u32(&bar_acc_full[b0]), (g / NACC) & 1u, err) ||
+          (two && !mbar_wait(smem_u32(&bar_acc_full[b1]), ((g + 1) / NACC) & 1u, err))) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const int l = S - 1 - g / nchunk;
-      const double scale = ldexp(1.0, -6 * (l + 2));
-      const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + half * 64);
+      const int l0 = S - 1 - g / nchunk;
+      const int l1 = two ? S - 1 - (g + 1) / nchunk : l0;
+      const int mul = (l1 == l0) ? 1 : 64;  // l1 = l0 - 1 otherwise
+      const double scale = ldexp(1.0, -6 * (l0 + 2));
+      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float v[16];
-        tmem_ld16(ta + c0, v);
+      for (int c0 = 0; c0 < 64; c0 += 8) {
+        float v0[8], v1[8];
+        tmem_ld8(lane_base + (uint32_t)(b0 * BN) + c0, v0);
+        if (two) {
+          tmem_ld8(lane_base + (uint32_t)(b1 * BN) + c0, v1);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] = fma(scale, (double)v[j], acc[c0 + j]);
+          for (int j = 0; j < 8; ++j) v1[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int x = __float2int_rn(v0[j]) + mul * __float2int_rn(v1[j]);
+          acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
+        }
       }
       tc_fence_before();
-      mbar_arrive(smem_u32(&bar_acc_empty[b]));
+      mbar_arrive(smem_u32(&bar_acc_empty[b0]));
+      if (two) mbar_arrive(smem_u32(&bar_acc_empty[b1]));
     }
     if (ok) {
       const int gi = tl.tm * BM + row;
@@ -469,10 +501,10 @@ cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
   const SliceDesc *sd = reinterpret_cast<const SliceDesc *>(base + p.off_sdesc) + ph.slice0;
   __nv_bfloat16 *slices = reinterpret_cast<__nv_bfloat16 *>(base + p.off_slices);
-  slice_scale_kernel<<<dim3(16, ph.nslice), 256, 0, s>>>(sd, db);
+  { slice_scale_kernel<<<dim3(16, ph.nslice), 256, 0, s>>>(sd, db); DDELM_COUNT_LAUNCH(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  slice_write_kernel<<<dim3(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice), 256, 0, s>>>(sd, db, slices);
+  { slice_write_kernel<<<dim3(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice), 256, 0, s>>>(sd, db, slices); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -487,7 +519,7 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
   const size_t smem = STAGES * STAGE_BYTES + 1024;
   cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  ozaki_gemm_kernel<<<ph.ntile, OZ_THREADS, smem, s>>>(od, ot, maps, db, err);
+  { ozaki_gemm_kernel<<<ph.ntile, OZ_THREADS, smem, s>>>(od, ot, maps, db, err); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

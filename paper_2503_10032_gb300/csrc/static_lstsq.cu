@@ -156,9 +156,13 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
   double *db = nullptr;
   int rc = scratch_base(&db);
   if (rc != DDELM_OK) return rc;
-#define CKS(x)                                     \
-  do {                                             \
-    if ((x) != cudaSuccess) return DDELM_ERR_CUDA; \
+#define CKS(x)                                         \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) {                           \
+      record_cuda_error(e_, #x, __FILE__, __LINE__);   \
+      return DDELM_ERR_CUDA;                           \
+    }                                                  \
   } while (0)
   char *base = reinterpret_cast<char *>(db);
   CKS(cudaMemcpyAsync(base, tab.data(), bytes_tab, cudaMemcpyHostToDevice, s));

@@ -65,7 +65,7 @@ class ddelm_solve_info(ctypes.Structure):
 
 EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm_backward",
            "ddelm_inspect", "ddelm_profile", "ddelm_local_lstsq_static", "ddelm_destroy",
-           "ddelm_status_string")
+           "ddelm_status_string", "ddelm_last_error")
 DDELM_STATIC_SCRATCH_DOUBLES = 1048576
 DDELM_SCHEME_AUTO, DDELM_SCHEME_FP64CQR3, DDELM_SCHEME_FP32 = 0, 1, 2
 DDELM_PROF_CLASSES = 8
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.ddelm_destroy.restype = None
     lib.ddelm_status_string.argtypes = [ctypes.c_int]
     lib.ddelm_status_string.restype = ctypes.c_char_p
+    lib.ddelm_last_error.argtypes = []
+    lib.ddelm_last_error.restype = ctypes.c_char_p
     return lib
 
 
@@ -110,7 +112,10 @@ _lib = load_library()
 
 class DDELMError(RuntimeError):
     def __init__(self, status, what=""):
-        super().__init__(f"{what}: {ddelm_status_string(status)} ({status})")
+        msg = f"{what}: {ddelm_status_string(status)} ({status})"
+        if status == DDELM_ERR_CUDA:
+            msg += f": {_lib.ddelm_last_error().decode()}"
+        super().__init__(msg)
         self.status = status
 
 
