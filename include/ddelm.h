@@ -99,6 +99,9 @@ typedef struct ddelm_options {
   int setup_wave;         /* subdomains whose setup scratch coexists (0: as many as fit 48 GiB) */
   int setup_scheme;       /* factorisation of [K; eps I]: DDELM_SCHEME_* (0: automatic) */
   int setup_passes;       /* DDELM_SCHEME_FP32: shifted FP32 passes before the last (0: automatic) */
+  int disable_graphs;     /* 1: issue every launch directly; 0: the setup (from the first
+                             ddelm_refactor) and the solve (from a handle's second ddelm_solve)
+                             are captured once as CUDA graphs and replayed */
 } ddelm_options;
 
 typedef struct ddelm_problem {
@@ -187,9 +190,11 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
  * (sub ignored), 7 the four sizes {m, M, nG, nDl} as doubles, 8 the algorithmic
  * flop counts {setup GEMMs, setup Cholesky + inverses, solve GEMMs, tensor-core
  * flops of the MIXED setup, FP64-engine setup flops left in MIXED, the FP32 part
- * of the Cholesky flops} (sub ignored, out_len >= 5; the sixth is written when
- * out_len >= 6), 9 the setup plan {scheme, Cholesky passes before the last,
- * setup waves, subdomains per wave} (sub ignored).  Blocks 0-2 are
+ * of the Cholesky flops, HBM bytes of the BF16 slicing} (sub ignored,
+ * out_len >= 5; entries past out_len are not written), 9 the setup plan
+ * {scheme, Cholesky passes before the last, setup waves, subdomains per wave,
+ * setup graph captured, solve graph captured} (sub ignored, out_len >= 4; the
+ * last two when out_len >= 6).  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */

@@ -3,6 +3,7 @@
 // matrix, local operators, coarse problem), the solve sequence and
 // inspection.  The library allocates no device memory: every buffer lives in
 // the caller's workspace.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -28,6 +29,10 @@ struct ddelm_handle {
   Plan plan;
   char *ws = nullptr;
   size_t ws_bytes = 0;
+  // CUDA graphs of the setup and of the solve sequence (captured on second use)
+  cudaGraphExec_t setup_exec = nullptr, solve_exec = nullptr;
+  long long solves = 0;
+  bool graph_off = false;  // capture unavailable (or disabled by the options)
   // profiling: event pairs around launches, reduced on ddelm_profile
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -136,7 +141,63 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
 // Assembly, shifted CholeskyQR of [K; eps I] and [K-bar; eps-bar I] (the
 // plan's step list, wave by wave), local operators and the coarse problem, all
 // from workspace-resident data.
-int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
+// Runs enqueue() on s, through a CUDA graph captured on first use (*exec), so
+// that a repeated sequence of launches costs one graph launch.  Profiling
+// (events around launches), the legacy default stream, or a failed capture run
+// the sequence directly.
+template <class F>
+int run_graph(ddelm_handle *h, cudaStream_t s, cudaGraphExec_t *exec, F enqueue) {
+  if (!s || h->prof || h->graph_off) return enqueue();
+  if (!*exec) {
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      h->graph_off = true;
+      return enqueue();
+    }
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    cudaGraphExec_t x = nullptr;
+    const bool ok = rc == DDELM_OK && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      (void)cudaGetLastError();
+      h->graph_off = true;
+      return enqueue();
+    }
+    *exec = x;
+  }
+  CK(cudaGraphLaunch(*exec, s));
+  return DDELM_OK;
+}
+
+int enqueue_setup(ddelm_handle *h, cudaStream_t s);
+
+// capture: false for a one-off setup (capturing would only add its cost)
+int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub, bool capture) {
+  Plan &p = h->plan;
+  double *db = dbase(h);
+  {
+    const int rc = capture ? run_graph(h, s, &h->setup_exec, [&] { return enqueue_setup(h, s); })
+                           : enqueue_setup(h, s);
+    if (rc != DDELM_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(s));
+  int oz_err = 0;
+  CK(cudaMemcpy(&oz_err, db + p.o_status + 2 * p.n_sub + 32, sizeof(int), cudaMemcpyDeviceToHost));
+  if (oz_err) return DDELM_ERR_TIMEOUT;
+  std::vector<int> st(2 * (size_t)p.n_sub + 1);
+  CK(cudaMemcpy(st.data(), db + p.o_status, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < st.size(); ++k)
+    if (st[k]) {
+      if (info_sub) *info_sub = int(k / 2);
+      return DDELM_ERR_RANK_DEFICIENT;
+    }
+  return DDELM_OK;
+}
+
+// Every launch and copy of the setup, in stream order (no host synchronisation).
+int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
   Plan &p = h->plan;
   double *db = dbase(h);
   CK(cudaMemsetAsync(db + p.o_status, 0, (4 * (size_t)p.n_sub + 64) * 8, s));
@@ -199,17 +260,6 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub) {
     LAUNCH(PC_OTHER, launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
     LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 3], h->ws, s));
   }
-  CK(cudaStreamSynchronize(s));
-  int oz_err = 0;
-  CK(cudaMemcpy(&oz_err, db + p.o_status + 2 * p.n_sub + 32, sizeof(int), cudaMemcpyDeviceToHost));
-  if (oz_err) return DDELM_ERR_TIMEOUT;
-  std::vector<int> st(2 * (size_t)p.n_sub + 1);
-  CK(cudaMemcpy(st.data(), db + p.o_status, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  for (size_t k = 0; k < st.size(); ++k)
-    if (st[k]) {
-      if (info_sub) *info_sub = int(k / 2);
-      return DDELM_ERR_RANK_DEFICIENT;
-    }
   return DDELM_OK;
 }
 
@@ -239,6 +289,7 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
     delete h;
     return rc;
   }
+  h->graph_off = prob->opt.disable_graphs != 0;
   if (workspace_bytes < h->plan.bytes_total) {
     delete h;
     return DDELM_ERR_INVALID_ARG;
@@ -246,9 +297,9 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
   h->ws = static_cast<char *>(d_workspace);
   h->ws_bytes = workspace_bytes;
   rc = upload(h, prob, static_cast<cudaStream_t>(stream));
-  if (rc == DDELM_OK) rc = compute_setup(h, static_cast<cudaStream_t>(stream), info_sub);
+  if (rc == DDELM_OK) rc = compute_setup(h, static_cast<cudaStream_t>(stream), info_sub, false);
   if (rc != DDELM_OK && rc != DDELM_ERR_RANK_DEFICIENT) {
-    delete h;
+    ddelm_destroy(h);
     return rc;
   }
   *out = h;
@@ -258,7 +309,7 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
 int ddelm_refactor(ddelm_handle *h, void *stream, int *info_sub) {
   if (!h) return DDELM_ERR_INVALID_ARG;
   if (info_sub) *info_sub = -1;
-  return compute_setup(h, static_cast<cudaStream_t>(stream), info_sub);
+  return compute_setup(h, static_cast<cudaStream_t>(stream), info_sub, true);
 }
 
 int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, double *d_c, double *d_mu,
@@ -274,27 +325,43 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
   }
-  LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, d_f_int, d_g_bnd, s));
-  const auto &G = p.setup_gemm;
-  for (int q = 0; q < 4; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + q], h->ws, s));
-  // barrier words and error flag
-  CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
-  CgArgs a;
-  a.mu_out = d_mu;
-  a.c_out = d_c;
-  a.max_iters = p.opt.max_iters;
-  a.tol = p.opt.tol;
-  a.theta = p.opt.theta;
-  LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
-  if (p.sz.sum_eval > 0) {
-    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + 4], h->ws, s));
-    if (d_u_eval) {
+  // the caller's data in, through the staging buffers (fixed addresses)
+  const int R = p.n_rhs;
+  if (p.sz.sum_int > 0) CK(cudaMemcpyAsync(db + p.o_fin, d_f_int, (size_t)p.sz.sum_int * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (p.sz.n_bnd > 0) CK(cudaMemcpyAsync(db + p.o_gin, d_g_bnd, (size_t)p.sz.n_bnd * R * 8, cudaMemcpyDeviceToDevice, s));
+  auto enqueue = [&]() -> int {
+    LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, db + p.o_fin, db + p.o_gin, s));
+    const auto &G = p.setup_gemm;
+    for (int q = 0; q < 4; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + q], h->ws, s));
+    // barrier words and error flag
+    CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
+    CgArgs a;
+    a.mu_out = db + p.o_muout;
+    a.c_out = db + p.o_cout;
+    a.max_iters = p.opt.max_iters;
+    a.tol = p.opt.tol;
+    a.theta = p.opt.theta;
+    LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
+    if (p.sz.sum_eval > 0) {
+      LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + 4], h->ws, s));
       for (const auto &d : p.subs)
         if (d.nE > 0)
-          CK(cudaMemcpyAsync(d_u_eval + d.eval_off * p.n_rhs, db + d.oU, (size_t)d.nE * p.n_rhs * 8,
+          CK(cudaMemcpyAsync(db + p.o_uout + d.eval_off * R, db + d.oU, (size_t)d.nE * R * 8,
                              cudaMemcpyDeviceToDevice, s));
     }
+    return DDELM_OK;
+  };
+  {
+    // a handle's first solve runs directly; later ones replay one captured graph
+    const int rc0 = h->solves++ == 0 ? enqueue() : run_graph(h, s, &h->solve_exec, enqueue);
+    if (rc0 != DDELM_OK) return rc0;
   }
+  // results out
+  if (d_c) CK(cudaMemcpyAsync(d_c, db + p.o_cout, (size_t)p.sz.sum_M * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (d_mu)
+    CK(cudaMemcpyAsync(d_mu, db + p.o_muout, (size_t)(p.n_pi + p.n_dl) * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (d_u_eval && p.sz.sum_eval > 0)
+    CK(cudaMemcpyAsync(d_u_eval, db + p.o_uout, (size_t)p.sz.sum_eval * R * 8, cudaMemcpyDeviceToDevice, s));
   int rc = DDELM_OK;
   double hinfo[40];
   int herr = 0;
@@ -429,6 +496,7 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       host_out[3] = p.oz_flops;
       host_out[4] = p.mixed ? fleft : fs;
       if (out_len >= 6) host_out[5] = p.chol_flops32;
+      if (out_len >= 7) host_out[6] = p.slice_bytes;
       return DDELM_OK;
     }
     case 9: {
@@ -437,6 +505,10 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       host_out[1] = p.n_pass;
       host_out[2] = p.n_waves;
       host_out[3] = p.wave;
+      if (out_len >= 6) {
+        host_out[4] = h->setup_exec ? 1.0 : 0.0;
+        host_out[5] = h->solve_exec ? 1.0 : 0.0;
+      }
       return DDELM_OK;
     }
     case 7: {
@@ -480,6 +552,8 @@ int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long 
 void ddelm_destroy(ddelm_handle *h) {
   if (!h) return;
   for (auto e : h->ev) cudaEventDestroy(e);
+  if (h->setup_exec) cudaGraphExecDestroy(h->setup_exec);
+  if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
   delete h;
 }
 

@@ -166,6 +166,7 @@ struct Plan {
   long long n_dbl = 0;     // doubles in the region
   long long o_w = 0, o_b = 0, o_xint = 0, o_aint = 0, o_gaint = 0;  // problem data
   long long o_status = 0;  // int status slots (in ints region? kept as doubles)
+  long long o_fin = 0, o_gin = 0, o_cout = 0, o_muout = 0, o_uout = 0;  // solve staging
   // coarse
   int n_pi = 0, n_dl = 0;
   long long o_Dpp = 0, o_Spi = 0, o_Vpi = 0, o_Sinv = 0, o_C1 = 0, o_C2 = 0, o_C3 = 0, o_SpiR = 0;
@@ -205,6 +206,7 @@ struct Plan {
   size_t off_sdesc = 0, off_odesc = 0, off_otile = 0, off_tmaps = 0, off_slices = 0;
   size_t bytes_slices = 0;
   double oz_flops = 0.0;          // BF16 tensor flops of one setup
+  double slice_bytes = 0.0;       // HBM bytes of the slicing kernels of one setup
   std::string err;
 };
 

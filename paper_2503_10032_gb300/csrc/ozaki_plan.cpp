@@ -65,6 +65,8 @@ int build_mixed(Plan &P, long long &cur) {
       s.S = S;
       s.out = elem;
       elem += (long long)S * s.Rpad * s.Kpad;
+      // algorithmic bytes of the slicing: the source read twice (scale, digits), the slices written
+      P.slice_bytes += 16.0 * R * (double)K + 2.0 * S * (double)s.Rpad * s.Kpad;
       s.scale = scl;  // relative; fixed below
       scl += rup(R, 32);
       int idx = int(P.sdesc.size());

@@ -274,6 +274,13 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.o_cg = take(12 * nd_ * nR + 14 * np * nR + 2048 * 32 + 128);
   P.o_loc = take(9LL * sum_nG * nR);
   P.o_status = take(4 * n_sub + 64);
+  // solve-call staging: the caller's f, g in, c, mu, u out (fixed addresses, so
+  // one captured graph serves every call)
+  P.o_fin = take(sumI * R);
+  P.o_gin = take((long long)nb * R);
+  P.o_cout = take(sumM * R);
+  P.o_muout = take((long long)(n_pi + nd) * R);
+  P.o_uout = take(sumE * R);
   // inspection copies
   if (P.keep) {
     P.o_keepX = cur;

@@ -36,7 +36,8 @@ class ddelm_options(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("use_change_of_vars", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("keep_matrices", ctypes.c_int), ("setup_wave", ctypes.c_int),
-                ("setup_scheme", ctypes.c_int), ("setup_passes", ctypes.c_int)]
+                ("setup_scheme", ctypes.c_int), ("setup_passes", ctypes.c_int),
+                ("disable_graphs", ctypes.c_int)]
 
 
 class ddelm_problem(ctypes.Structure):
@@ -125,10 +126,10 @@ def ddelm_status_string(status: int) -> str:
 
 def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change_of_vars=True,
                  precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False, setup_wave=0,
-                 setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0):
+                 setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0, graphs=True):
     return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
                          max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
-                         int(setup_passes))
+                         int(setup_passes), int(not graphs))
 
 
 class ProblemArgs:
