@@ -109,6 +109,7 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   put(tab, p.off_gtile, p.gtile);
   put(tab, p.off_cdesc, p.cdesc);
   put(tab, p.off_mdesc, p.mdesc);
+  put(tab, p.off_conv, p.conv);
   put(tab, p.off_ints, p.ints);
   put(tab, p.off_sdesc, p.sdesc);
   put(tab, p.off_odesc, p.odesc);
@@ -260,6 +261,7 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
     LAUNCH(PC_OTHER, launch_fill_identity(db + p.o_C2, p.n_pi, 1.0, s));
     LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_coarse + 3], h->ws, s));
   }
+  if (p.mixed) LAUNCH(PC_OTHER, launch_convert_f32(p, h->ws, s));  // operators of the inner FP32 CG
   return DDELM_OK;
 }
 
@@ -341,6 +343,7 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
     a.max_iters = p.opt.max_iters;
     a.tol = p.opt.tol;
     a.theta = p.opt.theta;
+    a.max_refine = p.opt.max_refine;
     LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
     if (p.sz.sum_eval > 0) {
       LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + 4], h->ws, s));
@@ -380,7 +383,7 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     info->iterations = iters;
-    info->refinements = 0;
+    info->refinements = p.mixed ? int(hinfo[33]) : 0;
     info->rel_residual = resmax;
     info->ms_total = ms;
     cudaEventDestroy(e0);

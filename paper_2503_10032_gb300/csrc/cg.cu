@@ -28,6 +28,10 @@ constexpr int CG_WARPS = CG_THREADS / 32;
 enum DlVec { V_MU = 0, V_RES, V_PD, V_Q, V_V, V_BKB, V_PV, V_W, V_B, V_TMP, N_DLVEC = 12 };
 enum PiVec { P_PSI = 0, P_RA, P_MPI, P_G, P_RNU, P_NU, P_DNU, P_DPI, P_PPI, P_MPF, P_GF, P_PSI2, P_S2, P_MPIF, N_PIVEC = 14 };
 enum Slab { S_H1 = 0, S_H2, S_VL, S_BL, S_TL, S_T2L, S_ZL, S_YL, N_SLAB = 9 };
+// inner FP32 CG (MIXED): Delta vectors, Pi vectors, local slabs
+enum FDl { F_P0 = 0, F_P1, F_Q, F_R, F_D, F_SPARE, N_FDL = 6 };
+enum FPv { FP_PSI = 0, FP_RA, FP_MPI, FP_G, FP_RNU, FP_NU, FP_DNU, N_FPV = 7 };
+enum FSlab { FS_H1 = 0, FS_H2, FS_VL, FS_BL, FS_TL, FS_T2L, FS_VH, FS_ZL, N_FSLAB = 8 };
 
 struct Ctx {
   const SubDev *subs;
@@ -36,6 +40,7 @@ struct Ctx {
   int n_sub, n_pi, n_dl, R;
   int o_pi_own, o_dl_own;
   int o_tpi, n_tpi, o_tdl, n_tdl, o_tg, n_tg, o_tc, n_tc;
+  int o_dl_rows, o_gam_rows;
   long long o_Sinv, o_C1, o_C2, o_C3;
   double *dl[N_DLVEC];
   double *pv[N_PIVEC];
@@ -46,8 +51,15 @@ struct Ctx {
   double theta, tol;
   int max_iters;
   double *mu_out, *c_out;
-  double *info;  // [0] iterations, [1..16] true residuals, [17..32] |b|
+  double *info;  // [0] iterations, [1..16] true residuals, [17..32] |b|, [33] refinement sweeps
   int mode;      // 0 forward solve, 1 adjoint
+  // MIXED: FP32 operators and inner-CG vectors (null in FP64 precision)
+  float *fb;
+  long long f_Sinv, f_C1, f_C2, f_C3;
+  float *fdl[N_FDL];
+  float *fpv[N_FPV];
+  float *fslab[N_FSLAB];
+  int max_refine;
 };
 
 __device__ __forceinline__ double ldg_cg(const double *p) { return __ldcg(p); }
@@ -532,6 +544,451 @@ __device__ int cg_solve(const Ctx &c, double *s_bn) {
   return it;
 }
 
+// ================================================================ MIXED
+// Inner FP32 CG on S_theta (the FP32 copies of Lambda, Lambda^T, Psi, Phi,
+// Phi^T and of the coarse matrices), organised per subdomain: a CTA stages the
+// subdomain's local vector (gathered from the owners' slab rows) in shared
+// memory and its warps take the rows of the local operator, so that the
+// interface gathers cost no extra phase.  FP64 iterative refinement around it
+// (residuals of the FP64 operator) recovers the FP64 solution.
+
+constexpr int MAXG = 256;   // largest local interface (nG) staged in shared memory
+
+// the staged local vector [nG][R] (then 64 floats of Pi-row data); one buffer
+// for every per-subdomain phase (they never overlap within a CTA)
+__shared__ float sh_stage[MAXG * 16 + 64];
+
+__device__ __forceinline__ float *fslab_row(const Ctx &c, int sl, const SubDev &d, int a) {
+  return c.fslab[sl] + (long long)(d.loc_off + a) * c.R;
+}
+
+// Row product with a shared-memory vector: sum_j m[j] xs[j*R + k].  RC == 1:
+// lanes over j, the result in every lane; RC == 16: lane = k + 16 h takes the
+// j of parity h, the result for column k in lanes k and k + 16.
+template <int RC>
+__device__ __forceinline__ float row_dot(const float *__restrict__ m, int n, const float *xs, int R) {
+  const int lane = threadIdx.x & 31;
+  float a = 0.f;
+  if (RC == 1) {
+    for (int j = lane; j < n; j += 32) a = fmaf(__ldg(m + j), xs[j], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  } else {
+    const int k = lane & 15, h = lane >> 4;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const float mv = (j0 + lane < n) ? __ldg(m + j0 + lane) : 0.f;
+#pragma unroll 4
+      for (int jj = 0; jj < 32; jj += 2) {
+        const float mm = __shfl_sync(0xffffffffu, mv, jj + h);
+        const int j = j0 + jj + h;
+        if (j < n && k < R) a = fmaf(mm, xs[j * R + k], a);
+      }
+    }
+    a += __shfl_xor_sync(0xffffffffu, a, 16);
+  }
+  return a;
+}
+
+// the lane that stores column k of a row_dot result (k < R)
+template <int RC>
+__device__ __forceinline__ bool row_writer(int R, int &k) {
+  const int lane = threadIdx.x & 31;
+  if (RC == 1) {
+    k = 0;
+    return lane == 0;
+  }
+  k = lane;
+  return lane < R;
+}
+
+// work items of a per-subdomain phase: (subdomain, row chunk)
+__device__ __forceinline__ int n_chunks(const Ctx &c) {
+  int ch = (2 * (int)gridDim.x + c.n_sub - 1) / c.n_sub;
+  return ch < 1 ? 1 : (ch > 8 ? 8 : ch);
+}
+
+// gathered slab sum at the Delta point of local interface row (d, a): the two
+// owners' rows (column k)
+__device__ __forceinline__ float gam_pair(const Ctx &c, int sl, const SubDev &d, int a, int k) {
+  const int2 rw = *reinterpret_cast<const int2 *>(c.ints + c.o_gam_rows + 2 * (d.loc_off + a));
+  return __ldcg(c.fslab[sl] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[sl] + (long long)rw.y * c.R + k);
+}
+
+// P1: H1 = Lambda_{Pi,Delta} x^, H2 = Psi_{Pi,Delta} x^ (the few Pi rows)
+template <int RC>
+__device__ void f_pi_rows(const Ctx &c, const float *x) {
+  float *xs = sh_stage;
+  const int R = c.R, w = threadIdx.x >> 5;
+  for (int s = blockIdx.x; s < c.n_sub; s += gridDim.x) {
+    const SubDev d = c.subs[s];
+    if (d.nPi == 0) continue;
+    const int *gdl = c.ints + d.gdl_off;
+    for (int e = threadIdx.x; e < d.nDl * R; e += blockDim.x) xs[e] = __ldcg(x + (long long)gdl[e / R] * R + e % R);
+    __syncthreads();
+    const float *lam = c.fb + d.oLam32, *psi = c.fb + d.oPsi32;
+    for (int t = w; t < 2 * d.nPi; t += CG_WARPS) {
+      const int a = t >> 1;
+      const float *row = ((t & 1) ? psi : lam) + (long long)a * d.nG + d.nPi;
+      const float v = row_dot<RC>(row, d.nDl, xs, R);
+      int k;
+      if (row_writer<RC>(R, k)) fslab_row(c, (t & 1) ? FS_H2 : FS_H1, d, a)[k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Pi gathers: out1 = s1 sum slab1, out2 = s2 sum slab2
+__device__ void f_pi_gather(const Ctx &c, int sl1, float s1, float *out1, int sl2, float s2, float *out2) {
+  for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
+    const int p = e / c.R, k = e % c.R;
+    float a1 = 0.f, a2 = 0.f;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      a1 += __ldcg(fslab_row(c, sl1, d, a) + k);
+      if (out2) a2 += __ldcg(fslab_row(c, sl2, d, a) + k);
+    }
+    out1[e] = s1 * a1;
+    if (out2) out2[e] = s2 * a2;
+  }
+}
+
+// coarse products: o1 = A1 x1 + b1s B1 y1, o2 = A2 x2 + b2s B2 y2 (FP32 matrices; B*, o2 optional)
+__device__ void f_coarse(const Ctx &c, long long A1, const float *x1, long long B1, const float *y1, float b1s,
+                         float *o1, long long A2, const float *x2, long long B2, const float *y2, float b2s,
+                         float *o2) {
+  const int lane = threadIdx.x & 31;
+  const int n = c.n_pi, R = c.R;
+  for (int t = gwarp(); t < n * R; t += nwarps()) {
+    const int p = t / R, k = t % R;
+    float s1 = 0.f, s2 = 0.f;
+    for (int q = lane; q < n; q += 32) {
+      const long long e = (long long)p * n + q;
+      s1 = fmaf(c.fb[A1 + e], __ldcg(x1 + q * R + k), s1);
+      if (B1 >= 0) s1 = fmaf(b1s * c.fb[B1 + e], __ldcg(y1 + q * R + k), s1);
+      if (o2) {
+        s2 = fmaf(c.fb[A2 + e], __ldcg(x2 + q * R + k), s2);
+        if (B2 >= 0) s2 = fmaf(b2s * c.fb[B2 + e], __ldcg(y2 + q * R + k), s2);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      o1[t] = s1;
+      if (o2) o2[t] = s2;
+    }
+  }
+}
+
+// P3: lambda = [R_Pi mpi; -x^]; VL = -(Lambda lambda)_Delta ;
+//     BL = -(lambda - Psi lambda)_Delta + Lambda_{Pi,Delta}^T g_Pi
+template <int RC>
+__device__ void f_dl_first(const Ctx &c, const float *x) {
+  float *xs = sh_stage, *gs = sh_stage + MAXG * 16;
+  const int R = c.R, w = threadIdx.x >> 5;
+  const int ch = n_chunks(c);
+  for (int it = blockIdx.x; it < c.n_sub * ch; it += gridDim.x) {
+    const int s = it / ch, q = it % ch;
+    const SubDev d = c.subs[s];
+    const int r0 = (d.nDl * q) / ch, r1 = (d.nDl * (q + 1)) / ch;
+    if (r0 >= r1) continue;
+    const int *gpi = c.ints + d.gpi_off, *gdl = c.ints + d.gdl_off;
+    for (int e = threadIdx.x; e < d.nG * R; e += blockDim.x) {
+      const int a = e / R, k = e % R;
+      xs[e] = a < d.nPi ? __ldcg(c.fpv[FP_MPI] + gpi[a] * R + k) : -__ldcg(x + (long long)gdl[a - d.nPi] * R + k);
+    }
+    for (int e = threadIdx.x; e < d.nPi * R; e += blockDim.x)
+      gs[e] = __ldcg(c.fpv[FP_G] + gpi[e / R] * R + e % R);
+    __syncthreads();
+    const float *lam = c.fb + d.oLam32, *psi = c.fb + d.oPsi32, *lamT = c.fb + d.oLamT32;
+    for (int dd = r0 + w; dd < r1; dd += CG_WARPS) {
+      const int a = d.nPi + dd;
+      const float sl = row_dot<RC>(lam + (long long)a * d.nG, d.nG, xs, R);
+      const float sp = row_dot<RC>(psi + (long long)a * d.nG, d.nG, xs, R);
+      const float sg = row_dot<RC>(lamT + (long long)a * d.nG, d.nPi, gs, R);
+      int k;
+      if (row_writer<RC>(R, k)) {
+        fslab_row(c, FS_VL, d, a)[k] = -sl;
+        fslab_row(c, FS_BL, d, a)[k] = -(xs[a * R + k] - sp) + sg;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// P4 / P5: out = -M y^ with y^ the gathered slab `in` (M = Phi or Phi^T); P4
+// also keeps v^ in the VH slab
+template <int RC>
+__device__ void f_dl_phi(const Ctx &c, bool transposed, int in, int out, bool keep_v) {
+  float *xs = sh_stage;
+  const int R = c.R, w = threadIdx.x >> 5;
+  const int ch = n_chunks(c);
+  for (int it = blockIdx.x; it < c.n_sub * ch; it += gridDim.x) {
+    const int s = it / ch, q = it % ch;
+    const SubDev d = c.subs[s];
+    const int r0 = (d.nDl * q) / ch, r1 = (d.nDl * (q + 1)) / ch;
+    if (r0 >= r1) continue;
+    for (int e = threadIdx.x; e < d.nDl * R; e += blockDim.x) {
+      const int b = e / R, k = e % R;
+      const float v = gam_pair(c, in, d, d.nPi + b, k);
+      xs[e] = v;
+      if (keep_v && b >= r0 && b < r1) fslab_row(c, FS_VH, d, d.nPi + b)[k] = v;
+    }
+    __syncthreads();
+    const float *M = c.fb + (transposed ? d.oPhiT32 : d.oPhi32);
+    for (int dd = r0 + w; dd < r1; dd += CG_WARPS) {
+      const float v = row_dot<RC>(M + (long long)dd * d.nDl, d.nDl, xs, R);
+      int k;
+      if (row_writer<RC>(R, k)) fslab_row(c, out, d, d.nPi + dd)[k] = -v;
+    }
+    __syncthreads();
+  }
+}
+
+// P6: w^ = theta (sum T2L)^ + (1 - theta) v^ ; ZL = Lambda^T [0; w^] (all Gamma rows)
+template <int RC>
+__device__ void f_g_lamT(const Ctx &c) {
+  float *xs = sh_stage;
+  const int R = c.R, w = threadIdx.x >> 5;
+  const int ch = n_chunks(c);
+  const float th = (float)c.theta;
+  for (int it = blockIdx.x; it < c.n_sub * ch; it += gridDim.x) {
+    const int s = it / ch, q = it % ch;
+    const SubDev d = c.subs[s];
+    const int r0 = (d.nG * q) / ch, r1 = (d.nG * (q + 1)) / ch;
+    if (r0 >= r1) continue;
+    for (int e = threadIdx.x; e < d.nDl * R; e += blockDim.x) {
+      const int b = e / R, k = e % R;
+      xs[e] = th * gam_pair(c, FS_T2L, d, d.nPi + b, k) + (1.f - th) * __ldcg(fslab_row(c, FS_VH, d, d.nPi + b) + k);
+    }
+    __syncthreads();
+    const float *lamT = c.fb + d.oLamT32;
+    for (int a = r0 + w; a < r1; a += CG_WARPS) {
+      const float v = row_dot<RC>(lamT + (long long)a * d.nG + d.nPi, d.nDl, xs, R);
+      int k;
+      if (row_writer<RC>(R, k)) fslab_row(c, FS_ZL, d, a)[k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// YL of local Delta row a (column k): ZL + Psi_{Delta,Pi} nu^ - Lambda_{Pi,Delta}^T Dnu^
+__device__ __forceinline__ float f_yl(const Ctx &c, const SubDev &d, int a, int k) {
+  const int *gpi = c.ints + d.gpi_off;
+  const float *psi = c.fb + d.oPsi32 + (long long)a * d.nG;
+  const float *lamT = c.fb + d.oLamT32 + (long long)a * d.nG;
+  float v = __ldcg(fslab_row(c, FS_ZL, d, a) + k);
+  for (int b = 0; b < d.nPi; ++b) {
+    const int gp = gpi[b];
+    v = fmaf(psi[b], __ldcg(c.fpv[FP_NU] + gp * c.R + k), v);
+    v = fmaf(-lamT[b], __ldcg(c.fpv[FP_DNU] + gp * c.R + k), v);
+  }
+  return v;
+}
+
+// q = S32 x; the last phase (gathers of YL and BL) is fused into the dot product
+// p.q that follows, so this returns with q written and a partial dot pending in
+// red slot 0 (no barrier taken after it).
+template <int RC>
+__device__ bool f_apply_S(const Ctx &c, const float *x, float *q) {
+  f_pi_rows<RC>(c, x);
+  if (!grid_sync(c)) return false;
+  f_pi_gather(c, FS_H1, 1.f, c.fpv[FP_PSI], FS_H2, -1.f, c.fpv[FP_RA]);
+  if (!grid_sync(c)) return false;
+  if (c.n_pi > 0)
+    f_coarse(c, c.f_Sinv, c.fpv[FP_RA], c.f_C1, c.fpv[FP_PSI], 1.f, c.fpv[FP_MPI], c.f_C2, c.fpv[FP_PSI], c.f_C3,
+             c.fpv[FP_RA], -1.f, c.fpv[FP_G]);
+  if (!grid_sync(c)) return false;
+  f_dl_first<RC>(c, x);
+  if (!grid_sync(c)) return false;
+  f_dl_phi<RC>(c, false, FS_VL, FS_TL, true);
+  if (!grid_sync(c)) return false;
+  f_dl_phi<RC>(c, true, FS_TL, FS_T2L, false);
+  if (!grid_sync(c)) return false;
+  f_g_lamT<RC>(c);
+  if (!grid_sync(c)) return false;
+  f_pi_gather(c, FS_ZL, 1.f, c.fpv[FP_RNU], -1, 0.f, nullptr);
+  if (!grid_sync(c)) return false;
+  if (c.n_pi > 0)
+    f_coarse(c, c.f_Sinv, c.fpv[FP_RNU], -1, nullptr, 0.f, c.fpv[FP_NU], c.f_C3, c.fpv[FP_RNU], -1, nullptr, 0.f,
+             c.fpv[FP_DNU]);
+  if (!grid_sync(c)) return false;
+  // q[delta] = sum_owners (YL + BL)
+  for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
+    const int gd = e / c.R, k = e % c.R;
+    const int sa = c.ints[c.o_dl_own + 4 * gd], la = c.ints[c.o_dl_own + 4 * gd + 1];
+    const int sb = c.ints[c.o_dl_own + 4 * gd + 2], lb = c.ints[c.o_dl_own + 4 * gd + 3];
+    const SubDev &da = c.subs[sa];
+    const SubDev &dB = c.subs[sb];
+    const int2 rw = *reinterpret_cast<const int2 *>(c.ints + c.o_dl_rows + 2 * gd);
+    q[e] = f_yl(c, da, da.nPi + la, k) + f_yl(c, dB, dB.nPi + lb, k) +
+           __ldcg(c.fslab[FS_BL] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[FS_BL] + (long long)rw.y * c.R + k);
+  }
+  return true;
+}
+
+// partial dot of FP32 columns (FP64 accumulation past the warp level), same
+// element walk as the updates
+template <int RC>
+__device__ void f_partial_dot(const Ctx &c, const float *x, const float *y, int slot) {
+  __shared__ double sred[CG_WARPS][16];
+  double acc[RC];
+#pragma unroll
+  for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+  const int R = c.R;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+    const double v = (double)__ldcg(x + e) * (double)__ldcg(y + e);
+    const int col = e % R;
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k == col) acc[k] += v;
+  }
+  warp_sum<RC>(acc);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < RC; ++k) sred[threadIdx.x >> 5][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < RC) {
+    double sm = 0.0;
+    for (int w = 0; w < CG_WARPS; ++w) sm += sred[w][threadIdx.x];
+    c.red[(long long)blockIdx.x * 32 + slot * 16 + threadIdx.x] = sm;
+  }
+  __syncthreads();
+}
+
+// FP32 CG on S32 d = r (r already in F_R, d accumulates in F_D from 0), per
+// column until |r_k| <= tol_in |r_k(0)|; returns iterations or -1 (timeout).
+template <int RC>
+__device__ int f_cg(const Ctx &c, const double *tol_in, int max_it) {
+  __shared__ double s_r0[16], s_rr[16], s_pq[16], s_rn[16];
+  __shared__ float s_alpha[16], s_beta[16];
+  __shared__ int s_done;
+  float *Rv = c.fdl[F_R], *Dv = c.fdl[F_D], *Qv = c.fdl[F_Q];
+  float *P[2] = {c.fdl[F_P0], c.fdl[F_P1]};
+  const int R = c.R;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+    P[0][e] = Rv[e];
+    Dv[e] = 0.f;
+  }
+  f_partial_dot<RC>(c, Rv, Rv, 1);
+  if (!grid_sync(c)) return -1;
+  finish_dot<RC>(c, 1, s_rr);
+  if (threadIdx.x < RC) s_r0[threadIdx.x] = s_rr[threadIdx.x];
+  __syncthreads();
+  int it = 0, cur = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < R && k < RC; ++k)
+        if (s_r0[k] > 0.0 && s_rr[k] > tol_in[k] * tol_in[k] * s_r0[k]) done = 0;
+      s_done = done || it >= max_it;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (!f_apply_S<RC>(c, P[cur], Qv)) return -1;
+    f_partial_dot<RC>(c, P[cur], Qv, 0);
+    if (!grid_sync(c)) return -1;
+    finish_dot<RC>(c, 0, s_pq);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      const bool live = k < R && s_r0[k] > 0.0 && s_rr[k] > tol_in[k] * tol_in[k] * s_r0[k] && s_pq[k] != 0.0;
+      s_alpha[k] = live ? (float)(s_rr[k] / s_pq[k]) : 0.f;
+    }
+    __syncthreads();
+    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+      const float al = s_alpha[e % R];
+      Dv[e] = fmaf(al, P[cur][e], Dv[e]);
+      Rv[e] = fmaf(-al, __ldcg(Qv + e), Rv[e]);
+    }
+    f_partial_dot<RC>(c, Rv, Rv, 1);
+    if (!grid_sync(c)) return -1;
+    finish_dot<RC>(c, 1, s_rn);
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      s_beta[k] = (s_alpha[k] != 0.f && s_rr[k] > 0.0) ? (float)(s_rn[k] / s_rr[k]) : 0.f;
+      if (s_alpha[k] != 0.f) s_rr[k] = s_rn[k];
+    }
+    __syncthreads();
+    // the next direction goes to the other buffer: this iteration's readers of
+    // P[cur] never see it change
+    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+      const int k = e % R;
+      P[cur ^ 1][e] = s_alpha[k] != 0.f ? fmaf(s_beta[k], P[cur][e], Rv[e]) : P[cur][e];
+    }
+    cur ^= 1;
+    ++it;
+    if (!grid_sync(c)) return -1;
+  }
+  return it;
+}
+
+// MIXED solve of S_theta mu = B: FP64 residuals, FP32 corrections.  Returns the
+// inner iterations or -1; s_bn receives |B| per column.
+template <int RC>
+__device__ int refine_solve(const Ctx &c, double *s_bn) {
+  __shared__ double s_rn[16];
+  __shared__ int s_done;
+  double *B = c.dl[V_B], *MU = c.dl[V_MU], *RES = c.dl[V_RES], *Q = c.dl[V_Q];
+  const int R = c.R;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+    MU[e] = 0.0;
+    RES[e] = B[e];
+  }
+  partial_dot<RC>(c, B, B, 0);
+  if (!grid_sync(c)) return -1;
+  finish_dot<RC>(c, 0, s_bn);
+  if (threadIdx.x < RC) {
+    s_rn[threadIdx.x] = s_bn[threadIdx.x];
+    s_bn[threadIdx.x] = sqrt(s_bn[threadIdx.x]);
+  }
+  __syncthreads();
+  // each sweep reduces its residual by tol_in: 1e-5 (about what the FP32
+  // operator allows), or only as far as the target needs (with a margin of 3)
+  __shared__ double s_tin[16];
+  int total = 0, sweeps = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < R && k < RC; ++k)
+        if (s_bn[k] > 0.0 && sqrt(s_rn[k]) >= c.tol * s_bn[k]) done = 0;
+      s_done = done || sweeps >= c.max_refine || total >= c.max_iters;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (threadIdx.x < RC) {
+      const int k = threadIdx.x;
+      const double rn = sqrt(s_rn[k]);
+      s_tin[k] = rn > 0.0 ? fmax(1e-5, fmin(0.5, 0.3 * c.tol * s_bn[k] / rn)) : 1e-5;
+    }
+    __syncthreads();
+    // r32 = RES / |RES| per column (columns already converged: 0)
+    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+      const int k = e % R;
+      const double rn = sqrt(s_rn[k]);
+      const bool live = s_bn[k] > 0.0 && rn >= c.tol * s_bn[k];
+      c.fdl[F_R][e] = live ? (float)(RES[e] / rn) : 0.f;
+    }
+    if (!grid_sync(c)) return -1;
+    const int it = f_cg<RC>(c, s_tin, c.max_iters - total);
+    if (it < 0) return -1;
+    total += it;
+    ++sweeps;
+    for (int e = gthread(); e < c.n_dl * R; e += nthreads())
+      MU[e] = fma(sqrt(s_rn[e % R]), (double)c.fdl[F_D][e], MU[e]);
+    if (!grid_sync(c)) return -1;
+    if (!apply_S<RC>(c, MU, Q)) return -1;
+    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) RES[e] = B[e] - ldg_cg(Q + e);
+    partial_dot<RC>(c, RES, RES, 0);
+    if (!grid_sync(c)) return -1;
+    finish_dot<RC>(c, 0, s_rn);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.info[33] = sweeps;
+  return total;
+}
+
 template <int RC>
 __device__ void forward_program(const Ctx &c) {
   __shared__ double s_bn[16], s_rn[16];
@@ -561,7 +1018,7 @@ __device__ void forward_program(const Ctx &c) {
   ph_dl_first<RC>(c, c.pv[P_MPF], nullptr, c.pv[P_GF], 1);
   if (!grid_sync(c)) return;
   if (!second_half<RC>(c, B)) return;
-  const int it = cg_solve<RC>(c, s_bn);
+  const int it = c.fb ? refine_solve<RC>(c, s_bn) : cg_solve<RC>(c, s_bn);
   if (it < 0) return;
   // ---------------- true residual |b - S mu| / |b|
   if (!apply_S<RC>(c, MU, Q)) return;
@@ -763,6 +1220,8 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   c.n_tg = p.n_tasks_g;
   c.o_tc = p.o_tasks_c;
   c.n_tc = p.n_tasks_c;
+  c.o_dl_rows = p.o_dl_rows;
+  c.o_gam_rows = p.o_gam_rows;
   c.o_Sinv = p.o_Sinv;
   c.o_C1 = p.o_C1;
   c.o_C2 = p.o_C2;
@@ -784,6 +1243,18 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   c.mu_out = a.mu_out;
   c.c_out = a.c_out;
   c.mode = a.mode;
+  c.max_refine = a.max_refine;
+  c.fb = nullptr;
+  if (p.mixed && p.o_f32 >= 0 && a.mode == 0) {
+    c.fb = reinterpret_cast<float *>(c.db + p.o_f32);
+    c.f_Sinv = p.f_Sinv;
+    c.f_C1 = p.f_C1;
+    c.f_C2 = p.f_C2;
+    c.f_C3 = p.f_C3;
+    for (int k = 0; k < N_FDL; ++k) c.fdl[k] = c.fb + p.f_dl + k * nd * R;
+    for (int k = 0; k < N_FPV; ++k) c.fpv[k] = c.fb + p.f_pv + k * np * R;
+    for (int k = 0; k < N_FSLAB; ++k) c.fslab[k] = c.fb + p.f_slab + (long long)k * p.sum_nG * R;
+  }
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -258,6 +258,14 @@ __global__ void __launch_bounds__(CT) chol_inv32_kernel(const CholDesc *__restri
   if (threadIdx.x == 0 && s_bad) status[cd.status] = 1;
 }
 
+// FP32 copies of the operators the inner CG of MIXED precision applies
+__global__ void convert_f32_kernel(const ConvSeg *__restrict__ segs, const double *__restrict__ db,
+                                   float *__restrict__ fb) {
+  const ConvSeg sg = segs[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < sg.n; e += (long long)gridDim.x * blockDim.x)
+    fb[sg.dst + e] = (float)db[sg.src + e];
+}
+
 // small batched matrix operations of the polishing step:
 //   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B  (two terms of (I + A)^{-1/2}, B = A A) ;
 //   op 2: C symmetric from its upper triangle.
@@ -425,6 +433,16 @@ cudaError_t launch_chol_table(const CholDesc *descs, int n, int maxM, double *db
     if (e != cudaSuccess) return e;
   }
   { chol_inv_kernel<<<n, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32(const Plan &p, void *ws, cudaStream_t s) {
+  if (p.conv.empty()) return cudaSuccess;
+  char *base = static_cast<char *>(ws);
+  const ConvSeg *segs = reinterpret_cast<const ConvSeg *>(base + p.off_conv);
+  const double *db = reinterpret_cast<const double *>(base + p.off_dbl);
+  float *fb = reinterpret_cast<float *>(const_cast<double *>(db) + p.o_f32);
+  { convert_f32_kernel<<<dim3(8, (unsigned)p.conv.size()), 256, 0, s>>>(segs, db, fb); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

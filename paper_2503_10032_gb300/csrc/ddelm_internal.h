@@ -66,6 +66,7 @@ struct SubDev {
   long long oLam, oLamT;   // Lambda^i and its transpose [nG x nG]
   long long oPsi;          // Psi^i [nG x nG]
   long long oPhi, oPhiT;   // Phi^i and its transpose [nDl x nDl]
+  long long oLam32, oLamT32, oPsi32, oPhi32, oPhiT32;  // MIXED: FP32 copies (float offsets)
   // solve-time vectors ([rows x R])
   long long oF;     // [nI + nB] x R data rows
   long long oT, oQtf, oY, oAy, oP;  // M x R, M x R, M x R, nG x R, nG x R
@@ -113,6 +114,11 @@ struct MatopDesc {
   int pad;
 };
 
+// FP64 -> FP32 copy of n elements (dbase offset src, FP32-region offset dst)
+struct ConvSeg {
+  long long src, dst, n;
+};
+
 struct MatopPhase {
   int desc0, ndesc;
 };
@@ -157,6 +163,8 @@ struct Plan {
   int o_tasks_dl = 0, n_tasks_dl = 0;  // (sub, local Delta row)
   int o_tasks_g = 0, n_tasks_g = 0;    // (sub, local Gamma row)
   int o_tasks_c = 0, n_tasks_c = 0;    // (sub, coefficient row j < M)
+  int o_dl_rows = 0;                    // per Delta point: the 2 owners' slab rows
+  int o_gam_rows = 0;                   // per local interface row: those rows of its Delta point (-1 on Pi)
   int o_bnd_map = 0;                    // local boundary -> global Dirichlet index
   int o_bnd_own = 0;                    // per global Dirichlet point: 2 x (sub, local row)
   // workspace layout
@@ -167,6 +175,12 @@ struct Plan {
   long long o_w = 0, o_b = 0, o_xint = 0, o_aint = 0, o_gaint = 0;  // problem data
   long long o_status = 0;  // int status slots (in ints region? kept as doubles)
   long long o_fin = 0, o_gin = 0, o_cout = 0, o_muout = 0, o_uout = 0;  // solve staging
+  // MIXED: FP32 region (dbase offset o_f32, n_f32 floats): operator copies and
+  // the inner CG's Delta vectors (6), Pi vectors (7) and local slabs (8)
+  long long o_f32 = -1, n_f32 = 0;
+  long long f_Sinv = 0, f_C1 = 0, f_C2 = 0, f_C3 = 0, f_dl = 0, f_pv = 0, f_slab = 0;
+  std::vector<ConvSeg> conv;
+  size_t off_conv = 0;
   // coarse
   int n_pi = 0, n_dl = 0;
   long long o_Dpp = 0, o_Spi = 0, o_Vpi = 0, o_Sinv = 0, o_C1 = 0, o_C2 = 0, o_C3 = 0, o_SpiR = 0;
@@ -219,6 +233,7 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s);
 cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_matop_phase(const Plan &p, const MatopPhase &ph, void *ws, cudaStream_t s);
+cudaError_t launch_convert_f32(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fill_identity(double *dst, int n, double diag, cudaStream_t s);
 cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, const double *g_bnd,
@@ -236,6 +251,7 @@ struct CgArgs {
   double tol;
   double theta;
   int mode = 0;  // 0 solve, 1 adjoint
+  int max_refine = 8;  // MIXED: outer refinement sweeps
 };
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s);
 

@@ -281,6 +281,49 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.o_cout = take(sumM * R);
   P.o_muout = take((long long)(n_pi + nd) * R);
   P.o_uout = take(sumE * R);
+  // MIXED: FP32 copies of the local and coarse operators and the vectors of the
+  // inner FP32 CG (float offsets from the start of this region)
+  if (o.precision == DDELM_PREC_MIXED) {
+    for (const auto &d : P.subs)
+      if (d.nG > 256) return fail("MIXED precision supports at most 256 interface points per subdomain");
+    long long fcur = 0;
+    auto ftake = [&](long long n) {
+      long long off = fcur;
+      fcur += (std::max(n, 1LL) + 63) / 64 * 64;
+      return off;
+    };
+    for (int i = 0; i < n_sub; ++i) {
+      SubDev &d = P.subs[i];
+      const long long g2 = (long long)d.nG * d.nG, l2 = (long long)d.nDl * d.nDl;
+      d.oLam32 = ftake(g2);
+      d.oLamT32 = ftake(g2);
+      d.oPsi32 = ftake(g2);
+      d.oPhi32 = ftake(l2);
+      d.oPhiT32 = ftake(l2);
+      P.conv.push_back({d.oLam, d.oLam32, g2});
+      P.conv.push_back({d.oLamT, d.oLamT32, g2});
+      P.conv.push_back({d.oPsi, d.oPsi32, g2});
+      P.conv.push_back({d.oPhi, d.oPhi32, l2});
+      P.conv.push_back({d.oPhiT, d.oPhiT32, l2});
+    }
+    const long long np2 = (long long)std::max(n_pi, 1) * std::max(n_pi, 1);
+    P.f_Sinv = ftake(np2);
+    P.f_C1 = ftake(np2);
+    P.f_C2 = ftake(np2);
+    P.f_C3 = ftake(np2);
+    if (n_pi > 0) {
+      P.conv.push_back({P.o_Sinv, P.f_Sinv, np2});
+      P.conv.push_back({P.o_C1, P.f_C1, np2});
+      P.conv.push_back({P.o_C2, P.f_C2, np2});
+      P.conv.push_back({P.o_C3, P.f_C3, np2});
+    }
+    const long long ndR = (long long)std::max(nd, 1) * R, npR = (long long)std::max(n_pi, 1) * R;
+    P.f_dl = ftake(6 * ndR);
+    P.f_pv = ftake(7 * npR);
+    P.f_slab = ftake(8LL * sum_nG * R);
+    P.n_f32 = fcur;
+    P.o_f32 = take((fcur + 1) / 2);
+  }
   // inspection copies
   if (P.keep) {
     P.o_keepX = cur;
@@ -572,6 +615,25 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       I.push_back(k);
     }
   P.n_tasks_c = (int(I.size()) - P.o_tasks_c) / 2;
+  // slab rows of the two owners of every Delta point, by global point and by
+  // local interface row (-1 on Pi rows): the gathers read slabs in one step
+  if (I.size() % 2) I.push_back(-1);  // int2 reads
+  P.o_dl_rows = int(I.size());
+  for (int gd = 0; gd < nd; ++gd)
+    for (int o = 0; o < 2; ++o) {
+      const int s = I[P.o_dl_own + 4 * gd + 2 * o], l = I[P.o_dl_own + 4 * gd + 2 * o + 1];
+      I.push_back(P.subs[s].loc_off + P.subs[s].nPi + l);
+    }
+  P.o_gam_rows = int(I.size());
+  I.resize(I.size() + 2 * (size_t)sum_nG, -1);
+  for (int i = 0; i < n_sub; ++i) {
+    const SubDev &d = P.subs[i];
+    for (int b = 0; b < d.nDl; ++b) {
+      const int gd = sg[i].dg[b];
+      I[P.o_gam_rows + 2 * (d.loc_off + d.nPi + b)] = I[P.o_dl_rows + 2 * gd];
+      I[P.o_gam_rows + 2 * (d.loc_off + d.nPi + b) + 1] = I[P.o_dl_rows + 2 * gd + 1];
+    }
+  }
 
   // ---- GEMM phases
   auto phase_begin = [&](int skinny = 0) {
@@ -1008,6 +1070,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       if (c.prec == 1 && c.band != 0) return fail("internal: banded FP32 Cholesky");
       if (c.status < 0 || c.status > 2 * n_sub) return fail("internal: status slot");
     }
+    for (const auto &cv : P.conv)
+      if (!in(cv.src, cv.n) || cv.dst < 0 || cv.dst + cv.n > P.n_f32) return fail("internal: FP32 copy bounds");
     for (const auto &md : P.mdesc) {
       const long long mm = (long long)md.M * md.M;
       if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm))) || md.op < 0 || md.op > 2 ||
@@ -1101,6 +1165,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   off = al(off + std::max<size_t>(P.gtile.size(), 1) * sizeof(GemmTile));
   P.off_cdesc = off;
   off = al(off + std::max<size_t>(P.cdesc.size(), 1) * sizeof(CholDesc));
+  P.off_conv = off;
+  off = al(off + std::max<size_t>(P.conv.size(), 1) * sizeof(ConvSeg));
   P.off_mdesc = off;
   off = al(off + std::max<size_t>(P.mdesc.size(), 1) * sizeof(MatopDesc));
   P.off_ints = off;
