@@ -268,7 +268,7 @@ __global__ void convert_f32_kernel(const ConvSeg *__restrict__ segs, const doubl
 
 // small batched matrix operations of the polishing step:
 //   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B  (two terms of (I + A)^{-1/2}, B = A A) ;
-//   op 2: C symmetric from its upper triangle.
+//   op 2: C symmetric from its upper triangle ;  op 3: C = A.
 // op 1 flags the subdomain when max |A| > 1e-5: beyond that the neglected
 // third-order term could reach the FP64 level.
 __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__restrict__ db, int *__restrict__ status) {
@@ -283,8 +283,10 @@ __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__rest
       const double a = db[md.a + e];
       big |= !(fabs(a) <= 1e-5);
       db[md.c + e] = (i == j ? 1.0 : 0.0) - 0.5 * a + 0.375 * db[md.b + e];
-    } else if (i > j) {
-      db[md.c + e] = db[md.c + j * md.M + i];
+    } else if (md.op == 2) {
+      if (i > j) db[md.c + e] = db[md.c + j * md.M + i];
+    } else {
+      db[md.c + e] = db[md.a + e];
     }
   }
   if (big) status[md.status] = 1;

@@ -109,7 +109,7 @@ struct CholDesc {
 
 struct MatopDesc {
   long long a, b, c;
-  int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B ; op 2: lower(C) = upper(C)^T
+  int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B ; op 2: lower(C) = upper(C)^T ; op 3: C = A
   int status;  // op 1: set when max |A| exceeds the range of the two-term series
   int pad;
 };

@@ -729,15 +729,30 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     auto vk = [&](int i, int t, int k) { return (k % 2) ? scr[i].v[t].Vb : scr[i].v[t].Va; };  // pass-k factor
     auto zk = [&](int i, int t, int k) { return (k % 2) ? scr[i].v[t].Zb : scr[i].v[t].Za; };  // ridge block after pass k
     auto tk = [&](int i, int t, int k) { return k == 0 ? vk(i, t, 0) : (k % 2) ? scr[i].v[t].Ta : scr[i].v[t].Tb; };
-    // Gram of the features
+    // Gram of the features.  K_c and K-bar share their interior and boundary
+    // rows (Sec. 3.1 changes only the interface rows): G_common = K_IB^T K_IB
+    // once, copied, then each adds the Gram of its own interface rows.
     {
+      const int lv0 = fp32 && N > 0 ? lv_shifted32 : lv_first64;
       GemmPhase ph = phase_begin();
+      for (int i = w0; i < w1; ++i) {
+        const SubDev &d = P.subs[i];
+        add(ph, qk(i, 0, 0), qk(i, 0, 0), scr[i].v[0].G, d.M, d.M, d.nI + d.nB, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0,
+            true);
+      }
+      gemm_step(ph, lv0);
+      const int m0 = int(P.mdesc.size());
+      for (int i = w0; i < w1; ++i)
+        P.mdesc.push_back(MatopDesc{scr[i].v[0].G, 0, scr[i].v[1].G, P.subs[i].M, 3, 2 * i + 1});
+      matop_step(m0);  // G-bar = G_common
+      GemmPhase ph2 = phase_begin();
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t) {
           const SubDev &d = P.subs[i];
-          add(ph, qk(i, t, 0), qk(i, t, 0), scr[i].v[t].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0, true);
+          const long long rows = qk(i, t, 0) + (long long)(d.nI + d.nB) * d.M;  // the nG interface rows
+          add(ph2, rows, rows, scr[i].v[t].G, d.M, d.M, d.nG, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0, true);
         }
-      gemm_step(ph, fp32 && N > 0 ? lv_shifted32 : lv_first64);
+      gemm_step(ph2, lv0);
     }
     for (int k = 0; k <= N; ++k) {
       const bool last = k == N;
@@ -1074,7 +1089,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       if (!in(cv.src, cv.n) || cv.dst < 0 || cv.dst + cv.n > P.n_f32) return fail("internal: FP32 copy bounds");
     for (const auto &md : P.mdesc) {
       const long long mm = (long long)md.M * md.M;
-      if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm))) || md.op < 0 || md.op > 2 ||
+      if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm))) || (md.op == 3 && !in(md.a, mm)) ||
+          md.op < 0 || md.op > 3 ||
           md.status < 0 || md.status >= 2 * n_sub)
         return fail("internal: matrix operation bounds");
     }
