@@ -36,7 +36,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 EPS_REL = 1e-8
 THETA = 0.999
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
-SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2}
+SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2, "cqr2series": 3}
 
 
 def measured_peaks():
@@ -217,8 +217,8 @@ def main():
         sub_sizes.append({"m": m_, "M": M_, "nG": nG_, "nDl": nDl_})
     flops = D.ddelm_inspect(solver.h, 0, 8, 7)
     plan = D.ddelm_inspect(solver.h, 0, 9, 4)
-    scheme_desc = ("fp64-cholesky-cqr3" if int(plan[0]) == 1 else
-                   f"fp32-cholesky x{int(plan[1])} shifted + 1 polished")
+    scheme_desc = {1: "fp64-cholesky-cqr3", 3: "fp64-cholesky x2 + series"}.get(
+        int(plan[0]), f"fp32-cholesky x{int(plan[1])} shifted + 1 polished")
 
     def step():
         solver.refactor()

@@ -63,7 +63,7 @@ extern "C" {
 
 #define DDELM_OK 0
 #define DDELM_ERR_INVALID_ARG (-1)    /* bad sizes, null pointers, workspace too small */
-#define DDELM_ERR_RANK_DEFICIENT (-2) /* a local factorisation failed: a Cholesky pivot was not positive, or (FP32 scheme) the last factor left max |V^T G V - I| > 1e-5 (info: subdomain) */
+#define DDELM_ERR_RANK_DEFICIENT (-2) /* a local factorisation failed: a Cholesky pivot was not positive, or a series scheme met max |E| > 1e-4 (info: subdomain) */
 #define DDELM_ERR_NOT_CONVERGED (-3)  /* CG reached max_iters; outputs are still written */
 #define DDELM_ERR_CUDA (-4)           /* a CUDA runtime call failed */
 #define DDELM_ERR_TIMEOUT (-5)        /* a device-side grid barrier gave up waiting */
@@ -80,12 +80,18 @@ extern "C" {
  *  FP32:     shifted CholeskyQR with FP32 Cholesky factors used only as
  *            preconditioners (every update of Q, the ridge block and R^{-1} stays
  *            FP64-exact), then one unshifted FP32 pass whose residual
- *            E = V^T G V - I is removed by V (I - E/2 + 3/8 E^2).
+ *            E = V^T G V - I is removed by V (I - E/2 + 3/8 E^2 - 5/16 E^3).
+ *  CQR2_SERIES: two FP64 Cholesky passes (the first shifted); the third
+ *            Gram G is within ~1e-5 of I and (I + E)^{-1/2}, E = G - I, is
+ *            taken from its series to third order instead of a Cholesky.
+ * The series are checked: max |E| > 1e-4 fails the setup (RANK_DEFICIENT).
  * Automatic: FP64CQR3 in FP64 precision; in MIXED, FP32 once some subdomain has
- * M >= 512 (where the O(M^3) FP64 Cholesky of one SM per matrix dominates). */
+ * M >= 512 (where the O(M^3) FP64 Cholesky of one SM per matrix dominates),
+ * else CQR2_SERIES. */
 #define DDELM_SCHEME_AUTO 0
 #define DDELM_SCHEME_FP64CQR3 1
 #define DDELM_SCHEME_FP32 2
+#define DDELM_SCHEME_CQR2_SERIES 3
 
 typedef struct ddelm_options {
   double theta;           /* Eq. (nn-mixed) mixing weight; the paper uses 0.999 */

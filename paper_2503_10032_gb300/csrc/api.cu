@@ -569,7 +569,7 @@ const char *ddelm_status_string(int status) {
     case DDELM_ERR_INVALID_ARG:
       return "invalid argument";
     case DDELM_ERR_RANK_DEFICIENT:
-      return "a local factorisation failed (a non-positive pivot, or an FP32 factor too far from V^T G V = I)";
+      return "a local factorisation failed (a non-positive pivot, or a Gram too far from I for the series)";
     case DDELM_ERR_NOT_CONVERGED:
       return "CG reached max_iters before the tolerance";
     case DDELM_ERR_CUDA:

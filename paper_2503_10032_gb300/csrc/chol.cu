@@ -267,10 +267,11 @@ __global__ void convert_f32_kernel(const ConvSeg *__restrict__ segs, const doubl
 }
 
 // small batched matrix operations of the polishing step:
-//   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B  (two terms of (I + A)^{-1/2}, B = A A) ;
-//   op 2: C symmetric from its upper triangle ;  op 3: C = A.
-// op 1 flags the subdomain when max |A| > 1e-5: beyond that the neglected
-// third-order term could reach the FP64 level.
+//   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B - 5/16 D  (the series of
+//   (I + A)^{-1/2} with B = A^2, D = A^3) ;  op 2: C symmetric from its upper
+//   triangle ;  op 3: C = A ;  op 4: C = A - I.
+// op 1 flags the subdomain when max |A| > 1e-4: beyond that the neglected
+// fourth-order term could reach the FP64 level.
 __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__restrict__ db, int *__restrict__ status) {
   const MatopDesc md = descs[blockIdx.y];
   const long long n = (long long)md.M * md.M;
@@ -281,12 +282,16 @@ __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__rest
       db[md.c + e] = i == j ? -1.0 : 0.0;
     } else if (md.op == 1) {
       const double a = db[md.a + e];
-      big |= !(fabs(a) <= 1e-5);
-      db[md.c + e] = (i == j ? 1.0 : 0.0) - 0.5 * a + 0.375 * db[md.b + e];
+      big |= !(fabs(a) <= 1e-4);
+      double w = (i == j ? 1.0 : 0.0) - 0.5 * a + 0.375 * db[md.b + e];
+      if (md.d >= 0) w -= 0.3125 * db[md.d + e];
+      db[md.c + e] = w;
     } else if (md.op == 2) {
       if (i > j) db[md.c + e] = db[md.c + j * md.M + i];
-    } else {
+    } else if (md.op == 3) {
       db[md.c + e] = db[md.a + e];
+    } else {
+      db[md.c + e] = db[md.a + e] - (i == j ? 1.0 : 0.0);
     }
   }
   if (big) status[md.status] = 1;

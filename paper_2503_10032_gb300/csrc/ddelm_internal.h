@@ -109,9 +109,10 @@ struct CholDesc {
 
 struct MatopDesc {
   long long a, b, c;
-  int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B ; op 2: lower(C) = upper(C)^T ; op 3: C = A
-  int status;  // op 1: set when max |A| exceeds the range of the two-term series
-  int pad;
+  int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B - 5/16 D ; op 2: lower(C) = upper(C)^T ;
+               // op 3: C = A ; op 4: C = A - I
+  int status;  // op 1: set when max |A| exceeds the range of the series
+  long long d; // op 1: third-order term (< 0: none)
 };
 
 // FP64 -> FP32 copy of n elements (dbase offset src, FP32-region offset dst)

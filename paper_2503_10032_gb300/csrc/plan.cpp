@@ -72,7 +72,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail("theta must be in [0,1]");
   if (!(o.eps_rel >= 0.0) || !(o.tol > 0.0) || o.max_iters < 1) return fail("bad options");
   if (o.precision != DDELM_PREC_FP64 && o.precision != DDELM_PREC_MIXED) return fail("bad precision");
-  if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_FP32 || o.setup_passes < 0 ||
+  if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_CQR2_SERIES || o.setup_passes < 0 ||
       o.setup_passes > 8)
     return fail("bad setup scheme");
   P.opt = o;
@@ -338,12 +338,17 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   {
     int sch = o.setup_scheme;
     if (sch == DDELM_SCHEME_AUTO)
-      sch = (o.precision == DDELM_PREC_MIXED && max_M >= 512) ? DDELM_SCHEME_FP32 : DDELM_SCHEME_FP64CQR3;
+      sch = o.precision != DDELM_PREC_MIXED ? DDELM_SCHEME_FP64CQR3
+                                            : (max_M >= 512 ? DDELM_SCHEME_FP32 : DDELM_SCHEME_CQR2_SERIES);
     P.scheme = sch;
     if (sch == DDELM_SCHEME_FP64CQR3) {
       P.n_pass = 2;
       P.polish = false;
       P.tri_v = true;
+    } else if (sch == DDELM_SCHEME_CQR2_SERIES) {
+      P.n_pass = 2;
+      P.polish = true;
+      P.tri_v = false;
     } else {
       // cond(G + eps^2 I) <= M / eps_rel^2 (tr G <= M lambda_max is attained when
       // one direction dominates, as with tanh features); each shifted FP32 pass
@@ -352,6 +357,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       const double eps2 = std::max(o.eps_rel * o.eps_rel, 1e-300);
       const int auto_pass = int(std::ceil(std::log10(std::max(10.0, max_M / eps2)) / 4.0));
       P.n_pass = o.setup_passes > 0 ? o.setup_passes : std::min(8, std::max(2, auto_pass));
+      if (P.n_pass < 2) return fail("the FP32 scheme needs at least two shifted passes");
       P.polish = true;
       P.tri_v = false;
     }
@@ -694,13 +700,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // [K; eps I] and [K-bar; eps-bar I] by shifted CholeskyQR with every O(m M^2)
   // and O(M^3) product a GEMM phase, then the local operators.
   const bool fp32 = P.scheme == DDELM_SCHEME_FP32;
+  const bool series = P.scheme == DDELM_SCHEME_CQR2_SERIES;
   const int N = P.n_pass;
   // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
   // accurate well below the shift; every other product keeps 54 bits.
   // Products of the triangular factors (R^{-1} accumulated pass by pass) span
   // many orders of magnitude inside a row, and the slice truncation is
   // relative to the row maximum: they keep 60 bits.
-  const int lv_exact = 9, lv_factor = 10, lv_first64 = 6, lv_shifted32 = 5, lv_small = 4;
+  const int lv_exact = 9, lv_factor = 10, lv_first64 = 6, lv_shifted32 = 5, lv_small = 4, lv_tiny = 3;
   auto gemm_step = [&](GemmPhase &ph, int levels) {
     P.steps.push_back({STEP_GEMM, int(P.setup_gemm.size())});
     P.setup_gemm.push_back(ph);
@@ -743,7 +750,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       gemm_step(ph, lv0);
       const int m0 = int(P.mdesc.size());
       for (int i = w0; i < w1; ++i)
-        P.mdesc.push_back(MatopDesc{scr[i].v[0].G, 0, scr[i].v[1].G, P.subs[i].M, 3, 2 * i + 1});
+        P.mdesc.push_back(MatopDesc{scr[i].v[0].G, 0, scr[i].v[1].G, P.subs[i].M, 3, 2 * i + 1, -1});
       matop_step(m0);  // G-bar = G_common
       GemmPhase ph2 = phase_begin();
       for (int i = w0; i < w1; ++i)
@@ -756,6 +763,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
     for (int k = 0; k <= N; ++k) {
       const bool last = k == N;
+      if (last && series) break;  // the series replaces the last Cholesky
       // Cholesky pass k: G = Q_k^T Q_k + Z_k^T Z_k (k = 0: Y^T Y and the ridge)
       const int c0 = int(P.cdesc.size());
       for (int i = w0; i < w1; ++i)
@@ -840,32 +848,45 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       }
     }
     if (P.polish) {
-      // last factor V_l (FP32 Cholesky of G): E = V_l^T G V_l - I is small and
-      // V3 = V_l (I - E/2 + 3/8 E^2) makes [Q; Z] V3 orthonormal to O(|E|^3)
+      // The last pass leaves a Gram close to I.  FP32 scheme: with V_l the FP32
+      // Cholesky inverse of G, E = V_l^T G V_l - I; series scheme (no last
+      // Cholesky): E = G - I.  Then W = I - E/2 + 3/8 E^2 - 5/16 E^3, the series
+      // of (I + E)^{-1/2}, and V3 = V_l W (or W): [Q; Z] V3 is orthonormal to
+      // O(|E|^4).
       auto H = [&](int i, int t) { return zk(i, t, N - 1); };  // free after the last Gram
       auto E = [&](int i, int t) { return zk(i, t, N); };
       auto E2 = [&](int i, int t) { return vk(i, t, N - 1); };
+      auto E3 = [&](int i, int t) { return tk(i, t, N); };      // the accumulated product is tk(N-1)
       int m0 = int(P.mdesc.size());
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t)
-          P.mdesc.push_back(MatopDesc{scr[i].v[t].G, 0, scr[i].v[t].G, P.subs[i].M, 2, 2 * i + t});
-      for (int i = w0; i < w1; ++i)
-        for (int t = 0; t < 2; ++t) P.mdesc.push_back(MatopDesc{0, 0, E(i, t), P.subs[i].M, 0, 2 * i + t});
+          P.mdesc.push_back(MatopDesc{scr[i].v[t].G, 0, scr[i].v[t].G, P.subs[i].M, 2, 2 * i + t, -1});
+      if (!series)
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) P.mdesc.push_back(MatopDesc{0, 0, E(i, t), P.subs[i].M, 0, 2 * i + t, -1});
       matop_step(m0);  // G lower = G upper ; E = -I
-      GemmPhase ph = phase_begin();
-      for (int i = w0; i < w1; ++i)
-        for (int t = 0; t < 2; ++t) {
-          const SubDev &d = P.subs[i];
-          add(ph, scr[i].v[t].G, vk(i, t, N), H(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
-        }
-      gemm_step(ph, lv_exact);
-      GemmPhase ph2 = phase_begin();
-      for (int i = w0; i < w1; ++i)
-        for (int t = 0; t < 2; ++t) {
-          const SubDev &d = P.subs[i];
-          add(ph2, vk(i, t, N), H(i, t), E(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0);
-        }
-      gemm_step(ph2, lv_exact);
+      if (series) {
+        m0 = int(P.mdesc.size());
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t)
+            P.mdesc.push_back(MatopDesc{scr[i].v[t].G, 0, E(i, t), P.subs[i].M, 4, 2 * i + t, -1});
+        matop_step(m0);  // E = G - I
+      } else {
+        GemmPhase ph = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph, scr[i].v[t].G, vk(i, t, N), H(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+          }
+        gemm_step(ph, lv_exact);
+        GemmPhase ph2 = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph2, vk(i, t, N), H(i, t), E(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0);
+          }
+        gemm_step(ph2, lv_exact);
+      }
       GemmPhase ph3 = phase_begin();
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t) {
@@ -873,19 +894,29 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           add(ph3, E(i, t), E(i, t), E2(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, 0, 1.0, 0.0);
         }
       gemm_step(ph3, lv_small);
-      m0 = int(P.mdesc.size());
-      for (int i = w0; i < w1; ++i)
-        for (int t = 0; t < 2; ++t)
-          P.mdesc.push_back(MatopDesc{E(i, t), E2(i, t), E2(i, t), P.subs[i].M, 1, 2 * i + t});
-      matop_step(m0);  // W = I - E/2 + 3/8 E^2 (checks |E|)
-      GemmPhase ph4 = phase_begin();
+      GemmPhase ph5 = phase_begin();
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t) {
           const SubDev &d = P.subs[i];
-          add(ph4, vk(i, t, N), E2(i, t), scr[i].v[t].V3, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_A_UPPER, 1.0,
-              0.0);
+          add(ph5, E2(i, t), E(i, t), E3(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, 0, 1.0, 0.0);
         }
-      gemm_step(ph4, lv_exact);
+      gemm_step(ph5, lv_tiny);
+      m0 = int(P.mdesc.size());
+      for (int i = w0; i < w1; ++i)
+        for (int t = 0; t < 2; ++t)
+          P.mdesc.push_back(MatopDesc{E(i, t), E2(i, t), series ? scr[i].v[t].V3 : E2(i, t), P.subs[i].M, 1,
+                                      2 * i + t, E3(i, t)});
+      matop_step(m0);  // W = I - E/2 + 3/8 E^2 - 5/16 E^3 (checks |E|)
+      if (!series) {
+        GemmPhase ph4 = phase_begin();
+        for (int i = w0; i < w1; ++i)
+          for (int t = 0; t < 2; ++t) {
+            const SubDev &d = P.subs[i];
+            add(ph4, vk(i, t, N), E2(i, t), scr[i].v[t].V3, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_A_UPPER, 1.0,
+                0.0);
+          }
+        gemm_step(ph4, lv_exact);
+      }
     }
     // R^{-1} = T_{N-1} V3
     {
@@ -1089,8 +1120,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       if (!in(cv.src, cv.n) || cv.dst < 0 || cv.dst + cv.n > P.n_f32) return fail("internal: FP32 copy bounds");
     for (const auto &md : P.mdesc) {
       const long long mm = (long long)md.M * md.M;
-      if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm))) || (md.op == 3 && !in(md.a, mm)) ||
-          md.op < 0 || md.op > 3 ||
+      if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm) || (md.d >= 0 && !in(md.d, mm)))) ||
+          ((md.op == 3 || md.op == 4) && !in(md.a, mm)) || md.op < 0 || md.op > 4 ||
           md.status < 0 || md.status >= 2 * n_sub)
         return fail("internal: matrix operation bounds");
     }

@@ -69,12 +69,35 @@ def test_fp32_cholesky_scheme(D, case, prec):
 
 
 def test_too_few_fp32_passes_is_reported(D):
-    """One shifted FP32 pass cannot bring a Gram of condition 1e16 near the identity:
+    """Two shifted FP32 passes cannot bring a Gram of condition ~1e18 near the identity:
     the setup must fail with a status (the series check or a pivot), never return."""
     p = inputs.small_problem(2, 2, M=200, n_int=700, edge_pts=20, n_rhs=1, seed=9)
     with pytest.raises(D.DDELMError):
         D.Solver(p, eps_rel=1e-8, tol=1e-11, precision=D.DDELM_PREC_MIXED,
-                 setup_scheme=D.DDELM_SCHEME_FP32, setup_passes=1)
+                 setup_scheme=D.DDELM_SCHEME_FP32, setup_passes=2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", SCHEME_CASES[:3])
+def test_cqr2_series_scheme(D, case, prec):
+    """Two Cholesky passes, the third replaced by the series of (I + E)^{-1/2}."""
+    nx, ny, M, nI, e, eps, R, seed, _ = case
+    p = inputs.small_problem(nx, ny, M=M, n_int=nI, edge_pts=e, n_rhs=R, seed=seed)
+    o = odd.DDELMOracle(p, odd.Options(eps_rel=eps))
+    pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
+    s, mu, u, info, rc = _solve(D, p, eps_rel=eps, tol=1e-11, precision=pr,
+                                setup_scheme=D.DDELM_SCHEME_CQR2_SERIES)
+    assert rc == D.DDELM_OK
+    tol_op = 1e-9 if eps >= 1e-6 else 1e-6
+    for i in range(p.n_sub):
+        L = o.loc[i]
+        G = slice(L.m - L.nG, L.m)
+        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < tol_op
+        assert _rel(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G]) < tol_op
+    ref = odd.solve(p, odd.Options(eps_rel=eps))
+    tol = 1e-8 if eps >= 1e-6 else 1e-7
+    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < tol
+    assert _rel(u, ref["u_eval"]) < tol
 
 
 def test_fp32_scheme_uneven(D):
@@ -89,7 +112,7 @@ def test_fp32_scheme_uneven(D):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("scheme", [1, 2, 3])
 def test_variable_coefficient_operator(D, prec, scheme):
     """-div(a grad u) = f with a = 1 + 0.5 sin(2 pi x) sin(2 pi y): local operators and solution."""
     p = inputs.small_problem(3, 3, M=80, n_int=200, edge_pts=6, n_rhs=2, seed=21, op=inputs.OP_DIFFUSION)
