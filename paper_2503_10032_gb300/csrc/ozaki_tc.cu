@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
     for (int j = 0; j < 8; ++j) {
       const long long a = shift > 0 ? (v[j] + (1ll << (shift - 1))) >> shift : v[j];
       v[j] -= a << shift;
-      dig[j] = __float2bfloat16_rn((float)a);
+      dig[j] = __float2bfloat16_rn((float)(int)a);  // |a| <= 64: a 32-bit conversion (64-bit ones run on the FP64 pipe)
     }
     *reinterpret_cast<uint4 *>(out + p * plane) = *reinterpret_cast<const uint4 *>(dig);
   }
