@@ -32,7 +32,8 @@ constexpr int NB = 16;   // panel rows
 // with a unit pivot.
 template <typename T>
 __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
-  __shared__ T s_piv;
+  __shared__ T s_piv, s_rinv;
+  __shared__ T rinv[NB];
   const int tid = threadIdx.x;
   const int BW = band > 0 ? band : M;
   for (int k0 = 0; k0 < M; k0 += NB) {
@@ -51,10 +52,11 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
           piv = T(1);
         }
         s_piv = sqrt(piv);
+        s_rinv = T(1) / s_piv;
       }
       __syncthreads();
-      const T r = s_piv;
-      for (int c = t + tid; c < W; c += CT) P[t * W + c] = c == t ? r : P[t * W + c] / r;
+      const T r = s_piv, ri = s_rinv;
+      for (int c = t + tid; c < W; c += CT) P[t * W + c] = c == t ? r : P[t * W + c] * ri;
       __syncthreads();
       for (int e = tid; e < (nb - t - 1) * W; e += CT) {
         const int u = t + 1 + e / W, c = e % W;
@@ -121,17 +123,34 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
       const int r = e / W, c = e % W;
       P[r * W + c] = A[(long long)(i0 + r) * M + i0 + c];
     }
+    if (tid < nb) rinv[tid] = T(1) / A[(long long)(i0 + tid) * M + i0 + tid];
     __syncthreads();
-    for (int j = i0 + tid; j < M; j += CT) {
+    // tpc consecutive lanes share a column (strided k), so that the short block
+    // rows near the bottom still keep every warp busy
+    const int ncol = M - i0;
+    int tpc = 1;
+    while (tpc < 16 && ncol * tpc * 2 <= CT) tpc *= 2;
+    const int part = tid % tpc;
+    for (int jj = tid / tpc; jj < ncol; jj += CT / tpc) {
+      const int j = i0 + jj;
       T acc[NB];
 #pragma unroll
       for (int r = 0; r < NB; ++r) acc[r] = T(0);
       const int kend = min(j, i0 + W - 1);
-      for (int k = i1; k <= kend; ++k) {
+      for (int k = i1 + part; k <= kend; k += tpc) {
         const T vk = V[(long long)k * M + j];
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k - i0)], vk, acc[r]);
       }
+      if (tpc > 1) {
+        // the tpc lanes of this column: aligned, inside one warp, same iteration
+        const unsigned gmask = ((tpc == 32) ? 0xffffffffu : ((1u << tpc) - 1u)) << ((tid & 31) & ~(tpc - 1));
+        __syncwarp(gmask);
+        for (int o = 1; o < tpc; o <<= 1)
+#pragma unroll
+          for (int r = 0; r < NB; ++r) acc[r] += __shfl_xor_sync(gmask, acc[r], o);
+      }
+      if (part == 0) {
       T x[NB];
 #pragma unroll
       for (int r = NB - 1; r >= 0; --r) {
@@ -144,11 +163,12 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
 #pragma unroll
         for (int u = r + 1; u < NB; ++u)
           if (u < nb) v = fma(-P[r * W + u], x[u], v);
-        x[r] = (j >= i) ? v / P[r * W + r] : T(0);
+        x[r] = (j >= i) ? v * rinv[r] : T(0);
       }
 #pragma unroll
       for (int r = 0; r < NB; ++r)
         if (r < nb && j >= i0 + r) V[(long long)(i0 + r) * M + j] = x[r];
+      }
     }
     __syncthreads();
   }
