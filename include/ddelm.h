@@ -189,6 +189,23 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
 int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
                    double *d_grad_g, ddelm_solve_info *info, void *stream);
 
+/* The interface residual of Eq. (nn-mixed) at a given mu: with the handle's
+ * factors and the data (f, g) (device, as in ddelm_solve), writes
+ * d_r [n_delta][n_rhs] = b_theta - S_theta mu_Delta for the caller's
+ * d_mu_delta [n_delta][n_rhs], and (nullable) the coefficients d_c
+ * [sum M][n_rhs] and d_u_eval of Eq. (coarse_sol_2) at that mu (all device).
+ * With f = g = 0 it applies -S_theta and the linear part of the
+ * reconstruction.  Synchronous; DDELM_ERR_TIMEOUT on a barrier timeout. */
+int ddelm_interface_residual(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd,
+                             const double *d_mu_delta, double *d_r, double *d_c, double *d_u_eval, void *stream);
+
+/* Solves S_theta mu_Delta = b for a given device right-hand side d_b
+ * [n_delta][n_rhs] (CG, MIXED: FP32 sweeps inside FP64 refinement) into
+ * d_mu_delta (device).  info as in ddelm_solve (rel_residual: the true FP64
+ * |b - S_theta mu| / |b|; ms_total not measured).  Synchronous. */
+int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta, ddelm_solve_info *info,
+                          void *stream);
+
 /* Copies a local block of subdomain `sub` to host memory for inspection
  * (synchronous).  which: 0 K_c^i [m x M], 1 K-bar^i [m x M], 2 A_m^i [nG x M],
  * 3 Lambda^i = A_m^i K^+ E_Gamma [nG x nG], 4 Psi^i = E_Gamma^T K K^+ E_Gamma

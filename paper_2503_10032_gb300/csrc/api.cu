@@ -392,6 +392,89 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   return rc;
 }
 
+int ddelm_interface_residual(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd,
+                             const double *d_mu_delta, double *d_r, double *d_c, double *d_u_eval, void *stream) {
+  if (!h || !d_mu_delta) return DDELM_ERR_INVALID_ARG;
+  Plan &p = h->plan;
+  if ((p.sz.sum_int > 0 && !d_f_int) || (p.sz.n_bnd > 0 && !d_g_bnd)) return DDELM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *db = dbase(h);
+  const int R = p.n_rhs;
+  double *mu = nullptr, *rhs = nullptr, *res = nullptr;
+  cg_vectors(p, h->ws, &mu, &rhs, &res);
+  if (p.sz.sum_int > 0) CK(cudaMemcpyAsync(db + p.o_fin, d_f_int, (size_t)p.sz.sum_int * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (p.sz.n_bnd > 0) CK(cudaMemcpyAsync(db + p.o_gin, d_g_bnd, (size_t)p.sz.n_bnd * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (p.n_dl > 0) CK(cudaMemcpyAsync(mu, d_mu_delta, (size_t)p.n_dl * R * 8, cudaMemcpyDeviceToDevice, s));
+  LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, db + p.o_fin, db + p.o_gin, s));
+  const auto &G = p.setup_gemm;
+  for (int q = 0; q < 4; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + q], h->ws, s));
+  CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
+  CgArgs a;
+  a.mu_out = db + p.o_muout;
+  a.c_out = db + p.o_cout;
+  a.max_iters = p.opt.max_iters;
+  a.tol = p.opt.tol;
+  a.theta = p.opt.theta;
+  a.mode = 2;
+  LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
+  if (p.sz.sum_eval > 0) {
+    LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + 4], h->ws, s));
+    if (d_u_eval)
+      for (const auto &d : p.subs)
+        if (d.nE > 0)
+          CK(cudaMemcpyAsync(d_u_eval + d.eval_off * R, db + d.oU, (size_t)d.nE * R * 8, cudaMemcpyDeviceToDevice,
+                             s));
+  }
+  if (d_r && p.n_dl > 0) CK(cudaMemcpyAsync(d_r, res, (size_t)p.n_dl * R * 8, cudaMemcpyDeviceToDevice, s));
+  if (d_c) CK(cudaMemcpyAsync(d_c, db + p.o_cout, (size_t)p.sz.sum_M * R * 8, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, db + p.o_status + 2 * p.n_sub + 16, sizeof(int), cudaMemcpyDeviceToHost));
+  return herr ? DDELM_ERR_TIMEOUT : DDELM_OK;
+}
+
+int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta, ddelm_solve_info *info,
+                          void *stream) {
+  if (!h || !d_b || !d_mu_delta) return DDELM_ERR_INVALID_ARG;
+  Plan &p = h->plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *db = dbase(h);
+  const int R = p.n_rhs;
+  double *mu = nullptr, *rhs = nullptr, *res = nullptr;
+  cg_vectors(p, h->ws, &mu, &rhs, &res);
+  if (p.n_dl == 0) return DDELM_OK;
+  CK(cudaMemcpyAsync(rhs, d_b, (size_t)p.n_dl * R * 8, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(db + p.o_status + 2 * p.n_sub + 8, 0, 16 * 8, s));
+  CgArgs a;
+  a.mu_out = nullptr;
+  a.c_out = nullptr;
+  a.max_iters = p.opt.max_iters;
+  a.tol = p.opt.tol;
+  a.theta = p.opt.theta;
+  a.max_refine = p.opt.max_refine;
+  a.mode = 3;
+  LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
+  CK(cudaMemcpyAsync(d_mu_delta, mu, (size_t)p.n_dl * R * 8, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  const long long nd = p.n_dl > 0 ? p.n_dl : 1, np = p.n_pi > 0 ? p.n_pi : 1;
+  double hinfo[40];
+  CK(cudaMemcpy(hinfo, db + p.o_cg + 12 * nd * R + 14 * np * R + 2048 * 32 - 64, sizeof(hinfo),
+                cudaMemcpyDeviceToHost));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, db + p.o_status + 2 * p.n_sub + 16, sizeof(int), cudaMemcpyDeviceToHost));
+  int rc = herr ? DDELM_ERR_TIMEOUT : DDELM_OK;
+  double resmax = 0.0;
+  for (int k = 0; k < R; ++k) resmax = hinfo[1 + k] > resmax ? hinfo[1 + k] : resmax;
+  if (rc == DDELM_OK && int(hinfo[0]) >= p.opt.max_iters && !(resmax < p.opt.tol)) rc = DDELM_ERR_NOT_CONVERGED;
+  if (info) {
+    info->iterations = int(hinfo[0]);
+    info->refinements = p.mixed ? int(hinfo[33]) : 0;
+    info->rel_residual = resmax;
+    info->ms_total = 0.0;
+  }
+  return rc;
+}
+
 int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
                    double *d_grad_g, ddelm_solve_info *info, void *stream) {
   if (!h) return DDELM_ERR_INVALID_ARG;

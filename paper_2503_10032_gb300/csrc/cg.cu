@@ -993,6 +993,19 @@ template <int RC>
 __device__ void forward_program(const Ctx &c) {
   __shared__ double s_bn[16], s_rn[16];
   double *B = c.dl[V_B], *MU = c.dl[V_MU], *Q = c.dl[V_Q];
+  if (c.mode == 3) {  // S_theta mu = B for a given B (tangent and other interface solves)
+    const int it = c.fb ? refine_solve<RC>(c, s_bn) : cg_solve<RC>(c, s_bn);
+    if (it < 0) return;
+    if (!apply_S<RC>(c, MU, Q)) return;
+    for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) c.dl[V_TMP][e] = B[e] - ldg_cg(Q + e);
+    partial_dot<RC>(c, c.dl[V_TMP], c.dl[V_TMP], 0);
+    if (!grid_sync(c)) return;
+    finish_dot<RC>(c, 0, s_rn);
+    if (blockIdx.x == 0 && threadIdx.x < RC && threadIdx.x < c.R)
+      c.info[1 + threadIdx.x] = s_bn[threadIdx.x] > 0.0 ? sqrt(s_rn[threadIdx.x]) / s_bn[threadIdx.x] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.info[0] = it;
+    return;
+  }
   // ---------------- right-hand side b_theta
   // dpi = -sum a_Pi ; ppi = sum p_Pi (a, p are the per-subdomain A_m y and Q_Gamma Q^T f)
   for (int e = gthread(); e < c.n_pi * c.R; e += nthreads()) {
@@ -1018,8 +1031,17 @@ __device__ void forward_program(const Ctx &c) {
   ph_dl_first<RC>(c, c.pv[P_MPF], nullptr, c.pv[P_GF], 1);
   if (!grid_sync(c)) return;
   if (!second_half<RC>(c, B)) return;
-  const int it = c.fb ? refine_solve<RC>(c, s_bn) : cg_solve<RC>(c, s_bn);
-  if (it < 0) return;
+  int it = 0;
+  if (c.mode == 2) {  // mu given: only |b| for the relative residual
+    partial_dot<RC>(c, B, B, 0);
+    if (!grid_sync(c)) return;
+    finish_dot<RC>(c, 0, s_bn);
+    if (threadIdx.x < RC) s_bn[threadIdx.x] = sqrt(s_bn[threadIdx.x]);
+    __syncthreads();
+  } else {
+    it = c.fb ? refine_solve<RC>(c, s_bn) : cg_solve<RC>(c, s_bn);
+    if (it < 0) return;
+  }
   // ---------------- true residual |b - S mu| / |b|
   if (!apply_S<RC>(c, MU, Q)) return;
   for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) c.dl[V_TMP][e] = B[e] - ldg_cg(Q + e);
@@ -1192,13 +1214,23 @@ __device__ void adjoint_program(const Ctx &c) {
 
 template <int RC>
 __global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
-  if (c.mode == 0)
-    forward_program<RC>(c);
-  else
+  if (c.mode == 1)
     adjoint_program<RC>(c);
+  else
+    forward_program<RC>(c);  // 0 solve, 2 residual at a given mu, 3 solve for a given right-hand side
 }
 
 }  // namespace
+
+// the CG region's mu, right-hand side and residual Delta vectors ([n_dl x R] each)
+void cg_vectors(const Plan &p, void *ws, double **mu, double **rhs, double **res) {
+  double *db = reinterpret_cast<double *>(static_cast<char *>(ws) + p.off_dbl);
+  const long long nd = p.n_dl > 0 ? p.n_dl : 1, R = p.n_rhs;
+  double *cg = db + p.o_cg;
+  *mu = cg + V_MU * nd * R;
+  *rhs = cg + V_B * nd * R;
+  *res = cg + V_TMP * nd * R;
+}
 
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) {
   char *base = static_cast<char *>(ws);
@@ -1245,7 +1277,7 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   c.mode = a.mode;
   c.max_refine = a.max_refine;
   c.fb = nullptr;
-  if (p.mixed && p.o_f32 >= 0 && a.mode == 0) {
+  if (p.mixed && p.o_f32 >= 0 && (a.mode == 0 || a.mode == 3)) {
     c.fb = reinterpret_cast<float *>(c.db + p.o_f32);
     c.f_Sinv = p.f_Sinv;
     c.f_C1 = p.f_C1;

@@ -251,9 +251,10 @@ struct CgArgs {
   int max_iters;
   double tol;
   double theta;
-  int mode = 0;  // 0 solve, 1 adjoint
+  int mode = 0;  // 0 solve, 1 adjoint, 2 residual at a given mu, 3 solve for a given right-hand side
   int max_refine = 8;  // MIXED: outer refinement sweeps
 };
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s);
+void cg_vectors(const Plan &p, void *ws, double **mu, double **rhs, double **res);
 
 }  // namespace ddelm

@@ -65,6 +65,7 @@ class ddelm_solve_info(ctypes.Structure):
 
 
 EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm_backward",
+           "ddelm_interface_residual", "ddelm_interface_solve",
            "ddelm_inspect", "ddelm_profile", "ddelm_local_lstsq_static", "ddelm_destroy",
            "ddelm_status_string", "ddelm_last_error")
 DDELM_STATIC_SCRATCH_DOUBLES = 1048576
@@ -94,6 +95,11 @@ def load_library(path: str = LIB_PATH):
     lib.ddelm_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
     lib.ddelm_backward.restype = ctypes.c_int
+    lib.ddelm_interface_residual.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]
+    lib.ddelm_interface_residual.restype = ctypes.c_int
+    lib.ddelm_interface_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
+    lib.ddelm_interface_solve.restype = ctypes.c_int
     lib.ddelm_inspect.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
     lib.ddelm_inspect.restype = ctypes.c_int
     lib.ddelm_local_lstsq_static.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -212,6 +218,18 @@ def ddelm_backward(h, grad_c_ptr, grad_u_ptr, grad_f_ptr, grad_g_ptr, stream):
     return rc, info
 
 
+def ddelm_interface_residual(h, f_ptr, g_ptr, mu_ptr, r_ptr, c_ptr, u_ptr, stream):
+    return _lib.ddelm_interface_residual(h, *(ctypes.c_void_p(x) for x in (f_ptr, g_ptr, mu_ptr, r_ptr, c_ptr,
+                                                                          u_ptr)), ctypes.c_void_p(stream))
+
+
+def ddelm_interface_solve(h, b_ptr, mu_ptr, stream):
+    info = ddelm_solve_info()
+    rc = _lib.ddelm_interface_solve(h, ctypes.c_void_p(b_ptr), ctypes.c_void_p(mu_ptr), ctypes.byref(info),
+                                    ctypes.c_void_p(stream))
+    return rc, info
+
+
 def ddelm_inspect(h, sub: int, which: int, n: int) -> np.ndarray:
     out = np.zeros(max(n, 1), np.float64)
     rc = _lib.ddelm_inspect(h, sub, which, out.ctypes.data_as(_dp), out.size)
@@ -238,6 +256,7 @@ class Solver:
         self.torch = torch
         self.device = torch.device(device)
         self.prob = prob
+        self.opt_kw = dict(opt_kw)
         self.opts = make_options(**opt_kw)
         self.pa = ProblemArgs(prob, self.opts)
         self.sizes = ddelm_query(self.pa)
@@ -276,6 +295,31 @@ class Solver:
         if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
             raise DDELMError(rc, "ddelm_solve")
         return c, mu, u[:sz.sum_eval], info, rc
+
+    def interface_residual(self, f_int, g_bnd, mu_delta):
+        """(r = b_theta - S_theta mu_Delta, c, u_eval) at a given mu_Delta [n_delta, R]."""
+        torch = self.torch
+        R = self.prob.n_rhs
+        sz = self.sizes
+        r = torch.empty((max(sz.n_delta, 1), R), dtype=torch.float64, device=self.device)
+        c = torch.empty((sz.sum_M, R), dtype=torch.float64, device=self.device)
+        u = torch.empty((max(sz.sum_eval, 1), R), dtype=torch.float64, device=self.device)
+        mu = mu_delta.contiguous()
+        rc = ddelm_interface_residual(self.h, f_int.contiguous().data_ptr(), g_bnd.contiguous().data_ptr(),
+                                      mu.data_ptr(), r.data_ptr(), c.data_ptr(), u.data_ptr(),
+                                      self.stream.cuda_stream)
+        if rc != DDELM_OK:
+            raise DDELMError(rc, "ddelm_interface_residual")
+        return r[:sz.n_delta], c, u[:sz.sum_eval]
+
+    def interface_solve(self, b):
+        """mu_Delta with S_theta mu_Delta = b (b: [n_delta, R] device tensor)."""
+        torch = self.torch
+        mu = torch.empty((max(self.sizes.n_delta, 1), self.prob.n_rhs), dtype=torch.float64, device=self.device)
+        rc, info = ddelm_interface_solve(self.h, b.contiguous().data_ptr(), mu.data_ptr(), self.stream.cuda_stream)
+        if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
+            raise DDELMError(rc, "ddelm_interface_solve")
+        return mu[:self.sizes.n_delta], info
 
     def backward(self, grad_c=None, grad_u=None):
         """(dL/df [sum n_int, R], dL/dg [n_bnd, R], info) for cotangents of c and/or u."""

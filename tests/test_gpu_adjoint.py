@@ -104,3 +104,41 @@ def test_fourier_coefficient_gradient(D):
     u_now = U @ a0
     grad_ref = 2.0 / len(u_now) * U.T @ (u_now - np.sin(np.pi * p.x_eval[:, 0]) * np.sin(np.pi * p.x_eval[:, 1]))
     assert _rel(grad, grad_ref) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_scale_gradient(D, prec):
+    """dL/ds for the hidden-layer scale s (w = s w_hat, b = s b_hat), with
+    L = mean (u - sin(pi x) sin(pi y))^2: the tangent path against central
+    differences of the FP64 oracle's solution."""
+    import dataclasses
+    import torch
+    from paper_2503_10032_gb300.autograd import solve_u_scaled
+    p = inputs.make_problem(3, 3, 40, 120, 4, scale=8.0, init="paper", seed=43,
+                            solutions=[inputs._sin2pix_cos3piy()], n_eval=16)
+    pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
+    s = D.Solver(p, eps_rel=1e-6, tol=1e-12, precision=pr)
+    f = _t(p.f_int)
+    g = _t(p.g_bnd)
+    target = np.sin(np.pi * p.x_eval[:, 0]) * np.sin(np.pi * p.x_eval[:, 1])
+    ut = _t(target)[:, None]
+    sc = torch.tensor(p.scale, dtype=torch.float64, device="cuda", requires_grad=True)
+    u = solve_u_scaled(s, f, g, sc)
+    L = ((u - ut) ** 2).mean()
+    L.backward()
+    grad = float(sc.grad)
+
+    def loss_oracle(scale):
+        q = dataclasses.replace(p, scale=scale)
+        uo = odd.solve(q, odd.Options(eps_rel=1e-6))["u_eval"][:, 0]
+        return float(np.mean((uo - target) ** 2))
+
+    h = 1e-4 * p.scale
+    fd = (loss_oracle(p.scale + h) - loss_oracle(p.scale - h)) / (2 * h)
+    assert abs(grad - fd) <= 1e-5 * abs(fd), (grad, fd)
+    # the tangent of u itself against the oracle's central difference
+    from paper_2503_10032_gb300.tangent import scale_tangent
+    _, du = scale_tangent(s, f, g)
+    up = odd.solve(dataclasses.replace(p, scale=p.scale + h), odd.Options(eps_rel=1e-6))["u_eval"]
+    um = odd.solve(dataclasses.replace(p, scale=p.scale - h), odd.Options(eps_rel=1e-6))["u_eval"]
+    assert _rel(du.cpu().numpy(), (up - um) / (2 * h)) < 1e-5
