@@ -125,7 +125,34 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__rest
   double acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-  if (d.ta) {
+  if (d.ta && n == 1) {
+    // one right-hand side: four independent loads in flight per thread
+    const int i = m0 + tx;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (i < d.m) {
+      const long long sb = d.tb ? 1 : d.ldb;  // stride of B's single column
+      int k = ty;
+      for (; k + 24 < d.k; k += 32) {
+        const double x0 = A[(long long)k * d.lda + i], x1 = A[(long long)(k + 8) * d.lda + i];
+        const double x2 = A[(long long)(k + 16) * d.lda + i], x3 = A[(long long)(k + 24) * d.lda + i];
+        a0 = fma(x0, B[k * sb], a0);
+        a1 = fma(x1, B[(k + 8) * sb], a1);
+        a2 = fma(x2, B[(k + 16) * sb], a2);
+        a3 = fma(x3, B[(k + 24) * sb], a3);
+      }
+      for (; k < d.k; k += 8) a0 = fma(A[(long long)k * d.lda + i], B[k * sb], a0);
+    }
+    red[ty][tx][0] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (ty == 0 && i < d.m) {
+      double sm = 0.0;
+      for (int w = 0; w < 8; ++w) sm += red[w][tx][0];
+      double *cp = C + (long long)i * d.ldc;
+      double v = d.alpha * sm;
+      if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+      *cp = v;
+    }
+  } else if (d.ta) {
     const int i = m0 + tx;
     if (i < d.m)
       for (int k = ty; k < d.k; k += 8) {
