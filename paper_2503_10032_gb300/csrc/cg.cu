@@ -686,7 +686,7 @@ __device__ void f_coarse(const Ctx &c, long long A1, const float *x1, long long 
 // P3: lambda = [R_Pi mpi; -x^]; VL = -(Lambda lambda)_Delta ;
 //     BL = -(lambda - Psi lambda)_Delta + Lambda_{Pi,Delta}^T g_Pi
 template <int RC>
-__device__ void f_dl_first(const Ctx &c, const float *x) {
+__device__ void f_dl_first(const Ctx &c, const float *x, const float *mpi, const float *g) {
   float *xs = sh_stage, *gs = sh_stage + MAXG * 16;
   const int R = c.R, w = threadIdx.x >> 5;
   const int ch = n_chunks(c);
@@ -698,10 +698,10 @@ __device__ void f_dl_first(const Ctx &c, const float *x) {
     const int *gpi = c.ints + d.gpi_off, *gdl = c.ints + d.gdl_off;
     for (int e = threadIdx.x; e < d.nG * R; e += blockDim.x) {
       const int a = e / R, k = e % R;
-      xs[e] = a < d.nPi ? __ldcg(c.fpv[FP_MPI] + gpi[a] * R + k) : -__ldcg(x + (long long)gdl[a - d.nPi] * R + k);
+      xs[e] = a < d.nPi ? mpi[gpi[a] * R + k] : -__ldcg(x + (long long)gdl[a - d.nPi] * R + k);
     }
     for (int e = threadIdx.x; e < d.nPi * R; e += blockDim.x)
-      gs[e] = __ldcg(c.fpv[FP_G] + gpi[e / R] * R + e % R);
+      gs[e] = g[gpi[e / R] * R + e % R];
     __syncthreads();
     const float *lam = c.fb + d.oLam32, *psi = c.fb + d.oPsi32, *lamT = c.fb + d.oLamT32;
     for (int dd = r0 + w; dd < r1; dd += CG_WARPS) {
@@ -776,17 +776,68 @@ __device__ void f_g_lamT(const Ctx &c) {
 }
 
 // YL of local Delta row a (column k): ZL + Psi_{Delta,Pi} nu^ - Lambda_{Pi,Delta}^T Dnu^
-__device__ __forceinline__ float f_yl(const Ctx &c, const SubDev &d, int a, int k) {
+__device__ __forceinline__ float f_yl(const Ctx &c, const SubDev &d, int a, int k, const float *nu,
+                                     const float *dnu) {
   const int *gpi = c.ints + d.gpi_off;
   const float *psi = c.fb + d.oPsi32 + (long long)a * d.nG;
   const float *lamT = c.fb + d.oLamT32 + (long long)a * d.nG;
   float v = __ldcg(fslab_row(c, FS_ZL, d, a) + k);
   for (int b = 0; b < d.nPi; ++b) {
     const int gp = gpi[b];
-    v = fmaf(psi[b], __ldcg(c.fpv[FP_NU] + gp * c.R + k), v);
-    v = fmaf(-lamT[b], __ldcg(c.fpv[FP_DNU] + gp * c.R + k), v);
+    v = fmaf(psi[b], nu[gp * c.R + k], v);
+    v = fmaf(-lamT[b], dnu[gp * c.R + k], v);
   }
   return v;
+}
+
+// Small coarse spaces (|Pi|^2 R <= 4096): every CTA gathers the Pi sums and
+// applies the coarse matrices itself, in shared memory, which saves the two
+// grid barriers between gather and product (twice per application).
+constexpr int SMALL_COARSE = 4096;
+__shared__ float sh_pi[6][256];  // |Pi| R <= 256 (implied by |Pi|^2 R <= 4096, R <= 16)
+
+__device__ __forceinline__ bool small_coarse(const Ctx &c) {
+  return c.n_pi > 0 && c.n_pi * c.n_pi * c.R <= SMALL_COARSE;
+}
+
+// in shared memory: o1 = s1 sum sl1 over the Pi owners, o2 = s2 sum sl2 (o2 optional)
+__device__ void f_pi_gather_local(const Ctx &c, int sl1, float s1, float *o1, int sl2, float s2, float *o2) {
+  for (int e = threadIdx.x; e < c.n_pi * c.R; e += blockDim.x) {
+    const int p = e / c.R, k = e % c.R;
+    float a1 = 0.f, a2 = 0.f;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      a1 += __ldcg(fslab_row(c, sl1, d, a) + k);
+      if (o2) a2 += __ldcg(fslab_row(c, sl2, d, a) + k);
+    }
+    o1[e] = s1 * a1;
+    if (o2) o2[e] = s2 * a2;
+  }
+}
+
+// in shared memory: o1 = A1 x1 + b1s B1 y1, o2 = A2 x2 + b2s B2 y2 (B*, o2 optional)
+__device__ void f_coarse_local(const Ctx &c, long long A1, const float *x1, long long B1, const float *y1, float b1s,
+                               float *o1, long long A2, const float *x2, long long B2, const float *y2, float b2s,
+                               float *o2) {
+  const int n = c.n_pi, R = c.R;
+  for (int t = threadIdx.x; t < n * R; t += blockDim.x) {
+    const int p = t / R, k = t % R;
+    float s1 = 0.f, s2 = 0.f;
+    for (int q = 0; q < n; ++q) {
+      const long long e = (long long)p * n + q;
+      s1 = fmaf(c.fb[A1 + e], x1[q * R + k], s1);
+      if (B1 >= 0) s1 = fmaf(b1s * c.fb[B1 + e], y1[q * R + k], s1);
+      if (o2) {
+        s2 = fmaf(c.fb[A2 + e], x2[q * R + k], s2);
+        if (B2 >= 0) s2 = fmaf(b2s * c.fb[B2 + e], y2[q * R + k], s2);
+      }
+    }
+    o1[t] = s1;
+    if (o2) o2[t] = s2;
+  }
 }
 
 // q = S32 x; the last phase (gathers of YL and BL) is fused into the dot product
@@ -794,15 +845,27 @@ __device__ __forceinline__ float f_yl(const Ctx &c, const SubDev &d, int a, int 
 // red slot 0 (no barrier taken after it).
 template <int RC>
 __device__ bool f_apply_S(const Ctx &c, const float *x, float *q) {
+  const bool sm = small_coarse(c);
   f_pi_rows<RC>(c, x);
   if (!grid_sync(c)) return false;
-  f_pi_gather(c, FS_H1, 1.f, c.fpv[FP_PSI], FS_H2, -1.f, c.fpv[FP_RA]);
-  if (!grid_sync(c)) return false;
-  if (c.n_pi > 0)
-    f_coarse(c, c.f_Sinv, c.fpv[FP_RA], c.f_C1, c.fpv[FP_PSI], 1.f, c.fpv[FP_MPI], c.f_C2, c.fpv[FP_PSI], c.f_C3,
-             c.fpv[FP_RA], -1.f, c.fpv[FP_G]);
-  if (!grid_sync(c)) return false;
-  f_dl_first<RC>(c, x);
+  const float *mpi = c.fpv[FP_MPI], *g = c.fpv[FP_G];
+  if (sm) {
+    f_pi_gather_local(c, FS_H1, 1.f, sh_pi[0], FS_H2, -1.f, sh_pi[1]);
+    __syncthreads();
+    f_coarse_local(c, c.f_Sinv, sh_pi[1], c.f_C1, sh_pi[0], 1.f, sh_pi[2], c.f_C2, sh_pi[0], c.f_C3, sh_pi[1], -1.f,
+                   sh_pi[3]);
+    __syncthreads();
+    mpi = sh_pi[2];
+    g = sh_pi[3];
+  } else {
+    f_pi_gather(c, FS_H1, 1.f, c.fpv[FP_PSI], FS_H2, -1.f, c.fpv[FP_RA]);
+    if (!grid_sync(c)) return false;
+    if (c.n_pi > 0)
+      f_coarse(c, c.f_Sinv, c.fpv[FP_RA], c.f_C1, c.fpv[FP_PSI], 1.f, c.fpv[FP_MPI], c.f_C2, c.fpv[FP_PSI], c.f_C3,
+               c.fpv[FP_RA], -1.f, c.fpv[FP_G]);
+    if (!grid_sync(c)) return false;
+  }
+  f_dl_first<RC>(c, x, mpi, g);
   if (!grid_sync(c)) return false;
   f_dl_phi<RC>(c, false, FS_VL, FS_TL, true);
   if (!grid_sync(c)) return false;
@@ -810,12 +873,22 @@ __device__ bool f_apply_S(const Ctx &c, const float *x, float *q) {
   if (!grid_sync(c)) return false;
   f_g_lamT<RC>(c);
   if (!grid_sync(c)) return false;
-  f_pi_gather(c, FS_ZL, 1.f, c.fpv[FP_RNU], -1, 0.f, nullptr);
-  if (!grid_sync(c)) return false;
-  if (c.n_pi > 0)
-    f_coarse(c, c.f_Sinv, c.fpv[FP_RNU], -1, nullptr, 0.f, c.fpv[FP_NU], c.f_C3, c.fpv[FP_RNU], -1, nullptr, 0.f,
-             c.fpv[FP_DNU]);
-  if (!grid_sync(c)) return false;
+  const float *nu = c.fpv[FP_NU], *dnu = c.fpv[FP_DNU];
+  if (sm) {
+    f_pi_gather_local(c, FS_ZL, 1.f, sh_pi[4], -1, 0.f, nullptr);
+    __syncthreads();
+    f_coarse_local(c, c.f_Sinv, sh_pi[4], -1, nullptr, 0.f, sh_pi[5], c.f_C3, sh_pi[4], -1, nullptr, 0.f, sh_pi[2]);
+    __syncthreads();
+    nu = sh_pi[5];
+    dnu = sh_pi[2];
+  } else {
+    f_pi_gather(c, FS_ZL, 1.f, c.fpv[FP_RNU], -1, 0.f, nullptr);
+    if (!grid_sync(c)) return false;
+    if (c.n_pi > 0)
+      f_coarse(c, c.f_Sinv, c.fpv[FP_RNU], -1, nullptr, 0.f, c.fpv[FP_NU], c.f_C3, c.fpv[FP_RNU], -1, nullptr, 0.f,
+               c.fpv[FP_DNU]);
+    if (!grid_sync(c)) return false;
+  }
   // q[delta] = sum_owners (YL + BL)
   for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
     const int gd = e / c.R, k = e % c.R;
@@ -824,7 +897,7 @@ __device__ bool f_apply_S(const Ctx &c, const float *x, float *q) {
     const SubDev &da = c.subs[sa];
     const SubDev &dB = c.subs[sb];
     const int2 rw = *reinterpret_cast<const int2 *>(c.ints + c.o_dl_rows + 2 * gd);
-    q[e] = f_yl(c, da, da.nPi + la, k) + f_yl(c, dB, dB.nPi + lb, k) +
+    q[e] = f_yl(c, da, da.nPi + la, k, nu, dnu) + f_yl(c, dB, dB.nPi + lb, k, nu, dnu) +
            __ldcg(c.fslab[FS_BL] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[FS_BL] + (long long)rw.y * c.R + k);
   }
   return true;

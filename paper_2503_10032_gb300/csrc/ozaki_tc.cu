@@ -141,6 +141,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// named barrier of the 256 epilogue threads (warps 2-9)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 // pairs (p, q) of level l with p, q < S, in a fixed order
 __device__ __forceinline__ int level_pairs(int l, int S, int &p0) {
   p0 = l - (S - 1) > 0 ? l - (S - 1) : 0;
@@ -157,6 +160,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[NACC], bar_acc_empty[NACC],
       bar_drain;
   __shared__ uint32_t tmem_base_sh;
+  __shared__ double s_scale[256];  // row scales (times alpha), then column scales
+  __shared__ int s_fail;
 
   const OzTile tl = tiles[blockIdx.x];
   const OzDesc d = descs[tl.desc];
@@ -302,6 +307,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
     const int half = ew >> 2;                 // column half
     const int row = quad * 32 + lane;
+    const int et = threadIdx.x - 64;          // 0..255 among the epilogue threads
+    // the tile's row and column scales (times alpha) in shared memory
+    if (et < 128) {
+      const int gi = tl.tm * BM + et;
+      s_scale[et] = gi < d.m ? db[d.scaleA + gi] * d.alpha : 0.0;
+    } else {
+      const int gj = tl.tn * BN + et - 128;
+      s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
+    }
+    if (et == 0) s_fail = 0;
+    epi_sync();
     double acc[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0.0;
@@ -340,17 +356,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_arrive(smem_u32(&bar_acc_empty[b0]));
       if (two) mbar_arrive(smem_u32(&bar_acc_empty[b1]));
     }
-    if (ok) {
+    // every epilogue thread gets here (a failed wait only breaks the loop)
+    if (!ok) s_fail = 1;
+    epi_sync();
+    if (!s_fail) {
       const int gi = tl.tm * BM + row;
       if (gi < d.m) {
-        const double si = db[d.scaleA + gi] * d.alpha;
+        const double si = s_scale[row];
         double *crow = db + d.c + (long long)gi * d.ldc;
         const int j0 = tl.tn * BN + half * 64;
 #pragma unroll
         for (int j = 0; j < 64; ++j) {
           const int gj = j0 + j;
           if (gj < d.n) {
-            double v = si * db[d.scaleB + gj] * acc[j];
+            double v = si * s_scale[128 + half * 64 + j] * acc[j];
             if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
             crow[gj] = v;
           }
