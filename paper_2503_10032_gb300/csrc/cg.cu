@@ -588,6 +588,30 @@ __device__ __forceinline__ float row_dot(const float *__restrict__ m, int n, con
   return a;
 }
 
+// cnt <= 4 consecutive rows (stride ld) at once, so that their loads overlap
+template <int RC>
+__device__ __forceinline__ void row_dot4(const float *__restrict__ m, long long ld, int cnt, int n, const float *xs,
+                                         int R, float (&v)[4]) {
+  if (RC == 1) {
+    const int lane = threadIdx.x & 31;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = lane; j < n; j += 32) {
+      const float x = xs[j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < cnt) a[i] = fmaf(__ldg(m + i * ld + j), x, a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+      v[i] = a[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = i < cnt ? row_dot<RC>(m + i * ld, n, xs, R) : 0.f;
+  }
+}
+
 // the lane that stores column k of a row_dot result (k < R)
 template <int RC>
 __device__ __forceinline__ bool row_writer(int R, int &k) {
@@ -602,7 +626,7 @@ __device__ __forceinline__ bool row_writer(int R, int &k) {
 
 // work items of a per-subdomain phase: (subdomain, row chunk)
 __device__ __forceinline__ int n_chunks(const Ctx &c) {
-  int ch = (2 * (int)gridDim.x + c.n_sub - 1) / c.n_sub;
+  int ch = ((int)gridDim.x + c.n_sub - 1) / c.n_sub;
   return ch < 1 ? 1 : (ch > 8 ? 8 : ch);
 }
 
@@ -739,10 +763,15 @@ __device__ void f_dl_phi(const Ctx &c, bool transposed, int in, int out, bool ke
     }
     __syncthreads();
     const float *M = c.fb + (transposed ? d.oPhiT32 : d.oPhi32);
-    for (int dd = r0 + w; dd < r1; dd += CG_WARPS) {
-      const float v = row_dot<RC>(M + (long long)dd * d.nDl, d.nDl, xs, R);
+    for (int dd = r0 + 4 * w; dd < r1; dd += 4 * CG_WARPS) {
+      const int cnt = min(4, r1 - dd);
+      float v[4];
+      row_dot4<RC>(M + (long long)dd * d.nDl, d.nDl, cnt, d.nDl, xs, R, v);
       int k;
-      if (row_writer<RC>(R, k)) fslab_row(c, out, d, d.nPi + dd)[k] = -v;
+      if (row_writer<RC>(R, k))
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < cnt) fslab_row(c, out, d, d.nPi + dd + i)[k] = -v[i];
     }
     __syncthreads();
   }
@@ -766,10 +795,15 @@ __device__ void f_g_lamT(const Ctx &c) {
     }
     __syncthreads();
     const float *lamT = c.fb + d.oLamT32;
-    for (int a = r0 + w; a < r1; a += CG_WARPS) {
-      const float v = row_dot<RC>(lamT + (long long)a * d.nG + d.nPi, d.nDl, xs, R);
+    for (int a = r0 + 4 * w; a < r1; a += 4 * CG_WARPS) {
+      const int cnt = min(4, r1 - a);
+      float v[4];
+      row_dot4<RC>(lamT + (long long)a * d.nG + d.nPi, d.nG, cnt, d.nDl, xs, R, v);
       int k;
-      if (row_writer<RC>(R, k)) fslab_row(c, FS_ZL, d, a)[k] = v;
+      if (row_writer<RC>(R, k))
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < cnt) fslab_row(c, FS_ZL, d, a + i)[k] = v[i];
     }
     __syncthreads();
   }
