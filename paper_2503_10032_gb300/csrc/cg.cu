@@ -70,22 +70,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Sense-counting grid barrier; gives up after 2 s of waiting (error word set).
+// Counting grid barrier with a generation word; gives up after 2 s of waiting
+// (error word set).  The arrival is an acq_rel atomic and the wait an acquire
+// load: together with the CTA barriers around them they order every thread's
+// prior writes before every thread's later reads, without a full fence.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ bool grid_sync(const Ctx &c) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = c.bar + 1;
-    const unsigned my = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(c.bar, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(c.bar, 0u);
-      __threadfence();
-      atomicAdd(c.bar + 1, 1u);
+    unsigned *count = c.bar, *gen = c.bar + 1;
+    unsigned my;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(my) : "l"(gen) : "memory");
+    unsigned arrived;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(count) : "memory");
+    if (arrived + 1 == gridDim.x) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(my + 1u) : "memory");
     } else {
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
-      while (*vgen == my) {
+      while (ld_acquire_u32(gen) == my) {
         if ((++spins & 1023u) == 0u) {
           if (*(volatile int *)c.err) break;
           if (global_ns() - t0 > 2000000000ull) {
@@ -95,7 +104,6 @@ __device__ bool grid_sync(const Ctx &c) {
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int *)c.err == 0;
@@ -626,7 +634,7 @@ __device__ __forceinline__ bool row_writer(int R, int &k) {
 
 // work items of a per-subdomain phase: (subdomain, row chunk)
 __device__ __forceinline__ int n_chunks(const Ctx &c) {
-  int ch = ((int)gridDim.x + c.n_sub - 1) / c.n_sub;
+  int ch = (int)gridDim.x / c.n_sub;  // at most one work item per CTA
   return ch < 1 ? 1 : (ch > 8 ? 8 : ch);
 }
 
