@@ -127,16 +127,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+// x16 TMEM load without the wait (tmem_wait_ld() before using the registers)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -337,18 +338,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const double scale = ldexp(1.0, -6 * (l0 + 2));
       const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 8) {
-        float v0[8], v1[8];
-        tmem_ld8(lane_base + (uint32_t)(b0 * BN) + c0, v0);
-        if (two) {
-          tmem_ld8(lane_base + (uint32_t)(b1 * BN) + c0, v1);
-        } else {
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        // both accumulators' loads in flight before the one wait
+        uint32_t r0[16], r1[16];
+        tmem_ld16_nowait(lane_base + (uint32_t)(b0 * BN) + c0, r0);
+        if (two) tmem_ld16_nowait(lane_base + (uint32_t)(b1 * BN) + c0, r1);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v1[j] = 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int x = __float2int_rn(v0[j]) + mul * __float2int_rn(v1[j]);
+        for (int j = 0; j < 16; ++j) {
+          const int x = __float2int_rn(__uint_as_float(r0[j])) + (two ? mul * __float2int_rn(__uint_as_float(r1[j])) : 0);
           acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
         }
       }
