@@ -15,12 +15,16 @@
 //
 // Kernel layout (one CTA per 128x128 output tile, 10 warps):
 //   warp 0     TMA producer: 128x64 BF16 boxes of A and B slices, 128B swizzle,
-//              6-stage shared-memory ring guarded by mbarriers;
+//              4-stage shared-memory ring guarded by mbarriers.  Two levels
+//              (la, la-1) are computed together: a stage holds A_p, B_{la-p}
+//              and B_{la-1-p}, so each A box feeds two MMAs (the slice GEMM is
+//              bound by L2->SM traffic; this loads ~22% fewer boxes);
 //   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
 //              (M=128, N=128, K=16, both operands K-major), four FP32
-//              accumulators of 128 TMEM columns each, committed per level/chunk;
+//              accumulators of 128 TMEM columns (two per level pair, double
+//              buffered), committed per level pair and k-chunk;
 //   warps 2-9  epilogue: tcgen05.ld of their lane quadrant and column half,
-//              two level sums at a time combined exactly in int32, FP64
+//              the pair's level sums combined exactly in int32, FP64
 //              accumulation in registers, scaled store of C.
 // Every wait is bounded (2 s); on a timeout the CTA records an error, waits for
 // its own copies and MMAs, frees its TMEM and returns.
@@ -37,8 +41,8 @@ namespace ddelm {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 6;
-constexpr int STAGE_BYTES = (BM + BN) * BK * 2;  // 32 KB
+constexpr int STAGES = 4;
+constexpr int STAGE_BYTES = (BM + 2 * BN) * BK * 2;  // 48 KB: A_p, B_{la-p}, B_{lb-p}
 constexpr int OZ_THREADS = 320;
 constexpr int NACC = 4;                // FP32 level accumulators of 128 TMEM columns
 constexpr unsigned TMEM_COLS = 512;
@@ -145,13 +149,6 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // named barrier of the 256 epilogue threads (warps 2-9)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// pairs (p, q) of level l with p, q < S, in a fixed order
-__device__ __forceinline__ int level_pairs(int l, int S, int &p0) {
-  p0 = l - (S - 1) > 0 ? l - (S - 1) : 0;
-  const int p1 = l < S - 1 ? l : S - 1;
-  return p1 - p0 + 1;
-}
-
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozaki_gemm_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles,
                       const CUtensorMap *__restrict__ maps, double *__restrict__ db, int *__restrict__ err) {
@@ -171,7 +168,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int kblo = tl.kb0, kbhi = tl.kb1;      // 64-wide k blocks this tile needs
   const int kcb = d.kc / BK;                   // k blocks per exact chunk
   const int nchunk = kbhi > kblo ? (kbhi - kblo + kcb - 1) / kcb : 0;
-  const int ngroups = S * nchunk;
+  // a group is (level pair, k-chunk): levels la = S-1-2j (smaller weight) and
+  // lb = la-1 accumulate together, in TMEM accumulators 2(G%2) and 2(G%2)+1
+  const int nlp = (S + 1) / 2;
+  const int ngroups = nlp * nchunk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -208,12 +208,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       long long issued = 0;
       bool ok = true;
       for (int g = 0; g < ngroups && ok; ++g) {
-        const int l = S - 1 - g / nchunk, c = g % nchunk;
-        int p0;
-        const int np = level_pairs(l, S, p0);
+        const int la = S - 1 - 2 * (g / nchunk), lb = la - 1, c = g % nchunk;
         const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
-        for (int t = 0; t < np && ok; ++t) {
-          const int p = p0 + t, q = l - p;
+        // stage p: A_p with B_{la-p} (level la) and, for p <= lb, B_{lb-p} (level lb)
+        for (int p = 0; p <= la && ok; ++p) {
+          const bool both = lb >= 0 && p <= lb;
           for (int kb = kb0; kb < kb1; ++kb) {
             if (issued >= STAGES && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
               ok = false;
@@ -222,9 +221,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
             const uint32_t sb = sa + BM * BK * 2;
             const uint32_t fb = smem_u32(&bar_full[st]);
-            mbar_expect_tx(fb, STAGE_BYTES);
+            mbar_expect_tx(fb, both ? STAGE_BYTES : (BM + BN) * BK * 2);
             tma_load_2d(sa, ma, kb * BK, p * d.RpadA + tl.tm * BM, fb);
-            tma_load_2d(sb, mb, kb * BK, q * d.RpadB + tl.tn * BN, fb);
+            tma_load_2d(sb, mb, kb * BK, (la - p) * d.RpadB + tl.tn * BN, fb);
+            if (both) tma_load_2d(sb + BN * BK * 2, mb, kb * BK, (lb - p) * d.RpadB + tl.tn * BN, fb);
             ++issued;
             if (++st == STAGES) {
               st = 0;
@@ -255,16 +255,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int g = 0; g < ngroups && ok; ++g) {
-        const int b = g % NACC;
-        if (g >= NACC && !mbar_wait(smem_u32(&bar_acc_empty[b]), ((g / NACC) - 1) & 1u, err)) break;
+        const int bA = (g & 1) * 2;
+        if (g >= 2 && (!mbar_wait(smem_u32(&bar_acc_empty[bA]), ((g >> 1) - 1) & 1u, err) ||
+                       !mbar_wait(smem_u32(&bar_acc_empty[bA + 1]), ((g >> 1) - 1) & 1u, err)))
+          break;
         tc_fence_after();
-        const int l = S - 1 - g / nchunk, c = g % nchunk;
-        int p0;
-        const int np = level_pairs(l, S, p0);
+        const int la = S - 1 - 2 * (g / nchunk), lb = la - 1, c = g % nchunk;
         const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
-        const uint32_t dacc = tmem + (uint32_t)(b * BN);
-        uint32_t accum = 0;
-        for (int t = 0; t < np && ok; ++t) {
+        const uint32_t da = tmem + (uint32_t)(bA * BN), dbb = tmem + (uint32_t)((bA + 1) * BN);
+        uint32_t acc_a = 0, acc_b = 0;
+        for (int p = 0; p <= la && ok; ++p) {
+          const bool both = lb >= 0 && p <= lb;
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
               ok = false;
@@ -275,8 +276,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t sb = sa + BM * BK * 2;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(dacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), accum);
-              accum = 1;
+              mma_bf16(da, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), acc_a);
+              acc_a = 1;
+              if (both) {
+                mma_bf16(dbb, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + BN * BK * 2 + kk * 32), acc_b);
+                acc_b = 1;
+              }
             }
             mma_commit(smem_u32(&bar_empty[st]));
             if (++st == STAGES) {
@@ -285,7 +290,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             }
           }
         }
-        if (ok) mma_commit(smem_u32(&bar_acc_full[b]));
+        if (ok) {
+          // both accumulators are released to the epilogue (the second may be unused)
+          mma_commit(smem_u32(&bar_acc_full[bA]));
+          mma_commit(smem_u32(&bar_acc_full[bA + 1]));
+        }
       }
       // all MMAs issued by this thread complete before TMEM is released
       mma_commit(smem_u32(&bar_drain));
@@ -323,36 +332,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0.0;
     bool ok = true;
-    for (int g = 0; g < ngroups && ok; g += 2) {
-      const bool two = g + 1 < ngroups;
-      const int b0 = g % NACC, b1 = (g + 1) % NACC;
-      if (!mbar_wait(smem_u32(&bar_acc_full[b0]), (g / NACC) & 1u, err) ||
-          (two && !mbar_wait(smem_u32(&bar_acc_full[b1]), ((g + 1) / NACC) & 1u, err))) {
+    for (int g = 0; g < ngroups && ok; ++g) {
+      const int bA = (g & 1) * 2;
+      const uint32_t par = (g >> 1) & 1u;
+      if (!mbar_wait(smem_u32(&bar_acc_full[bA]), par, err) || !mbar_wait(smem_u32(&bar_acc_full[bA + 1]), par, err)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const int l0 = S - 1 - g / nchunk;
-      const int l1 = two ? S - 1 - (g + 1) / nchunk : l0;
-      const int mul = (l1 == l0) ? 1 : 64;  // l1 = l0 - 1 otherwise
-      const double scale = ldexp(1.0, -6 * (l0 + 2));
+      const int la = S - 1 - 2 * (g / nchunk), lb = la - 1;
+      const bool two = lb >= 0;
+      const double scale = ldexp(1.0, -6 * (la + 2));
       const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 16) {
         // both accumulators' loads in flight before the one wait
         uint32_t r0[16], r1[16];
-        tmem_ld16_nowait(lane_base + (uint32_t)(b0 * BN) + c0, r0);
-        if (two) tmem_ld16_nowait(lane_base + (uint32_t)(b1 * BN) + c0, r1);
+        tmem_ld16_nowait(lane_base + (uint32_t)(bA * BN) + c0, r0);
+        if (two) tmem_ld16_nowait(lane_base + (uint32_t)((bA + 1) * BN) + c0, r1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int x = __float2int_rn(__uint_as_float(r0[j])) + (two ? mul * __float2int_rn(__uint_as_float(r1[j])) : 0);
+          const int x = __float2int_rn(__uint_as_float(r0[j])) + (two ? 64 * __float2int_rn(__uint_as_float(r1[j])) : 0);
           acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
         }
       }
       tc_fence_before();
-      mbar_arrive(smem_u32(&bar_acc_empty[b0]));
-      if (two) mbar_arrive(smem_u32(&bar_acc_empty[b1]));
+      mbar_arrive(smem_u32(&bar_acc_empty[bA]));
+      mbar_arrive(smem_u32(&bar_acc_empty[bA + 1]));
     }
     // every epilogue thread gets here (a failed wait only breaks the loop)
     if (!ok) s_fail = 1;
