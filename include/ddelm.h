@@ -217,7 +217,8 @@ int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta
  * out_len >= 5; entries past out_len are not written), 9 the setup plan
  * {scheme, Cholesky passes before the last, setup waves, subdomains per wave,
  * setup graph captured, solve graph captured} (sub ignored, out_len >= 4; the
- * last two when out_len >= 6).  Blocks 0-2 are
+ * last two when out_len >= 6), 10 V = R^{-1} of the ridge factorisation of
+ * [K_c^i; eps I] [M x M].  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */

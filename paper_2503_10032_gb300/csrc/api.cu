@@ -566,6 +566,10 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       src = d.oPhi;
       n = (size_t)d.nDl * d.nDl;
       break;
+    case 10:
+      src = d.oV;
+      n = (size_t)d.M * d.M;
+      break;
     case 8: {  // algorithmic flops: setup GEMMs, Cholesky+inverse, solve GEMMs (no CG),
                // tensor-core flops of the MIXED setup, FP64-engine flops left in MIXED
       if (out_len < 5) return DDELM_ERR_INVALID_ARG;

@@ -31,7 +31,7 @@ constexpr int NB = 16;   // panel rows
 // in-band entries are touched.  A non-positive pivot sets *bad and continues
 // with a unit pivot.
 template <typename T>
-__device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
+__device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int invb = 0) {
   __shared__ T s_piv, s_rinv;
   __shared__ T rinv[NB];
   const int tid = threadIdx.x;
@@ -126,8 +126,9 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad) {
     if (tid < nb) rinv[tid] = T(1) / A[(long long)(i0 + tid) * M + i0 + tid];
     __syncthreads();
     // tpc consecutive lanes share a column (strided k), so that the short block
-    // rows near the bottom still keep every warp busy
-    const int ncol = M - i0;
+    // rows near the bottom still keep every warp busy.  invb > 0: columns only
+    // up to the end of the invb-block holding row i0 (diagonal blocks of R^{-1})
+    const int ncol = (invb > 0 ? min(M, (i0 / invb + 1) * invb) : M) - i0;
     int tpc = 1;
     while (tpc < 16 && ncol * tpc * 2 <= CT) tpc *= 2;
     const int part = tid % tpc;
@@ -235,7 +236,8 @@ __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict
     for (int j = threadIdx.x; j < M; j += CT) G[(long long)j * M + j] += add;
     __syncthreads();
   }
-  chol_inv_core<double>(G, V, M, cd.band, P, &s_bad);
+  if (cd.epsout >= 0 && threadIdx.x == 0) db[cd.epsout] = sqrt(eps2);
+  chol_inv_core<double>(G, V, M, cd.band, P, &s_bad, cd.inv_block);
   if (cd.z >= 0) {
     double *Z = db + cd.z;
     const double e = sqrt(eps2);
@@ -289,7 +291,7 @@ __global__ void convert_f32_kernel(const ConvSeg *__restrict__ segs, const doubl
 // small batched matrix operations of the polishing step:
 //   op 0: C = -I ;  op 1: C = I - A/2 + 3/8 B - 5/16 D  (the series of
 //   (I + A)^{-1/2} with B = A^2, D = A^3) ;  op 2: C symmetric from its upper
-//   triangle ;  op 3: C = A ;  op 4: C = A - I.
+//   triangle ;  op 3: C = A ;  op 4: C = A - I ;  op 5: C = b A (b a scalar in memory).
 // op 1 flags the subdomain when max |A| > 1e-4: beyond that the neglected
 // fourth-order term could reach the FP64 level.
 __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__restrict__ db, int *__restrict__ status) {
@@ -310,8 +312,10 @@ __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__rest
       if (i > j) db[md.c + e] = db[md.c + j * md.M + i];
     } else if (md.op == 3) {
       db[md.c + e] = db[md.a + e];
-    } else {
+    } else if (md.op == 4) {
       db[md.c + e] = db[md.a + e] - (i == j ? 1.0 : 0.0);
+    } else {
+      db[md.c + e] = db[md.b] * db[md.a + e];
     }
   }
   if (big) status[md.status] = 1;

@@ -102,15 +102,16 @@ struct CholDesc {
   int prec;     // 0 FP64, 1 FP32
   int band;     // > 0: G and R vanish beyond this many superdiagonals
   int status;   // index into the status array
-  int pad;
+  int inv_block; // > 0: only the inv_block x inv_block diagonal blocks of R^{-1} (the rest by GEMMs)
   double eps_rel;
   double shift_rel;
+  long long epsout;  // >= 0: dbase offset receiving eps = sqrt(eps^2) (the ridge block is formed later)
 };
 
 struct MatopDesc {
   long long a, b, c;
   int M, op;   // op 0: C = -I ; op 1: C = I - A/2 + 3/8 B - 5/16 D ; op 2: lower(C) = upper(C)^T ;
-               // op 3: C = A ; op 4: C = A - I
+               // op 3: C = A ; op 4: C = A - I ; op 5: C = b A (b: the scalar at offset b)
   int status;  // op 1: set when max |A| exceeds the range of the series
   long long d; // op 1: third-order term (< 0: none)
 };
@@ -175,6 +176,7 @@ struct Plan {
   long long n_dbl = 0;     // doubles in the region
   long long o_w = 0, o_b = 0, o_xint = 0, o_aint = 0, o_gaint = 0;  // problem data
   long long o_status = 0;  // int status slots (in ints region? kept as doubles)
+  long long o_eps = 0;     // per local matrix: eps of the ridge (2 per subdomain)
   long long o_fin = 0, o_gin = 0, o_cout = 0, o_muout = 0, o_uout = 0;  // solve staging
   // MIXED: FP32 region (dbase offset o_f32, n_f32 floats): operator copies and
   // the inner CG's Delta vectors (6), Pi vectors (7) and local slabs (8)

@@ -274,6 +274,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.o_cg = take(12 * nd_ * nR + 14 * np * nR + 2048 * 32 + 128);
   P.o_loc = take(9LL * sum_nG * nR);
   P.o_status = take(4 * n_sub + 64);
+  P.o_eps = take(2LL * n_sub);
   // solve-call staging: the caller's f, g in, c, mu, u out (fixed addresses, so
   // one captured graph serves every call)
   P.o_fin = take(sumI * R);
@@ -701,6 +702,10 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // and O(M^3) product a GEMM phase, then the local operators.
   const bool fp32 = P.scheme == DDELM_SCHEME_FP32;
   const bool series = P.scheme == DDELM_SCHEME_CQR2_SERIES;
+  // MIXED, FP64 passes: the Cholesky kernel (FP64 on CUDA cores, one SM per
+  // matrix) inverts only the 128 x 128 diagonal blocks of R
+  constexpr int INVB = 128;
+  const bool blocked_inv = !fp32 && o.precision == DDELM_PREC_MIXED;
   const int N = P.n_pass;
   // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
   // accurate well below the shift; every other product keeps 54 bits.
@@ -798,9 +803,56 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             c.shift_kind = last ? 0 : 2;
             c.shift_rel = std::max(1e-4, 2.0 * d.M * 5.9604644775390625e-8);
           }
+          c.epsout = -1;
+          if (blocked_inv && d.M > INVB) {
+            // R^{-1} beyond the diagonal blocks comes from the tensor cores below;
+            // the ridge block eps R^{-1} after it
+            c.inv_block = INVB;
+            if (c.z >= 0) {
+              c.epsout = P.o_eps + 2 * i + t;
+              c.z = -1;
+            }
+          }
           P.cdesc.push_back(c);
         }
       chol_step(c0);
+      if (blocked_inv) {
+        // block back substitution, block rows from the bottom:
+        //   T = R[r, r+1:] V[r+1:, r+1:] ;  V[r, r+1:] = -V_rr T
+        int maxnb = 0;
+        for (int i = w0; i < w1; ++i) maxnb = std::max(maxnb, (P.subs[i].M + INVB - 1) / INVB);
+        for (int st = 0; st + 2 <= maxnb; ++st) {
+          // (a phase's descriptors and tiles are contiguous: build one phase at a time)
+          for (int half = 0; half < 2; ++half) {
+            GemmPhase ph = phase_begin();
+            for (int i = w0; i < w1; ++i)
+              for (int t = 0; t < 2; ++t) {
+                const SubDev &d = P.subs[i];
+                const int nbi = (d.M + INVB - 1) / INVB;
+                const int r = nbi - 2 - st;
+                if (d.M <= INVB || r < 0) continue;
+                const long long M = d.M, r0 = (long long)r * INVB, r1 = r0 + INVB, n1 = M - r1;
+                const long long V = (last && !P.polish) ? scr[i].v[t].V3 : vk(i, t, k);
+                const long long Tb = scr[i].v[t].W32;  // INVB x n1 scratch (FP64 passes leave it free)
+                if (half == 0)
+                  add(ph, scr[i].v[t].G + r0 * M + r1, V + r1 * M + r1, Tb, INVB, int(n1), int(n1), d.M, d.M,
+                      int(n1), 0, 0, GEMM_B_UPPER, 1.0, 0.0);
+                else
+                  add(ph, V + r0 * M + r0, Tb, V + r0 * M + r1, INVB, int(n1), INVB, d.M, int(n1), d.M, 0, 0,
+                      GEMM_A_UPPER, -1.0, 0.0);
+              }
+            gemm_step(ph, lv_factor);
+          }
+        }
+        if (k == 0) {
+          const int m0 = int(P.mdesc.size());
+          for (int i = w0; i < w1; ++i)
+            for (int t = 0; t < 2; ++t)
+              if (P.subs[i].M > INVB)
+                P.mdesc.push_back(MatopDesc{vk(i, t, 0), P.o_eps + 2 * i + t, zk(i, t, 0), P.subs[i].M, 5, 2 * i + t, -1});
+          if ((int)P.mdesc.size() > m0) matop_step(m0);  // Z1 = eps V1
+        }
+      }
       if (last) break;
       // Q_{k+1} = Q_k V_k, Z_{k+1} = Z_k V_k, T_k = T_{k-1} V_k (T_0 = V_0)
       {
@@ -1072,6 +1124,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     c.v = P.o_Vpi;
     c.z = -1;
     c.w = -1;
+    c.epsout = -1;
     c.M = n_pi;
     c.m = n_pi;
     c.status = 2 * n_sub;
@@ -1079,7 +1132,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   }
   P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
   for (const auto &c : P.cdesc) {
-    const double f = 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
+    double f = 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
+    if (c.inv_block > 0) {  // factor + the diagonal blocks of the inverse
+      f = c.M * (double)c.M * c.M / 3.0;
+      for (int b0 = 0; b0 < c.M; b0 += c.inv_block) {
+        const double bs = std::min(c.inv_block, c.M - b0);
+        f += bs * bs * bs / 3.0;
+      }
+    }
     P.chol_flops += f;
     if (c.prec == 1) P.chol_flops32 += f;
   }
@@ -1109,11 +1169,16 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
     for (const auto &t : P.gtile)
       if (t.desc < 0 || t.desc >= (int)P.gdesc.size()) return fail("internal: GEMM tile");
+    for (const auto &ph : P.setup_gemm)  // a phase's tiles use only its own descriptors
+      for (int q = ph.tile0; q < ph.tile0 + ph.ntile; ++q)
+        if (P.gtile[q].desc < ph.desc0 || P.gtile[q].desc >= ph.desc0 + ph.ndesc)
+          return fail("internal: GEMM phase tiles");
     for (const auto &c : P.cdesc) {
       const long long mm = (long long)c.M * c.M;
       if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm)) || (c.prec == 1 && !in(c.w, mm)))
         return fail("internal: Cholesky bounds");
       if (c.prec == 1 && c.band != 0) return fail("internal: banded FP32 Cholesky");
+      if (c.epsout >= 0 && !in(c.epsout, 1)) return fail("internal: eps slot");
       if (c.status < 0 || c.status > 2 * n_sub) return fail("internal: status slot");
     }
     for (const auto &cv : P.conv)
@@ -1121,7 +1186,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (const auto &md : P.mdesc) {
       const long long mm = (long long)md.M * md.M;
       if (!in(md.c, mm) || (md.op == 1 && (!in(md.a, mm) || !in(md.b, mm) || (md.d >= 0 && !in(md.d, mm)))) ||
-          ((md.op == 3 || md.op == 4) && !in(md.a, mm)) || md.op < 0 || md.op > 4 ||
+          ((md.op == 3 || md.op == 4 || md.op == 5) && !in(md.a, mm)) || (md.op == 5 && !in(md.b, 1)) ||
+          md.op < 0 || md.op > 5 ||
           md.status < 0 || md.status >= 2 * n_sub)
         return fail("internal: matrix operation bounds");
     }

@@ -138,6 +138,7 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
     cd[k].M = M;
     cd[k].m = m;
     cd[k].w = -1;
+    cd[k].epsout = -1;
     cd[k].ridge = k == 0;
     cd[k].shift_kind = k == 0 ? 1 : 0;
     cd[k].status = k;

@@ -341,7 +341,7 @@ class Solver:
         sizes = ddelm_inspect(self.h, sub, 7, 4)
         m, M, nG, nDl = (int(v) for v in sizes)
         shapes = {0: (m, M), 1: (m, M), 2: (nG, M), 3: (nG, nG), 4: (nG, nG), 5: (nDl, nDl),
-                  6: (self.sizes.n_pi, self.sizes.n_pi)}
+                  6: (self.sizes.n_pi, self.sizes.n_pi), 10: (M, M)}
         shp = shapes[which]
         return ddelm_inspect(self.h, sub, which, shp[0] * shp[1]).reshape(shp)
 
