@@ -13,7 +13,7 @@
 // TMEM once per k-chunk and added in FP64 (levels from the smallest to the
 // largest).  The truncation after S levels is the only approximation.
 //
-// Kernel layout (one CTA per 128x128 output tile, 10 warps):
+// Kernel layout (persistent: one CTA per SM walking 128x128 output tiles, 10 warps):
 //   warp 0     TMA producer: 128x64 BF16 boxes of A and B slices, 128B swizzle,
 //              4-stage shared-memory ring guarded by mbarriers.  Two levels
 //              (la, la-1) are computed together: a stage holds A_p, B_{la-p}
@@ -149,8 +149,26 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // named barrier of the 256 epilogue threads (warps 2-9)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// group count of one tile: (level pair, k-chunk) pairs
+struct TileGeom {
+  int S, kblo, kbhi, kcb, nchunk, ngroups;
+};
+__device__ __forceinline__ TileGeom tile_geom(const OzDesc &d, const OzTile &tl) {
+  TileGeom t;
+  t.S = d.S;
+  t.kblo = tl.kb0;
+  t.kbhi = tl.kb1;
+  t.kcb = d.kc / BK;
+  t.nchunk = t.kbhi > t.kblo ? (t.kbhi - t.kblo + t.kcb - 1) / t.kcb : 0;
+  t.ngroups = ((t.S + 1) / 2) * t.nchunk;
+  return t;
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ...; the shared-memory ring,
+// the TMEM accumulators and every barrier phase run on across tiles, so a
+// tile's epilogue overlaps the next tile's loads and MMAs.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    ozaki_gemm_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles,
+    ozaki_gemm_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles, int ntile,
                       const CUtensorMap *__restrict__ maps, double *__restrict__ db, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -159,19 +177,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       bar_drain;
   __shared__ uint32_t tmem_base_sh;
   __shared__ double s_scale[256];  // row scales (times alpha), then column scales
-  __shared__ int s_fail;
-
-  const OzTile tl = tiles[blockIdx.x];
-  const OzDesc d = descs[tl.desc];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int S = d.S;
-  const int kblo = tl.kb0, kbhi = tl.kb1;      // 64-wide k blocks this tile needs
-  const int kcb = d.kc / BK;                   // k blocks per exact chunk
-  const int nchunk = kbhi > kblo ? (kbhi - kblo + kcb - 1) / kcb : 0;
-  // a group is (level pair, k-chunk): levels la = S-1-2j (smaller weight) and
-  // lb = la-1 accumulate together, in TMEM accumulators 2(G%2) and 2(G%2)+1
-  const int nlp = (S + 1) / 2;
-  const int ngroups = nlp * nchunk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -199,42 +205,47 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
-      const CUtensorMap *ma = maps + d.tmapA;
-      const CUtensorMap *mb = maps + d.tmapB;
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
       int st = 0;
       uint32_t ph = 0;
       long long issued = 0;
       bool ok = true;
-      for (int g = 0; g < ngroups && ok; ++g) {
-        const int la = S - 1 - 2 * (g / nchunk), lb = la - 1, c = g % nchunk;
-        const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
-        // stage p: A_p with B_{la-p} (level la) and, for p <= lb, B_{lb-p} (level lb)
-        for (int p = 0; p <= la && ok; ++p) {
-          const bool both = lb >= 0 && p <= lb;
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (issued >= STAGES && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t sb = sa + BM * BK * 2;
-            const uint32_t fb = smem_u32(&bar_full[st]);
-            mbar_expect_tx(fb, both ? STAGE_BYTES : (BM + BN) * BK * 2);
-            tma_load_2d(sa, ma, kb * BK, p * d.RpadA + tl.tm * BM, fb);
-            tma_load_2d(sb, mb, kb * BK, (la - p) * d.RpadB + tl.tn * BN, fb);
-            if (both) tma_load_2d(sb + BN * BK * 2, mb, kb * BK, (lb - p) * d.RpadB + tl.tn * BN, fb);
-            ++issued;
-            if (++st == STAGES) {
-              st = 0;
-              ph ^= 1u;
+      for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
+        const OzTile tl = tiles[ti];
+        const OzDesc d = descs[tl.desc];
+        const TileGeom tg = tile_geom(d, tl);
+        const CUtensorMap *ma = maps + d.tmapA;
+        const CUtensorMap *mb = maps + d.tmapB;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
+        for (int g = 0; g < tg.ngroups && ok; ++g) {
+          const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1, c = g % tg.nchunk;
+          const int kb0 = tg.kblo + c * tg.kcb, kb1 = min(tg.kbhi, kb0 + tg.kcb);
+          // stage p: A_p with B_{la-p} (level la) and, for p <= lb, B_{lb-p} (level lb)
+          for (int p = 0; p <= la && ok; ++p) {
+            const bool both = lb >= 0 && p <= lb;
+            for (int kb = kb0; kb < kb1; ++kb) {
+              if (issued >= STAGES && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+              const uint32_t sb = sa + BM * BK * 2;
+              const uint32_t fb = smem_u32(&bar_full[st]);
+              mbar_expect_tx(fb, both ? STAGE_BYTES : (BM + BN) * BK * 2);
+              tma_load_2d(sa, ma, kb * BK, p * d.RpadA + tl.tm * BM, fb);
+              tma_load_2d(sb, mb, kb * BK, (la - p) * d.RpadB + tl.tn * BN, fb);
+              if (both) tma_load_2d(sb + BN * BK * 2, mb, kb * BK, (lb - p) * d.RpadB + tl.tn * BN, fb);
+              ++issued;
+              if (++st == STAGES) {
+                st = 0;
+                ph ^= 1u;
+              }
             }
           }
         }
       }
       // drain: every stage issued must have landed before the CTA may exit
-      for (int k = 0; k < STAGES && k < issued; ++k) {
+      for (int q = 0; q < STAGES && q < issued; ++q) {
         if (--st < 0) {
           st = STAGES - 1;
           ph ^= 1u;
@@ -254,46 +265,54 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int st = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int g = 0; g < ngroups && ok; ++g) {
-        const int bA = (g & 1) * 2;
-        if (g >= 2 && (!mbar_wait(smem_u32(&bar_acc_empty[bA]), ((g >> 1) - 1) & 1u, err) ||
-                       !mbar_wait(smem_u32(&bar_acc_empty[bA + 1]), ((g >> 1) - 1) & 1u, err)))
-          break;
-        tc_fence_after();
-        const int la = S - 1 - 2 * (g / nchunk), lb = la - 1, c = g % nchunk;
-        const int kb0 = kblo + c * kcb, kb1 = min(kbhi, kb0 + kcb);
-        const uint32_t da = tmem + (uint32_t)(bA * BN), dbb = tmem + (uint32_t)((bA + 1) * BN);
-        uint32_t acc_a = 0, acc_b = 0;
-        for (int p = 0; p <= la && ok; ++p) {
-          const bool both = lb >= 0 && p <= lb;
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t sb = sa + BM * BK * 2;
+      long long G = 0;  // groups across tiles
+      for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
+        const OzTile tl = tiles[ti];
+        const TileGeom tg = tile_geom(descs[tl.desc], tl);
+        for (int g = 0; g < tg.ngroups && ok; ++g, ++G) {
+          const int bA = (int)(G & 1) * 2;
+          const uint32_t pe = (uint32_t)(((G >> 1) - 1) & 1);
+          if (G >= 2 && (!mbar_wait(smem_u32(&bar_acc_empty[bA]), pe, err) ||
+                         !mbar_wait(smem_u32(&bar_acc_empty[bA + 1]), pe, err))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1, c = g % tg.nchunk;
+          const int kb0 = tg.kblo + c * tg.kcb, kb1 = min(tg.kbhi, kb0 + tg.kcb);
+          const uint32_t da = tmem + (uint32_t)(bA * BN), dbb = tmem + (uint32_t)((bA + 1) * BN);
+          uint32_t acc_a = 0, acc_b = 0;
+          for (int p = 0; p <= la && ok; ++p) {
+            const bool both = lb >= 0 && p <= lb;
+            for (int kb = kb0; kb < kb1; ++kb) {
+              if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+              const uint32_t sb = sa + BM * BK * 2;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(da, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), acc_a);
-              acc_a = 1;
-              if (both) {
-                mma_bf16(dbb, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + BN * BK * 2 + kk * 32), acc_b);
-                acc_b = 1;
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                mma_bf16(da, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), acc_a);
+                acc_a = 1;
+                if (both) {
+                  mma_bf16(dbb, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + BN * BK * 2 + kk * 32), acc_b);
+                  acc_b = 1;
+                }
+              }
+              mma_commit(smem_u32(&bar_empty[st]));
+              if (++st == STAGES) {
+                st = 0;
+                ph ^= 1u;
               }
             }
-            mma_commit(smem_u32(&bar_empty[st]));
-            if (++st == STAGES) {
-              st = 0;
-              ph ^= 1u;
-            }
           }
-        }
-        if (ok) {
-          // both accumulators are released to the epilogue (the second may be unused)
-          mma_commit(smem_u32(&bar_acc_full[bA]));
-          mma_commit(smem_u32(&bar_acc_full[bA + 1]));
+          if (ok) {
+            // both accumulators are released to the epilogue (the second may be unused)
+            mma_commit(smem_u32(&bar_acc_full[bA]));
+            mma_commit(smem_u32(&bar_acc_full[bA + 1]));
+          }
         }
       }
       // all MMAs issued by this thread complete before TMEM is released
@@ -308,75 +327,80 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: warps 2..9
-    // Groups are taken in pairs (two TMEM accumulators; the MMA issuer fills
-    // the other two meanwhile).  A pair is either two k-chunks of one level or
-    // level l+1 followed by level l; in both cases x = L_a + (1 or 64) L_b is an
-    // exact int32 (|L| < 2^23.6), so one FP64 FMA per pair combines the levels
-    // (the FP64 pipe of this GPU does 4 flop/clk/SM).
+    // Each group holds levels la and la-1 of one k-chunk in two TMEM
+    // accumulators (the MMA issuer fills the other two meanwhile);
+    // x = L_la + 64 L_{la-1} is an exact int32 (|L| < 2^23.6), so one FP64 FMA
+    // per group combines the two levels (this GPU's FP64 pipe does 4 flop/clk/SM).
+    // After a failed wait every thread still walks the same tiles and named
+    // barriers (skipping the work), so the barriers cannot deadlock.
     const int ew = warp - 2;                  // 0..7
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
     const int half = ew >> 2;                 // column half
     const int row = quad * 32 + lane;
     const int et = threadIdx.x - 64;          // 0..255 among the epilogue threads
-    // the tile's row and column scales (times alpha) in shared memory
-    if (et < 128) {
-      const int gi = tl.tm * BM + et;
-      s_scale[et] = gi < d.m ? db[d.scaleA + gi] * d.alpha : 0.0;
-    } else {
-      const int gj = tl.tn * BN + et - 128;
-      s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
-    }
-    if (et == 0) s_fail = 0;
-    epi_sync();
-    double acc[64];
-#pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0.0;
     bool ok = true;
-    for (int g = 0; g < ngroups && ok; ++g) {
-      const int bA = (g & 1) * 2;
-      const uint32_t par = (g >> 1) & 1u;
-      if (!mbar_wait(smem_u32(&bar_acc_full[bA]), par, err) || !mbar_wait(smem_u32(&bar_acc_full[bA + 1]), par, err)) {
-        ok = false;
-        break;
+    long long G = 0;
+    for (int ti = blockIdx.x; ti < ntile; ti += gridDim.x) {
+      const OzTile tl = tiles[ti];
+      const OzDesc d = descs[tl.desc];
+      const TileGeom tg = tile_geom(d, tl);
+      epi_sync();  // the previous tile's stores no longer read the scales
+      // the tile's row and column scales (times alpha) in shared memory
+      if (et < 128) {
+        const int gi = tl.tm * BM + et;
+        s_scale[et] = gi < d.m ? db[d.scaleA + gi] * d.alpha : 0.0;
+      } else {
+        const int gj = tl.tn * BN + et - 128;
+        s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
       }
-      tc_fence_after();
-      const int la = S - 1 - 2 * (g / nchunk), lb = la - 1;
-      const bool two = lb >= 0;
-      const double scale = ldexp(1.0, -6 * (la + 2));
-      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+      epi_sync();
+      double acc[64];
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        // both accumulators' loads in flight before the one wait
-        uint32_t r0[16], r1[16];
-        tmem_ld16_nowait(lane_base + (uint32_t)(bA * BN) + c0, r0);
-        if (two) tmem_ld16_nowait(lane_base + (uint32_t)((bA + 1) * BN) + c0, r1);
-        tmem_wait_ld();
+      for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+      for (int g = 0; g < tg.ngroups; ++g, ++G) {
+        const int bA = (int)(G & 1) * 2;
+        const uint32_t par = (uint32_t)((G >> 1) & 1);
+        if (ok && (!mbar_wait(smem_u32(&bar_acc_full[bA]), par, err) ||
+                   !mbar_wait(smem_u32(&bar_acc_full[bA + 1]), par, err)))
+          ok = false;
+        if (!ok) continue;
+        tc_fence_after();
+        const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1;
+        const bool two = lb >= 0;
+        const double scale = ldexp(1.0, -6 * (la + 2));
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int x = __float2int_rn(__uint_as_float(r0[j])) + (two ? 64 * __float2int_rn(__uint_as_float(r1[j])) : 0);
-          acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          // both accumulators' loads in flight before the one wait
+          uint32_t r0[16], r1[16];
+          tmem_ld16_nowait(lane_base + (uint32_t)(bA * BN) + c0, r0);
+          if (two) tmem_ld16_nowait(lane_base + (uint32_t)((bA + 1) * BN) + c0, r1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int x =
+                __float2int_rn(__uint_as_float(r0[j])) + (two ? 64 * __float2int_rn(__uint_as_float(r1[j])) : 0);
+            acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
+          }
         }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bar_acc_empty[bA]));
+        mbar_arrive(smem_u32(&bar_acc_empty[bA + 1]));
       }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&bar_acc_empty[bA]));
-      mbar_arrive(smem_u32(&bar_acc_empty[bA + 1]));
-    }
-    // every epilogue thread gets here (a failed wait only breaks the loop)
-    if (!ok) s_fail = 1;
-    epi_sync();
-    if (!s_fail) {
-      const int gi = tl.tm * BM + row;
-      if (gi < d.m) {
-        const double si = s_scale[row];
-        double *crow = db + d.c + (long long)gi * d.ldc;
-        const int j0 = tl.tn * BN + half * 64;
+      if (ok) {
+        const int gi = tl.tm * BM + row;
+        if (gi < d.m) {
+          const double si = s_scale[row];
+          double *crow = db + d.c + (long long)gi * d.ldc;
+          const int j0 = tl.tn * BN + half * 64;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          const int gj = j0 + j;
-          if (gj < d.n) {
-            double v = si * s_scale[128 + half * 64 + j] * acc[j];
-            if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
-            crow[gj] = v;
+          for (int j = 0; j < 64; ++j) {
+            const int gj = j0 + j;
+            if (gj < d.n) {
+              double v = si * s_scale[128 + half * 64 + j] * acc[j];
+              if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
+              crow[gj] = v;
+            }
           }
         }
       }
@@ -530,7 +554,18 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
   const size_t smem = STAGES * STAGE_BYTES + 1024;
   cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  { ozaki_gemm_kernel<<<ph.ntile, OZ_THREADS, smem, s>>>(od, ot, maps, db, err); DDELM_COUNT_LAUNCH(); }
+  static int nsm = 0;  // one persistent CTA per SM
+  if (nsm == 0) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || nsm <= 0) {
+      nsm = 0;
+      return e != cudaSuccess ? e : cudaErrorUnknown;
+    }
+  }
+  const int grid = ph.ntile < nsm ? ph.ntile : nsm;
+  { ozaki_gemm_kernel<<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
