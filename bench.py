@@ -421,7 +421,7 @@ def main():
     if fp64_cmp is not None:
         line["fp64"] = fp64_cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, dt, ns = oracle_sample(prob, max(1, prob.n_sub // 4))
+        est, dt, ns = oracle_sample(prob, prob.n_sub)  # the whole local setup: ~10-20 s of host work
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count() or 1,
                                 "kind": "oracle",
                                 "sample": f"FP64 oracle local setup of {ns} of {prob.n_sub} subdomains "
