@@ -24,21 +24,29 @@ extern std::atomic<long long> g_kernel_launches;
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
 // ---------------------------------------------------------------- rows
-// Rows of the local matrices other than the interior collocation rows.
+// Rows of the local matrices other than the interior collocation rows.  They
+// are written in two passes: the first evaluates tanh once per (point, neuron)
+// and writes point values and fluxes; the second forms the rows that are
+// combinations of rows of the first (the change of variables of Sec. 3.2 and
+// the A_m corner rows), reading them instead of evaluating tanh again.
 enum RowKind : int {
   ROW_POINT = 0,  // C phi = B phi = phi(x)
-  ROW_TINV = 1,   // (T^i)^{-1} C phi: phi(x) - alpha phi(x_a) - beta phi(x_b)
-  ROW_FLUX = 2,   // F phi = (w . n)(1 - tanh^2)
-  ROW_AM = 3,     // A_m corner row: mean edge fluxes (Sec. 3.2)
+  ROW_DELTA = 1,  // Delta point: phi(x) to out0/out1 and F phi = (w . n)(1 - tanh^2) to out2/out3;
+                  // second pass: phi(x) - alpha phi(x_a) - beta phi(x_b) ((T^i)^{-1} C phi)
+  ROW_AM = 3,     // A_m corner row: mean edge fluxes (Sec. 3.2), second pass only
 };
 
 struct SpecialRow {
   int kind, sub;
   long long out0, out1;  // row starts in dbase (out1 < 0: single output)
+  long long out2, out3;  // ROW_DELTA: K-bar Delta row and A_m Delta row (flux)
+  long long ca, cb;      // rows holding phi(x_a), phi(x_b) (ROW_DELTA; < 0: none) or phi(corner) (ROW_AM)
   double x, y, nx, ny;
-  double alpha, xa, ya, beta, xb, yb;
-  // A_m: two edges (start x, start y, end x, end y, normal x, normal y) and e
-  double am[2][6];
+  double alpha, beta;
+  // ROW_AM: per edge meeting the corner, its outward normal, the first of its
+  // e flux rows (consecutive A_m rows) and e
+  double am_n[2][2];
+  long long am_f[2];
   int am_e[2];
 };
 

@@ -6,7 +6,9 @@
 //   L phi (Poisson)   = 2 |w|^2 t (1 - t^2)
 //   L phi (diffusion) = 2 a |w|^2 t (1 - t^2) - (grad a . w)(1 - t^2)
 //   B phi = C phi = t,   F phi = (w . n)(1 - t^2)
-// with t = tanh(w . x + b).
+// with t = tanh(w . x + b).  The interior rows and the first pass over the
+// other rows take one tanh per (point, neuron); the rows that combine point
+// values or fluxes (change of variables, A_m corner rows) are formed from them.
 #include <algorithm>
 
 #include "ddelm_internal.h"
@@ -55,46 +57,65 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
   }
 }
 
+// First pass over the special rows: one tanh per (point, neuron).
 __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__restrict__ rows,
                                                            const SubDev *__restrict__ subs,
                                                            double *__restrict__ db, long long o_w,
                                                            long long o_b) {
   const SpecialRow rw = rows[blockIdx.x];
+  if (rw.kind == ROW_AM) return;
   const SubDev d = subs[rw.sub];
   const double *w = db + o_w + 2 * d.w_off;
   const double *b = db + o_b + d.w_off;
   double *o0 = db + rw.out0;
   double *o1 = rw.out1 >= 0 ? db + rw.out1 : nullptr;
+  const bool delta = rw.kind == ROW_DELTA;
   for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
-    const double wx = w[2 * j], wy = w[2 * j + 1], bj = b[j];
-    double v;
-    if (rw.kind == ROW_POINT) {
-      v = feat_t(wx, wy, bj, rw.x, rw.y);
-    } else if (rw.kind == ROW_TINV) {
-      v = feat_t(wx, wy, bj, rw.x, rw.y);
-      if (rw.alpha != 0.0) v -= rw.alpha * feat_t(wx, wy, bj, rw.xa, rw.ya);
-      if (rw.beta != 0.0) v -= rw.beta * feat_t(wx, wy, bj, rw.xb, rw.yb);
-    } else if (rw.kind == ROW_FLUX) {
-      const double t = feat_t(wx, wy, bj, rw.x, rw.y);
-      v = (rw.nx * wx + rw.ny * wy) * (1.0 - t * t);
-    } else {  // ROW_AM: sum over the two edges of the mean flux over {corner, e edge points}
-      v = 0.0;
-      for (int e = 0; e < 2; ++e) {
-        const double sx = rw.am[e][0], sy = rw.am[e][1], ex = rw.am[e][2], ey = rw.am[e][3];
-        const double wn = rw.am[e][4] * wx + rw.am[e][5] * wy;
-        const int ne = rw.am_e[e];
-        double t = feat_t(wx, wy, bj, rw.x, rw.y);
-        double acc = 1.0 - t * t;
-        for (int k = 1; k <= ne; ++k) {
-          const double f = double(k) / double(ne + 1);
-          t = feat_t(wx, wy, bj, sx + f * (ex - sx), sy + f * (ey - sy));
-          acc += 1.0 - t * t;
-        }
-        v += wn * acc / double(ne + 1);
-      }
+    const double wx = w[2 * j], wy = w[2 * j + 1];
+    const double t = feat_t(wx, wy, b[j], rw.x, rw.y);
+    o0[j] = t;
+    if (o1) o1[j] = t;
+    if (delta) {
+      const double f = (rw.nx * wx + rw.ny * wy) * (1.0 - t * t);
+      db[rw.out2 + j] = f;
+      db[rw.out3 + j] = f;
     }
-    o0[j] = v;
-    if (o1) o1[j] = v;
+  }
+}
+
+// Second pass: rows that combine first-pass rows of the same subdomain.
+//   Delta row with the change of variables: phi(x) - alpha phi(x_a) - beta phi(x_b)
+//   A_m corner row: sum over the two edges of the mean of F phi over the corner
+//   and the e edge points (the corner's flux from its point value)
+__global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *__restrict__ rows,
+                                                              const SubDev *__restrict__ subs,
+                                                              double *__restrict__ db, long long o_w) {
+  const SpecialRow rw = rows[blockIdx.x];
+  const bool tinv = rw.kind == ROW_DELTA && (rw.ca >= 0 || rw.cb >= 0);
+  if (!tinv && rw.kind != ROW_AM) return;
+  const SubDev d = subs[rw.sub];
+  const double *w = db + o_w + 2 * d.w_off;
+  const long long M = d.M;
+  for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+    if (tinv) {
+      double v = db[rw.out0 + j];
+      if (rw.ca >= 0) v -= rw.alpha * db[rw.ca + j];
+      if (rw.cb >= 0) v -= rw.beta * db[rw.cb + j];
+      db[rw.out0 + j] = v;
+      db[rw.out1 + j] = v;
+    } else {
+      const double wx = w[2 * j], wy = w[2 * j + 1];
+      const double tc = db[rw.ca + j];
+      const double sc = 1.0 - tc * tc;
+      double v = 0.0;
+      for (int e = 0; e < 2; ++e) {
+        const int ne = rw.am_e[e];
+        double acc = (rw.am_n[e][0] * wx + rw.am_n[e][1] * wy) * sc;
+        for (int k = 0; k < ne; ++k) acc += db[rw.am_f[e] + k * M + j];
+        v += acc / double(ne + 1);
+      }
+      db[rw.out0 + j] = v;
+    }
   }
 }
 
@@ -115,7 +136,10 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
     { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
   }
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
-  if (r1 > r0) { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
+  if (r1 > r0) {
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w); DDELM_COUNT_LAUNCH(); }
+  }
   const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
   if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();

@@ -140,6 +140,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     std::vector<double> al, be;
     std::vector<int> alp, bep;
     std::vector<std::vector<EdgeRef>> am_edges;  // per local Pi: the two edges meeting it
+    std::map<int, int> dstart;                    // edge id -> index of its first Delta point
   };
   std::vector<SubGeo> sg(n_sub);
   const int H = g.H();
@@ -178,6 +179,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       const int n = pr.edge_pts[e.id];
       auto a = locpi.find({e.sv[0], e.sv[1]});
       auto b = locpi.find({e.ev[0], e.ev[1]});
+      s.dstart[e.id] = int(s.dxy.size());
       for (int k = 1; k <= n; ++k) {
         double f = double(k) / double(n + 1);
         s.dxy.push_back(g.edge_point(e, k));
@@ -467,59 +469,54 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       P.rows.push_back(r);
     }
     const int g0 = d.nI + d.nB;
+    auto pi_row = [&](int k) { return d.oK + (long long)(g0 + k) * M; };  // phi at local Pi point k
     for (int k = 0; k < d.nPi; ++k) {  // Pi rows: point values in K_c and K-bar
       SpecialRow r = base(ROW_POINT);
       r.x = s.pxy[k].x;
       r.y = s.pxy[k].y;
-      r.out0 = d.oK + (long long)(g0 + k) * M;
+      r.out0 = pi_row(k);
       r.out1 = d.oKb + (long long)(g0 + k) * M;
       P.rows.push_back(r);
-      SpecialRow a = base(ROW_AM);  // A_m corner row
-      a.x = s.pxy[k].x;
-      a.y = s.pxy[k].y;
-      a.out0 = d.oA + (long long)k * M;
-      for (int t = 0; t < 2; ++t) {
-        const EdgeRef &e = s.am_edges[k][t];
-        V2 sa = g.vxy(e.sv), sb = g.vxy(e.ev);
-        a.am[t][0] = sa.x;
-        a.am[t][1] = sa.y;
-        a.am[t][2] = sb.x;
-        a.am[t][3] = sb.y;
-        a.am[t][4] = e.n[0];
-        a.am[t][5] = e.n[1];
-        a.am_e[t] = pr.edge_pts[e.id];
-      }
-      P.rows.push_back(a);
     }
     for (int k = 0; k < d.nDl; ++k) {
-      // K_c Delta row (also A-bar row): (T^i)^{-1} C phi, or C phi without the change
-      SpecialRow r = base(o.use_change_of_vars ? ROW_TINV : ROW_POINT);
+      // K_c Delta row (also A-bar row): (T^i)^{-1} C phi, or C phi without the
+      // change of variables; K-bar Delta row (also A_m Delta row): F phi
+      SpecialRow r = base(ROW_DELTA);
       r.x = s.dxy[k].x;
       r.y = s.dxy[k].y;
+      r.nx = s.dnrm[k].x;
+      r.ny = s.dnrm[k].y;
+      r.ca = r.cb = -1;
       if (o.use_change_of_vars) {
-        r.alpha = s.al[k];
-        r.beta = s.be[k];
         if (s.alp[k] >= 0) {
-          r.xa = s.pxy[s.alp[k]].x;
-          r.ya = s.pxy[s.alp[k]].y;
+          r.alpha = s.al[k];
+          r.ca = pi_row(s.alp[k]);
         }
         if (s.bep[k] >= 0) {
-          r.xb = s.pxy[s.bep[k]].x;
-          r.yb = s.pxy[s.bep[k]].y;
+          r.beta = s.be[k];
+          r.cb = pi_row(s.bep[k]);
         }
       }
       r.out0 = d.oK + (long long)(g0 + d.nPi + k) * M;
       r.out1 = d.oAbar + (long long)k * M;
+      r.out2 = d.oKb + (long long)(g0 + d.nPi + k) * M;
+      r.out3 = d.oA + (long long)(d.nPi + k) * M;
       P.rows.push_back(r);
-      // flux row: K-bar Delta row and A_m Delta row
-      SpecialRow f = base(ROW_FLUX);
-      f.x = s.dxy[k].x;
-      f.y = s.dxy[k].y;
-      f.nx = s.dnrm[k].x;
-      f.ny = s.dnrm[k].y;
-      f.out0 = d.oKb + (long long)(g0 + d.nPi + k) * M;
-      f.out1 = d.oA + (long long)(d.nPi + k) * M;
-      P.rows.push_back(f);
+    }
+    for (int k = 0; k < d.nPi; ++k) {  // A_m corner rows from the flux rows of the two edges
+      SpecialRow a = base(ROW_AM);
+      a.out0 = d.oA + (long long)k * M;
+      a.ca = pi_row(k);
+      for (int t = 0; t < 2; ++t) {
+        const EdgeRef &e = s.am_edges[k][t];
+        a.am_n[t][0] = e.n[0];
+        a.am_n[t][1] = e.n[1];
+        a.am_e[t] = pr.edge_pts[e.id];
+        // an edge meeting a cross point is an interface edge: its Delta points are
+        // the e points the mean runs over
+        a.am_f[t] = d.oA + (long long)(d.nPi + s.dstart.at(e.id)) * M;
+      }
+      P.rows.push_back(a);
     }
   }
   sub_row0[n_sub] = int(P.rows.size());
@@ -1196,6 +1193,15 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (const auto &r : P.rows) {
       const long long M = P.subs[r.sub].M;
       if (!in(r.out0, M) || (r.out1 >= 0 && !in(r.out1, M))) return fail("internal: row output bounds");
+      if (r.kind == ROW_DELTA && (!in(r.out2, M) || !in(r.out3, M) || (r.ca >= 0 && !in(r.ca, M)) ||
+                                  (r.cb >= 0 && !in(r.cb, M))))
+        return fail("internal: Delta row bounds");
+      if (r.kind == ROW_AM) {
+        if (!in(r.ca, M)) return fail("internal: corner row bounds");
+        for (int t = 0; t < 2; ++t)
+          if (r.am_e[t] < 0 || (r.am_e[t] > 0 && !in(r.am_f[t], (long long)r.am_e[t] * M)))
+            return fail("internal: A_m flux row bounds");
+      }
     }
     for (const auto &d : P.subs) {
       const long long M = d.M, m = d.m;
