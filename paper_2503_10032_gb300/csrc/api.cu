@@ -5,6 +5,7 @@
 // the caller's workspace.
 #include <algorithm>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -129,6 +130,17 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   for (long long j = 0; j < sumM; ++j) b[j] = prob->scale * prob->b_hat[j];
   CK(cudaMemcpyAsync(db + p.o_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(db + p.o_b, b.data(), b.size() * 8, cudaMemcpyHostToDevice, s));
+  // feature constants: the kernels evaluate tanh(u / 2) at u = 2 (w . x + b)
+  std::vector<double> fc(4 * sumM), ex2(256);
+  for (long long j = 0; j < sumM; ++j) {
+    fc[4 * j] = 2.0 * w[2 * j];
+    fc[4 * j + 1] = 2.0 * w[2 * j + 1];
+    fc[4 * j + 2] = 2.0 * b[j];
+    fc[4 * j + 3] = 2.0 * (w[2 * j] * w[2 * j] + w[2 * j + 1] * w[2 * j + 1]);
+  }
+  for (int j = 0; j < 256; ++j) ex2[j] = double(std::exp2l(-(long double)j / 256.0L));
+  CK(cudaMemcpyAsync(db + p.o_fc, fc.data(), fc.size() * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_exp2, ex2.data(), ex2.size() * 8, cudaMemcpyHostToDevice, s));
   if (sumI > 0) {
     CK(cudaMemcpyAsync(db + p.o_xint, prob->x_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
     if (p.op == DDELM_OP_DIFFUSION) {

@@ -183,6 +183,8 @@ struct Plan {
   size_t off_dbl = 0;      // byte offset of the double region
   long long n_dbl = 0;     // doubles in the region
   long long o_w = 0, o_b = 0, o_xint = 0, o_aint = 0, o_gaint = 0;  // problem data
+  long long o_fc = 0;    // per neuron (2 w_x, 2 w_y, 2 b, 2 |w|^2)
+  long long o_exp2 = 0;  // 2^(-j/256), j < 256 (the feature tanh)
   long long o_status = 0;  // int status slots (in ints region? kept as doubles)
   long long o_eps = 0;     // per local matrix: eps of the ridge (2 per subdomain)
   long long o_fin = 0, o_gin = 0, o_cout = 0, o_muout = 0, o_uout = 0;  // solve staging

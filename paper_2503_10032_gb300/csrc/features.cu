@@ -6,7 +6,7 @@
 //   L phi (Poisson)   = 2 |w|^2 t (1 - t^2)
 //   L phi (diffusion) = 2 a |w|^2 t (1 - t^2) - (grad a . w)(1 - t^2)
 //   B phi = C phi = t,   F phi = (w . n)(1 - t^2)
-// with t = tanh(w . x + b).  The interior rows and the first pass over the
+// with t = tanh(w . x + b) (tanh_half below).  The interior rows and the first pass over the
 // other rows take one tanh per (point, neuron); the rows that combine point
 // values or fluxes (change of variables, A_m corner rows) are formed from them.
 #include <algorithm>
@@ -17,20 +17,66 @@ namespace ddelm {
 
 namespace {
 
-__device__ __forceinline__ double feat_t(double wx, double wy, double b, double x, double y) {
-  return tanh(fma(wx, x, wy * y) + b);
+// tanh(u / 2) in about 18 FP64 operations (the FP64 pipe of this GPU is the
+// scarce unit of the feature kernels), absolute error below 2e-16:
+//   E = exp(-|u|) by the table-driven method of Tang (ACM TOMS 15(2), 1989):
+//   |u| = k ln2/256 + r with ln2/256 split as in Cody and Waite (hi with 39
+//   significant bits, so that k hi is exact for k < 2^14), 2^(-j/256) from a
+//   256-entry table (j = k mod 256) and exp(-r) from its degree-4 Taylor
+//   polynomial (|r| <= ln2/512: remainder below 4e-17);
+//   tanh(|u| / 2) = (1 - E) / (1 + E), the quotient from one Newton step on
+//   an FP32 reciprocal of 1 + E in [1, 2] and one residual correction.
+// |u| is clamped at 40 (tanh(20) rounds to 1); NaN propagates.
+__device__ __forceinline__ double tanh_half(double u, const double *__restrict__ exp2tab) {
+  const long long ub = __double_as_longlong(u);
+  const long long ab = ub & 0x7FFFFFFFFFFFFFFFll;
+  if (ab > 0x7FF0000000000000ll) return u;                      // NaN
+  const double a = ab > 0x4044000000000000ll ? 40.0 : __longlong_as_double(ab);  // min(|u|, 40)
+  const double inv_l = 0x1.71547652b82fep+8;      // 256 / ln 2
+  const double l_hi = 0x1.62e42fefa4000p-9;       // ln 2 / 256, high part
+  const double l_lo = -0x1.8432a1b0e2634p-51;     // ln 2 / 256 - l_hi
+  const double shifter = 0x1.8p52;                // k lands in the low mantissa bits
+  const double kt = fma(a, inv_l, shifter);
+  const int k = __double2loint(kt);               // 0 <= k <= 14773
+  const double kd = kt - shifter;
+  double r = fma(-kd, l_hi, a);
+  r = fma(-kd, l_lo, r);
+  double q = fma(r, 1.0 / 24.0, -1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  q = fma(r, q, -1.0);                            // exp(-r) = 1 + r q
+  const double tj = exp2tab[k & 255];
+  double e = fma(tj, r * q, tj);                  // 2^(-j/256) exp(-r)
+  e = __hiloint2double(__double2hiint(e) - ((k >> 8) << 20), __double2loint(e));  // * 2^(-k/256 div)
+  const double num = 1.0 - e, den = 1.0 + e;
+  // FP32 reciprocal of den from its high word (20 mantissa bits), back to FP64
+  const unsigned dh = (unsigned)__double2hiint(den);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float((dh - 0x38000000u) << 3)));
+  const unsigned yb = __float_as_uint(yf);
+  double y = __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
+  y = fma(y, fma(-den, y, 1.0), y);               // relative error ~2^-40
+  const double q0 = num * y;
+  const double t = fma(fma(-den, q0, num), y, q0);
+  return ub < 0 ? -t : t;
+}
+
+__device__ __forceinline__ void load_exp2tab(double *s, const double *__restrict__ g) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) s[i] = g[i];
+  __syncthreads();
 }
 
 // Interior collocation rows: rows [0, nI) of K_c^i and K-bar^i.
 __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__restrict__ subs, int sub0,
                                                             double *__restrict__ db, long long o_w,
-                                                            long long o_b, long long o_xint,
+                                                            long long o_fc, long long o_exp2, long long o_xint,
                                                             long long o_aint, long long o_gaint, int op) {
+  __shared__ double s_exp2[256];
   const SubDev d = subs[sub0 + blockIdx.y];
   const int r0 = blockIdx.x * 8;
   if (r0 >= d.nI) return;
+  load_exp2tab(s_exp2, db + o_exp2);
   const double *w = db + o_w + 2 * d.w_off;
-  const double *b = db + o_b + d.w_off;
+  const double4 *fc = reinterpret_cast<const double4 *>(db + o_fc) + d.w_off;
   for (int rr = 0; rr < 8; ++rr) {
     const int r = r0 + rr;
     if (r >= d.nI) break;
@@ -45,12 +91,11 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
     double *o0 = db + d.oK + (long long)r * d.M;
     double *o1 = db + d.oKb + (long long)r * d.M;
     for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
-      const double wx = w[2 * j], wy = w[2 * j + 1];
-      const double t = feat_t(wx, wy, b[j], x, y);
-      const double s1 = 1.0 - t * t;
-      const double w2 = wx * wx + wy * wy;
-      double v = 2.0 * w2 * t * s1;
-      if (op == DDELM_OP_DIFFUSION) v = a * v - (ax * wx + ay * wy) * s1;
+      const double4 c = fc[j];  // 2 w_x, 2 w_y, 2 b, 2 |w|^2
+      const double t = tanh_half(fma(c.x, x, fma(c.y, y, c.z)), s_exp2);
+      const double s1 = fma(-t, t, 1.0);
+      double v = (c.w * t) * s1;  // 2 |w|^2 t (1 - t^2)
+      if (op == DDELM_OP_DIFFUSION) v = a * v - (ax * w[2 * j] + ay * w[2 * j + 1]) * s1;
       o0[j] = v;
       o1[j] = v;
     }
@@ -61,22 +106,24 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
 __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__restrict__ rows,
                                                            const SubDev *__restrict__ subs,
                                                            double *__restrict__ db, long long o_w,
-                                                           long long o_b) {
+                                                           long long o_fc, long long o_exp2) {
+  __shared__ double s_exp2[256];
   const SpecialRow rw = rows[blockIdx.x];
   if (rw.kind == ROW_AM) return;
+  load_exp2tab(s_exp2, db + o_exp2);
   const SubDev d = subs[rw.sub];
   const double *w = db + o_w + 2 * d.w_off;
-  const double *b = db + o_b + d.w_off;
+  const double4 *fc = reinterpret_cast<const double4 *>(db + o_fc) + d.w_off;
   double *o0 = db + rw.out0;
   double *o1 = rw.out1 >= 0 ? db + rw.out1 : nullptr;
   const bool delta = rw.kind == ROW_DELTA;
   for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
-    const double wx = w[2 * j], wy = w[2 * j + 1];
-    const double t = feat_t(wx, wy, b[j], rw.x, rw.y);
+    const double4 c = fc[j];
+    const double t = tanh_half(fma(c.x, rw.x, fma(c.y, rw.y, c.z)), s_exp2);
     o0[j] = t;
     if (o1) o1[j] = t;
     if (delta) {
-      const double f = (rw.nx * wx + rw.ny * wy) * (1.0 - t * t);
+      const double f = (rw.nx * w[2 * j] + rw.ny * w[2 * j + 1]) * fma(-t, t, 1.0);
       db[rw.out2 + j] = f;
       db[rw.out3 + j] = f;
     }
@@ -133,15 +180,15 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
   for (int i = s0; i < s1; ++i) max_nI = std::max(max_nI, p.subs[i].nI);
   if (max_nI > 0) {
     dim3 grid((max_nI + 7) / 8, s1 - s0);
-    { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_b, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
+    { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
   }
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
   if (r1 > r0) {
-    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
     { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w); DDELM_COUNT_LAUNCH(); }
   }
   const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
-  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_b); DDELM_COUNT_LAUNCH(); }
+  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

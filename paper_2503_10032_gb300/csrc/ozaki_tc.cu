@@ -515,16 +515,38 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   for (int j = 0; j < 8; ++j) v[j] = (r < s.R) ? fixed_point(tile[rr][kq + j], e, s.S) : 0;
   __nv_bfloat16 *out = slices + s.out + (long long)r * s.Kpad + k0 + kq;
   const long long plane = (long long)s.Rpad * s.Kpad;
+  // Digit p is a_p = R_p - 64 R_{p-1} with R_p = round(X / 64^(S-1-p)) (half
+  // up), which is what peeling rounded leading digits off X gives.  As
+  // |a_p| <= 64, the low 8 bits of R_p and R_{p-1} fix it: 32-bit integer
+  // arithmetic, and the float is made exactly with the 1.5 * 2^23 offset.
+  unsigned rprev[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) rprev[j] = 0u;
   for (int p = 0; p < s.S; ++p) {
-    const int shift = 6 * (s.S - 1 - p);
-    __align__(16) __nv_bfloat16 dig[8];
+    const int k = 6 * (s.S - 1 - p);
+    float f[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const long long a = shift > 0 ? (v[j] + (1ll << (shift - 1))) >> shift : v[j];
-      v[j] -= a << shift;
-      dig[j] = __float2bfloat16_rn((float)(int)a);  // |a| <= 64: a 32-bit conversion (64-bit ones run on the FP64 pipe)
+      const unsigned lo = (unsigned)v[j], hi = (unsigned)(v[j] >> 32);
+      unsigned rp;
+      if (k == 0) {
+        rp = lo;
+      } else {  // (X >> (k - 1)) + 1 >> 1, low bits
+        const int k1 = k - 1;
+        const unsigned x = k1 < 32 ? __funnelshift_r(lo, hi, k1) : (unsigned)((int)hi >> (k1 - 32));
+        rp = (x + 1u) >> 1;
+      }
+      const unsigned d = rp - (rprev[j] << 6) + 128u;  // a_p + 128 in [64, 192] mod 256
+      rprev[j] = rp;
+      f[j] = __uint_as_float((d & 0xFFu) | 0x4B400000u) - 12583040.0f;  // (1.5 * 2^23 + 128) + a - that
     }
-    *reinterpret_cast<uint4 *>(out + p * plane) = *reinterpret_cast<const uint4 *>(dig);
+    // |a| <= 64 is exact in BF16: its bits are the high half of the float's
+    uint4 q;
+    q.x = __byte_perm(__float_as_uint(f[0]), __float_as_uint(f[1]), 0x7632);
+    q.y = __byte_perm(__float_as_uint(f[2]), __float_as_uint(f[3]), 0x7632);
+    q.z = __byte_perm(__float_as_uint(f[4]), __float_as_uint(f[5]), 0x7632);
+    q.w = __byte_perm(__float_as_uint(f[6]), __float_as_uint(f[7]), 0x7632);
+    *reinterpret_cast<uint4 *>(out + p * plane) = q;
   }
 }
 

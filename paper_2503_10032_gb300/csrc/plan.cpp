@@ -213,6 +213,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.o_xint = take(2 * sumI);
   P.o_aint = take(sumI);
   P.o_gaint = take(2 * sumI);
+  P.o_fc = take(4 * sumM);
+  P.o_exp2 = take(256);
   long long wo = 0, io = 0, eo = 0;
   int max_M = 0, sum_nG = 0;
   long long setup_scratch_begin = 0;

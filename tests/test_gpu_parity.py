@@ -94,3 +94,22 @@ def test_poisson_2x2_m100_matches_oracle(D, eps_rel, tol, pde_err):
     assert _rel(mu[1:], ref["mu_delta"]) < tol
     assert _rel(u, ref["u_eval"]) < tol
     assert _rel(u, p.u_eval_exact) < pde_err   # sanity against sin(pi x) sin(pi y)
+
+
+@pytest.mark.parametrize("case", [SMALL[2], SMALL[5]])
+def test_feature_rows_to_rounding(D, case):
+    """Every row of K_c and K-bar (tanh point values, fluxes, the change of variables,
+    Laplacian rows) within a few units of rounding of the oracle's, relative to
+    the row's largest entry: the feature tanh is accurate to ~2e-16 absolute."""
+    nx, ny, M, nI, e, eps, th, R, seed = case
+    p = inputs.small_problem(nx, ny, M=M, n_int=nI, edge_pts=e, n_rhs=R, seed=seed)
+    o = odd.DDELMOracle(p, odd.Options(eps_rel=eps, theta=th))
+    s = D.Solver(p, theta=th, eps_rel=eps, tol=1e-13, keep_matrices=True)
+    worst = 0.0
+    for i in range(p.n_sub):
+        L = o.loc[i]
+        for which, ref in ((0, L.K), (1, L.Kbar), (2, L.Ahat)):
+            got = s.inspect(i, which)
+            scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1e-300)
+            worst = max(worst, float((np.abs(got - ref) / scale).max()))
+    assert worst < 2e-14, worst
