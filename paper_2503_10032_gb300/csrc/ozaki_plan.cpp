@@ -66,7 +66,7 @@ int build_mixed(Plan &P, long long &cur) {
       s.out = elem;
       elem += (long long)S * s.Rpad * s.Kpad;
       // algorithmic bytes of the slicing: the source read twice (scale, digits), the slices written
-      P.slice_bytes += 16.0 * R * (double)K + 2.0 * S * (double)s.Rpad * s.Kpad;
+      P.slice_bytes += 16.0 * R * (double)K + 2.0 * S * R * (double)rup(K, 8);
       s.scale = scl;  // relative; fixed below
       scl += rup(R, 32);
       int idx = int(P.sdesc.size());
@@ -133,8 +133,10 @@ int build_mixed(Plan &P, long long &cur) {
   return DDELM_OK;
 }
 
-// One 2-D tensor map per slice buffer: [S*Rpad rows][Kpad] BF16, box 64 x 128,
-// 128-byte swizzle (the canonical K-major layout tcgen05 reads).
+// One 3-D tensor map per slice buffer: S levels of R rows of K BF16 (row
+// stride Kpad, level stride Rpad Kpad), box 64 x 128 x 1, 128-byte swizzle
+// (the canonical K-major layout tcgen05 reads).  Boxes reaching past R or K
+// are zero-filled by the copy, so the slicing writes no padding.
 int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps) {
   maps.assign(std::max<size_t>(P.sdesc.size(), 1) * 128, 0);
   if (P.sdesc.empty()) return DDELM_OK;
@@ -156,12 +158,12 @@ int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps
     const SliceDesc &s = P.sdesc[i];
     void *gaddr = slices + s.out * 2;
     if ((reinterpret_cast<uintptr_t>(gaddr) & 15u) != 0) return DDELM_ERR_INVALID_ARG;
-    cuuint64_t dims[2] = {(cuuint64_t)s.Kpad, (cuuint64_t)s.S * (cuuint64_t)s.Rpad};
-    cuuint64_t strides[1] = {(cuuint64_t)s.Kpad * 2};
-    cuuint32_t box[2] = {64, 128};
-    cuuint32_t estr[2] = {1, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)s.K, (cuuint64_t)s.R, (cuuint64_t)s.S};
+    cuuint64_t strides[2] = {(cuuint64_t)s.Kpad * 2, (cuuint64_t)s.Rpad * (cuuint64_t)s.Kpad * 2};
+    cuuint32_t box[3] = {64, 128, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
-    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, gaddr, dims, strides, box, estr,
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, gaddr, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return DDELM_ERR_CUDA;

@@ -95,10 +95,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+// box (64 k, 128 rows, 1 level) at (k, row, level); rows >= R and k >= K of the
+// slice buffer are outside the map and arrive as zeros
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
 
@@ -232,9 +235,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint32_t sb = sa + BM * BK * 2;
               const uint32_t fb = smem_u32(&bar_full[st]);
               mbar_expect_tx(fb, both ? STAGE_BYTES : (BM + BN) * BK * 2);
-              tma_load_2d(sa, ma, kb * BK, p * d.RpadA + tl.tm * BM, fb);
-              tma_load_2d(sb, mb, kb * BK, (la - p) * d.RpadB + tl.tn * BN, fb);
-              if (both) tma_load_2d(sb + BN * BK * 2, mb, kb * BK, (lb - p) * d.RpadB + tl.tn * BN, fb);
+              tma_load_3d(sa, ma, kb * BK, tl.tm * BM, p, fb);
+              tma_load_3d(sb, mb, kb * BK, tl.tn * BN, la - p, fb);
+              if (both) tma_load_3d(sb + BN * BK * 2, mb, kb * BK, tl.tn * BN, lb - p, fb);
               ++issued;
               if (++st == STAGES) {
                 st = 0;
@@ -419,8 +422,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // Integer arithmetic only (the FP64 pipe is the scarce unit of this GPU):
 // sigma_r = 2^(E_max - 1022) from the largest biased exponent E_max of the
 // row, so that |op(X)[r][k]| / sigma_r < 1; then X = round(x / sigma * 64^S)
-// is an exact shift of the 53-bit mantissa, and the balanced base-64 digits of
-// X are the slices (|a_0| <= 64, |a_p| <= 32).
+// is an exact shift of the 53-bit mantissa, and its balanced base-64 digits
+// (|a_0| <= 64, a_p in [-32, 31]) are the slices: with
+// OFF = 32 (1 + 64 + ... + 64^(S-1)), the digits of X + OFF in base 64 less 32.
 
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
@@ -465,21 +469,21 @@ __global__ void __launch_bounds__(256) slice_scale_kernel(const SliceDesc *__res
   }
 }
 
-// x / 2^e * 64^S rounded to an integer (|result| <= 64^S)
-__device__ __forceinline__ long long fixed_point(double x, int e, int S) {
+// X + OFF for X = x / 2^e * 64^S rounded half away from zero (|X| <= 64^S):
+// X = ((m 2^8 >> B) + 1) >> 1 with m the 53-bit mantissa and B = 7 - sh,
+// sh = E - 1075 - e + 6S <= 7 as |x| < 2^e; c = 6S - 1075 - e
+__device__ __forceinline__ unsigned long long fixed_offset(double x, int c, unsigned long long off) {
   const long long bits = __double_as_longlong(x);
   const int E = int((bits >> 52) & 0x7FF);
-  if (E == 0) return 0;  // zero or subnormal: below every kept digit
-  const long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
-  const int sh = E - 1075 - e + 6 * S;
-  long long v;
-  if (sh >= 0) v = m << sh;
-  else if (sh > -63) v = (m + (1ll << (-sh - 1))) >> (-sh);
-  else v = 0;
-  return bits < 0 ? -v : v;
+  const int B = min(max(7 - (E + c), 0), 63);
+  const unsigned long long m8 = ((static_cast<unsigned long long>(bits) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 8;
+  unsigned long long v = ((m8 >> B) + 1ull) >> 1;
+  if (E == 0) v = 0ull;  // zero or subnormal: below every kept digit
+  return (bits < 0 ? off - v : off + v);
 }
 
-// slices [S][Rpad][Kpad] BF16, zero padding; a 32 x 64 tile per block, eight
+// slices [S][Rpad][Kpad] BF16 of the rows r < R, columns k < K (the rest is
+// never read: the tensor maps end at R x K); a 32 x 64 tile per block, eight
 // consecutive k per thread, one 16-byte store per slice
 __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__restrict__ sd,
                                                           const double *__restrict__ db,
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   __shared__ double tile[32][65];
   const SliceDesc s = sd[blockIdx.z];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
-  if (r0 >= s.Rpad || k0 >= s.Kpad) return;
+  if (r0 >= s.R || k0 >= s.K) return;
   const double *X = db + s.x;
   if (s.trans) {  // coalesced along r, transposed through shared memory
     const int rr = threadIdx.x & 31;
@@ -505,40 +509,30 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   __syncthreads();
   const int rr = threadIdx.x >> 3, kq = (threadIdx.x & 7) * 8;
   const int r = r0 + rr;
-  int e = 0;
-  if (r < s.R) {
-    const long long sb = __double_as_longlong(db[s.scale + r]);
-    e = int((sb >> 52) & 0x7FF) - 1023;
-  }
-  long long v[8];
+  if (r >= s.R || k0 + kq >= s.K) return;
+  const long long sb = __double_as_longlong(db[s.scale + r]);
+  const int e = int((sb >> 52) & 0x7FF) - 1023;
+  const int S = s.S;
+  const unsigned long long off = ((1ull << (6 * S)) - 1ull) / 63ull * 32ull;
+  unsigned wlo[8], whi[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = (r < s.R) ? fixed_point(tile[rr][kq + j], e, s.S) : 0;
+  for (int j = 0; j < 8; ++j) {
+    const unsigned long long w = fixed_offset(tile[rr][kq + j], 6 * S - 1075 - e, off);
+    wlo[j] = (unsigned)w;
+    whi[j] = (unsigned)(w >> 32);
+  }
   __nv_bfloat16 *out = slices + s.out + (long long)r * s.Kpad + k0 + kq;
   const long long plane = (long long)s.Rpad * s.Kpad;
-  // Digit p is a_p = R_p - 64 R_{p-1} with R_p = round(X / 64^(S-1-p)) (half
-  // up), which is what peeling rounded leading digits off X gives.  As
-  // |a_p| <= 64, the low 8 bits of R_p and R_{p-1} fix it: 32-bit integer
-  // arithmetic, and the float is made exactly with the 1.5 * 2^23 offset.
-  unsigned rprev[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) rprev[j] = 0u;
-  for (int p = 0; p < s.S; ++p) {
-    const int k = 6 * (s.S - 1 - p);
+  for (int p = 0; p < S; ++p) {
+    const int k = 6 * (S - 1 - p);
     float f[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const unsigned lo = (unsigned)v[j], hi = (unsigned)(v[j] >> 32);
-      unsigned rp;
-      if (k == 0) {
-        rp = lo;
-      } else {  // (X >> (k - 1)) + 1 >> 1, low bits
-        const int k1 = k - 1;
-        const unsigned x = k1 < 32 ? __funnelshift_r(lo, hi, k1) : (unsigned)((int)hi >> (k1 - 32));
-        rp = (x + 1u) >> 1;
-      }
-      const unsigned d = rp - (rprev[j] << 6) + 128u;  // a_p + 128 in [64, 192] mod 256
-      rprev[j] = rp;
-      f[j] = __uint_as_float((d & 0xFFu) | 0x4B400000u) - 12583040.0f;  // (1.5 * 2^23 + 128) + a - that
+      // bits [k, 32 + k) of X + OFF (arithmetic above bit 63)
+      const unsigned t = k < 32 ? __funnelshift_r(wlo[j], whi[j], k) : (unsigned)((int)whi[j] >> (k - 32));
+      // the float a_p exactly: (1.5 * 2^23 + field) - (1.5 * 2^23 + bias)
+      f[j] = p == 0 ? __uint_as_float(((t + 96u) & 0xFFu) | 0x4B400000u) - 12583040.0f   // a_0 + 128
+                    : __uint_as_float((t & 63u) | 0x4B400000u) - 12582944.0f;          // a_p + 32
     }
     // |a| <= 64 is exact in BF16: its bits are the high half of the float's
     uint4 q;
