@@ -119,6 +119,8 @@ int build_mixed(Plan &P, long long &cur) {
         }
     }
     op.nslice = int(P.sdesc.size()) - op.slice0;
+    for (int t = op.slice0; t < op.slice0 + op.nslice; ++t)
+      if (P.sdesc[t].S != S) return DDELM_ERR_INVALID_ARG;  // the slicing launch takes one level count
     P.oz_phase[q] = op;
     max_scales = std::max(max_scales, scl);
     max_slices = std::max(max_slices, (size_t)elem * 2);

@@ -485,6 +485,9 @@ __device__ __forceinline__ unsigned long long fixed_offset(double x, int c, unsi
 // slices [S][Rpad][Kpad] BF16 of the rows r < R, columns k < K (the rest is
 // never read: the tensor maps end at R x K); a 32 x 64 tile per block, eight
 // consecutive k per thread, one 16-byte store per slice
+// (S, the levels of the phase, is a template parameter: the digit loop unrolls
+// into fixed shifts)
+template <int S>
 __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__restrict__ sd,
                                                           const double *__restrict__ db,
                                                           __nv_bfloat16 *__restrict__ slices) {
@@ -512,8 +515,7 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   if (r >= s.R || k0 + kq >= s.K) return;
   const long long sb = __double_as_longlong(db[s.scale + r]);
   const int e = int((sb >> 52) & 0x7FF) - 1023;
-  const int S = s.S;
-  const unsigned long long off = ((1ull << (6 * S)) - 1ull) / 63ull * 32ull;
+  constexpr unsigned long long off = ((1ull << (6 * S)) - 1ull) / 63ull * 32ull;
   unsigned wlo[8], whi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -523,6 +525,7 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   }
   __nv_bfloat16 *out = slices + s.out + (long long)r * s.Kpad + k0 + kq;
   const long long plane = (long long)s.Rpad * s.Kpad;
+#pragma unroll
   for (int p = 0; p < S; ++p) {
     const int k = 6 * (S - 1 - p);
     float f[8];
@@ -555,7 +558,15 @@ cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream
   { slice_scale_kernel<<<dim3(16, ph.nslice), 256, 0, s>>>(sd, db); DDELM_COUNT_LAUNCH(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  { slice_write_kernel<<<dim3(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice), 256, 0, s>>>(sd, db, slices); DDELM_COUNT_LAUNCH(); }
+  const dim3 grid(ph.max_kpad / 64, ph.max_rpad / 32, ph.nslice);
+  switch (p.sdesc[ph.slice0].S) {  // one level count per phase
+#define DDELM_SLICE_CASE(n) \
+  case n: { slice_write_kernel<n><<<grid, 256, 0, s>>>(sd, db, slices); DDELM_COUNT_LAUNCH(); } break;
+    DDELM_SLICE_CASE(1) DDELM_SLICE_CASE(2) DDELM_SLICE_CASE(3) DDELM_SLICE_CASE(4) DDELM_SLICE_CASE(5)
+    DDELM_SLICE_CASE(6) DDELM_SLICE_CASE(7) DDELM_SLICE_CASE(8) DDELM_SLICE_CASE(9) DDELM_SLICE_CASE(10)
+#undef DDELM_SLICE_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
