@@ -259,8 +259,10 @@ void ddelm_destroy(ddelm_handle *h);
 
 const char *ddelm_status_string(int status);
 
-/* The CUDA error behind the last DDELM_ERR_CUDA returned on the calling host
- * thread: error name, message, the failing call and its source location
+/* The reason behind the last failure on the calling host thread: for
+ * DDELM_ERR_CUDA the CUDA error name, message, the failing call and its source
+ * location; for a problem that ddelm_query or ddelm_setup rejected
+ * (DDELM_ERR_INVALID_ARG) "problem rejected: " and the check that failed
  * ("" if none).  The string stays valid until the next failing call. */
 const char *ddelm_last_error(void);
 

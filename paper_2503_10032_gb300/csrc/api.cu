@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "ddelm_internal.h"
@@ -23,6 +24,9 @@ void record_cuda_error(cudaError_t e, const char *what, const char *file, int li
   const char *f = std::strrchr(file, '/');
   std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) in %s at %s:%d", cudaGetErrorName(e),
                 cudaGetErrorString(e), what, f ? f + 1 : file, line);
+}
+void record_plan_error(const std::string &why) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "problem rejected: %s", why.empty() ? "invalid plan" : why.c_str());
 }
 }  // namespace ddelm
 
@@ -282,16 +286,21 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
 extern "C" {
 
 int ddelm_query(const ddelm_problem *prob, ddelm_sizes *out) {
+  ddelm::g_last_error[0] = '\0';
   if (!out) return DDELM_ERR_INVALID_ARG;
   Plan p;
   int rc = build_plan(prob, p);
-  if (rc != DDELM_OK) return rc;
+  if (rc != DDELM_OK) {
+    record_plan_error(p.err);
+    return rc;
+  }
   *out = p.sz;
   return DDELM_OK;
 }
 
 int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_bytes, void *stream,
                 ddelm_handle **out, int *info_sub) {
+  ddelm::g_last_error[0] = '\0';
   if (!out || !d_workspace) return DDELM_ERR_INVALID_ARG;
   *out = nullptr;
   if (info_sub) *info_sub = -1;
@@ -300,6 +309,7 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
   if (!h) return DDELM_ERR_INVALID_ARG;
   int rc = build_plan(prob, h->plan);
   if (rc != DDELM_OK) {
+    record_plan_error(h->plan.err);
     delete h;
     return rc;
   }

@@ -31,7 +31,7 @@ struct OzDesc {
   double alpha, beta;
 };
 
-// one 128 x 128 output tile; only the 64-wide k blocks [kb0, kb1) can be
+// one 128 x 64 output tile; only the 64-wide k blocks [kb0, kb1) can be
 // nonzero in op(A)[tile rows] op(B)[:, tile columns] (triangular operands)
 struct OzTile {
   int desc, tm, tn, kb0, kb1, pad0, pad1, pad2;

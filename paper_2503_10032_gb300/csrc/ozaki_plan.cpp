@@ -13,7 +13,7 @@
 namespace ddelm {
 
 namespace {
-constexpr int OZ_BM = 128, OZ_BK = 64, OZ_KC = 1024;
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_KC = 1024;
 long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
 }  // namespace
 
@@ -46,7 +46,10 @@ int build_mixed(Plan &P, long long &cur) {
       continue;
     }
     const int S = q < P.setup_levels.size() ? P.setup_levels[q] : 9;  // 6 bits per level
-    if (S < 1 || S > 10) return DDELM_ERR_INVALID_ARG;  // the fixed-point split holds 64^S in an int64
+    if (S < 1 || S > 10) {  // the fixed-point split holds 64^S in an int64
+      P.err = "internal: slice level count";
+      return DDELM_ERR_INVALID_ARG;
+    }
     std::map<Key, int> seen;
     long long elem = 0, scl = 0;
     auto slice_of = [&](long long x, int ld, int trans, int R, int K) {
@@ -100,27 +103,30 @@ int build_mixed(Plan &P, long long &cur) {
       const int di = int(P.odesc.size());
       P.odesc.push_back(o);
       op.ndesc++;
-      const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + OZ_BM - 1) / OZ_BM;
+      const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + OZ_BN - 1) / OZ_BN;
       const int nkb = o.Kpad / OZ_BK;
       // tensor-core work: every level's pairs over the k blocks a tile needs
       double pairs = 0;
       for (int l = 0; l < S; ++l) pairs += l + 1;
       for (int x = 0; x < tm; ++x)
         for (int y = 0; y < tn; ++y) {
-          if (d.syrk && x > y) continue;
+          if (d.syrk && x * OZ_BM >= (y + 1) * OZ_BN) continue;  // strictly below the diagonal
           int kb0 = 0, kb1 = nkb;
           // op(B)[k][j] = 0 for k > j ; op(A)[i][k] = 0 for k < i
-          if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (OZ_BM / OZ_BK));
+          if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (OZ_BN / OZ_BK));
           if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / OZ_BK));
           if (kb1 < kb0) kb1 = kb0;
           P.otile.push_back({di, x, y, kb0, kb1, 0, 0, 0});
           op.ntile++;
-          P.oz_flops += 2.0 * OZ_BM * OZ_BM * (double)(kb1 - kb0) * OZ_BK * pairs;
+          P.oz_flops += 2.0 * OZ_BM * OZ_BN * (double)(kb1 - kb0) * OZ_BK * pairs;
         }
     }
     op.nslice = int(P.sdesc.size()) - op.slice0;
     for (int t = op.slice0; t < op.slice0 + op.nslice; ++t)
-      if (P.sdesc[t].S != S) return DDELM_ERR_INVALID_ARG;  // the slicing launch takes one level count
+      if (P.sdesc[t].S != S) {  // the slicing launch takes one level count
+        P.err = "internal: slice levels within a phase";
+        return DDELM_ERR_INVALID_ARG;
+      }
     P.oz_phase[q] = op;
     max_scales = std::max(max_scales, scl);
     max_slices = std::max(max_slices, (size_t)elem * 2);
@@ -136,7 +142,7 @@ int build_mixed(Plan &P, long long &cur) {
 }
 
 // One 3-D tensor map per slice buffer: S levels of R rows of K BF16 (row
-// stride Kpad, level stride Rpad Kpad), box 64 x 128 x 1, 128-byte swizzle
+// stride Kpad, level stride Rpad Kpad), box 64 x 64 x 1, 128-byte swizzle
 // (the canonical K-major layout tcgen05 reads).  Boxes reaching past R or K
 // are zero-filled by the copy, so the slicing writes no padding.
 int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps) {
@@ -162,7 +168,7 @@ int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps
     if ((reinterpret_cast<uintptr_t>(gaddr) & 15u) != 0) return DDELM_ERR_INVALID_ARG;
     cuuint64_t dims[3] = {(cuuint64_t)s.K, (cuuint64_t)s.R, (cuuint64_t)s.S};
     cuuint64_t strides[2] = {(cuuint64_t)s.Kpad * 2, (cuuint64_t)s.Rpad * (cuuint64_t)s.Kpad * 2};
-    cuuint32_t box[3] = {64, 128, 1};
+    cuuint32_t box[3] = {64, 64, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
     CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, gaddr, dims, strides, box, estr,

@@ -13,18 +13,18 @@
 // TMEM once per k-chunk and added in FP64 (levels from the smallest to the
 // largest).  The truncation after S levels is the only approximation.
 //
-// Kernel layout (persistent: one CTA per SM walking 128x128 output tiles, 10 warps):
-//   warp 0     TMA producer: 128x64 BF16 boxes of A and B slices, 128B swizzle,
-//              4-stage shared-memory ring guarded by mbarriers.  Two levels
-//              (la, la-1) are computed together: a stage holds A_p, B_{la-p}
-//              and B_{la-1-p}, so each A box feeds two MMAs (the slice GEMM is
-//              bound by L2->SM traffic; this loads ~22% fewer boxes);
+// Kernel layout (persistent: one CTA per SM walking 128x64 output tiles, 10 warps):
+//   warp 0     TMA producer: 64x64 BF16 boxes of A and B slices, 128B swizzle,
+//              4-stage shared-memory ring guarded by mbarriers.  Four levels
+//              (la .. la-3) are computed together: a stage holds A_p (two
+//              boxes) and B_{la-p} .. B_{la-3-p}, so each A box feeds up to
+//              four MMAs;
 //   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
-//              (M=128, N=128, K=16, both operands K-major), four FP32
-//              accumulators of 128 TMEM columns (two per level pair, double
-//              buffered), committed per level pair and k-chunk;
+//              (M=128, N=64, K=16, both operands K-major), two sets of four
+//              FP32 accumulators of 64 TMEM columns (one set per level group,
+//              double buffered), committed per level group and k-chunk;
 //   warps 2-9  epilogue: tcgen05.ld of their lane quadrant and column half,
-//              the pair's level sums combined exactly in int32, FP64
+//              the group's level sums combined exactly in int64, FP64
 //              accumulation in registers, scaled store of C.
 // Every wait is bounded (2 s); on a timeout the CTA records an error, waits for
 // its own copies and MMAs, frees its TMEM and returns.
@@ -40,12 +40,13 @@ namespace ddelm {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int LV = 4;                  // levels per group: la, la-1, la-2, la-3
 constexpr int STAGES = 4;
-constexpr int STAGE_BYTES = (BM + 2 * BN) * BK * 2;  // 48 KB: A_p, B_{la-p}, B_{lb-p}
+constexpr int BOX_BYTES = 64 * BK * 2;                 // one 64-row box: 8 KB
+constexpr int STAGE_BYTES = (BM + LV * BN) * BK * 2;  // 48 KB: A_p, B_{la-p} .. B_{la-3-p}
 constexpr int OZ_THREADS = 320;
-constexpr int NACC = 4;                // FP32 level accumulators of 128 TMEM columns
-constexpr unsigned TMEM_COLS = 512;
+constexpr unsigned TMEM_COLS = 512;    // two sets of LV accumulators of BN columns
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -105,7 +106,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// K-major operand tile of 128 rows x 64 BF16 (128 B) with the 128-byte swizzle:
+// K-major operand tile of 64 or 128 rows x 64 BF16 (128 B) with the 128-byte swizzle:
 // 8-row atoms of 1024 B, SBO = 1024 B, LBO unused (1), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   uint64_t d = 0;
@@ -117,7 +118,7 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=128
+// kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=64
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -144,6 +145,17 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
       : "memory");
 }
 
+// The FP32 level sums hold integers below 2^24 in magnitude: their value by
+// integer arithmetic (conversion instructions share this GPU's narrow FP64
+// pipe).  Zero has exponent field 0: the shift is clamped to 31, past m.
+__device__ __forceinline__ int f32_exact_int(uint32_t u) {
+  const int e = (int)((u >> 23) & 0xFFu);
+  const uint32_t m = (u & 0x7FFFFFu) | 0x800000u;
+  const int v = (int)(m >> min(150 - e, 31));
+  const int sg = (int)u >> 31;
+  return (v ^ sg) - sg;
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -163,7 +175,7 @@ __device__ __forceinline__ TileGeom tile_geom(const OzDesc &d, const OzTile &tl)
   t.kbhi = tl.kb1;
   t.kcb = d.kc / BK;
   t.nchunk = t.kbhi > t.kblo ? (t.kbhi - t.kblo + t.kcb - 1) / t.kcb : 0;
-  t.ngroups = ((t.S + 1) / 2) * t.nchunk;
+  t.ngroups = ((t.S + LV - 1) / LV) * t.nchunk;
   return t;
 }
 
@@ -176,8 +188,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[NACC], bar_acc_empty[NACC],
-      bar_drain;
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2], bar_drain;
   __shared__ uint32_t tmem_base_sh;
   __shared__ double s_scale[256];  // row scales (times alpha), then column scales
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    for (int b = 0; b < NACC; ++b) {
+    for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 256);
     }
@@ -221,11 +232,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
         for (int g = 0; g < tg.ngroups && ok; ++g) {
-          const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1, c = g % tg.nchunk;
+          const int la = tg.S - 1 - LV * (g / tg.nchunk), c = g % tg.nchunk;
           const int kb0 = tg.kblo + c * tg.kcb, kb1 = min(tg.kbhi, kb0 + tg.kcb);
-          // stage p: A_p with B_{la-p} (level la) and, for p <= lb, B_{lb-p} (level lb)
+          // stage p: A_p (two 64-row boxes) and B_{l-p} in slot la - l for the
+          // group's levels l >= p
           for (int p = 0; p <= la && ok; ++p) {
-            const bool both = lb >= 0 && p <= lb;
+            const int lmin = max(p, max(la - (LV - 1), 0));  // levels la .. lmin
+            const int nb = la - lmin + 1;
             for (int kb = kb0; kb < kb1; ++kb) {
               if (issued >= STAGES && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
                 ok = false;
@@ -234,10 +247,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
               const uint32_t sb = sa + BM * BK * 2;
               const uint32_t fb = smem_u32(&bar_full[st]);
-              mbar_expect_tx(fb, both ? STAGE_BYTES : (BM + BN) * BK * 2);
+              mbar_expect_tx(fb, (uint32_t)(2 + nb) * BOX_BYTES);
               tma_load_3d(sa, ma, kb * BK, tl.tm * BM, p, fb);
-              tma_load_3d(sb, mb, kb * BK, tl.tn * BN, la - p, fb);
-              if (both) tma_load_3d(sb + BN * BK * 2, mb, kb * BK, tl.tn * BN, lb - p, fb);
+              tma_load_3d(sa + BOX_BYTES, ma, kb * BK, tl.tm * BM + 64, p, fb);
+              for (int t = 0; t < nb; ++t) tma_load_3d(sb + t * BOX_BYTES, mb, kb * BK, tl.tn * BN, la - t - p, fb);
               ++issued;
               if (++st == STAGES) {
                 st = 0;
@@ -273,36 +286,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const OzTile tl = tiles[ti];
         const TileGeom tg = tile_geom(descs[tl.desc], tl);
         for (int g = 0; g < tg.ngroups && ok; ++g, ++G) {
-          const int bA = (int)(G & 1) * 2;
+          const int set = (int)(G & 1);
           const uint32_t pe = (uint32_t)(((G >> 1) - 1) & 1);
-          if (G >= 2 && (!mbar_wait(smem_u32(&bar_acc_empty[bA]), pe, err) ||
-                         !mbar_wait(smem_u32(&bar_acc_empty[bA + 1]), pe, err))) {
+          if (G >= 2 && !mbar_wait(smem_u32(&bar_acc_empty[set]), pe, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1, c = g % tg.nchunk;
+          const int la = tg.S - 1 - LV * (g / tg.nchunk), c = g % tg.nchunk;
           const int kb0 = tg.kblo + c * tg.kcb, kb1 = min(tg.kbhi, kb0 + tg.kcb);
-          const uint32_t da = tmem + (uint32_t)(bA * BN), dbb = tmem + (uint32_t)((bA + 1) * BN);
-          uint32_t acc_a = 0, acc_b = 0;
+          const uint32_t d0 = tmem + (uint32_t)(set * LV * BN);  // accumulator of level la - t at d0 + t BN
+          uint32_t accf = 0u;                                     // bit t: accumulator t started
           for (int p = 0; p <= la && ok; ++p) {
-            const bool both = lb >= 0 && p <= lb;
+            const int lmin = max(p, max(la - (LV - 1), 0));
+            const int nb = la - lmin + 1;
             for (int kb = kb0; kb < kb1; ++kb) {
               if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
+              // descriptors of the stage's boxes; a 16-element k step is +32 B,
+              // +2 in the descriptor's address field (no carry below 256 KB)
               const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
-              const uint32_t sb = sa + BM * BK * 2;
+              const uint64_t ad = smem_desc_sw128(sa);
+              const uint64_t bd = smem_desc_sw128(sa + BM * BK * 2);
+              for (int t = 0; t < nb; ++t) {
+                const uint32_t dt = d0 + (uint32_t)(t * BN);
+                const uint64_t bt = bd + (uint64_t)(t * (BOX_BYTES >> 4));
+                const uint32_t first = (accf >> t) & 1u;
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-                mma_bf16(da, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), acc_a);
-                acc_a = 1;
-                if (both) {
-                  mma_bf16(dbb, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + BN * BK * 2 + kk * 32), acc_b);
-                  acc_b = 1;
-                }
+                for (int kk = 0; kk < BK / 16; ++kk) mma_bf16(dt, ad + 2 * kk, bt + 2 * kk, kk > 0 ? 1u : first);
+                accf |= 1u << t;
               }
               mma_commit(smem_u32(&bar_empty[st]));
               if (++st == STAGES) {
@@ -311,11 +326,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               }
             }
           }
-          if (ok) {
-            // both accumulators are released to the epilogue (the second may be unused)
-            mma_commit(smem_u32(&bar_acc_full[bA]));
-            mma_commit(smem_u32(&bar_acc_full[bA + 1]));
-          }
+          if (ok) mma_commit(smem_u32(&bar_acc_full[set]));  // the group's accumulators to the epilogue
         }
       }
       // all MMAs issued by this thread complete before TMEM is released
@@ -330,15 +341,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: warps 2..9
-    // Each group holds levels la and la-1 of one k-chunk in two TMEM
-    // accumulators (the MMA issuer fills the other two meanwhile);
-    // x = L_la + 64 L_{la-1} is an exact int32 (|L| < 2^23.6), so one FP64 FMA
-    // per group combines the two levels (this GPU's FP64 pipe does 4 flop/clk/SM).
+    // Each group holds up to four levels la .. la-3 of one k-chunk in TMEM
+    // accumulators (the MMA issuer fills the other set meanwhile); their FP32
+    // sums are integers below 2^23.6, read by integer arithmetic, and
+    // x = L_la + 64 L_{la-1} + 64^2 L_{la-2} + 64^3 L_{la-3} (< 2^41.7) is an
+    // exact int64, so one exact conversion and one FP64 FMA per group combine
+    // four levels (this GPU's FP64 pipe, which also runs the conversions, does
+    // 4 flop/clk/SM).  The row scale rides on the FMA's level scale, the column
+    // scale on the store.
     // After a failed wait every thread still walks the same tiles and named
     // barriers (skipping the work), so the barriers cannot deadlock.
     const int ew = warp - 2;                  // 0..7
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                 // column half
+    const int half = ew >> 2;                 // 32-column half of the tile
     const int row = quad * 32 + lane;
     const int et = threadIdx.x - 64;          // 0..255 among the epilogue threads
     bool ok = true;
@@ -349,58 +364,56 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const TileGeom tg = tile_geom(d, tl);
       epi_sync();  // the previous tile's stores no longer read the scales
       // the tile's row and column scales (times alpha) in shared memory
-      if (et < 128) {
+      if (et < BM) {
         const int gi = tl.tm * BM + et;
         s_scale[et] = gi < d.m ? db[d.scaleA + gi] * d.alpha : 0.0;
-      } else {
-        const int gj = tl.tn * BN + et - 128;
+      } else if (et < BM + BN) {
+        const int gj = tl.tn * BN + et - BM;
         s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
       }
       epi_sync();
-      double acc[64];
+      double acc[32];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+      for (int j = 0; j < 32; ++j) acc[j] = 0.0;
       for (int g = 0; g < tg.ngroups; ++g, ++G) {
-        const int bA = (int)(G & 1) * 2;
+        const int set = (int)(G & 1);
         const uint32_t par = (uint32_t)((G >> 1) & 1);
-        if (ok && (!mbar_wait(smem_u32(&bar_acc_full[bA]), par, err) ||
-                   !mbar_wait(smem_u32(&bar_acc_full[bA + 1]), par, err)))
-          ok = false;
+        if (ok && !mbar_wait(smem_u32(&bar_acc_full[set]), par, err)) ok = false;
         if (!ok) continue;
         tc_fence_after();
-        const int la = tg.S - 1 - 2 * (g / tg.nchunk), lb = la - 1;
-        const bool two = lb >= 0;
-        const double scale = ldexp(1.0, -6 * (la + 2));
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+        const int la = tg.S - 1 - LV * (g / tg.nchunk);
+        const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
+        const double scale = ldexp(s_scale[row], -6 * (la + 2));
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * 32);
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-          // both accumulators' loads in flight before the one wait
-          uint32_t r0[16], r1[16];
-          tmem_ld16_nowait(lane_base + (uint32_t)(bA * BN) + c0, r0);
-          if (two) tmem_ld16_nowait(lane_base + (uint32_t)((bA + 1) * BN) + c0, r1);
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+          // every level's loads in flight before the one wait
+          uint32_t r[LV][16];
+#pragma unroll
+          for (int t = 0; t < LV; ++t)
+            if (t < nl) tmem_ld16_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int x =
-                __float2int_rn(__uint_as_float(r0[j])) + (two ? 64 * __float2int_rn(__uint_as_float(r1[j])) : 0);
+            const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
+            const int x23 = (nl > 2 ? f32_exact_int(r[2][j]) : 0) + (nl > 3 ? 64 * f32_exact_int(r[3][j]) : 0);
+            const long long x = (long long)x01 + (long long)x23 * 4096;
             acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
           }
         }
         tc_fence_before();
-        mbar_arrive(smem_u32(&bar_acc_empty[bA]));
-        mbar_arrive(smem_u32(&bar_acc_empty[bA + 1]));
+        mbar_arrive(smem_u32(&bar_acc_empty[set]));
       }
       if (ok) {
         const int gi = tl.tm * BM + row;
         if (gi < d.m) {
-          const double si = s_scale[row];
           double *crow = db + d.c + (long long)gi * d.ldc;
-          const int j0 = tl.tn * BN + half * 64;
+          const int j0 = tl.tn * BN + half * 32;
 #pragma unroll
-          for (int j = 0; j < 64; ++j) {
+          for (int j = 0; j < 32; ++j) {
             const int gj = j0 + j;
             if (gj < d.n) {
-              double v = si * s_scale[128 + half * 64 + j] * acc[j];
+              double v = s_scale[BM + half * 32 + j] * acc[j];
               if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
               crow[gj] = v;
             }

@@ -1262,7 +1262,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     for (const auto &t : P.otile) {
       if (t.desc < 0 || t.desc >= (int)P.odesc.size()) return fail("internal: tensor-core tile");
       const OzDesc &od = P.odesc[t.desc];
-      if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * 128 > od.RpadB) return fail("internal: tensor-core tile box");
+      if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * 64 > od.RpadB) return fail("internal: tensor-core tile box");
       if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
     }
     const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;

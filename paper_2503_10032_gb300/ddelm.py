@@ -120,8 +120,9 @@ _lib = load_library()
 class DDELMError(RuntimeError):
     def __init__(self, status, what=""):
         msg = f"{what}: {ddelm_status_string(status)} ({status})"
-        if status == DDELM_ERR_CUDA:
-            msg += f": {_lib.ddelm_last_error().decode()}"
+        last = _lib.ddelm_last_error().decode()
+        if status == DDELM_ERR_CUDA or (status == DDELM_ERR_INVALID_ARG and last.startswith("problem rejected")):
+            msg += f": {last}"
         super().__init__(msg)
         self.status = status
 

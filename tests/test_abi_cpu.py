@@ -52,3 +52,21 @@ def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(lib.DDELMError):
         lib.ddelm_query(lib.ProblemArgs(p, lib.make_options()))
     assert lib.ddelm_status_string(lib.DDELM_ERR_TIMEOUT).startswith("a device")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_workload_plans(lib, prec):
+    """The host plan of every workload passes its own bounds and shape checks
+    (every kernel access, tensor-map box and tile range) in both precisions."""
+    from paper_2503_10032_gb300 import inputs
+    pr = lib.DDELM_PREC_FP64 if prec == "fp64" else lib.DDELM_PREC_MIXED
+    for name in inputs.CONFIGS:
+        sz = lib.ddelm_query(lib.ProblemArgs(inputs.config(name), lib.make_options(precision=pr)))
+        assert sz.workspace_bytes > 0, name
+
+
+def test_rejection_names_the_check(lib):
+    from paper_2503_10032_gb300 import inputs
+    p = inputs.small_problem(2, 2, M=6, n_int=10, edge_pts=2)
+    with pytest.raises(lib.DDELMError, match="theta must be in"):
+        lib.ddelm_query(lib.ProblemArgs(p, lib.make_options(theta=1.5)))
