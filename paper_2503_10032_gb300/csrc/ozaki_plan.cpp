@@ -5,8 +5,7 @@
 
 #include <algorithm>
 #include <cstring>
-#include <map>
-#include <tuple>
+#include <unordered_map>
 
 #include "ddelm_internal.h"
 
@@ -31,10 +30,33 @@ int build_mixed(Plan &P, long long &cur) {
   struct Key {
     long long x;
     int ld, trans, R, K;
-    bool operator<(const Key &o) const {
-      return std::tie(x, ld, trans, R, K) < std::tie(o.x, o.ld, o.trans, o.R, o.K);
+    bool operator==(const Key &o) const {
+      return x == o.x && ld == o.ld && trans == o.trans && R == o.R && K == o.K;
     }
   };
+  struct KeyHash {
+    size_t operator()(const Key &k) const {
+      unsigned long long h = (unsigned long long)k.x * 0x9E3779B97F4A7C15ull;
+      h ^= ((unsigned long long)(unsigned)k.ld << 32 | (unsigned)k.R) + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+      h ^= ((unsigned long long)(unsigned)k.K << 1 | (unsigned)k.trans) + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
+      return (size_t)h;
+    }
+  };
+  // table sizes (upper bounds) up front: the plan is rebuilt on every setup
+  {
+    size_t nd = 0, nt = 0;
+    for (size_t q = 0; q < (size_t)P.ph_coarse && q < P.setup_gemm.size(); ++q) {
+      const GemmPhase &gp = P.setup_gemm[q];
+      nd += gp.ndesc;
+      for (int t = 0; t < gp.ndesc; ++t) {
+        const GemmDesc &d = P.gdesc[gp.desc0 + t];
+        nt += (size_t)((d.m + OZ_BM - 1) / OZ_BM) * ((d.n + OZ_BN - 1) / OZ_BN);
+      }
+    }
+    P.odesc.reserve(nd);
+    P.sdesc.reserve(2 * nd);
+    P.otile.reserve(nt);
+  }
   std::vector<std::pair<int, long long>> scale_fix;  // (slice desc, relative scale offset)
   long long scale_base = 0;
   std::vector<int> phase_slices_begin;
@@ -50,7 +72,8 @@ int build_mixed(Plan &P, long long &cur) {
       P.err = "internal: slice level count";
       return DDELM_ERR_INVALID_ARG;
     }
-    std::map<Key, int> seen;
+    std::unordered_map<Key, int, KeyHash> seen;
+    seen.reserve(2 * (size_t)gp.ndesc);
     long long elem = 0, scl = 0;
     auto slice_of = [&](long long x, int ld, int trans, int R, int K) {
       Key k{x, ld, trans, R, K};

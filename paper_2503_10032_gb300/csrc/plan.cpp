@@ -449,6 +449,11 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
 
   // ---- special rows
   std::vector<int> sub_row0(n_sub + 1, 0);
+  {
+    size_t nr = 0;
+    for (const auto &d : P.subs) nr += (size_t)d.nB + 2 * (size_t)d.nPi + d.nDl + d.nE;
+    P.rows.reserve(nr);
+  }
   for (int i = 0; i < n_sub; ++i) {
     sub_row0[i] = int(P.rows.size());
     const SubDev &d = P.subs[i];
@@ -642,6 +647,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   }
 
   // ---- GEMM phases
+  // FP64 GEMM tiles; MIXED setup phases run on the tensor-core path and need none
+  bool fp64_tiles = true;
   auto phase_begin = [&](int skinny = 0) {
     GemmPhase ph;
     ph.desc0 = int(P.gdesc.size());
@@ -680,6 +687,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     if (bu && au) f /= 3.0;
     else if (bu || au || upper_tiles) f /= 2.0;
     P.gemm_flops.push_back(f);
+    if (!fp64_tiles) return;
     if (ph.skinny) {
       for (int x = 0; x < (m + 31) / 32; ++x) {
         P.gtile.push_back({di, x, 0, 0});
@@ -701,6 +709,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // and O(M^3) product a GEMM phase, then the local operators.
   const bool fp32 = P.scheme == DDELM_SCHEME_FP32;
   const bool series = P.scheme == DDELM_SCHEME_CQR2_SERIES;
+  fp64_tiles = o.precision != DDELM_PREC_MIXED;
   // MIXED, FP64 passes: the Cholesky kernel (FP64 on CUDA cores, one SM per
   // matrix) inverts only the 128 x 128 diagonal blocks of R
   constexpr int INVB = 128;
@@ -1011,6 +1020,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
   }
   P.ph_coarse = int(P.setup_gemm.size());
+  fp64_tiles = true;
   // coarse: 11: S_Pi += D^T D ; 12: Sinv = V_Pi V_Pi^T ; 13: C1 = Sinv D^T, C3 = D Sinv ;
   //         14: C2 = I - D C1
   if (n_pi > 0) {
