@@ -31,7 +31,7 @@ struct OzDesc {
   double alpha, beta;
 };
 
-// one 128 x 64 output tile; only the 64-wide k blocks [kb0, kb1) can be
+// one 128 x bn output tile; only the 64-wide k blocks [kb0, kb1) can be
 // nonzero in op(A)[tile rows] op(B)[:, tile columns] (triangular operands)
 struct OzTile {
   int desc, tm, tn, kb0, kb1, pad0, pad1, pad2;
@@ -42,6 +42,7 @@ struct OzPhase {
   int desc0, ndesc;      // OzDesc range
   int tile0, ntile;      // OzTile range
   int max_rpad, max_kpad;
+  int bn;                // tile width: 64 (four levels per group) or 128 (two)
 };
 
 cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);

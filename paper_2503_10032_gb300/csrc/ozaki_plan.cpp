@@ -12,7 +12,11 @@
 namespace ddelm {
 
 namespace {
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_KC = 1024;
+constexpr int OZ_BM = 128, OZ_BK = 64, OZ_KC = 1024;
+// tile width of a phase: 128 (two levels per group) when every product has a
+// contraction longer than one k-chunk, where A traffic dominates; else 64
+// (four levels per group: a quarter of the FP64 level combinations)
+constexpr int OZ_WIDE_K = 1024;
 long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
 }  // namespace
 
@@ -26,7 +30,7 @@ int build_mixed(Plan &P, long long &cur) {
   long long max_scales = 0;
   size_t max_slices = 0;
   const size_t n_setup = (size_t)P.ph_coarse;  // every wave's factorisation and local operator phases
-  P.oz_phase.assign(P.setup_gemm.size(), OzPhase{0, 0, 0, 0, 0, 0, 0, 0});
+  P.oz_phase.assign(P.setup_gemm.size(), OzPhase{0, 0, 0, 0, 0, 0, 0, 0, 64});
   struct Key {
     long long x;
     int ld, trans, R, K;
@@ -50,7 +54,7 @@ int build_mixed(Plan &P, long long &cur) {
       nd += gp.ndesc;
       for (int t = 0; t < gp.ndesc; ++t) {
         const GemmDesc &d = P.gdesc[gp.desc0 + t];
-        nt += (size_t)((d.m + OZ_BM - 1) / OZ_BM) * ((d.n + OZ_BN - 1) / OZ_BN);
+        nt += (size_t)((d.m + OZ_BM - 1) / OZ_BM) * ((d.n + 63) / 64);
       }
     }
     P.odesc.reserve(nd);
@@ -62,7 +66,7 @@ int build_mixed(Plan &P, long long &cur) {
   std::vector<int> phase_slices_begin;
   for (size_t q = 0; q < n_setup && q < P.setup_gemm.size(); ++q) {
     const GemmPhase &gp = P.setup_gemm[q];
-    OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0};
+    OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0, 64};
     if (gp.ndesc == 0) {
       P.oz_phase[q] = op;
       continue;
@@ -72,6 +76,10 @@ int build_mixed(Plan &P, long long &cur) {
       P.err = "internal: slice level count";
       return DDELM_ERR_INVALID_ARG;
     }
+    bool wide = gp.ndesc > 0;
+    for (int t = 0; t < gp.ndesc; ++t) wide = wide && P.gdesc[gp.desc0 + t].k > OZ_WIDE_K;
+    const int OZ_BN = wide ? 128 : 64;
+    op.bn = OZ_BN;
     std::unordered_map<Key, int, KeyHash> seen;
     seen.reserve(2 * (size_t)gp.ndesc);
     long long elem = 0, scl = 0;

@@ -40,13 +40,17 @@ namespace ddelm {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int LV = 4;                  // levels per group: la, la-1, la-2, la-3
+// Two tile shapes, chosen per phase by the plan: 128 x 64 tiles with four
+// levels per group (LV = 4), and 128 x 128 tiles with two (LV = 2) for
+// large-K products, where the wider tile halves the A traffic.  Either way a
+// stage is 48 KB (A_p and LV boxes of B, BN rows each) and the two sets of
+// LV accumulators of BN columns fill the 512 TMEM columns.
+constexpr int BM = 128, BK = 64;
 constexpr int STAGES = 4;
-constexpr int BOX_BYTES = 64 * BK * 2;                 // one 64-row box: 8 KB
-constexpr int STAGE_BYTES = (BM + LV * BN) * BK * 2;  // 48 KB: A_p, B_{la-p} .. B_{la-3-p}
+constexpr int BOX_BYTES = 64 * BK * 2;  // one 64-row box: 8 KB
+constexpr int STAGE_BYTES = 6 * BOX_BYTES;
 constexpr int OZ_THREADS = 320;
-constexpr unsigned TMEM_COLS = 512;    // two sets of LV accumulators of BN columns
+constexpr unsigned TMEM_COLS = 512;
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -118,15 +122,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=64
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=BN
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
+template <int BN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc<BN>()), "r"(accum)
       : "memory");
 }
 
@@ -168,7 +175,7 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 struct TileGeom {
   int S, kblo, kbhi, kcb, nchunk, ngroups;
 };
-__device__ __forceinline__ TileGeom tile_geom(const OzDesc &d, const OzTile &tl) {
+__device__ __forceinline__ TileGeom tile_geom(const OzDesc &d, const OzTile &tl, int LV) {
   TileGeom t;
   t.S = d.S;
   t.kblo = tl.kb0;
@@ -182,6 +189,7 @@ __device__ __forceinline__ TileGeom tile_geom(const OzDesc &d, const OzTile &tl)
 // Persistent: CTA b takes tiles b, b + gridDim.x, ...; the shared-memory ring,
 // the TMEM accumulators and every barrier phase run on across tiles, so a
 // tile's epilogue overlaps the next tile's loads and MMAs.
+template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozaki_gemm_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles, int ntile,
                       const CUtensorMap *__restrict__ maps, double *__restrict__ db, int *__restrict__ err) {
@@ -191,6 +199,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2], bar_drain;
   __shared__ uint32_t tmem_base_sh;
   __shared__ double s_scale[256];  // row scales (times alpha), then column scales
+  constexpr int LV = 256 / BN;      // levels per group
+  constexpr int BB = BN / 64;        // 64-row boxes per B operand
+  static_assert(BM + LV * BN == 384, "a stage holds six boxes");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
         const OzTile tl = tiles[ti];
         const OzDesc d = descs[tl.desc];
-        const TileGeom tg = tile_geom(d, tl);
+        const TileGeom tg = tile_geom(d, tl, LV);
         const CUtensorMap *ma = maps + d.tmapA;
         const CUtensorMap *mb = maps + d.tmapB;
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
@@ -247,10 +258,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
               const uint32_t sb = sa + BM * BK * 2;
               const uint32_t fb = smem_u32(&bar_full[st]);
-              mbar_expect_tx(fb, (uint32_t)(2 + nb) * BOX_BYTES);
+              mbar_expect_tx(fb, (uint32_t)(2 + nb * BB) * BOX_BYTES);
               tma_load_3d(sa, ma, kb * BK, tl.tm * BM, p, fb);
               tma_load_3d(sa + BOX_BYTES, ma, kb * BK, tl.tm * BM + 64, p, fb);
-              for (int t = 0; t < nb; ++t) tma_load_3d(sb + t * BOX_BYTES, mb, kb * BK, tl.tn * BN, la - t - p, fb);
+              for (int t = 0; t < nb; ++t)
+#pragma unroll
+                for (int h = 0; h < BB; ++h)
+                  tma_load_3d(sb + (t * BB + h) * BOX_BYTES, mb, kb * BK, tl.tn * BN + 64 * h, la - t - p, fb);
               ++issued;
               if (++st == STAGES) {
                 st = 0;
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       long long G = 0;  // groups across tiles
       for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
         const OzTile tl = tiles[ti];
-        const TileGeom tg = tile_geom(descs[tl.desc], tl);
+        const TileGeom tg = tile_geom(descs[tl.desc], tl, LV);
         for (int g = 0; g < tg.ngroups && ok; ++g, ++G) {
           const int set = (int)(G & 1);
           const uint32_t pe = (uint32_t)(((G >> 1) - 1) & 1);
@@ -313,10 +327,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint64_t bd = smem_desc_sw128(sa + BM * BK * 2);
               for (int t = 0; t < nb; ++t) {
                 const uint32_t dt = d0 + (uint32_t)(t * BN);
-                const uint64_t bt = bd + (uint64_t)(t * (BOX_BYTES >> 4));
+                const uint64_t bt = bd + (uint64_t)(t * BB * (BOX_BYTES >> 4));
                 const uint32_t first = (accf >> t) & 1u;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) mma_bf16(dt, ad + 2 * kk, bt + 2 * kk, kk > 0 ? 1u : first);
+                for (int kk = 0; kk < BK / 16; ++kk) mma_bf16<BN>(dt, ad + 2 * kk, bt + 2 * kk, kk > 0 ? 1u : first);
                 accf |= 1u << t;
               }
               mma_commit(smem_u32(&bar_empty[st]));
@@ -353,7 +367,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // barriers (skipping the work), so the barriers cannot deadlock.
     const int ew = warp - 2;                  // 0..7
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                 // 32-column half of the tile
+    const int half = ew >> 2;                 // column half of the tile
+    constexpr int CW = BN / 2;                // its width
     const int row = quad * 32 + lane;
     const int et = threadIdx.x - 64;          // 0..255 among the epilogue threads
     bool ok = true;
@@ -361,7 +376,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int ti = blockIdx.x; ti < ntile; ti += gridDim.x) {
       const OzTile tl = tiles[ti];
       const OzDesc d = descs[tl.desc];
-      const TileGeom tg = tile_geom(d, tl);
+      const TileGeom tg = tile_geom(d, tl, LV);
       epi_sync();  // the previous tile's stores no longer read the scales
       // the tile's row and column scales (times alpha) in shared memory
       if (et < BM) {
@@ -372,9 +387,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
       }
       epi_sync();
-      double acc[32];
+      double acc[CW];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+      for (int j = 0; j < CW; ++j) acc[j] = 0.0;
       for (int g = 0; g < tg.ngroups; ++g, ++G) {
         const int set = (int)(G & 1);
         const uint32_t par = (uint32_t)((G >> 1) & 1);
@@ -384,9 +399,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int la = tg.S - 1 - LV * (g / tg.nchunk);
         const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
         const double scale = ldexp(s_scale[row], -6 * (la + 2));
-        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * 32);
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16) {
+        for (int c0 = 0; c0 < CW; c0 += 16) {
           // every level's loads in flight before the one wait
           uint32_t r[LV][16];
 #pragma unroll
@@ -396,9 +411,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
-            const int x23 = (nl > 2 ? f32_exact_int(r[2][j]) : 0) + (nl > 3 ? 64 * f32_exact_int(r[3][j]) : 0);
-            const long long x = (long long)x01 + (long long)x23 * 4096;
-            acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
+            if constexpr (LV > 2) {
+              const int x23 = (nl > 2 ? f32_exact_int(r[2][j]) : 0) + (nl > 3 ? 64 * f32_exact_int(r[3][j]) : 0);
+              const long long x = (long long)x01 + (long long)x23 * 4096;
+              acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
+            } else {
+              acc[c0 + j] = fma(scale, (double)x01, acc[c0 + j]);
+            }
           }
         }
         tc_fence_before();
@@ -408,12 +427,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int gi = tl.tm * BM + row;
         if (gi < d.m) {
           double *crow = db + d.c + (long long)gi * d.ldc;
-          const int j0 = tl.tn * BN + half * 32;
+          const int j0 = tl.tn * BN + half * CW;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < CW; ++j) {
             const int gj = j0 + j;
             if (gj < d.n) {
-              double v = s_scale[BM + half * 32 + j] * acc[j];
+              double v = s_scale[BM + half * CW + j] * acc[j];
               if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
               crow[gj] = v;
             }
@@ -592,7 +611,9 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
   const OzTile *ot = reinterpret_cast<const OzTile *>(base + p.off_otile) + ph.tile0;
   const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(base + p.off_tmaps);
   const size_t smem = STAGES * STAGE_BYTES + 1024;
-  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ph.bn != 64 && ph.bn != 128) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(ph.bn == 64 ? ozaki_gemm_kernel<64> : ozaki_gemm_kernel<128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   static int nsm = 0;  // one persistent CTA per SM
   if (nsm == 0) {
@@ -605,7 +626,8 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
     }
   }
   const int grid = ph.ntile < nsm ? ph.ntile : nsm;
-  { ozaki_gemm_kernel<<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
+  if (ph.bn == 64) { ozaki_gemm_kernel<64><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
+  else { ozaki_gemm_kernel<128><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -1269,11 +1269,16 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           od.S > P.sdesc[od.tmapB].S || od.kc % 64 || od.kc > 1024)
         return fail("internal: tensor-core GEMM shape");
     }
-    for (const auto &t : P.otile) {
-      if (t.desc < 0 || t.desc >= (int)P.odesc.size()) return fail("internal: tensor-core tile");
-      const OzDesc &od = P.odesc[t.desc];
-      if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * 64 > od.RpadB) return fail("internal: tensor-core tile box");
-      if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
+    for (const auto &ph : P.oz_phase) {
+      if (ph.bn != 64 && ph.bn != 128) return fail("internal: tensor-core tile width");
+      for (int q = ph.tile0; q < ph.tile0 + ph.ntile; ++q) {
+        const OzTile &t = P.otile[q];
+        if (t.desc < ph.desc0 || t.desc >= ph.desc0 + ph.ndesc) return fail("internal: tensor-core tile");
+        const OzDesc &od = P.odesc[t.desc];
+        if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * ph.bn > od.RpadB)
+          return fail("internal: tensor-core tile box");
+        if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
+      }
     }
     const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;
     if (!in(P.o_cg, cg_need) || !in(P.o_loc, 9LL * sum_nG * R) || !in(P.o_status, 4LL * n_sub + 64))
