@@ -163,6 +163,79 @@ __device__ __forceinline__ int f32_exact_int(uint32_t u) {
   return (v ^ sg) - sg;
 }
 
+// x8 TMEM load without the wait
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// w += (x01 + 4096 x23) 2^(24 q), q in {0, 1, 2}, on a 96-bit two's complement
+// integer (w0 least significant); |x01|, |x23| < 2^30.  32-bit integer work
+// only: this GPU runs int-to-double conversions on its narrow FP64 pipe.
+__device__ __forceinline__ void add96(uint32_t &w0, uint32_t &w1, uint32_t &w2, int x01, int x23, int q) {
+  uint32_t yl, yh;  // y = x01 + 4096 x23 (|y| < 2^43)
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
+      : "=r"(yl), "=r"(yh)
+      : "r"((uint32_t)x01), "r"((uint32_t)x23 << 12), "r"((uint32_t)(x01 >> 31)), "r"((uint32_t)(x23 >> 20)));
+  uint32_t u0, u1, u2;
+  if (q == 0) {
+    u0 = yl;
+    u1 = yh;
+    u2 = (uint32_t)((int)yh >> 31);
+  } else if (q == 1) {
+    u0 = yl << 24;
+    u1 = (yl >> 8) | (yh << 24);
+    u2 = (uint32_t)((int)yh >> 8);
+  } else {
+    u0 = 0u;
+    u1 = yl << 16;
+    u2 = (yl >> 16) | (yh << 16);
+  }
+  asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+      : "+r"(w0), "+r"(w1), "+r"(w2)
+      : "r"(u0), "r"(u1), "r"(u2));
+}
+
+// X 2^eoff for the 96-bit two's complement integer X = (w2, w1, w0), rounded
+// to nearest even, by integer arithmetic; results outside the normal range
+// take the FP64 route (out of line)
+__device__ __noinline__ double i96_slow(uint32_t b2, uint32_t b1, int sg, int e) {
+  const double v = ldexp((double)b2 * 4294967296.0 + (double)b1, e);
+  return sg ? -v : v;
+}
+__device__ __forceinline__ double i96_ldexp(uint32_t w0, uint32_t w1, uint32_t w2, int eoff) {
+  const uint32_t sg = (uint32_t)((int)w2 >> 31);
+  uint32_t a0, a1, a2;  // |X|
+  asm("add.cc.u32 %0, %3, %6;\n\taddc.cc.u32 %1, %4, 0;\n\taddc.u32 %2, %5, 0;"
+      : "=r"(a0), "=r"(a1), "=r"(a2)
+      : "r"(w0 ^ sg), "r"(w1 ^ sg), "r"(w2 ^ sg), "r"(sg & 1u));
+  if ((a0 | a1 | a2) == 0u) return 0.0;
+  const int n = a2 ? __clz((int)a2) : (a1 ? 32 + __clz((int)a1) : 64 + __clz((int)a0));
+  uint32_t b2, b1, b0;  // |X| << n: leading one at bit 95
+  if (n >= 64) {
+    b2 = a0 << (n - 64);
+    b1 = 0u;
+    b0 = 0u;
+  } else if (n >= 32) {
+    b2 = __funnelshift_l(a0, a1, n - 32);
+    b1 = a0 << (n - 32);
+    b0 = 0u;
+  } else {
+    b2 = __funnelshift_l(a1, a2, n);
+    b1 = __funnelshift_l(a0, a1, n);
+    b0 = a0 << n;
+  }
+  const int E = 1023 + 95 - n + eoff;  // biased exponent
+  if (E < 1 || E > 2046) return i96_slow(b2, b1, (int)(sg & 1u), 95 - n - 63 + eoff);
+  uint32_t hi = ((uint32_t)(E - 1) << 20) + (b2 >> 11);  // the leading one adds the last exponent unit
+  uint32_t lo = (b2 << 21) | (b1 >> 11);
+  const bool up = ((b1 >> 10) & 1u) && (((b1 & 0x3FFu) | b0) || (lo & 1u));
+  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(lo), "+r"(hi) : "r"(up ? 1u : 0u));
+  return __hiloint2double((int)(hi | (sg & 0x80000000u)), (int)lo);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -378,63 +451,113 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const OzDesc d = descs[tl.desc];
       const TileGeom tg = tile_geom(d, tl, LV);
       epi_sync();  // the previous tile's stores no longer read the scales
-      // the tile's row and column scales (times alpha) in shared memory
+      // the tile's row and column scales in shared memory (alpha is applied separately)
       if (et < BM) {
         const int gi = tl.tm * BM + et;
-        s_scale[et] = gi < d.m ? db[d.scaleA + gi] * d.alpha : 0.0;
+        s_scale[et] = gi < d.m ? db[d.scaleA + gi] : 0.0;
       } else if (et < BM + BN) {
         const int gj = tl.tn * BN + et - BM;
         s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
       }
       epi_sync();
-      double acc[CW];
+      if constexpr (LV == 4) {
+        // the exact sum X = sum_g (x01 + 4096 x23)_g 2^(24 q_g) (q_g: the
+        // group's level block, least significant first) in 96-bit integers;
+        // the element is X 2^(-6(S+1)) times the row and column scales
+        uint32_t w0[CW], w1[CW], w2[CW];
 #pragma unroll
-      for (int j = 0; j < CW; ++j) acc[j] = 0.0;
-      for (int g = 0; g < tg.ngroups; ++g, ++G) {
-        const int set = (int)(G & 1);
-        const uint32_t par = (uint32_t)((G >> 1) & 1);
-        if (ok && !mbar_wait(smem_u32(&bar_acc_full[set]), par, err)) ok = false;
-        if (!ok) continue;
-        tc_fence_after();
-        const int la = tg.S - 1 - LV * (g / tg.nchunk);
-        const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
-        const double scale = ldexp(s_scale[row], -6 * (la + 2));
-        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
+        for (int j = 0; j < CW; ++j) w0[j] = w1[j] = w2[j] = 0u;
+        for (int g = 0; g < tg.ngroups; ++g, ++G) {
+          const int set = (int)(G & 1);
+          const uint32_t par = (uint32_t)((G >> 1) & 1);
+          if (ok && !mbar_wait(smem_u32(&bar_acc_full[set]), par, err)) ok = false;
+          if (!ok) continue;
+          tc_fence_after();
+          const int q = g / tg.nchunk;
+          const int la = tg.S - 1 - LV * q;
+          const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
+          const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
 #pragma unroll
-        for (int c0 = 0; c0 < CW; c0 += 16) {
-          // every level's loads in flight before the one wait
-          uint32_t r[LV][16];
+          for (int c0 = 0; c0 < CW; c0 += 8) {
+            // every level's loads in flight before the one wait
+            uint32_t r[LV][8];
 #pragma unroll
-          for (int t = 0; t < LV; ++t)
-            if (t < nl) tmem_ld16_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
-          tmem_wait_ld();
+            for (int t = 0; t < LV; ++t)
+              if (t < nl) tmem_ld8_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
+            tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
-            if constexpr (LV > 2) {
+            for (int j = 0; j < 8; ++j) {
+              const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
               const int x23 = (nl > 2 ? f32_exact_int(r[2][j]) : 0) + (nl > 3 ? 64 * f32_exact_int(r[3][j]) : 0);
-              const long long x = (long long)x01 + (long long)x23 * 4096;
-              acc[c0 + j] = fma(scale, (double)x, acc[c0 + j]);
-            } else {
-              acc[c0 + j] = fma(scale, (double)x01, acc[c0 + j]);
+              add96(w0[c0 + j], w1[c0 + j], w2[c0 + j], x01, x23, q);
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(smem_u32(&bar_acc_empty[set]));
+        }
+        if (ok) {
+          const int gi = tl.tm * BM + row;
+          if (gi < d.m) {
+            double *crow = db + d.c + (long long)gi * d.ldc;
+            const int j0 = tl.tn * BN + half * CW;
+            const int ei = (int)((__double2hiint(s_scale[row]) >> 20) & 0x7FF) - 1023 - 6 * (tg.S + 1);
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const int gj = j0 + j;
+              if (gj < d.n) {
+                const int ej = (int)((__double2hiint(s_scale[BM + half * CW + j]) >> 20) & 0x7FF) - 1023;
+                double v = i96_ldexp(w0[j], w1[j], w2[j], ei + ej);
+                if (d.alpha != 1.0) v *= d.alpha;
+                if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
+                crow[gj] = v;
+              }
             }
           }
         }
-        tc_fence_before();
-        mbar_arrive(smem_u32(&bar_acc_empty[set]));
-      }
-      if (ok) {
-        const int gi = tl.tm * BM + row;
-        if (gi < d.m) {
-          double *crow = db + d.c + (long long)gi * d.ldc;
-          const int j0 = tl.tn * BN + half * CW;
+      } else {
+        double acc[CW];
 #pragma unroll
-          for (int j = 0; j < CW; ++j) {
-            const int gj = j0 + j;
-            if (gj < d.n) {
-              double v = s_scale[BM + half * CW + j] * acc[j];
-              if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
-              crow[gj] = v;
+        for (int j = 0; j < CW; ++j) acc[j] = 0.0;
+        for (int g = 0; g < tg.ngroups; ++g, ++G) {
+          const int set = (int)(G & 1);
+          const uint32_t par = (uint32_t)((G >> 1) & 1);
+          if (ok && !mbar_wait(smem_u32(&bar_acc_full[set]), par, err)) ok = false;
+          if (!ok) continue;
+          tc_fence_after();
+          const int la = tg.S - 1 - LV * (g / tg.nchunk);
+          const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
+          const double scale = ldexp(s_scale[row] * d.alpha, -6 * (la + 2));
+          const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
+#pragma unroll
+          for (int c0 = 0; c0 < CW; c0 += 16) {
+            // every level's loads in flight before the one wait
+            uint32_t r[LV][16];
+#pragma unroll
+            for (int t = 0; t < LV; ++t)
+              if (t < nl) tmem_ld16_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
+              acc[c0 + j] = fma(scale, (double)x01, acc[c0 + j]);
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(smem_u32(&bar_acc_empty[set]));
+        }
+        if (ok) {
+          const int gi = tl.tm * BM + row;
+          if (gi < d.m) {
+            double *crow = db + d.c + (long long)gi * d.ldc;
+            const int j0 = tl.tn * BN + half * CW;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const int gj = j0 + j;
+              if (gj < d.n) {
+                double v = s_scale[BM + half * CW + j] * acc[j];
+                if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
+                crow[gj] = v;
+              }
             }
           }
         }
