@@ -13,19 +13,21 @@
 // TMEM once per k-chunk and added in FP64 (levels from the smallest to the
 // largest).  The truncation after S levels is the only approximation.
 //
-// Kernel layout (persistent: one CTA per SM walking 128x64 output tiles, 10 warps):
+// Kernel layout (persistent: one CTA per SM walking 128 x BN output tiles, 18 warps):
 //   warp 0     TMA producer: 64x64 BF16 boxes of A and B slices, 128B swizzle,
-//              4-stage shared-memory ring guarded by mbarriers.  Four levels
-//              (la .. la-3) are computed together: a stage holds A_p (two
-//              boxes) and B_{la-p} .. B_{la-3-p}, so each A box feeds up to
-//              four MMAs;
+//              4-stage shared-memory ring guarded by mbarriers.  LV levels
+//              (la .. la-LV+1) are computed together: a stage holds A_p (two
+//              boxes) and B_{la-p} .. B_{la-LV+1-p}, so each A box feeds up to
+//              LV MMAs (BN = 64, LV = 4 or, for large-K products, BN = 128,
+//              LV = 2);
 //   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
-//              (M=128, N=64, K=16, both operands K-major), two sets of four
-//              FP32 accumulators of 64 TMEM columns (one set per level group,
+//              (M=128, N=BN, K=16, both operands K-major), two sets of LV
+//              FP32 accumulators of BN TMEM columns (one set per level group,
 //              double buffered), committed per level group and k-chunk;
-//   warps 2-9  epilogue: tcgen05.ld of their lane quadrant and column half,
-//              the group's level sums combined exactly in int64, FP64
-//              accumulation in registers, scaled store of C.
+//   warps 2-17 epilogue: tcgen05.ld of their lane quadrant and column quarter,
+//              the level sums read by integer arithmetic and combined exactly
+//              (96-bit integers for LV = 4, FP64 FMAs for LV = 2), scaled
+//              store of C.
 // Every wait is bounded (2 s); on a timeout the CTA records an error, waits for
 // its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -49,7 +51,8 @@ constexpr int BM = 128, BK = 64;
 constexpr int STAGES = 4;
 constexpr int BOX_BYTES = 64 * BK * 2;  // one 64-row box: 8 KB
 constexpr int STAGE_BYTES = 6 * BOX_BYTES;
-constexpr int OZ_THREADS = 320;
+constexpr int EPI_WARPS = 16;          // epilogue: 4 TMEM lane quadrants x 4 column parts
+constexpr int OZ_THREADS = 64 + 32 * EPI_WARPS;
 constexpr unsigned TMEM_COLS = 512;
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -241,8 +244,8 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// named barrier of the 256 epilogue threads (warps 2-9)
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// named barrier of the epilogue threads (warps 2 .. 2 + EPI_WARPS - 1)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
 // group count of one tile: (level pair, k-chunk) pairs
 struct TileGeom {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
-      mbar_init(smem_u32(&bar_acc_empty[b]), 256);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 32 * EPI_WARPS);
     }
     mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..9
+    // ---------------- epilogue: warps 2 .. 2 + EPI_WARPS - 1
     // Each group holds up to four levels la .. la-3 of one k-chunk in TMEM
     // accumulators (the MMA issuer fills the other set meanwhile); their FP32
     // sums are integers below 2^23.6, read by integer arithmetic, and
@@ -438,12 +441,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // scale on the store.
     // After a failed wait every thread still walks the same tiles and named
     // barriers (skipping the work), so the barriers cannot deadlock.
-    const int ew = warp - 2;                  // 0..7
+    const int ew = warp - 2;                  // 0 .. EPI_WARPS - 1
     const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                 // column half of the tile
-    constexpr int CW = BN / 2;                // its width
+    const int half = ew >> 2;                 // column part of the tile
+    constexpr int CW = BN / (EPI_WARPS / 4);  // its width
     const int row = quad * 32 + lane;
-    const int et = threadIdx.x - 64;          // 0..255 among the epilogue threads
+    const int et = threadIdx.x - 64;          // among the epilogue threads
     bool ok = true;
     long long G = 0;
     for (int ti = blockIdx.x; ti < ntile; ti += gridDim.x) {
@@ -529,15 +532,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const double scale = ldexp(s_scale[row] * d.alpha, -6 * (la + 2));
           const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
 #pragma unroll
-          for (int c0 = 0; c0 < CW; c0 += 16) {
+          for (int c0 = 0; c0 < CW; c0 += 8) {
             // every level's loads in flight before the one wait
-            uint32_t r[LV][16];
+            uint32_t r[LV][8];
 #pragma unroll
             for (int t = 0; t < LV; ++t)
-              if (t < nl) tmem_ld16_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
+              if (t < nl) tmem_ld8_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 8; ++j) {
               const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
               acc[c0 + j] = fma(scale, (double)x01, acc[c0 + j]);
             }
