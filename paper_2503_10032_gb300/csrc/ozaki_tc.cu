@@ -156,8 +156,9 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 }
 
 // The FP32 level sums hold integers below 2^24 in magnitude: their value by
-// integer arithmetic (conversion instructions share this GPU's narrow FP64
-// pipe).  Zero has exponent field 0: the shift is clamped to 31, past m.
+// integer bit extraction on the ALU pipe (float-to-int conversions run on the
+// narrow XU pipe).  Zero has exponent field 0: the shift is clamped to 31,
+// past m.
 __device__ __forceinline__ int f32_exact_int(uint32_t u) {
   const int e = (int)((u >> 23) & 0xFFu);
   const uint32_t m = (u & 0x7FFFFFu) | 0x800000u;
