@@ -167,6 +167,14 @@ __device__ __forceinline__ int f32_exact_int(uint32_t u) {
   return (v ^ sg) - sg;
 }
 
+// x4 TMEM load without the wait
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+
 // x8 TMEM load without the wait
 __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -482,15 +490,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int nl = min(la + 1, LV);  // levels la .. la - nl + 1
           const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
 #pragma unroll
-          for (int c0 = 0; c0 < CW; c0 += 8) {
-            // every level's loads in flight before the one wait
-            uint32_t r[LV][8];
+          for (int c0 = 0; c0 < CW; c0 += 4) {
+            // every level's loads in flight before the one wait (four columns:
+            // the register file of 18 warps per SM allows no more)
+            uint32_t r[LV][4];
 #pragma unroll
             for (int t = 0; t < LV; ++t)
-              if (t < nl) tmem_ld8_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
+              if (t < nl) tmem_ld4_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
               const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
               const int x23 = (nl > 2 ? f32_exact_int(r[2][j]) : 0) + (nl > 3 ? 64 * f32_exact_int(r[3][j]) : 0);
               add96(w0[c0 + j], w1[c0 + j], w2[c0 + j], x01, x23, q);
@@ -533,15 +542,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const double scale = ldexp(s_scale[row] * d.alpha, -6 * (la + 2));
           const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * LV * BN + half * CW);
 #pragma unroll
-          for (int c0 = 0; c0 < CW; c0 += 8) {
-            // every level's loads in flight before the one wait
-            uint32_t r[LV][8];
+          for (int c0 = 0; c0 < CW; c0 += 4) {
+            // every level's loads in flight before the one wait (four columns:
+            // the register file of 18 warps per SM allows no more)
+            uint32_t r[LV][4];
 #pragma unroll
             for (int t = 0; t < LV; ++t)
-              if (t < nl) tmem_ld8_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
+              if (t < nl) tmem_ld4_nowait(base + (uint32_t)(t * BN) + c0, r[t]);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
               const int x01 = f32_exact_int(r[0][j]) + (nl > 1 ? 64 * f32_exact_int(r[1][j]) : 0);
               acc[c0 + j] = fma(scale, (double)x01, acc[c0 + j]);
             }
