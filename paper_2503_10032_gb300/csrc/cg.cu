@@ -645,16 +645,32 @@ __device__ __forceinline__ float gam_pair(const Ctx &c, int sl, const SubDev &d,
   return __ldcg(c.fslab[sl] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[sl] + (long long)rw.y * c.R + k);
 }
 
+// The vector S is applied to: x itself (xp == nullptr), or the CG direction
+// p' = r + beta p formed on the fly from the residual x and the previous
+// direction xp (columns with alpha == 0 keep p), bit for bit what the update
+// loop stores, so that no grid barrier has to separate that loop from the
+// next application.
+struct DirIn {
+  const float *x, *xp;
+  const float *alpha, *beta;  // per column, shared memory
+};
+__device__ __forceinline__ float dir_at(const DirIn &v, long long idx, int k) {
+  const float r = __ldcg(v.x + idx);
+  if (!v.xp) return r;
+  const float p = __ldcg(v.xp + idx);
+  return v.alpha[k] != 0.f ? fmaf(v.beta[k], p, r) : p;
+}
+
 // P1: H1 = Lambda_{Pi,Delta} x^, H2 = Psi_{Pi,Delta} x^ (the few Pi rows)
 template <int RC>
-__device__ void f_pi_rows(const Ctx &c, const float *x) {
+__device__ void f_pi_rows(const Ctx &c, const DirIn &x) {
   float *xs = sh_stage;
   const int R = c.R, w = threadIdx.x >> 5;
   for (int s = blockIdx.x; s < c.n_sub; s += gridDim.x) {
     const SubDev d = c.subs[s];
     if (d.nPi == 0) continue;
     const int *gdl = c.ints + d.gdl_off;
-    for (int e = threadIdx.x; e < d.nDl * R; e += blockDim.x) xs[e] = __ldcg(x + (long long)gdl[e / R] * R + e % R);
+    for (int e = threadIdx.x; e < d.nDl * R; e += blockDim.x) xs[e] = dir_at(x, (long long)gdl[e / R] * R + e % R, e % R);
     __syncthreads();
     const float *lam = c.fb + d.oLam32, *psi = c.fb + d.oPsi32;
     for (int t = w; t < 2 * d.nPi; t += CG_WARPS) {
@@ -718,7 +734,7 @@ __device__ void f_coarse(const Ctx &c, long long A1, const float *x1, long long 
 // P3: lambda = [R_Pi mpi; -x^]; VL = -(Lambda lambda)_Delta ;
 //     BL = -(lambda - Psi lambda)_Delta + Lambda_{Pi,Delta}^T g_Pi
 template <int RC>
-__device__ void f_dl_first(const Ctx &c, const float *x, const float *mpi, const float *g) {
+__device__ void f_dl_first(const Ctx &c, const DirIn &x, const float *mpi, const float *g) {
   float *xs = sh_stage, *gs = sh_stage + MAXG * 16;
   const int R = c.R, w = threadIdx.x >> 5;
   const int ch = n_chunks(c);
@@ -730,7 +746,7 @@ __device__ void f_dl_first(const Ctx &c, const float *x, const float *mpi, const
     const int *gpi = c.ints + d.gpi_off, *gdl = c.ints + d.gdl_off;
     for (int e = threadIdx.x; e < d.nG * R; e += blockDim.x) {
       const int a = e / R, k = e % R;
-      xs[e] = a < d.nPi ? mpi[gpi[a] * R + k] : -__ldcg(x + (long long)gdl[a - d.nPi] * R + k);
+      xs[e] = a < d.nPi ? mpi[gpi[a] * R + k] : -dir_at(x, (long long)gdl[a - d.nPi] * R + k, k);
     }
     for (int e = threadIdx.x; e < d.nPi * R; e += blockDim.x)
       gs[e] = g[gpi[e / R] * R + e % R];
@@ -886,7 +902,7 @@ __device__ void f_coarse_local(const Ctx &c, long long A1, const float *x1, long
 // p.q that follows, so this returns with q written and a partial dot pending in
 // red slot 0 (no barrier taken after it).
 template <int RC>
-__device__ bool f_apply_S(const Ctx &c, const float *x, float *q) {
+__device__ bool f_apply_S(const Ctx &c, const DirIn &x, float *q) {
   const bool sm = small_coarse(c);
   f_pi_rows<RC>(c, x);
   if (!grid_sync(c)) return false;
@@ -1003,7 +1019,11 @@ __device__ int f_cg(const Ctx &c, const double *tol_in, int max_it) {
     }
     __syncthreads();
     if (s_done) break;
-    if (!f_apply_S<RC>(c, P[cur], Qv)) return -1;
+    // the direction of this iteration: P[cur], stored by the previous
+    // iteration's update without a barrier after it, so formed here from the
+    // residual and the previous direction
+    const DirIn dir = it == 0 ? DirIn{P[cur], nullptr, nullptr, nullptr} : DirIn{Rv, P[cur ^ 1], s_alpha, s_beta};
+    if (!f_apply_S<RC>(c, dir, Qv)) return -1;
     f_partial_dot<RC>(c, P[cur], Qv, 0);
     if (!grid_sync(c)) return -1;
     finish_dot<RC>(c, 0, s_pq);
@@ -1027,15 +1047,16 @@ __device__ int f_cg(const Ctx &c, const double *tol_in, int max_it) {
       if (s_alpha[k] != 0.f) s_rr[k] = s_rn[k];
     }
     __syncthreads();
-    // the next direction goes to the other buffer: this iteration's readers of
-    // P[cur] never see it change
+    // the next direction goes to the other buffer, which this iteration's
+    // application read (before the barriers above); its next readers (the dot
+    // and the update of the next iteration) come after the next application's
+    // barriers, and that application forms the values itself
     for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
       const int k = e % R;
       P[cur ^ 1][e] = s_alpha[k] != 0.f ? fmaf(s_beta[k], P[cur][e], Rv[e]) : P[cur][e];
     }
     cur ^= 1;
     ++it;
-    if (!grid_sync(c)) return -1;
   }
   return it;
 }
