@@ -162,6 +162,7 @@ def run_reference(args):
 
 
 def main():
+    global THETA
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -174,7 +175,10 @@ def main():
     ap.add_argument("--scheme", default="auto", choices=list(SCHEMES))
     ap.add_argument("--passes", type=int, default=0, help="FP32 scheme: shifted passes (0: automatic)")
     ap.add_argument("--solve-steps", type=int, default=5, help="timed solves with the reused handle")
+    ap.add_argument("--theta", type=float, default=THETA,
+                    help="NN weight of Eq. (nn-mixed); 0 gives the coarse-space method without the NN term")
     args = ap.parse_args()
+    THETA = args.theta
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
