@@ -76,8 +76,14 @@ int build_mixed(Plan &P, long long &cur) {
       P.err = "internal: slice level count";
       return DDELM_ERR_INVALID_ARG;
     }
-    bool wide = gp.ndesc > 0;
-    for (int t = 0; t < gp.ndesc; ++t) wide = wide && P.gdesc[gp.desc0 + t].k > OZ_WIDE_K;
+    bool wide = gp.ndesc > 0, long_k = false;
+    for (int t = 0; t < gp.ndesc; ++t) {
+      wide = wide && P.gdesc[gp.desc0 + t].k > OZ_WIDE_K;
+      long_k = long_k || P.gdesc[gp.desc0 + t].k > 16 * OZ_KC;
+    }
+    // the 96-bit integer sum of the four-level tiles holds up to 16 k-chunks
+    // (|X| < 2^(43 + 48 + 4)); longer contractions take the FP64 combination
+    wide = wide || long_k;
     const int OZ_BN = wide ? 128 : 64;
     op.bn = OZ_BN;
     std::unordered_map<Key, int, KeyHash> seen;
