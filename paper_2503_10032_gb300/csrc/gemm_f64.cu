@@ -107,10 +107,13 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmDesc *__restrict
   }
 }
 
-// n <= 16 columns (right-hand sides): a block per 32 output rows, the n
-// accumulators of a row in registers.  op(A) transposed: a thread per row and
-// 8 k-lanes (coalesced along the rows); otherwise a warp per row.
-__global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__restrict__ descs,
+// n <= 16 columns (right-hand sides): a block of 32 warps per 32 output rows,
+// the n accumulators of a row in registers.  op(A) transposed: a thread per
+// row and 32 k-lanes for one column (8 for several: their partial sums fill
+// shared memory), coalesced along the rows; otherwise a warp per row.  Sums
+// are reduced in a fixed order (deterministic).
+constexpr int SKINNY_THREADS = 1024;
+__global__ void __launch_bounds__(SKINNY_THREADS) gemm_skinny_kernel(const GemmDesc *__restrict__ descs,
                                                           const GemmTile *__restrict__ tiles,
                                                           double *__restrict__ db) {
   __shared__ double red[8][32][17];
@@ -126,27 +129,28 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__rest
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = 0.0;
   if (d.ta && n == 1) {
-    // one right-hand side: four independent loads in flight per thread
+    // one right-hand side: 32 k-lanes, four independent loads in flight per thread
+    double (*red1)[33] = reinterpret_cast<double (*)[33]>(&red[0][0][0]);  // [32][33]
     const int i = m0 + tx;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (i < d.m) {
       const long long sb = d.tb ? 1 : d.ldb;  // stride of B's single column
       int k = ty;
-      for (; k + 24 < d.k; k += 32) {
-        const double x0 = A[(long long)k * d.lda + i], x1 = A[(long long)(k + 8) * d.lda + i];
-        const double x2 = A[(long long)(k + 16) * d.lda + i], x3 = A[(long long)(k + 24) * d.lda + i];
+      for (; k + 96 < d.k; k += 128) {
+        const double x0 = A[(long long)k * d.lda + i], x1 = A[(long long)(k + 32) * d.lda + i];
+        const double x2 = A[(long long)(k + 64) * d.lda + i], x3 = A[(long long)(k + 96) * d.lda + i];
         a0 = fma(x0, B[k * sb], a0);
-        a1 = fma(x1, B[(k + 8) * sb], a1);
-        a2 = fma(x2, B[(k + 16) * sb], a2);
-        a3 = fma(x3, B[(k + 24) * sb], a3);
+        a1 = fma(x1, B[(k + 32) * sb], a1);
+        a2 = fma(x2, B[(k + 64) * sb], a2);
+        a3 = fma(x3, B[(k + 96) * sb], a3);
       }
-      for (; k < d.k; k += 8) a0 = fma(A[(long long)k * d.lda + i], B[k * sb], a0);
+      for (; k < d.k; k += 32) a0 = fma(A[(long long)k * d.lda + i], B[k * sb], a0);
     }
-    red[ty][tx][0] = (a0 + a1) + (a2 + a3);
+    red1[ty][tx] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (ty == 0 && i < d.m) {
       double sm = 0.0;
-      for (int w = 0; w < 8; ++w) sm += red[w][tx][0];
+      for (int w = 0; w < 32; ++w) sm += red1[w][tx];
       double *cp = C + (long long)i * d.ldc;
       double v = d.alpha * sm;
       if (d.beta != 0.0) v = fma(d.beta, *cp, v);
@@ -154,15 +158,16 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__rest
     }
   } else if (d.ta) {
     const int i = m0 + tx;
-    if (i < d.m)
+    if (i < d.m && ty < 8)
       for (int k = ty; k < d.k; k += 8) {
         const double a = A[(long long)k * d.lda + i];
 #pragma unroll
         for (int c = 0; c < 16; ++c)
           if (c < n) acc[c] = fma(a, d.tb ? B[(long long)c * d.ldb + k] : B[(long long)k * d.ldb + c], acc[c]);
       }
+    if (ty < 8)
 #pragma unroll
-    for (int c = 0; c < 16; ++c) red[ty][tx][c] = acc[c];
+      for (int c = 0; c < 16; ++c) red[ty][tx][c] = acc[c];
     __syncthreads();
     if (ty == 0 && i < d.m) {
       for (int c = 0; c < n; ++c) {
@@ -174,8 +179,33 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(const GemmDesc *__rest
         *cp = v;
       }
     }
+  } else if (n == 1) {
+    // one right-hand side: a warp per row, four partial sums, one reduction
+    const long long sb = d.tb ? 1 : d.ldb;
+    for (int r = ty; r < 32; r += SKINNY_THREADS / 32) {
+      const int i = m0 + r;
+      if (i >= d.m) break;
+      const double *arow = A + (long long)i * d.lda;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int k = tx;
+      for (; k + 96 < d.k; k += 128) {
+        a0 = fma(arow[k], B[k * sb], a0);
+        a1 = fma(arow[k + 32], B[(k + 32) * sb], a1);
+        a2 = fma(arow[k + 64], B[(k + 64) * sb], a2);
+        a3 = fma(arow[k + 96], B[(k + 96) * sb], a3);
+      }
+      for (; k < d.k; k += 32) a0 = fma(arow[k], B[k * sb], a0);
+      double sm = (a0 + a1) + (a2 + a3);
+      for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      if (tx == 0) {
+        double *cp = C + (long long)i * d.ldc;
+        double v = d.alpha * sm;
+        if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+        *cp = v;
+      }
+    }
   } else {
-    for (int r = ty; r < 32; r += 8) {
+    for (int r = ty; r < 32; r += SKINNY_THREADS / 32) {
       const int i = m0 + r;
       if (i >= d.m) break;
 #pragma unroll
@@ -210,7 +240,7 @@ cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cuda
   const GemmTile *tiles = reinterpret_cast<const GemmTile *>(base + p.off_gtile) + ph.tile0;
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
   if (ph.skinny)
-    { gemm_skinny_kernel<<<ph.ntile, 256, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+    { gemm_skinny_kernel<<<ph.ntile, SKINNY_THREADS, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
     { gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
@@ -221,7 +251,7 @@ cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int 
                               cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (skinny)
-    { gemm_skinny_kernel<<<ntiles, 256, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+    { gemm_skinny_kernel<<<ntiles, SKINNY_THREADS, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
     { gemm_f64_kernel<<<ntiles, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
