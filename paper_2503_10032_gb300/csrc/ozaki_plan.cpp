@@ -15,7 +15,7 @@ namespace {
 constexpr int OZ_BM = 128, OZ_BK = 64, OZ_KC = 1024;
 // tile width of a phase: 128 (two levels per group) when every product has a
 // contraction longer than one k-chunk, where A traffic dominates; else 64
-// (four levels per group: a quarter of the FP64 level combinations)
+// (four levels per group, combined exactly in integers)
 constexpr int OZ_WIDE_K = 1024;
 long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
 }  // namespace
