@@ -35,6 +35,32 @@ TOL = 1e-8
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 EPS_REL = 1e-8
 THETA = 0.999
+
+# DRAM traffic of the slice-GEMM class (dram__bytes_read.sum + dram__bytes_write.sum),
+# taken once with ncu (one pass) over the 26 launches of one step of the default
+# workload, and valid only for the kernel and plan sources it was taken on: the
+# bench reports it (per launch, like "achieved") only when their hash matches.
+TC_TRAFFIC = {
+    "workload": "poisson_8x8_m400",
+    "dram_bytes_per_step": 24642797824,
+    "launches_per_step": 26,
+    "sources_sha256": "a205d71a9dce2462d85986e7f42e7823df1ecdadd4f9f35e21c5525d04787a45",
+    "source": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--clock-control none -k regex:ozaki_gemm -s 26 -c 26 python bench.py --steps 1 --warmup 3 "
+               "--no-cpu-baseline --no-fp64-compare --solve-steps 0 (second setup; per launch = step / 26)"),
+}
+TC_SOURCES = ("paper_2503_10032_gb300/csrc/ozaki_tc.cu", "paper_2503_10032_gb300/csrc/ozaki_plan.cpp",
+              "paper_2503_10032_gb300/csrc/plan.cpp")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in TC_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
 SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2, "cqr2series": 3}
 
@@ -378,9 +404,14 @@ def main():
     else:
         work = float("nan")
     achieved = work / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
+    traffic = None
+    if (names[k_dom] == "tc_gemm" and args.workload == TC_TRAFFIC["workload"] and prec == D.DDELM_PREC_MIXED
+            and args.scheme == "auto" and kernel_sources_sha256() == TC_TRAFFIC["sources_sha256"]):
+        traffic = TC_TRAFFIC["dram_bytes_per_step"] / TC_TRAFFIC["launches_per_step"]
     roofline = {"kernel": names[k_dom], "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak if math.isfinite(achieved) else None,
-                "traffic": None, "peak_source": peak_src,
+                "traffic": traffic, "traffic_source": TC_TRAFFIC["source"] if traffic is not None else None,
+                "peak_source": peak_src,
                 "time_share": {n: float(prof_ms[i] / max(prof_ms[:n_cls].sum(), 1e-12)) for i, n in enumerate(names)},
                 "launches": {n: int(prof_n[i]) for i, n in enumerate(names)}}
 
