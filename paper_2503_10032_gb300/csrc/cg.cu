@@ -752,16 +752,23 @@ __device__ void f_dl_first(const Ctx &c, const DirIn &x, const float *mpi, const
       gs[e] = g[gpi[e / R] * R + e % R];
     __syncthreads();
     const float *lam = c.fb + d.oLam32, *psi = c.fb + d.oPsi32, *lamT = c.fb + d.oLamT32;
-    for (int dd = r0 + w; dd < r1; dd += CG_WARPS) {
-      const int a = d.nPi + dd;
-      const float sl = row_dot<RC>(lam + (long long)a * d.nG, d.nG, xs, R);
-      const float sp = row_dot<RC>(psi + (long long)a * d.nG, d.nG, xs, R);
-      const float sg = row_dot<RC>(lamT + (long long)a * d.nG, d.nPi, gs, R);
+    // four rows per warp at a time, so that their loads overlap
+    for (int dd = r0 + 4 * w; dd < r1; dd += 4 * CG_WARPS) {
+      const int cnt = min(4, r1 - dd);
+      const int a0 = d.nPi + dd;
+      float sl[4], sp[4], sg[4];
+      row_dot4<RC>(lam + (long long)a0 * d.nG, d.nG, cnt, d.nG, xs, R, sl);
+      row_dot4<RC>(psi + (long long)a0 * d.nG, d.nG, cnt, d.nG, xs, R, sp);
+      row_dot4<RC>(lamT + (long long)a0 * d.nG, d.nG, cnt, d.nPi, gs, R, sg);
       int k;
-      if (row_writer<RC>(R, k)) {
-        fslab_row(c, FS_VL, d, a)[k] = -sl;
-        fslab_row(c, FS_BL, d, a)[k] = -(xs[a * R + k] - sp) + sg;
-      }
+      if (row_writer<RC>(R, k))
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < cnt) {
+            const int a = a0 + i;
+            fslab_row(c, FS_VL, d, a)[k] = -sl[i];
+            fslab_row(c, FS_BL, d, a)[k] = -(xs[a * R + k] - sp[i]) + sg[i];
+          }
     }
     __syncthreads();
   }

@@ -144,6 +144,7 @@ struct GemmPhase {
   int desc0, ndesc;  // into the descriptor table
   int tile0, ntile;  // into the tile table
   int skinny;        // 1: every n <= 16; tiles are 32-row blocks (tn = 0)
+  int tile = 64;     // otherwise the edge of the square output tiles: 64, or 16 for tiny products
 };
 
 struct CholPhase {

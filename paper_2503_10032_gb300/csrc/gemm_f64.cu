@@ -1,20 +1,24 @@
 // Batched FP64 GEMM engine: C = alpha op(A) op(B) + beta C over a flat list
-// of 64x64 output tiles drawn from any number of descriptors of any shapes
-// (uneven subdomains are just more descriptors).  Triangular operands are
-// flagged so that the k loop skips the zero blocks.  FP64 runs on the CUDA
-// cores (DFMA); each thread owns a 4x4 register tile, operands are staged in
-// shared memory in 16-deep k slices with a double buffer.
+// of square output tiles (64 x 64, or 16 x 16 for tiny products such as a
+// small coarse space, which then spread over more SMs) drawn from any number
+// of descriptors of any shapes (uneven subdomains are just more descriptors).
+// Triangular operands are flagged so that the k loop skips the zero blocks.
+// FP64 runs on the CUDA cores (DFMA); each thread owns a (T/16) x (T/16)
+// register tile, operands are staged in shared memory in 16-deep k slices
+// with a double buffer.
 #include "ddelm_internal.h"
 
 namespace ddelm {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
+template <int BM>
 __device__ __forceinline__ void load_tiles(const double *__restrict__ A, const double *__restrict__ B,
                                            const GemmDesc &d, int m0, int n0, int k0, int kbeg, int kend,
-                                           double (*As)[BM + 1], double (*Bs)[BN + 1]) {
+                                           double (*As)[BM + 1], double (*Bs)[BM + 1]) {
+  constexpr int BN = BM;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int t = 0; t < (BM * BK) / NT; ++t) {
@@ -50,9 +54,11 @@ __device__ __forceinline__ void load_tiles(const double *__restrict__ A, const d
   }
 }
 
+template <int BM>
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmDesc *__restrict__ descs,
                                                       const GemmTile *__restrict__ tiles,
                                                       double *__restrict__ db) {
+  constexpr int BN = BM, RT = BM / 16;  // square tiles, RT x RT per thread
   __shared__ double As[2][BK][BM + 1];
   __shared__ double Bs[2][BK][BN + 1];
   const GemmTile tl = tiles[blockIdx.x];
@@ -65,38 +71,38 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmDesc *__restrict
   const double *B = db + d.b;
   double *C = db + d.c;
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  double acc[4][4];
+  double acc[RT][RT];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < RT; ++c) acc[r][c] = 0.0;
   const int kstart = (kbeg / BK) * BK;
   int buf = 0;
-  if (kstart < kend) load_tiles(A, B, d, m0, n0, kstart, kbeg, kend, As[0], Bs[0]);
+  if (kstart < kend) load_tiles<BM>(A, B, d, m0, n0, kstart, kbeg, kend, As[0], Bs[0]);
   __syncthreads();
   for (int k0 = kstart; k0 < kend; k0 += BK) {
-    if (k0 + BK < kend) load_tiles(A, B, d, m0, n0, k0 + BK, kbeg, kend, As[buf ^ 1], Bs[buf ^ 1]);
+    if (k0 + BK < kend) load_tiles<BM>(A, B, d, m0, n0, k0 + BK, kbeg, kend, As[buf ^ 1], Bs[buf ^ 1]);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[RT], b[RT];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty + 16 * r];
+      for (int r = 0; r < RT; ++r) a[r] = As[buf][kk][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][kk][tx + 16 * c];
+      for (int c = 0; c < RT; ++c) b[c] = Bs[buf][kk][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RT; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < RT; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
     buf ^= 1;
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RT; ++r) {
     const int gi = m0 + ty + 16 * r;
     if (gi >= d.m) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < RT; ++c) {
       const int gj = n0 + tx + 16 * c;
       if (gj >= d.n) continue;
       double *cp = C + (long long)gi * d.ldc + gj;
@@ -241,8 +247,12 @@ cudaError_t launch_gemm_phase(const Plan &p, const GemmPhase &ph, void *ws, cuda
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
   if (ph.skinny)
     { gemm_skinny_kernel<<<ph.ntile, SKINNY_THREADS, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+  else if (ph.tile == 16)
+    { gemm_f64_kernel<16><<<ph.ntile, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+  else if (ph.tile == 64)
+    { gemm_f64_kernel<64><<<ph.ntile, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
-    { gemm_f64_kernel<<<ph.ntile, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -253,7 +263,7 @@ cudaError_t launch_gemm_table(const GemmDesc *descs, const GemmTile *tiles, int 
   if (skinny)
     { gemm_skinny_kernel<<<ntiles, SKINNY_THREADS, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   else
-    { gemm_f64_kernel<<<ntiles, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
+    { gemm_f64_kernel<64><<<ntiles, NT, 0, s>>>(descs, tiles, db); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -649,12 +649,13 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // ---- GEMM phases
   // FP64 GEMM tiles; MIXED setup phases run on the tensor-core path and need none
   bool fp64_tiles = true;
-  auto phase_begin = [&](int skinny = 0) {
+  auto phase_begin = [&](int skinny = 0, int tile = 64) {
     GemmPhase ph;
     ph.desc0 = int(P.gdesc.size());
     ph.tile0 = int(P.gtile.size());
     ph.ndesc = ph.ntile = 0;
     ph.skinny = skinny;
+    ph.tile = tile;
     return ph;
   };
   auto add = [&](GemmPhase &ph, long long a, long long b, long long c, int m, int n, int k, int lda,
@@ -695,7 +696,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       }
       return;
     }
-    const int tm = (m + 63) / 64, tn = (n + 63) / 64;
+    const int T = ph.tile, tm = (m + T - 1) / T, tn = (n + T - 1) / T;
     for (int x = 0; x < tm; ++x)
       for (int y = 0; y < tn; ++y) {
         if (upper_tiles && x > y) continue;
@@ -1022,23 +1023,25 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.ph_coarse = int(P.setup_gemm.size());
   fp64_tiles = true;
   // coarse: 11: S_Pi += D^T D ; 12: Sinv = V_Pi V_Pi^T ; 13: C1 = Sinv D^T, C3 = D Sinv ;
-  //         14: C2 = I - D C1
+  //         14: C2 = I - D C1.  A small coarse space takes 16 x 16 tiles, so that
+  //         these products spread over more than a few SMs.
   if (n_pi > 0) {
-    GemmPhase a = phase_begin();
+    const int ct = n_pi <= 192 ? 16 : 64;
+    GemmPhase a = phase_begin(0, ct);
     add(a, P.o_Dpp, P.o_Dpp, P.o_Spi, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 1, 0, 0, 1.0, 1.0);
     push(a);
-    GemmPhase b = phase_begin();
+    GemmPhase b = phase_begin(0, ct);
     add(b, P.o_Vpi, P.o_Vpi, P.o_Sinv, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 1, GEMM_A_UPPER, 1.0, 0.0);
     push(b);
-    GemmPhase c = phase_begin();
+    GemmPhase c = phase_begin(0, ct);
     add(c, P.o_Sinv, P.o_Dpp, P.o_C1, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 1, 0, 1.0, 0.0);
     add(c, P.o_Dpp, P.o_Sinv, P.o_C3, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 0, 0, 1.0, 0.0);
     push(c);
-    GemmPhase e = phase_begin();
+    GemmPhase e = phase_begin(0, ct);
     add(e, P.o_Dpp, P.o_C1, P.o_C2, n_pi, n_pi, n_pi, n_pi, n_pi, n_pi, 0, 0, 0, -1.0, 1.0);
     push(e);
   } else {
-    for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0, 0});
+    for (int k = 0; k < 4; ++k) P.setup_gemm.push_back(GemmPhase{0, 0, 0, 0, 0, 64});
   }
   P.ph_solve = int(P.setup_gemm.size());
   // solve phases: 15: T = Q2[IB rows]^T F ; 16: Qtf = V3^T T ; 17: y = V Qtf, p = Q_Gamma Qtf ;
