@@ -154,6 +154,17 @@ def oracle_sample(prob, n_sample, budget_s=None):
     return dt * n / len(only), dt, len(only)
 
 
+def max_over_ranks(x, dist, device):
+    """The maximum of x over the ranks of the job (x itself on one process):
+    the whole-job time is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -277,10 +288,7 @@ def main():
     prof_ms, prof_n = solver.profile(enable=False, reset=True)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     value = world * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
@@ -372,10 +380,7 @@ def main():
         D.ddelm_destroy(h)
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_total = float(sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     e2e_value = world * e2e_steps / (e2e_total / 1e3)
     h2d = int(sizes.upload_bytes) + f_h.numel() * 8 + g_h.numel() * 8
     d2h = c_h.numel() * 8 + mu_h.numel() * 8 + u_h.numel() * 8
