@@ -14,6 +14,8 @@
 //   shift kind 2 (FP32 passes): s = shift_rel max diag(G + eps^2 I).
 // A pivot that is not positive marks the matrix in the status array; the
 // factorisation continues with a unit pivot so that no NaN propagates.
+#include <algorithm>
+
 #include "ddelm_internal.h"
 
 namespace ddelm {
@@ -324,19 +326,30 @@ __global__ void matop_kernel(const MatopDesc *__restrict__ descs, double *__rest
 // Sec. 3: D_PiPi = sum_i R_Pi^T Lambda_PiPi^i R_Pi and the first two terms of
 // S_Pi = sum_i R_Pi^T (I - Psi^i)_PiPi R_Pi (+ D_PiPi^T D_PiPi added by a GEMM).
 // One CTA walks the subdomains in order, so the sums are deterministic.
+// D_PiPi = sum_i R_Pi^T Lambda^i_PiPi R_Pi, S_Pi = sum_i R_Pi^T (I - Psi^i)_PiPi R_Pi:
+// a thread per global entry (P, Q), summing over the subdomains that hold both
+// corners in increasing subdomain order (the owner lists are in that order),
+// onto the zeroed matrices
 __global__ void coarse_assembly_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
-                                       double *__restrict__ db, int n_sub, int n_pi, long long o_Dpp,
+                                       double *__restrict__ db, int n_pi, int o_pi_own, long long o_Dpp,
                                        long long o_Spi) {
-  for (int i = 0; i < n_sub; ++i) {
-    const SubDev d = subs[i];
-    const int np = d.nPi;
-    if (threadIdx.x < np * np) {
-      const int a = threadIdx.x / np, b = threadIdx.x % np;
-      const int ga = ints[d.gpi_off + a], gb = ints[d.gpi_off + b];
-      db[o_Dpp + (long long)ga * n_pi + gb] += db[d.oLam + (long long)a * d.nG + b];
-      db[o_Spi + (long long)ga * n_pi + gb] += (a == b ? 1.0 : 0.0) - db[d.oPsi + (long long)a * d.nG + b];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n_pi * n_pi;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int P = int(e / n_pi), Q = int(e % n_pi);
+    double ds = 0.0, ss = 0.0;
+    for (int o = 0; o < 4; ++o) {
+      const int sub = ints[o_pi_own + 8 * P + 2 * o];
+      if (sub < 0) continue;
+      const int a = ints[o_pi_own + 8 * P + 2 * o + 1];
+      const SubDev &d = subs[sub];
+      for (int b = 0; b < d.nPi; ++b)
+        if (ints[d.gpi_off + b] == Q) {
+          ds += db[d.oLam + (long long)a * d.nG + b];
+          ss += (a == b ? 1.0 : 0.0) - db[d.oPsi + (long long)a * d.nG + b];
+        }
     }
-    __syncthreads();
+    db[o_Dpp + e] += ds;
+    db[o_Spi + e] += ss;
   }
 }
 
@@ -483,7 +496,9 @@ cudaError_t launch_coarse_assembly(const Plan &p, void *ws, cudaStream_t s) {
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  { coarse_assembly_kernel<<<1, 32, 0, s>>>(subs, ints, db, p.n_sub, p.n_pi, p.o_Dpp, p.o_Spi); DDELM_COUNT_LAUNCH(); }
+  const long long nn = (long long)p.n_pi * p.n_pi;
+  const unsigned grid = (unsigned)std::min<long long>((nn + 255) / 256, 4096);
+  { coarse_assembly_kernel<<<grid, 256, 0, s>>>(subs, ints, db, p.n_pi, p.o_pi_own, p.o_Dpp, p.o_Spi); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
