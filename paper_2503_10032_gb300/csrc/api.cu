@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -101,57 +102,110 @@ enum { PC_FEAT = 0, PC_GEMM = 1, PC_CHOL = 2, PC_CG = 3, PC_OTHER = 4, PC_SLICE 
   } while (0)
 
 template <class T>
-void put(std::vector<char> &buf, size_t off, const std::vector<T> &v) {
-  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+void put(char *buf, size_t off, const std::vector<T> &v) {
+  if (!v.empty()) std::memcpy(buf + off, v.data(), v.size() * sizeof(T));
+}
+
+// 2^(-j/256), j < 256, for the feature tanh (computed once per process)
+const std::vector<double> &exp2_table() {
+  static const std::vector<double> t = [] {
+    std::vector<double> v(256);
+    for (int j = 0; j < 256; ++j) v[j] = double(std::exp2l(-(long double)j / 256.0L));
+    return v;
+  }();
+  return t;
+}
+
+// Host staging of an upload: one page-locked buffer per process, grown on
+// demand and reused by every setup (a setup waits for its copies before it
+// lets the buffer go); pageable memory when page-locked memory is refused.
+struct Staging {
+  std::mutex m;
+  char *pinned = nullptr;
+  size_t cap = 0;
+};
+Staging &staging() {
+  static Staging st;
+  return st;
 }
 
 int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   Plan &p = h->plan;
-  std::vector<char> tab(p.bytes_tables, 0);
-  put(tab, p.off_subs, p.subs);
-  put(tab, p.off_rows, p.rows);
-  put(tab, p.off_gdesc, p.gdesc);
-  put(tab, p.off_gtile, p.gtile);
-  put(tab, p.off_cdesc, p.cdesc);
-  put(tab, p.off_mdesc, p.mdesc);
-  put(tab, p.off_conv, p.conv);
-  put(tab, p.off_ints, p.ints);
-  put(tab, p.off_sdesc, p.sdesc);
-  put(tab, p.off_odesc, p.odesc);
-  put(tab, p.off_otile, p.otile);
+  const long long sumM = p.sz.sum_M, sumI = p.sz.sum_int;
+  const bool diff = p.op == DDELM_OP_DIFFUSION;
+  // staging layout: the tables, then w, b, the feature constants, the exp2
+  // table, the interior points (and the coefficient and its gradient)
+  const size_t n_w = 2 * sumM, n_b = sumM, n_fc = 4 * sumM, n_x = sumI > 0 ? 2 * sumI : 0;
+  const size_t n_a = (sumI > 0 && diff) ? sumI : 0, n_ga = (sumI > 0 && diff) ? 2 * sumI : 0;
+  const size_t o_w = (p.bytes_tables + 15) / 16 * 16, o_b = o_w + 8 * n_w, o_fc = o_b + 8 * n_b,
+               o_ex = o_fc + 8 * n_fc, o_x = o_ex + 8 * 256, o_a = o_x + 8 * n_x, o_ga = o_a + 8 * n_a,
+               total = o_ga + 8 * n_ga;
+  Staging &st = staging();
+  std::lock_guard<std::mutex> lock(st.m);
+  std::vector<char> pageable;
+  char *buf = nullptr;
+  if (st.cap < total) {
+    if (st.pinned) cudaFreeHost(st.pinned);
+    st.pinned = nullptr;
+    st.cap = 0;
+    const size_t want = total + total / 4;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&st.pinned), want, cudaHostAllocDefault) == cudaSuccess)
+      st.cap = want;
+    else {
+      st.pinned = nullptr;
+      (void)cudaGetLastError();
+    }
+  }
+  if (st.pinned) {
+    buf = st.pinned;
+  } else {
+    pageable.resize(total);
+    buf = pageable.data();
+  }
+  put(buf, p.off_subs, p.subs);
+  put(buf, p.off_rows, p.rows);
+  put(buf, p.off_gdesc, p.gdesc);
+  put(buf, p.off_gtile, p.gtile);
+  put(buf, p.off_cdesc, p.cdesc);
+  put(buf, p.off_mdesc, p.mdesc);
+  put(buf, p.off_conv, p.conv);
+  put(buf, p.off_ints, p.ints);
+  put(buf, p.off_sdesc, p.sdesc);
+  put(buf, p.off_odesc, p.odesc);
+  put(buf, p.off_otile, p.otile);
   if (p.mixed) {
     std::vector<unsigned char> maps;
     const int rc = encode_tensor_maps(p, h->ws, maps);
     if (rc != DDELM_OK) return rc;
-    std::memcpy(tab.data() + p.off_tmaps, maps.data(), maps.size());
+    std::memcpy(buf + p.off_tmaps, maps.data(), maps.size());
   }
-  CK(cudaMemcpyAsync(h->ws, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
-  // problem data: w = s*w_hat, b = s*b_hat, interior points, coefficient
-  double *db = dbase(h);
-  const long long sumM = p.sz.sum_M, sumI = p.sz.sum_int;
-  std::vector<double> w(2 * sumM), b(sumM);
+  // problem data: w = s*w_hat, b = s*b_hat; the kernels evaluate tanh(u / 2)
+  // at u = 2 (w . x + b), with the per-neuron constants (2 w, 2 b, 2 |w|^2)
+  double *w = reinterpret_cast<double *>(buf + o_w), *b = reinterpret_cast<double *>(buf + o_b);
+  double *fc = reinterpret_cast<double *>(buf + o_fc);
   for (long long j = 0; j < 2 * sumM; ++j) w[j] = prob->scale * prob->w_hat[j];
   for (long long j = 0; j < sumM; ++j) b[j] = prob->scale * prob->b_hat[j];
-  CK(cudaMemcpyAsync(db + p.o_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(db + p.o_b, b.data(), b.size() * 8, cudaMemcpyHostToDevice, s));
-  // feature constants: the kernels evaluate tanh(u / 2) at u = 2 (w . x + b)
-  std::vector<double> fc(4 * sumM), ex2(256);
   for (long long j = 0; j < sumM; ++j) {
     fc[4 * j] = 2.0 * w[2 * j];
     fc[4 * j + 1] = 2.0 * w[2 * j + 1];
     fc[4 * j + 2] = 2.0 * b[j];
     fc[4 * j + 3] = 2.0 * (w[2 * j] * w[2 * j] + w[2 * j + 1] * w[2 * j + 1]);
   }
-  for (int j = 0; j < 256; ++j) ex2[j] = double(std::exp2l(-(long double)j / 256.0L));
-  CK(cudaMemcpyAsync(db + p.o_fc, fc.data(), fc.size() * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(db + p.o_exp2, ex2.data(), ex2.size() * 8, cudaMemcpyHostToDevice, s));
-  if (sumI > 0) {
-    CK(cudaMemcpyAsync(db + p.o_xint, prob->x_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
-    if (p.op == DDELM_OP_DIFFUSION) {
-      CK(cudaMemcpyAsync(db + p.o_aint, prob->a_int, sumI * 8, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(db + p.o_gaint, prob->grad_a_int, 2 * sumI * 8, cudaMemcpyHostToDevice, s));
-    }
-  }
+  std::memcpy(buf + o_ex, exp2_table().data(), 8 * 256);
+  if (n_x) std::memcpy(buf + o_x, prob->x_int, 8 * n_x);
+  if (n_a) std::memcpy(buf + o_a, prob->a_int, 8 * n_a);
+  if (n_ga) std::memcpy(buf + o_ga, prob->grad_a_int, 8 * n_ga);
+  double *db = dbase(h);
+  CK(cudaMemcpyAsync(h->ws, buf, p.bytes_tables, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_w, buf + o_w, 8 * n_w, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_b, buf + o_b, 8 * n_b, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_fc, buf + o_fc, 8 * n_fc, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(db + p.o_exp2, buf + o_ex, 8 * 256, cudaMemcpyHostToDevice, s));
+  if (n_x) CK(cudaMemcpyAsync(db + p.o_xint, buf + o_x, 8 * n_x, cudaMemcpyHostToDevice, s));
+  if (n_a) CK(cudaMemcpyAsync(db + p.o_aint, buf + o_a, 8 * n_a, cudaMemcpyHostToDevice, s));
+  if (n_ga) CK(cudaMemcpyAsync(db + p.o_gaint, buf + o_ga, 8 * n_ga, cudaMemcpyHostToDevice, s));
+  // the staging buffer is released (and may be refilled) only after the copies
+  CK(cudaStreamSynchronize(s));
   return DDELM_OK;
 }
 
