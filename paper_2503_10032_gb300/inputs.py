@@ -151,7 +151,7 @@ def coef_a(x, y):
 
 def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
                  op=OP_POISSON, box=(0.0, 1.0, 0.0, 1.0), n_eval=32,
-                 forcing=None, name=""):
+                 forcing=None, coef=None, exact_known=True, name=""):
     """Draw one problem.
 
     M, n_int: int or per-subdomain arrays.  edge_pts: int or per-edge array.
@@ -160,7 +160,8 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
     r = diam/2 on every side, so that b = -w . xi as in Sec. 4.1).
     solutions: list of (u, grad u, lap u) triples, one per right-hand side;
     forcing (optional): list of f(x, y) callables overriding -L u, with g = u on
-    the boundary all the same.
+    the boundary all the same.  coef (optional, diffusion): (x, y) -> (a, a_x, a_y)
+    in place of coef_a.  exact_known = False: u_eval_exact is NaN (no closed form).
     """
     rng = np.random.default_rng(seed)
     n_sub = nx * ny
@@ -190,7 +191,7 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
     x_ev = np.concatenate(x_ev)
     xb_pts = boundary_points(nx, ny, box, eps)
     if op == OP_DIFFUSION:
-        a, ax, ay = coef_a(x_int[:, 0], x_int[:, 1])
+        a, ax, ay = (coef or coef_a)(x_int[:, 0], x_int[:, 1])
         grad_a = np.stack([ax, ay], 1)
     else:
         a, grad_a = np.ones(len(x_int)), np.zeros((len(x_int), 2))
@@ -206,7 +207,7 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
             f = -lu(X, Y)
         f_cols.append(f)
         g_cols.append(u(xb_pts[:, 0], xb_pts[:, 1]))
-        u_cols.append(u(x_ev[:, 0], x_ev[:, 1]))
+        u_cols.append(u(x_ev[:, 0], x_ev[:, 1]) if exact_known else np.full(len(x_ev), np.nan))
     return Problem(nx=nx, ny=ny, box=tuple(float(v) for v in box), op=op, M=Ms,
                    w_hat=np.concatenate(w_hat), b_hat=np.concatenate(b_hat),
                    scale=float(scale), n_int=nIs, x_int=x_int, a_int=np.asarray(a, np.float64),
@@ -214,6 +215,58 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
                    f_int=np.stack(f_cols, 1), g_bnd=np.stack(g_cols, 1),
                    n_eval=np.full(n_sub, n_eval, np.int64), x_eval=x_ev,
                    u_eval_exact=np.stack(u_cols, 1), name=name)
+
+
+def grf(alpha, seed, n_terms=256):
+    """An approximate Gaussian random field (Sec. 4.3, Eq. (grf)):
+    sum_{i <= n_terms} a_i sin(w_i . x + b_i) with a_i ~ N(0, alpha^4 / 256),
+    w_i ~ N(0, alpha^2 I), b_i ~ U(0, 2 pi); returns (field, gradient) callables."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0.0, alpha * alpha / 16.0, n_terms)
+    w = rng.normal(0.0, alpha, (n_terms, 2))
+    b = rng.uniform(0.0, 2.0 * np.pi, n_terms)
+
+    def phase(x, y):
+        return np.outer(np.ravel(x), w[:, 0]) + np.outer(np.ravel(y), w[:, 1]) + b[None, :]
+
+    def field(x, y):
+        out = np.empty(np.size(x))
+        for c in range(0, np.size(x), 8192):
+            out[c:c + 8192] = np.sin(phase(np.ravel(x)[c:c + 8192], np.ravel(y)[c:c + 8192])) @ a
+        return out.reshape(np.shape(x))
+
+    def grad(x, y):
+        gx, gy = np.empty(np.size(x)), np.empty(np.size(x))
+        for c in range(0, np.size(x), 8192):
+            cs = np.cos(phase(np.ravel(x)[c:c + 8192], np.ravel(y)[c:c + 8192])) * a[None, :]
+            gx[c:c + 8192] = cs @ w[:, 0]
+            gy[c:c + 8192] = cs @ w[:, 1]
+        return gx.reshape(np.shape(x)), gy.reshape(np.shape(x))
+    return field, grad
+
+
+def grf_coefficient(alpha, seed):
+    """rho = tanh(grf) + 1.1 (Sec. 4.4) and its gradient (1 - tanh^2(grf)) grad grf."""
+    field, grad = grf(alpha, seed)
+
+    def coef(x, y):
+        g = field(x, y)
+        gx, gy = grad(x, y)
+        t = np.tanh(g)
+        return t + 1.1, (1.0 - t * t) * gx, (1.0 - t * t) * gy
+    return coef
+
+
+def _zero_solution():
+    def u(x, y):
+        return np.zeros(np.shape(x))
+
+    def grad(x, y):
+        return np.zeros(np.shape(x)), np.zeros(np.shape(x))
+
+    def lap(x, y):
+        return np.zeros(np.shape(x))
+    return u, grad, lap
 
 
 def fourier_forcing(coeffs):
@@ -270,11 +323,42 @@ def config(name: str) -> Problem:
         sols = [_sin_sin(p, q) for p in range(1, 5) for q in range(1, 5)]
         return make_problem(32, 32, 1000, 4000, 40, scale=32.0, init="paper", seed=1005,
                             solutions=sols, op=OP_DIFFUSION, name=name)
+    if name == "poisson_8x8_grf":           # the 8x8 M=400 shape, g = 0, f = GRF with alpha = 32 (Sec. 4.3)
+        f, _ = grf(32.0, 1007)
+        return make_problem(8, 8, 400, 1600, 40, scale=32.0, init="paper", seed=1007,
+                            solutions=[_zero_solution()], forcing=[f], exact_known=False, name=name)
+    if name == "varcoef_8x8_grf":           # -div(rho grad u) = 1, u = 0 on the boundary, rho = tanh(GRF) + 1.1 (Sec. 4.4)
+        return make_problem(8, 8, 400, 1600, 40, scale=32.0, init="paper", seed=1008,
+                            solutions=[_zero_solution()], forcing=[lambda x, y: np.ones(np.shape(x))],
+                            op=OP_DIFFUSION, coef=grf_coefficient(32.0, 1009), exact_known=False, name=name)
+    if name == "diffusion_4x4_m1000_r16":   # the 32x32 workload's per-subdomain shape on a 4x4 grid
+        sols = [_sin_sin(p, q) for p in range(1, 5) for q in range(1, 5)]
+        return make_problem(4, 4, 1000, 4000, 40, scale=32.0, init="paper", seed=1006,
+                            solutions=sols, op=OP_DIFFUSION, name=name)
     raise KeyError(name)
 
 
 CONFIGS = ("poisson_2x2_m100", "poisson_8x8_m400", "poisson_16x16_uneven",
            "poisson_8x8_fourier", "diffusion_32x32_m1000_r16")
+
+
+def interface_vectors(n_delta, n_rhs, count, seed):
+    """`count` seeded N(0, 1) interface vectors [n_delta x n_rhs] (inputs of the
+    operator-application checks)."""
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((n_delta, n_rhs)) for _ in range(count)]
+
+
+def fourier_basis(x):
+    """sin(p pi x) sin(q pi y), p, q = 1..4, at the points x [n x 2] -> [n x 16]
+    (column 4 (p-1) + (q-1)), the modes of the Fourier forcing."""
+    return np.stack([np.sin(p * np.pi * x[:, 0]) * np.sin(q * np.pi * x[:, 1])
+                     for p in range(1, 5) for q in range(1, 5)], 1)
+
+
+def fourier_coefficients():
+    """The 16 coefficients a_pq of the poisson_8x8_fourier forcing (row p-1, column q-1 flattened)."""
+    return np.random.default_rng(10040).standard_normal(16)
 
 
 def small_uneven_problem(nx=4, ny=3, M_range=(20, 90), seed=13, n_rhs=1, init="paper", scale=8.0):

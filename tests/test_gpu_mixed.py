@@ -5,6 +5,7 @@ import pytest
 
 from oracle import ddelm as odd
 from paper_2503_10032_gb300 import inputs
+from parity_util import close
 
 pytestmark = pytest.mark.gpu
 
@@ -19,9 +20,6 @@ def D():
     from paper_2503_10032_gb300 import ddelm
     return ddelm
 
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 CASES = [  # nx, ny, M, n_int, e, eps_rel, theta, R, seed
@@ -43,10 +41,10 @@ def test_mixed_local_operators_and_solution(D, case):
     for i in range(p.n_sub):
         L = o.loc[i]
         G = slice(L.m - L.nG, L.m)
-        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < tol_op
-        assert _rel(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G]) < tol_op
+        assert close(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G], tol_op, "s.inspect(i, 3) vs L.Ahat @ L.Kpinv[:, G]")
+        assert close(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G], tol_op, "s.inspect(i, 4) vs (L.K @ L.Kpinv)[G, G]")
         if L.nDl:
-            assert _rel(s.inspect(i, 5), L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]) < tol_op
+            assert close(s.inspect(i, 5), L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:], tol_op, "s.inspect(i, 5) vs L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]")
     f = torch.tensor(p.f_int, dtype=torch.float64, device="cuda")
     g = torch.tensor(p.g_bnd, dtype=torch.float64, device="cuda")
     c, mu, u, info, rc = s.solve(f, g)
@@ -54,8 +52,8 @@ def test_mixed_local_operators_and_solution(D, case):
     ref = odd.solve(p, odd.Options(eps_rel=eps, theta=th))
     tol = 1e-8 if eps >= 1e-6 else 1e-7
     assert rc == D.DDELM_OK
-    assert _rel(mu.cpu().numpy()[o.n_pi:], ref["mu_delta"]) < tol
-    assert _rel(u.cpu().numpy(), ref["u_eval"]) < tol
+    assert close(mu.cpu().numpy()[o.n_pi:], ref["mu_delta"], tol, "mu.cpu().numpy()[o.n_pi:] vs ref['mu_delta']")
+    assert close(u.cpu().numpy(), ref["u_eval"], tol, "u.cpu().numpy() vs ref['u_eval']")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -73,8 +71,8 @@ def test_uneven_subdomains(D, prec):
     torch.cuda.synchronize()
     assert rc == D.DDELM_OK
     n_pi = ref["oracle"].n_pi
-    assert _rel(mu.cpu().numpy()[n_pi:], ref["mu_delta"]) < 1e-8
-    assert _rel(u.cpu().numpy(), ref["u_eval"]) < 1e-8
+    assert close(mu.cpu().numpy()[n_pi:], ref["mu_delta"], 1e-8, "mu.cpu().numpy()[n_pi:] vs ref['mu_delta']")
+    assert close(u.cpu().numpy(), ref["u_eval"], 1e-8, "u.cpu().numpy() vs ref['u_eval']")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

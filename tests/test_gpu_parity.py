@@ -4,6 +4,7 @@ import pytest
 
 from oracle import ddelm as odd
 from paper_2503_10032_gb300 import inputs
+from parity_util import close
 
 pytestmark = pytest.mark.gpu
 
@@ -18,9 +19,6 @@ def D():
     from paper_2503_10032_gb300 import ddelm
     return ddelm
 
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def _run(D, p, **kw):
@@ -58,12 +56,12 @@ def test_assembly_and_local_operators(D, case):
         Lam = L.Ahat @ L.Kpinv[:, G]                       # -A^i K^+ B^i on Gamma^i
         Psi = (L.K @ L.Kpinv)[G, G]                        # E^T K K^+ E
         Phi = L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]        # A-bar K-bar^+ E_Delta
-        assert _rel(s.inspect(i, 3), Lam) < 1e-9
-        assert _rel(s.inspect(i, 4), Psi) < 1e-9
+        assert close(s.inspect(i, 3), Lam, 1e-9, "s.inspect(i, 3) vs Lam")
+        assert close(s.inspect(i, 4), Psi, 1e-9, "s.inspect(i, 4) vs Psi")
         if L.nDl:
-            assert _rel(s.inspect(i, 5), Phi) < 1e-9
+            assert close(s.inspect(i, 5), Phi, 1e-9, "s.inspect(i, 5) vs Phi")
     if o.n_pi:
-        assert _rel(s.inspect(0, 6), o.S_Pi) < 1e-9
+        assert close(s.inspect(0, 6), o.S_Pi, 1e-9, "s.inspect(0, 6) vs o.S_Pi")
 
 
 @pytest.mark.parametrize("case", SMALL)
@@ -74,10 +72,10 @@ def test_solution_matches_oracle(D, case):
     s, c, mu, u, info, rc = _run(D, p, theta=th, eps_rel=eps, tol=1e-11)
     assert rc == D.DDELM_OK, D.ddelm_status_string(rc)
     n_pi = ref["oracle"].n_pi
-    assert _rel(mu[n_pi:], ref["mu_delta"]) < 1e-9
+    assert close(mu[n_pi:], ref["mu_delta"], 1e-9, "mu[n_pi:] vs ref['mu_delta']")
     if n_pi:
-        assert _rel(mu[:n_pi], ref["mu_pi"]) < 1e-9
-    assert _rel(u, ref["u_eval"]) < 1e-9
+        assert close(mu[:n_pi], ref["mu_pi"], 1e-9, "mu[:n_pi] vs ref['mu_pi']")
+    assert close(u, ref["u_eval"], 1e-9, "u vs ref['u_eval']")
     assert info.rel_residual < 1e-10
     assert info.iterations > 0
 
@@ -91,9 +89,9 @@ def test_poisson_2x2_m100_matches_oracle(D, eps_rel, tol, pde_err):
     ref = odd.solve(p, odd.Options(eps_rel=eps_rel))
     s, c, mu, u, info, rc = _run(D, p, eps_rel=eps_rel, tol=1e-11)
     assert rc == D.DDELM_OK
-    assert _rel(mu[1:], ref["mu_delta"]) < tol
-    assert _rel(u, ref["u_eval"]) < tol
-    assert _rel(u, p.u_eval_exact) < pde_err   # sanity against sin(pi x) sin(pi y)
+    assert close(mu[1:], ref["mu_delta"], tol, "mu[1:] vs ref['mu_delta']")
+    assert close(u, ref["u_eval"], tol, "u vs ref['u_eval']")
+    assert close(u, p.u_eval_exact, pde_err, "u vs p.u_eval_exact")   # sanity against sin(pi x) sin(pi y)
 
 
 @pytest.mark.parametrize("case", [SMALL[2], SMALL[5]])

@@ -6,6 +6,7 @@ import pytest
 
 from oracle import ddelm as odd
 from paper_2503_10032_gb300 import inputs
+from parity_util import close
 
 pytestmark = pytest.mark.gpu
 
@@ -20,9 +21,6 @@ def D():
     from paper_2503_10032_gb300 import ddelm
     return ddelm
 
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def _solve(D, p, **kw):
@@ -58,14 +56,14 @@ def test_fp32_cholesky_scheme(D, case, prec):
     for i in range(p.n_sub):
         L = o.loc[i]
         G = slice(L.m - L.nG, L.m)
-        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < tol_op
-        assert _rel(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G]) < tol_op
+        assert close(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G], tol_op, "s.inspect(i, 3) vs L.Ahat @ L.Kpinv[:, G]")
+        assert close(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G], tol_op, "s.inspect(i, 4) vs (L.K @ L.Kpinv)[G, G]")
         if L.nDl:
-            assert _rel(s.inspect(i, 5), L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]) < tol_op
+            assert close(s.inspect(i, 5), L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:], tol_op, "s.inspect(i, 5) vs L.Abar @ L.Kbar_pinv[:, L.m - L.nDl:]")
     ref = odd.solve(p, odd.Options(eps_rel=eps))
     tol = 1e-8 if eps >= 1e-6 else 1e-7
-    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < tol
-    assert _rel(u, ref["u_eval"]) < tol
+    assert close(mu[o.n_pi:], ref["mu_delta"], tol, "mu[o.n_pi:] vs ref['mu_delta']")
+    assert close(u, ref["u_eval"], tol, "u vs ref['u_eval']")
 
 
 def test_too_few_fp32_passes_is_reported(D):
@@ -92,12 +90,12 @@ def test_cqr2_series_scheme(D, case, prec):
     for i in range(p.n_sub):
         L = o.loc[i]
         G = slice(L.m - L.nG, L.m)
-        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < tol_op
-        assert _rel(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G]) < tol_op
+        assert close(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G], tol_op, "s.inspect(i, 3) vs L.Ahat @ L.Kpinv[:, G]")
+        assert close(s.inspect(i, 4), (L.K @ L.Kpinv)[G, G], tol_op, "s.inspect(i, 4) vs (L.K @ L.Kpinv)[G, G]")
     ref = odd.solve(p, odd.Options(eps_rel=eps))
     tol = 1e-8 if eps >= 1e-6 else 1e-7
-    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < tol
-    assert _rel(u, ref["u_eval"]) < tol
+    assert close(mu[o.n_pi:], ref["mu_delta"], tol, "mu[o.n_pi:] vs ref['mu_delta']")
+    assert close(u, ref["u_eval"], tol, "u vs ref['u_eval']")
 
 
 def test_fp32_scheme_uneven(D):
@@ -107,8 +105,8 @@ def test_fp32_scheme_uneven(D):
                                 setup_scheme=D.DDELM_SCHEME_FP32)
     assert rc == D.DDELM_OK
     n_pi = ref["oracle"].n_pi
-    assert _rel(mu[n_pi:], ref["mu_delta"]) < 1e-8
-    assert _rel(u, ref["u_eval"]) < 1e-8
+    assert close(mu[n_pi:], ref["mu_delta"], 1e-8, "mu[n_pi:] vs ref['mu_delta']")
+    assert close(u, ref["u_eval"], 1e-8, "u vs ref['u_eval']")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -124,9 +122,9 @@ def test_variable_coefficient_operator(D, prec, scheme):
     assert rc == D.DDELM_OK
     for i in range(p.n_sub):
         L = o.loc[i]
-        assert _rel(s.inspect(i, 0), L.K) < 1e-13  # assembled K_c with the variable-coefficient rows
+        assert close(s.inspect(i, 0), L.K, 1e-13, "s.inspect(i, 0) vs L.K")  # assembled K_c with the variable-coefficient rows
         G = slice(L.m - L.nG, L.m)
-        assert _rel(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G]) < 1e-9
+        assert close(s.inspect(i, 3), L.Ahat @ L.Kpinv[:, G], 1e-9, "s.inspect(i, 3) vs L.Ahat @ L.Kpinv[:, G]")
     ref = odd.solve(p, odd.Options(eps_rel=1e-6))
-    assert _rel(mu[o.n_pi:], ref["mu_delta"]) < 1e-8
-    assert _rel(u, ref["u_eval"]) < 1e-8
+    assert close(mu[o.n_pi:], ref["mu_delta"], 1e-8, "mu[o.n_pi:] vs ref['mu_delta']")
+    assert close(u, ref["u_eval"], 1e-8, "u vs ref['u_eval']")
