@@ -41,26 +41,37 @@ using namespace ddelm;
 
 extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const double *d_F, int R,
                                         double eps_rel, double *d_C, void *stream) {
-  if (!d_K || !d_F || !d_C || m < 1 || M < 1 || M > 256 || R < 1 || R > 16 || !(eps_rel >= 0.0))
+  if (!d_K || !d_F || !d_C || m < 1 || M < 1 || M > 256 || R < 1 || R > 16 || !(eps_rel >= 0.0)) {
+    record_plan_error("ddelm_local_lstsq_static: null pointer, or m < 1, M outside 1..256, R outside 1..16, "
+                      "eps_rel < 0");
     return DDELM_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // layout (doubles): tables | K copy (later Q2) | F | Q1 | G V1 V2 V3 Z1 Z2 T1 V | T Qtf C | status
-  const long long TAB = 16384;
-  long long cur = TAB;
+  // The tables (GEMM descriptors and tiles, Cholesky descriptors) come first in
+  // the array; their size depends on m and M, so they are built before the
+  // data regions are laid out behind them.  Data offsets are fixed here as
+  // offsets from the end of the tables (DB0, known once the tables are built).
+  long long cur = 0;
   auto take = [&](long long n) {
     long long o = cur;
     cur += rup32(n);
     return o;
   };
+  // layout (doubles): K copy (later Q2) | F | Q1 | G V1 V2 V3 Z1 Z2 T1 V | T Qtf C | status
   const long long oK = take((long long)m * M), oF = take((long long)m * R), oQ1 = take((long long)m * M);
   const long long oG = take((long long)M * M), oV1 = take((long long)M * M), oV2 = take((long long)M * M);
   const long long oV3 = take((long long)M * M), oZ1 = take((long long)M * M), oZ2 = take((long long)M * M);
   const long long oT1 = take((long long)M * M), oV = take((long long)M * M);
   const long long oT = take((long long)M * R), oQtf = take((long long)M * R), oC = take((long long)M * R);
   const long long oSt = take(64);
-  if (cur > DDELM_STATIC_SCRATCH_DOUBLES) return DDELM_ERR_INVALID_ARG;  // beyond the static maximum
+  const long long data_doubles = cur;
+  if (data_doubles > DDELM_STATIC_SCRATCH_DOUBLES) {
+    record_plan_error("ddelm_local_lstsq_static: the sizes need more scratch than the static array holds");
+    return DDELM_ERR_INVALID_ARG;
+  }
 
-  // tables: one phase per dependent step
+  // tables: one phase per dependent step; descriptor offsets are relative to
+  // the start of the data regions and shifted once DB0 is known
   std::vector<GemmDesc> gd;
   std::vector<GemmTile> gt;
   struct Ph {
@@ -102,7 +113,6 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
       }
   };
   const int BU = GEMM_B_UPPER, AU = GEMM_A_UPPER;
-  std::vector<int> chol_after;  // chol pass index run after phase k (-1: none)
   begin(0);  // 0: G = K^T K
   add(oK, oK, oG, M, M, m, M, M, M, 1, 0, 0, 1.0, 0.0, true);
   begin(0);  // 1: Q1 = K V1
@@ -148,7 +158,22 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
   const size_t bytes_gd = gd.size() * sizeof(GemmDesc), bytes_gt = gt.size() * sizeof(GemmTile);
   const size_t off_gt = (bytes_gd + 255) / 256 * 256, off_cd = off_gt + (bytes_gt + 255) / 256 * 256;
   const size_t bytes_tab = off_cd + cd.size() * sizeof(CholDesc);
-  if (bytes_tab > TAB * sizeof(double)) return DDELM_ERR_INVALID_ARG;
+  const long long DB0 = rup32((long long)((bytes_tab + sizeof(double) - 1) / sizeof(double)));
+  if (DB0 + data_doubles > DDELM_STATIC_SCRATCH_DOUBLES) {
+    record_plan_error("ddelm_local_lstsq_static: the sizes need more scratch (tables and data) than the static "
+                      "array holds");
+    return DDELM_ERR_INVALID_ARG;
+  }
+  for (auto &d : gd) {
+    d.a += DB0;
+    d.b += DB0;
+    d.c += DB0;
+  }
+  for (auto &c : cd) {
+    c.g += DB0;
+    c.v += DB0;
+    if (c.z >= 0) c.z += DB0;
+  }
   std::vector<char> tab(bytes_tab, 0);
   std::memcpy(tab.data(), gd.data(), bytes_gd);
   std::memcpy(tab.data() + off_gt, gt.data(), bytes_gt);
@@ -166,14 +191,15 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
     }                                                  \
   } while (0)
   char *base = reinterpret_cast<char *>(db);
+  // the host table is pageable: cudaMemcpyAsync has consumed it when it returns
   CKS(cudaMemcpyAsync(base, tab.data(), bytes_tab, cudaMemcpyHostToDevice, s));
-  CKS(cudaMemcpyAsync(db + oK, d_K, sizeof(double) * (size_t)m * M, cudaMemcpyDeviceToDevice, s));
-  CKS(cudaMemcpyAsync(db + oF, d_F, sizeof(double) * (size_t)m * R, cudaMemcpyDeviceToDevice, s));
-  CKS(cudaMemsetAsync(db + oSt, 0, 64 * sizeof(double), s));  // status words start at zero
+  CKS(cudaMemcpyAsync(db + DB0 + oK, d_K, sizeof(double) * (size_t)m * M, cudaMemcpyDeviceToDevice, s));
+  CKS(cudaMemcpyAsync(db + DB0 + oF, d_F, sizeof(double) * (size_t)m * R, cudaMemcpyDeviceToDevice, s));
+  CKS(cudaMemsetAsync(db + DB0 + oSt, 0, 64 * sizeof(double), s));  // status words start at zero
   const GemmDesc *dgd = reinterpret_cast<const GemmDesc *>(base);
   const GemmTile *dgt = reinterpret_cast<const GemmTile *>(base + off_gt);
   const CholDesc *dcd = reinterpret_cast<const CholDesc *>(base + off_cd);
-  int *status = reinterpret_cast<int *>(db + oSt);
+  int *status = reinterpret_cast<int *>(db + DB0 + oSt);
   auto gemm = [&](int k) {
     return launch_gemm_table(dgd, dgt + phases[k].t0, phases[k].nt, db, phases[k].skinny, s);
   };
@@ -188,7 +214,7 @@ extern "C" int ddelm_local_lstsq_static(const double *d_K, int m, int M, const d
   CKS(gemm(6));
   CKS(launch_chol_table(dcd + 2, 1, M, db, status, s));
   for (int k = 7; k <= 11; ++k) CKS(gemm(k));
-  CKS(cudaMemcpyAsync(d_C, db + oC, sizeof(double) * (size_t)M * R, cudaMemcpyDeviceToDevice, s));
+  CKS(cudaMemcpyAsync(d_C, db + DB0 + oC, sizeof(double) * (size_t)M * R, cudaMemcpyDeviceToDevice, s));
   int st[3] = {0, 0, 0};
   CKS(cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
   CKS(cudaStreamSynchronize(s));
