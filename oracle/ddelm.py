@@ -45,6 +45,7 @@ class Options:
     theta: float = 0.999           # Eq. (nn-mixed); 0.999 in Sec. 4.2.2
     eps_rel: float = 1e-8          # ridge reading (module docstring)
     use_change_of_vars: bool = True  # K_c instead of K (Sec. 3.2)
+    use_Am: bool = True             # A_m instead of the plain flux rows A (Sec. 3.2)
     tol: float = 1e-9              # CG relative residual (Sec. 4)
     max_iters: int = 20000
 
@@ -110,7 +111,7 @@ class DDELMOracle:
         skips the coarse problem (used to time a bounded sample of the setup)."""
         self.p = prob
         self.o = opts or Options()
-        self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts)
+        self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts, use_Am=self.o.use_Am)
         self.n_pi, self.n_dl = self.lay.n_pi, self.lay.n_delta
         self._build_local(only)
         if only is None:

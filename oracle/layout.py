@@ -43,7 +43,12 @@ class SubLayout:
 
 
 class Layout:
-    def __init__(self, nx, ny, box, edge_pts):
+    def __init__(self, nx, ny, box, edge_pts, use_Am=True):
+        """use_Am: the corner rows of A_m (Sec. 3.2); False: the plain flux rows
+        of Eq. (ddelm), whose corner row (the corner normal is undefined) is the
+        sum over the two edges of the subdomain meeting the corner of the flux
+        there with that edge's normal."""
+        self.use_Am = use_Am
         self.nx, self.ny, self.box = nx, ny, box
         self.edge_pts = np.asarray(edge_pts, np.int64)
         x0, x1, y0, y1 = box
@@ -153,6 +158,9 @@ class Layout:
             t = []
             for eid, a, b, nrm in edges:
                 if v not in (a, b):
+                    continue
+                if not self.use_Am:
+                    t.append((1.0, self.vxy(v), nrm))
                     continue
                 e = int(self.edge_pts[eid])
                 wgt = 1.0 / (e + 1)

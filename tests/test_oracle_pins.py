@@ -138,6 +138,34 @@ def test_structured_equals_dense_bruteforce(case):
     assert _rel(np.concatenate(cs), np.concatenate(d["c"])) < 1e-10
 
 
+@pytest.mark.parametrize("theta", [0.0, 1.0])
+def test_plain_flux_rows(theta):
+    """The plain flux rows A of Eq. (ddelm) (no A_m): a corner's row is the flux at
+    the corner with each of the two edges' outward normals, summed (the corner
+    normal is undefined); its Delta rows are the A_m Delta rows; and the
+    structured method with these rows equals the dense brute force."""
+    p = inputs.small_problem(3, 3, M=12, n_int=40, edge_pts=3, n_rhs=1, seed=9)
+    o_a = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6, theta=theta, use_Am=False))
+    o_m = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6, theta=theta))
+    for i, (La, Lm) in enumerate(zip(o_a.loc, o_m.loc)):
+        sl = o_a.lay.subs[i]
+        np.testing.assert_array_equal(La.Ahat[La.nPi:], Lm.Ahat[Lm.nPi:])
+        for k, v in enumerate(sl.pi_vertex):
+            xy = o_a.lay.vxy(v)[None, :]
+            ix, iy = i % p.nx, i // p.nx
+            # the two edges of subdomain i meeting corner v: a vertical one (normal +-x), a horizontal one (+-y)
+            nx_ = 1.0 if v[0] == ix + 1 else -1.0
+            ny_ = 1.0 if v[1] == iy + 1 else -1.0
+            want = ddelm.F_phi(La.w, La.b, xy, np.array([[nx_, 0.0]])) + \
+                ddelm.F_phi(La.w, La.b, xy, np.array([[0.0, ny_]]))
+            np.testing.assert_allclose(La.Ahat[k], want[0], rtol=1e-13, atol=1e-13)
+    mu, S, b = o_a.solve_direct()
+    d = dense.solve_dense(o_a)
+    assert _rel(S, d["S"]) < 1e-11
+    assert _rel(mu, d["mu_delta"]) < 1e-10
+    assert _rel(S, o_m.assemble_S_theta()) > 1e-6   # the modification changes the operator
+
+
 def test_normal_equation_is_stacked_least_squares():
     """Eq. (nn-mixed) + Eq. (coarse_sol_2) minimise |K~ c + B~ mu - f~|^2 + |W^1/2 (D~ mu - d~)|^2."""
     p = inputs.small_problem(3, 3, M=10, n_int=40, edge_pts=2, n_rhs=1, seed=11)
