@@ -18,7 +18,8 @@
  *          [c; mu_Pi] = K~^+ (f~ - B~ mu_Delta), Eq. (coarse_sol_2), and the
  *          network values at caller-given points.
  *   backward (ddelm_backward): the adjoint of solve with respect to the
- *          right-hand-side values (gradients of a loss given dL/dc or dL/du).
+ *          right-hand-side values and the hidden-layer scale (gradients of a
+ *          loss given dL/dc or dL/du).
  *
  * Conventions shared by every entry point:
  *   - All floating-point data are IEEE double.  Host pointers are read during
@@ -64,7 +65,8 @@ extern "C" {
 #define DDELM_OK 0
 #define DDELM_ERR_INVALID_ARG (-1)    /* bad sizes, null pointers, workspace too small */
 #define DDELM_ERR_RANK_DEFICIENT (-2) /* a local factorisation failed: a Cholesky pivot was not positive, or a series scheme met max |E| > 1e-4 (info: subdomain) */
-#define DDELM_ERR_NOT_CONVERGED (-3)  /* CG reached max_iters; outputs are still written */
+#define DDELM_ERR_NOT_CONVERGED (-3)  /* CG reached max_iters, or the data / a CG scalar is not finite
+                                         (NaN or Inf); outputs are still written */
 #define DDELM_ERR_CUDA (-4)           /* a CUDA runtime call failed */
 #define DDELM_ERR_TIMEOUT (-5)        /* a device-side grid barrier gave up waiting */
 #define DDELM_ERR_UNSUPPORTED (-6)    /* an option or size this build does not support */
@@ -108,6 +110,15 @@ typedef struct ddelm_options {
   int disable_graphs;     /* 1: issue every launch directly; 0: the setup (from the first
                              ddelm_refactor) and the solve (from a handle's second ddelm_solve)
                              are captured once as CUDA graphs and replayed */
+  int barrier_timeout_ms; /* a grid barrier of the interface solve gives up (DDELM_ERR_TIMEOUT)
+                             after waiting this long (0: 2000) */
+  int inject_barrier_stall; /* tests only: every grid barrier of the interface solve waits for one
+                             arrival more than the grid has, so it can end only by its time limit;
+                             the kernel then returns and the call reports DDELM_ERR_TIMEOUT */
+  int plain_flux_corners; /* 0: the modified flux A_m of Sec. 3.2 (corner rows = mean fluxes along
+                             the two edges); 1: the plain flux rows A of Eq. (ddelm), the corner
+                             row being the sum, over the two edges of the subdomain that meet the
+                             corner, of the flux at the corner with that edge's normal */
 } ddelm_options;
 
 typedef struct ddelm_problem {
@@ -184,10 +195,26 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
  * [sum n_int][n_rhs] = dL/df and d_grad_g [n_bnd][n_rhs] = dL/dg (device,
  * nullable).  Reuses the setup's factors: the transposed local products with
  * V, R3^{-1}, Q_Gamma, A_m and K^+ E_Gamma, the transposed coarse steps, and
- * one CG on the symmetric S_theta.  info as in ddelm_solve (iterations of
- * that CG; rel_residual is not computed and reads 0). */
+ * one CG on the symmetric S_theta.
+ *
+ * h_grad_scale (host, nullable) receives dL/ds for the hidden-layer scale s
+ * (w = s w_hat, b = s b_hat, Sec. 2.2): the derivative of the loss through c and
+ * u at the data and solution of the handle's most recent ddelm_solve (a
+ * ddelm_interface_residual or ddelm_refactor call after it makes the call
+ * return DDELM_ERR_INVALID_ARG, as does scale = 0).  It is computed in reverse
+ * mode at that solution with the same adjoint solve and the setup's factors (no
+ * further setup or solve): every application of a local operator (Lambda^i,
+ * Psi^i, Phi^i, K^+ E_Gamma, the coarse matrices) and of K^+ to the data
+ * contributes its output cotangent times its input; these become, through the
+ * derivative of the ridge pseudo-inverse, low-rank cotangents of K_c^i, K-bar^i,
+ * A_m^i, A-bar^i and the evaluation matrix, contracted with their analytic
+ * s-derivatives (the ridge eps^2 = eps_rel^2 |K|_F^2 / M included).  It uses
+ * the setup scratch of the workspace.
+ *
+ * info as in ddelm_solve (iterations of the adjoint CG; rel_residual is not
+ * computed and reads 0). */
 int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
-                   double *d_grad_g, ddelm_solve_info *info, void *stream);
+                   double *d_grad_g, double *h_grad_scale, ddelm_solve_info *info, void *stream);
 
 /* The interface residual of Eq. (nn-mixed) at a given mu: with the handle's
  * factors and the data (f, g) (device, as in ddelm_solve), writes
@@ -238,19 +265,27 @@ int ddelm_profile(ddelm_handle *h, int enable, int reset, double *ms, long long 
 
 /* Ridge least-squares solve of ONE local ELM system, C = K^+ F (K^+ as in the
  * readings above, eps^2 = eps_rel^2 |K|_F^2 / M), by the library's shifted
- * CholeskyQR3 in FP64, for callers that cannot allocate device memory: the
- * scratch lives in a file-scope static device array of
- * DDELM_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
- * library keeps until the process exits.  Inputs d_K [m x M] and d_F [m x R]
- * (row-major) and the output d_C [M x R] are device buffers owned by the
- * caller.  Limits: 1 <= M <= 256, 1 <= R <= 16 and
- * 2 m M + m R + 8 M^2 + 3 M R + 16384 (rounded up) <= DDELM_STATIC_SCRATCH_DOUBLES;
- * larger sizes return DDELM_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or
- * allocating library routine is called.  The first call on a device resolves
- * the array's device address with that device current, so make it before any
- * stream capture.  All calls share the array (it keeps the last call's
- * contents): calls that overlap on the GPU race.  Returns after the stream
- * work has completed.  The paper has no counterpart to this entry point. */
+ * CholeskyQR3 in FP64, for callers that cannot allocate device memory: code
+ * that runs where cudaMalloc is not allowed (inside a host that owns every
+ * device allocation, or after the allocator has been locked down) or that is
+ * handed only fixed device buffers.  The scratch lives in a file-scope static
+ * device array of DDELM_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU
+ * loading the library keeps until the process exits.  Inputs d_K [m x M] and
+ * d_F [m x R] (row-major) and the output d_C [M x R] are device buffers owned
+ * by the caller.  Limits: 1 <= M <= 256, 1 <= R <= 16, and the call's tables
+ * plus its data must fit the array: the data take 2 m M + m R + 8 M^2 + 3 M R
+ * + 64 doubles (each of 15 regions rounded up to a multiple of 32), the tables
+ * 16 bytes per GEMM output tile (at most 2 ceil(m/64) ceil(M/64) + 5 ceil(M/64)^2
+ * + 3 ceil(M/32) tiles) plus about 2.5 KB; sizes beyond that return
+ * DDELM_ERR_INVALID_ARG with the reason in ddelm_last_error().  A local matrix
+ * whose Cholesky passes meet a pivot that is not positive (K rank deficient
+ * with eps_rel = 0) returns DDELM_ERR_RANK_DEFICIENT.  No cudaMalloc, cudaFree
+ * or allocating library routine is called.  The first call on a device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture begins.  All calls share the array (it keeps the
+ * last call's contents): calls that overlap on the GPU race.  The call blocks
+ * until its stream work has completed.  The paper has no counterpart to this
+ * entry point. */
 #define DDELM_STATIC_SCRATCH_DOUBLES 1048576
 int ddelm_local_lstsq_static(const double *d_K, int m, int M, const double *d_F, int R, double eps_rel,
                              double *d_C, void *stream);
@@ -261,9 +296,9 @@ const char *ddelm_status_string(int status);
 
 /* The reason behind the last failure on the calling host thread: for
  * DDELM_ERR_CUDA the CUDA error name, message, the failing call and its source
- * location; for a problem that ddelm_query or ddelm_setup rejected
- * (DDELM_ERR_INVALID_ARG) "problem rejected: " and the check that failed
- * ("" if none).  The string stays valid until the next failing call. */
+ * location; for a problem that ddelm_query, ddelm_setup or
+ * ddelm_local_lstsq_static rejected (DDELM_ERR_INVALID_ARG) "problem rejected: "
+ * and the check that failed ("" if none).  The string stays valid until the next failing call. */
 const char *ddelm_last_error(void);
 
 #ifdef __cplusplus

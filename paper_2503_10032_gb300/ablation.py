@@ -1,0 +1,85 @@
+"""The paper's ablation on the GPU (Sec. 4.2): CG iterations and the solution's
+error for the coarse-space variants of Table 1 ({K, K_c} x {A, A_m}, without
+the Neumann-Neumann term (theta = 0, Eq. (coarse_sol_1)) and with it
+(theta = 1, Eq. (nn))) and for the mixing weight theta of Table 2 (K_c, A_m),
+on the paper's problem u = sin(pi x) sin(pi y) at the paper's scale
+(inputs.paper_scale; the 2x2 and 4x4 grids are capped at 1024 neurons per
+subdomain).  CG runs to the paper's relative residual 1e-9.
+
+    python -m paper_2503_10032_gb300.ablation [--grids 2,4,8,16] [--precision fp64|mixed]
+
+Prints one JSON line per solve and the two tables in markdown.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+
+VARIANTS = [("K, A", False, False), ("K_c, A", True, False), ("K, A_m", False, True), ("K_c, A_m", True, True)]
+THETAS = [0.0, 0.5, 0.9, 0.99, 0.999, 0.9999, 1.0]
+
+
+def run_one(D, prob, torch, **kw):
+    s = D.Solver(prob, **kw)
+    f = torch.tensor(prob.f_int, dtype=torch.float64, device="cuda")
+    g = torch.tensor(prob.g_bnd, dtype=torch.float64, device="cuda")
+    c, mu, u, info, rc = s.solve(f, g)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()[:, 0]
+    ex = prob.u_eval_exact[:, 0]
+    err = float(np.linalg.norm(u - ex) / np.linalg.norm(ex))
+    s.close()
+    return dict(iterations=int(info.iterations), rel_residual=float(info.rel_residual), status=int(rc),
+                rel_l2_error=err)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grids", default="2,4,8,16")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--eps-rel", type=float, default=1e-8)
+    ap.add_argument("--max-iters", type=int, default=60000)
+    args = ap.parse_args(argv)
+    import torch
+    from . import build
+    build.build()
+    from . import ddelm as D
+    from . import inputs
+    prec = D.DDELM_PREC_FP64 if args.precision == "fp64" else D.DDELM_PREC_MIXED
+    grids = [int(x) for x in args.grids.split(",")]
+    t1, t2 = {}, {}
+    for n in grids:
+        prob = inputs.paper_scale(n)
+        common = dict(eps_rel=args.eps_rel, tol=1e-9, max_iters=args.max_iters, precision=prec)
+        for name, cov, am in VARIANTS:
+            for theta in (0.0, 1.0):
+                r = run_one(D, prob, torch, theta=theta, use_change_of_vars=cov, use_Am=am, **common)
+                t1[(name, theta, n)] = r
+                print(json.dumps(dict(table=1, grid=f"{n}x{n}", M=int(prob.M[0]), variant=name, theta=theta, **r)),
+                      flush=True)
+        for theta in THETAS:
+            r = run_one(D, prob, torch, theta=theta, **common)
+            t2[(theta, n)] = r
+            print(json.dumps(dict(table=2, grid=f"{n}x{n}", M=int(prob.M[0]), theta=theta, **r)), flush=True)
+    head = "| " + " | ".join(f"{n}x{n} err / iter" for n in grids) + " |"
+    print("\nTable 1 (theta 0: coarse space only; theta 1: with the Neumann-Neumann term)\n")
+    print("| variant | theta " + head)
+    print("|---|---|" + "---|" * len(grids))
+    for name, _, _ in VARIANTS:
+        for theta in (0.0, 1.0):
+            cells = [f"{t1[(name, theta, n)]['rel_l2_error']:.2e} / {t1[(name, theta, n)]['iterations']}" for n in grids]
+            print(f"| {name} | {theta:g} | " + " | ".join(cells) + " |")
+    print("\nTable 2 (K_c, A_m)\n")
+    print("| theta " + head)
+    print("|---|" + "---|" * len(grids))
+    for theta in THETAS:
+        cells = [f"{t2[(theta, n)]['rel_l2_error']:.2e} / {t2[(theta, n)]['iterations']}" for n in grids]
+        print(f"| {theta:g} | " + " | ".join(cells) + " |")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

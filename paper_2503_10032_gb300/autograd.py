@@ -7,8 +7,8 @@ values f_int and the Dirichlet values g_bnd (the map is linear in both).
 
 u = DDELMSolveScaled.apply(solver, f_int, g_bnd, scale) also takes the
 hidden-layer scale s as a 0-d tensor (equal to the solver's problem scale);
-its gradient is <dL/du, du/ds> with du/ds from the forward-mode tangent of
-`tangent.scale_tangent`.
+its gradient dL/ds comes from the same ddelm_backward call (the library's
+reverse-mode scale gradient at the forward solve), with no further setup.
 """
 from __future__ import annotations
 
@@ -40,19 +40,15 @@ class DDELMSolveScaled(torch.autograd.Function):
             raise ValueError("scale must equal the solver's problem scale")
         c, mu, u, info, rc = solver.solve(f_int.detach(), g_bnd.detach())
         ctx.solver = solver
-        ctx.save_for_backward(f_int.detach(), g_bnd.detach())
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
-        from .tangent import scale_tangent
-        f, g = ctx.saved_tensors
-        gf, gg, _ = ctx.solver.backward(grad_u=grad_u.contiguous())
-        gs = None
         if ctx.needs_input_grad[3]:
-            _, du_ds = scale_tangent(ctx.solver, f, g)
-            gs = (grad_u * du_ds).sum()
-        return None, gf, gg, gs
+            gf, gg, _, gs = ctx.solver.backward(grad_u=grad_u.contiguous(), scale=True)
+            return None, gf, gg, torch.tensor(gs, dtype=grad_u.dtype, device=grad_u.device)
+        gf, gg, _ = ctx.solver.backward(grad_u=grad_u.contiguous())
+        return None, gf, gg, None
 
 
 def solve_u_scaled(solver, f_int, g_bnd, scale):

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libddelm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "ozaki_plan.cpp", "features.cu", "gemm_f64.cu", "chol.cu", "cg.cu", "ozaki_tc.cu", "static_lstsq.cu", "api.cu"]
+SOURCES = ["plan.cpp", "ozaki_plan.cpp", "scale_plan.cpp", "features.cu", "gemm_f64.cu", "chol.cu", "cg.cu", "ozaki_tc.cu",
+           "scale_adjoint.cu", "static_lstsq.cu", "api.cu"]
 
 
 def _nvcc():

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -38,6 +39,7 @@ struct ddelm_handle {
   // CUDA graphs of the setup and of the solve sequence (captured on second use)
   cudaGraphExec_t setup_exec = nullptr, solve_exec = nullptr;
   long long solves = 0;
+  bool fwd_valid = false;  // the solve staging holds the data and solution of the last ddelm_solve
   bool graph_off = false;  // capture unavailable (or disabled by the options)
   // profiling: event pairs around launches, reduced on ddelm_profile
   bool prof = false;
@@ -143,6 +145,13 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   Staging &st = staging();
   std::lock_guard<std::mutex> lock(st.m);
   std::vector<char> pageable;
+  // Whatever the return path, the stream is drained before the lock is released
+  // (the guard is destroyed first): a copy that fails after others were queued
+  // must not let the next setup refill the buffer while they still read it.
+  struct DrainOnExit {
+    cudaStream_t s;
+    ~DrainOnExit() { (void)cudaStreamSynchronize(s); }
+  } drain{s};
   char *buf = nullptr;
   if (st.cap < total) {
     if (st.pinned) cudaFreeHost(st.pinned);
@@ -173,6 +182,10 @@ int upload(ddelm_handle *h, const ddelm_problem *prob, cudaStream_t s) {
   put(buf, p.off_sdesc, p.sdesc);
   put(buf, p.off_odesc, p.odesc);
   put(buf, p.off_otile, p.otile);
+  put(buf, p.off_ssubs, p.ssubs);
+  put(buf, p.off_srows, p.srows);
+  put(buf, p.off_scsub, p.scsub);
+  put(buf, p.off_dots, p.dots);
   if (p.mixed) {
     std::vector<unsigned char> maps;
     const int rc = encode_tensor_maps(p, h->ws, maps);
@@ -387,6 +400,7 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
 int ddelm_refactor(ddelm_handle *h, void *stream, int *info_sub) {
   if (!h) return DDELM_ERR_INVALID_ARG;
   if (info_sub) *info_sub = -1;
+  h->fwd_valid = false;
   return compute_setup(h, static_cast<cudaStream_t>(stream), info_sub, true);
 }
 
@@ -432,8 +446,10 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   };
   {
     // a handle's first solve runs directly; later ones replay one captured graph
+    h->fwd_valid = false;
     const int rc0 = h->solves++ == 0 ? enqueue() : run_graph(h, s, &h->solve_exec, enqueue);
     if (rc0 != DDELM_OK) return rc0;
+    h->fwd_valid = true;
   }
   // results out
   if (d_c) CK(cudaMemcpyAsync(d_c, db + p.o_cout, (size_t)p.sz.sum_M * R * 8, cudaMemcpyDeviceToDevice, s));
@@ -453,8 +469,14 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
   if (herr) rc = DDELM_ERR_TIMEOUT;
   const int iters = int(hinfo[0]);
   double resmax = 0.0;
-  for (int k = 0; k < p.n_rhs; ++k) resmax = hinfo[1 + k] > resmax ? hinfo[1 + k] : resmax;
+  bool finite = true;
+  for (int k = 0; k < p.n_rhs; ++k) {
+    resmax = hinfo[1 + k] > resmax ? hinfo[1 + k] : resmax;
+    finite = finite && std::isfinite(hinfo[1 + k]) && std::isfinite(hinfo[17 + k]);
+  }
   if (rc == DDELM_OK && iters >= p.opt.max_iters && !(resmax < p.opt.tol)) rc = DDELM_ERR_NOT_CONVERGED;
+  if (rc == DDELM_OK && !finite) rc = DDELM_ERR_NOT_CONVERGED;  // NaN or Inf in the data or the iteration
+  if (!finite) resmax = std::numeric_limits<double>::quiet_NaN();
   if (info) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -478,6 +500,7 @@ int ddelm_interface_residual(ddelm_handle *h, const double *d_f_int, const doubl
   const int R = p.n_rhs;
   double *mu = nullptr, *rhs = nullptr, *res = nullptr;
   cg_vectors(p, h->ws, &mu, &rhs, &res);
+  h->fwd_valid = false;  // the staging now holds this call's data
   if (p.sz.sum_int > 0) CK(cudaMemcpyAsync(db + p.o_fin, d_f_int, (size_t)p.sz.sum_int * R * 8, cudaMemcpyDeviceToDevice, s));
   if (p.sz.n_bnd > 0) CK(cudaMemcpyAsync(db + p.o_gin, d_g_bnd, (size_t)p.sz.n_bnd * R * 8, cudaMemcpyDeviceToDevice, s));
   if (p.n_dl > 0) CK(cudaMemcpyAsync(mu, d_mu_delta, (size_t)p.n_dl * R * 8, cudaMemcpyDeviceToDevice, s));
@@ -552,9 +575,10 @@ int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta
 }
 
 int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad_u, double *d_grad_f,
-                   double *d_grad_g, ddelm_solve_info *info, void *stream) {
+                   double *d_grad_g, double *h_grad_scale, ddelm_solve_info *info, void *stream) {
   if (!h) return DDELM_ERR_INVALID_ARG;
   Plan &p = h->plan;
+  if (h_grad_scale && (!h->fwd_valid || p.inv_scale == 0.0)) return DDELM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double *db = dbase(h);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -578,6 +602,40 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
   LAUNCH(PC_CG, launch_cg(p, h->ws, a, s));
   for (int q = 1; q <= 5; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_adj + q], h->ws, s));
   LAUNCH(PC_OTHER, launch_adjoint_scatter(p, h->ws, d_grad_f, d_grad_g, s));
+  if (h_grad_scale) {
+    // dL/ds at the last solve: b-bar = S_theta^{-1} mu-bar (the adjoint solution
+    // above) into the bank, the solve's mu back into the CG vector, the forward
+    // y, p, a of its data recomputed; then the interface vectors (mode 4), the
+    // coarse chain, and per wave the local matrices, their s-derivatives and the
+    // contraction
+    const long long nd = p.n_dl > 0 ? p.n_dl : 1;
+    double *mu = nullptr, *rhs = nullptr, *res = nullptr;
+    cg_vectors(p, h->ws, &mu, &rhs, &res);
+    if (p.n_dl > 0) {
+      CK(cudaMemcpyAsync(db + p.o_bank_dl + (long long)SD_BB * nd * p.n_rhs, mu, (size_t)p.n_dl * p.n_rhs * 8,
+                         cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(mu, db + p.o_muout + (long long)p.n_pi * p.n_rhs, (size_t)p.n_dl * p.n_rhs * 8,
+                         cudaMemcpyDeviceToDevice, s));
+    }
+    LAUNCH(PC_OTHER, launch_gather_rhs(p, h->ws, db + p.o_fin, db + p.o_gin, s));
+    for (int q = 0; q < 4; ++q) LAUNCH(PC_GEMM, launch_gemm_phase(p, G[p.ph_solve + q], h->ws, s));
+    CgArgs a4;
+    a4.mu_out = nullptr;
+    a4.c_out = nullptr;
+    a4.max_iters = p.opt.max_iters;
+    a4.tol = p.opt.tol;
+    a4.theta = p.opt.theta;
+    a4.mode = 4;
+    LAUNCH(PC_CG, launch_cg(p, h->ws, a4, s));
+    for (const auto &ph : p.sc_coarse) LAUNCH(PC_GEMM, launch_gemm_phase(p, ph, h->ws, s));
+    for (int w = 0; w < p.n_waves; ++w) {
+      LAUNCH(PC_FEAT, launch_scale_features(p, h->ws, w, s));
+      LAUNCH(PC_OTHER, launch_scale_gather(p, h->ws, w, p.opt.theta, s));
+      for (const auto &ph : p.sc_wave[w]) LAUNCH(PC_GEMM, launch_gemm_phase(p, ph, h->ws, s));
+      LAUNCH(PC_OTHER, launch_scale_dots(p, h->ws, w, s));
+    }
+    LAUNCH(PC_OTHER, launch_scale_total(p, h->ws, p.opt.eps_rel, s));
+  }
   if (info) CK(cudaEventRecord(e1, s));
   CK(cudaStreamSynchronize(s));
   const long long nd = p.n_dl > 0 ? p.n_dl : 1, np = p.n_pi > 0 ? p.n_pi : 1;
@@ -588,6 +646,9 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
   CK(cudaMemcpy(&herr, db + p.o_status + 2 * p.n_sub + 16, sizeof(int), cudaMemcpyDeviceToHost));
   int rc = herr ? DDELM_ERR_TIMEOUT : DDELM_OK;
   if (rc == DDELM_OK && int(it) >= p.opt.max_iters) rc = DDELM_ERR_NOT_CONVERGED;
+  if (h_grad_scale)
+    CK(cudaMemcpy(h_grad_scale, db + p.o_gs + (long long)p.dots.size() + p.n_sub, sizeof(double),
+                  cudaMemcpyDeviceToHost));
   if (info) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));

@@ -48,6 +48,8 @@ struct Ctx {
   double *red;  // [gridDim][2*16]
   unsigned *bar;  // [count, generation]
   int *err;
+  unsigned long long bar_limit_ns;  // a barrier wait gives up after this long
+  unsigned bar_extra;               // tests only: 1 = one arrival more than the grid (never released)
   double theta, tol;
   int max_iters;
   double *mu_out, *c_out;
@@ -60,6 +62,9 @@ struct Ctx {
   float *fpv[N_FPV];
   float *fslab[N_FSLAB];
   int max_refine;
+  // scale gradient (mode 4): the bank of interface vectors and the coarse cotangents
+  double *bkd, *bkp;
+  double *csb, *cc1b, *cc2b, *cc3b;
 };
 
 __device__ __forceinline__ double ldg_cg(const double *p) { return __ldcg(p); }
@@ -70,8 +75,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Counting grid barrier with a generation word; gives up after 2 s of waiting
-// (error word set).  The arrival is an acq_rel atomic and the wait an acquire
+// Counting grid barrier with a generation word; gives up after bar_limit_ns
+// of waiting (2 s unless the options set it; error word set).  The arrival is an acq_rel atomic and the wait an acquire
 // load: together with the CTA barriers around them they order every thread's
 // prior writes before every thread's later reads, without a full fence.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -88,7 +93,7 @@ __device__ bool grid_sync(const Ctx &c) {
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(my) : "l"(gen) : "memory");
     unsigned arrived;
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(count) : "memory");
-    if (arrived + 1 == gridDim.x) {
+    if (arrived + 1 == gridDim.x + c.bar_extra) {
       asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
       asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(my + 1u) : "memory");
     } else {
@@ -97,7 +102,7 @@ __device__ bool grid_sync(const Ctx &c) {
       while (ld_acquire_u32(gen) == my) {
         if ((++spins & 1023u) == 0u) {
           if (*(volatile int *)c.err) break;
-          if (global_ns() - t0 > 2000000000ull) {
+          if (global_ns() - t0 > c.bar_limit_ns) {
             atomicExch(c.err, 1);
             break;
           }
@@ -1355,10 +1360,207 @@ __device__ void adjoint_program(const Ctx &c) {
   (void)B;
 }
 
+// Pi rows of (K^+ E_Gamma)^T c-hat into slab H1 (c-hat in the coefficient buffers)
+template <int RC>
+__device__ void ph_pi_kpe(const Ctx &c) {
+  const int lane = threadIdx.x & 31;
+  for (int t = gwarp(); t < c.n_tpi; t += nwarps()) {
+    const int s = c.ints[c.o_tpi + 2 * t], a = c.ints[c.o_tpi + 2 * t + 1];
+    const SubDev d = c.subs[s];
+    double acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = 0.0;
+    for (int j = lane; j < d.M; j += 32) {
+      const double m = c.db[d.oKpE + (long long)j * d.nG + a];
+      const double *src = c.db + d.oC + (long long)j * c.R;
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) acc[k] = fma(m, src[k], acc[k]);
+    }
+    warp_sum<RC>(acc);
+    if (lane == 0) {
+      double *o = slab_row(c, S_H1, d, a);
+#pragma unroll
+      for (int k = 0; k < RC; ++k)
+        if (k < c.R) o[k] = acc[k];
+    }
+  }
+}
+
+// Interface vectors of the scale gradient (run after the adjoint solve; mu in
+// V_MU, b-bar = S_theta^{-1} mu-bar in the bank, c-hat and the forward y, p,
+// a = A_m y in the subdomain buffers).  The derivative of
+//   c-hat^T c(mu, s) + b-bar^T (b_theta(s) - S_theta(s) mu)
+// at fixed mu (= dL/ds, since S_theta b-bar = mu-bar) is a sum over every
+// application of a local operator in the right-hand side, in S_theta mu and in
+// the reconstruction of (cotangent of its output) x (its input)^T.  The reverse
+// passes of the right-hand side and of S_theta mu share their second half up
+// to sign (cotangents b-bar and -b-bar), so one pass with b-bar serves both;
+// the pairs then merge into four Lambda, two Psi and two Phi pairs per
+// right-hand side, stored here as interface vectors (see scale_plan.cpp), and
+// the cotangents of the four coarse matrices S_Pi^{-1}, C1, C2, C3 are formed
+// in full.
+template <int RC>
+__device__ void scale_program(const Ctx &c) {
+  const int R = c.R, nPR = c.n_pi * R, nDR = c.n_dl * R;
+  const long long nd = c.n_dl > 0 ? c.n_dl : 1, np = c.n_pi > 0 ? c.n_pi : 1;
+  auto BD = [&](int k) { return c.bkd + (long long)k * nd * R; };
+  auto BP = [&](int k) { return c.bkp + (long long)k * np * R; };
+  double *MU = c.dl[V_MU], *B = c.dl[V_B], *Q = c.dl[V_Q];
+  const bool coarse = c.n_pi > 0;
+  // ---- the right-hand side program (forward)
+  for (int e = gthread(); e < nPR; e += nthreads()) {
+    const int p = e / R, k = e % R;
+    double ad = 0.0, pp = 0.0;
+    for (int o = 0; o < 4; ++o) {
+      const int s = c.ints[c.o_pi_own + 8 * p + 2 * o];
+      if (s < 0) continue;
+      const int a = c.ints[c.o_pi_own + 8 * p + 2 * o + 1];
+      const SubDev &d = c.subs[s];
+      ad += c.db[d.oAy + (long long)a * R + k];
+      pp += c.db[d.oP + (long long)a * R + k];
+    }
+    c.pv[P_DPI][e] = -ad;
+    c.pv[P_PPI][e] = pp;
+  }
+  if (!grid_sync(c)) return;
+  if (coarse)
+    ph_coarse(c, c.o_Sinv, c.pv[P_PPI], c.o_C1, c.pv[P_DPI], 1.0, c.pv[P_MPF], c.o_C2, c.pv[P_DPI], c.o_C3,
+              c.pv[P_PPI], -1.0, c.pv[P_GF]);
+  if (!grid_sync(c)) return;
+  ph_dl_first<RC>(c, c.pv[P_MPF], nullptr, c.pv[P_GF], 1);
+  if (!grid_sync(c)) return;
+  if (!second_half<RC>(c, B)) return;
+  for (int e = gthread(); e < nDR; e += nthreads()) {
+    BD(SD_VR)[e] = c.dl[V_V][e];
+    BD(SD_PVR)[e] = c.dl[V_PV][e];
+    BD(SD_WR)[e] = c.dl[V_W][e];
+    BD(SD_MU)[e] = MU[e];
+    BD(SD_NEGBB)[e] = -BD(SD_BB)[e];
+  }
+  for (int e = gthread(); e < nPR; e += nthreads()) {
+    BP(SP_DPI)[e] = c.pv[P_DPI][e];
+    BP(SP_PPI)[e] = c.pv[P_PPI][e];
+    BP(SP_MPF)[e] = c.pv[P_MPF][e];
+    BP(SP_GF)[e] = c.pv[P_GF][e];
+    BP(SP_RNUR)[e] = c.pv[P_RNU][e];
+    BP(SP_NUR)[e] = c.pv[P_NU][e];
+    BP(SP_DNUR)[e] = c.pv[P_DNU][e];
+    BP(SP_ZERO)[e] = 0.0;
+  }
+  if (!grid_sync(c)) return;
+  // ---- S_theta mu (forward), and its combinations with the right-hand side's vectors
+  if (!apply_S<RC>(c, MU, Q)) return;
+  for (int e = gthread(); e < nDR; e += nthreads()) {
+    BD(SD_WRS)[e] = BD(SD_WR)[e] - c.dl[V_W][e];
+    BD(SD_PVSR)[e] = c.dl[V_PV][e] - BD(SD_PVR)[e];
+    BD(SD_VSR)[e] = c.dl[V_V][e] - BD(SD_VR)[e];
+  }
+  for (int e = gthread(); e < nPR; e += nthreads()) {
+    const double mpf = BP(SP_MPF)[e];
+    BP(SP_PIA)[e] = c.pv[P_DNU][e] - c.pv[P_G][e] - BP(SP_DNUR)[e] + BP(SP_GF)[e];
+    BP(SP_PIC)[e] = c.pv[P_MPI][e] - mpf;
+    BP(SP_PID)[e] = BP(SP_NUR)[e] - c.pv[P_NU][e] + mpf - c.pv[P_MPI][e];
+    BP(SP_RNURS)[e] = BP(SP_RNUR)[e] - c.pv[P_RNU][e];
+    BP(SP_RAS)[e] = c.pv[P_RA][e];
+    BP(SP_PSIS)[e] = c.pv[P_PSI][e];
+    BP(SP_DPIPSI)[e] = BP(SP_DPI)[e] - c.pv[P_PSI][e];
+    BP(SP_RAPPI)[e] = c.pv[P_RA][e] - BP(SP_PPI)[e];
+  }
+  if (!grid_sync(c)) return;
+  // ---- reconstruction (forward): psi2, s2, mu_Pi = mpf + S_Pi^{-1} s2 - C1 psi2
+  ph_pi_rows<RC>(c, MU);
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_H1, 1.0, BP(SP_PSI2), S_H2, 1.0, BP(SP_S2));
+  if (!grid_sync(c)) return;
+  if (coarse)
+    ph_coarse(c, c.o_Sinv, BP(SP_S2), c.o_C1, BP(SP_PSI2), -1.0, BP(SP_MPIF), -1, nullptr, -1, nullptr, 0.0,
+              nullptr);
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < nPR; e += nthreads()) BP(SP_MPIF)[e] += BP(SP_MPF)[e];
+  // ---- reverse of the reconstruction: mpif-bar = (K^+ E)^T c-hat on Pi, s2-bar, psi2-bar
+  ph_pi_kpe<RC>(c);
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_H1, 1.0, BP(SP_MPIFB), -1, 0.0, nullptr);
+  if (!grid_sync(c)) return;
+  if (coarse)
+    ph_coarse(c, c.o_Sinv, BP(SP_MPIFB), -1, nullptr, 0.0, BP(SP_S2B), c.o_C3, BP(SP_MPIFB), -1, nullptr, 0.0,
+              BP(SP_PSI2B));
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < nPR; e += nthreads()) BP(SP_PSI2B)[e] = -BP(SP_PSI2B)[e];
+  // ---- the second half reversed with b-bar: nu-bar, dnu-bar, rnu-bar, w-bar, pv-bar, v-bar
+  ph_pi_rows<RC>(c, BD(SD_BB));
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_H1, 1.0, BP(SP_GFB), S_H2, 1.0, BP(SP_NUB));
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < nPR; e += nthreads()) BP(SP_DNUB)[e] = -BP(SP_GFB)[e];
+  if (!grid_sync(c)) return;
+  if (coarse)
+    ph_coarse(c, c.o_Sinv, BP(SP_NUB), c.o_C1, BP(SP_DNUB), 1.0, BP(SP_RNUB), -1, nullptr, -1, nullptr, 0.0,
+              nullptr);
+  if (!grid_sync(c)) return;
+  ph_dl_first<RC>(c, BP(SP_RNUB), BD(SD_NEGBB), BP(SP_ZERO), 0);  // VL = -(Lambda L(rnu-bar, b-bar))_Delta
+  if (!grid_sync(c)) return;
+  ph_dl_gather(c, S_VL, -1.0, BD(SD_WB), nullptr, 0.0, -1, nullptr);
+  if (!grid_sync(c)) return;
+  ph_dl_phi<RC>(c, false, BD(SD_WB), S_TL);  // -Phi w-bar^
+  if (!grid_sync(c)) return;
+  ph_dl_gather(c, S_TL, c.theta, BD(SD_PVB), nullptr, 0.0, -1, nullptr);
+  if (!grid_sync(c)) return;
+  ph_dl_phi<RC>(c, true, BD(SD_PVB), S_T2L);  // -Phi^T pv-bar^
+  if (!grid_sync(c)) return;
+  ph_dl_gather(c, S_T2L, 1.0, BD(SD_VB), BD(SD_WB), 1.0 - c.theta, -1, nullptr);
+  if (!grid_sync(c)) return;
+  // ---- the first halves reversed: mpf-bar (right-hand side), mpi-bar (S_theta mu)
+  ph_g_lamT<RC>(c, BD(SD_VB));
+  if (!grid_sync(c)) return;
+  ph_pi_gather(c, S_ZL, 1.0, BP(SP_ZLV), -1, 0.0, nullptr);
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < nPR; e += nthreads()) {
+    const double zl = BP(SP_ZLV)[e], nu = BP(SP_NUB)[e];
+    BP(SP_MPFB)[e] = BP(SP_MPIFB)[e] - zl + nu;
+    BP(SP_MPIBS)[e] = zl - nu;
+  }
+  if (!grid_sync(c)) return;
+  if (coarse) {
+    ph_coarse(c, c.o_Sinv, BP(SP_MPIBS), c.o_C1, BP(SP_DNUB), -1.0, BP(SP_RABS), c.o_C3, BP(SP_MPIBS), c.o_C2,
+              BP(SP_DNUB), 1.0, BP(SP_PSIBS));
+    if (!grid_sync(c)) return;
+    ph_coarse(c, c.o_Sinv, BP(SP_MPFB), c.o_C1, BP(SP_GFB), -1.0, BP(SP_PPIB), c.o_C3, BP(SP_MPFB), c.o_C2,
+              BP(SP_GFB), 1.0, BP(SP_DPIB));
+  }
+  if (!grid_sync(c)) return;
+  for (int e = gthread(); e < nPR; e += nthreads()) {
+    BP(SP_PIB)[e] = BP(SP_PSIBS)[e] + BP(SP_PSI2B)[e];
+    BP(SP_PIE)[e] = BP(SP_S2B)[e] - BP(SP_RABS)[e];
+  }
+  // ---- cotangents of the coarse matrices (sums of outer products over the columns)
+  const int n = c.n_pi;
+  for (long long e = gthread(); e < (long long)n * n; e += nthreads()) {
+    const int p = int(e / n), q = int(e % n);
+    double sb = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    for (int k = 0; k < R; ++k) {
+      const long long ip = (long long)p * R + k, iq = (long long)q * R + k;
+      sb += BP(SP_NUB)[ip] * BP(SP_RNURS)[iq] + BP(SP_MPIBS)[ip] * BP(SP_RAS)[iq] +
+            BP(SP_MPFB)[ip] * BP(SP_PPI)[iq] + BP(SP_MPIFB)[ip] * BP(SP_S2)[iq];
+      c1 += BP(SP_MPIBS)[ip] * BP(SP_PSIS)[iq] + BP(SP_MPFB)[ip] * BP(SP_DPI)[iq] -
+            BP(SP_MPIFB)[ip] * BP(SP_PSI2)[iq];
+      c2 += BP(SP_GFB)[ip] * BP(SP_DPIPSI)[iq];
+      c3 += BP(SP_GFB)[ip] * (BP(SP_RAPPI)[iq] - BP(SP_RNURS)[iq]);
+    }
+    c.csb[e] = sb;
+    c.cc1b[e] = c1;
+    c.cc2b[e] = c2;
+    c.cc3b[e] = c3;
+  }
+}
+
 template <int RC>
 __global__ void __launch_bounds__(CG_THREADS, 1) cg_kernel(Ctx c) {
   if (c.mode == 1)
     adjoint_program<RC>(c);
+  else if (c.mode == 4)
+    scale_program<RC>(c);
   else
     forward_program<RC>(c);  // 0 solve, 2 residual at a given mu, 3 solve for a given right-hand side
 }
@@ -1419,6 +1621,15 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   c.c_out = a.c_out;
   c.mode = a.mode;
   c.max_refine = a.max_refine;
+  c.bar_limit_ns = p.opt.barrier_timeout_ms > 0 ? 1000000ull * (unsigned long long)p.opt.barrier_timeout_ms
+                                                : 2000000000ull;
+  c.bar_extra = p.opt.inject_barrier_stall ? 1u : 0u;
+  c.bkd = c.db + p.o_bank_dl;
+  c.bkp = c.db + p.o_bank_pi;
+  c.csb = c.db + p.o_cSb;
+  c.cc1b = c.db + p.o_cC1b;
+  c.cc2b = c.db + p.o_cC2b;
+  c.cc3b = c.db + p.o_cC3b;
   c.fb = nullptr;
   if (p.mixed && p.o_f32 >= 0 && (a.mode == 0 || a.mode == 3)) {
     c.fb = reinterpret_cast<float *>(c.db + p.o_f32);

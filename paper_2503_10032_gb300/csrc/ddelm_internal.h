@@ -22,6 +22,8 @@ extern std::atomic<long long> g_kernel_launches;
 #define DDELM_COUNT_LAUNCH() ::ddelm::g_kernel_launches.fetch_add(1, std::memory_order_relaxed)
 // keeps the message ddelm_last_error() returns (per host thread)
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// keeps "problem rejected: <why>" for ddelm_last_error() (per host thread)
+void record_plan_error(const std::string &why);
 
 // ---------------------------------------------------------------- rows
 // Rows of the local matrices other than the interior collocation rows.  They
@@ -82,6 +84,7 @@ struct SubDev {
   long long oU;     // network values at the evaluation points nE x R
   int gpi_off, gdl_off, bnd_off;  // ibase offsets of R_Pi, R_Delta, boundary index maps
   int loc_off;      // first row of this subdomain in the local vector buffers (nG rows)
+  long long dshift; // scale-gradient tables only: derivative block = value block + dshift
 };
 
 struct GemmDesc {
@@ -138,6 +141,39 @@ enum StepKind : int { STEP_GEMM = 0, STEP_CHOL = 1, STEP_MATOP = 2, STEP_FEAT = 
 struct Step {
   int kind, idx;
 };
+
+// ---------------------------------------------------------------- scale gradient
+// dL/ds for the hidden-layer scale s (w = s w_hat, b = s b_hat, Sec. 2.2) by
+// reverse mode at the solution: the persistent kernel forms, from the adjoint
+// solution b-bar = S_theta^{-1} mu-bar, the cotangent vectors of every local
+// operator application (a "bank" of interface vectors); per subdomain these
+// become low-rank cotangents of K_c, K-bar, A_m, A-bar and the evaluation
+// matrix (through d(K^+) for the ridge pseudo-inverse), which are contracted
+// with the matrices' analytic s-derivatives.
+enum ScaleDl { SD_BB = 0, SD_NEGBB, SD_MU, SD_VR, SD_PVR, SD_WR, SD_WRS, SD_PVSR, SD_VSR, SD_WB, SD_PVB, SD_VB, N_SD };
+enum ScalePi {
+  SP_DPI = 0, SP_PPI, SP_MPF, SP_GF, SP_RNUR, SP_NUR, SP_DNUR,             // right-hand-side program
+  SP_PIA, SP_PIC, SP_PID, SP_RNURS, SP_RAS, SP_PSIS, SP_DPIPSI, SP_RAPPI,  // combinations with S_theta mu
+  SP_PSI2, SP_S2, SP_MPIF,                                                 // reconstruction
+  SP_MPIFB, SP_S2B, SP_PSI2B, SP_GFB, SP_NUB, SP_DNUB, SP_RNUB, SP_ZLV,    // reverse pass
+  SP_MPFB, SP_MPIBS, SP_RABS, SP_PSIBS, SP_PPIB, SP_DPIB, SP_PIB, SP_PIE, SP_ZERO, N_SP
+};
+// per subdomain: the re-assembled local matrices (value block; their
+// s-derivatives at + dshift) and the factored cotangents and products
+struct ScaleSub {
+  long long Ks, Kbs, As, Abs, Es, dshift;
+  long long Bc, LA, LG, Ac, RAG, ybar, VtA, RK, QGB, LK, T2, Rt, Vty, PF, WFm;
+  long long t1, t2, t3, t4, RKb, LKb, V3QGB, V3VtA, V3Vty, V3Rt;
+  long long OK, OG, OA, OKb, OAb, OE;
+};
+// one block dot product sum_{r<rows, c<cols} a[r lda + c] b[r ldb + c] of subdomain sub
+struct DotDesc {
+  long long a, b;
+  int rows, cols, lda, ldb;
+  int sub, role;
+  double coef;
+};
+enum { DOT_LIN = 0, DOT_E2K = 1, DOT_KDK = 2, DOT_E2KB = 3, DOT_KBDKB = 4 };
 
 // ---------------------------------------------------------------- plan
 struct GemmPhase {
@@ -235,11 +271,28 @@ struct Plan {
   size_t bytes_slices = 0;
   double oz_flops = 0.0;          // BF16 tensor flops of one setup
   double slice_bytes = 0.0;       // HBM bytes of the slicing kernels of one setup
+  // scale gradient (ddelm_backward with a scale output)
+  double inv_scale = 0.0;                 // 1 / s
+  std::vector<long long> slot_begin, slot_end;  // contiguous setup-scratch extent of each wave slot
+  std::vector<SubDev> ssubs;              // feature tables writing into the scale buffers
+  std::vector<SpecialRow> srows;
+  std::vector<int> wave_erow0;            // evaluation rows of wave w in srows: [wave_erow0[w], wave_erow0[w+1])
+  std::vector<ScaleSub> scsub;
+  std::vector<DotDesc> dots;
+  std::vector<int> wave_dot0;             // dot descriptors of wave w
+  std::vector<GemmPhase> sc_coarse;       // coarse chain of the cotangents
+  std::vector<std::vector<GemmPhase>> sc_wave;  // per wave: the products of the factored cotangents
+  int sc_JL = 0, sc_JP = 0, sc_JF = 0, sc_Jc = 0, sc_NK = 0, sc_NAG = 0;
+  long long o_bank_dl = 0, o_bank_pi = 0;  // N_SD Delta vectors, N_SP Pi vectors ([n x R] each)
+  long long o_cSb = 0, o_cC1b = 0, o_cC2b = 0, o_cC3b = 0, o_cDb = 0, o_cDX = 0, o_cT1 = 0, o_cT3 = 0, o_cSPb = 0;
+  long long o_gs = 0;                       // per dot descriptor, then per subdomain, then the total
+  size_t off_ssubs = 0, off_srows = 0, off_scsub = 0, off_dots = 0;
   std::string err;
 };
 
 int build_plan(const ddelm_problem *prob, Plan &plan);
 int build_mixed(Plan &plan, long long &dbl_cursor);
+int build_scale(Plan &plan, long long &dbl_cursor);
 int encode_tensor_maps(const Plan &plan, void *ws, std::vector<unsigned char> &maps);
 
 // ---------------------------------------------------------------- launchers
@@ -264,10 +317,17 @@ struct CgArgs {
   int max_iters;
   double tol;
   double theta;
-  int mode = 0;  // 0 solve, 1 adjoint, 2 residual at a given mu, 3 solve for a given right-hand side
+  int mode = 0;  // 0 solve, 1 adjoint, 2 residual at a given mu, 3 solve for a given right-hand side,
+                 // 4 the scale-gradient vectors (after mode 1)
   int max_refine = 8;  // MIXED: outer refinement sweeps
 };
 cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s);
+// scale gradient launchers (features of wave w and their s-derivatives into the
+// scale buffers; the per-subdomain operands; the block dot products; the total)
+cudaError_t launch_scale_features(const Plan &p, void *ws, int wave, cudaStream_t s);
+cudaError_t launch_scale_gather(const Plan &p, void *ws, int wave, double theta, cudaStream_t s);
+cudaError_t launch_scale_dots(const Plan &p, void *ws, int wave, cudaStream_t s);
+cudaError_t launch_scale_total(const Plan &p, void *ws, double eps_rel, cudaStream_t s);
 void cg_vectors(const Plan &p, void *ws, double **mu, double **rhs, double **res);
 
 }  // namespace ddelm

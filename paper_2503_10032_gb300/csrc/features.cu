@@ -166,7 +166,154 @@ __global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *
   }
 }
 
+// ---- s-derivatives of the features (the hidden-layer scale: w = s w_hat,
+// b = s b_hat, so z = w . x + b = s z_hat and dz/ds = z / s).  With t = tanh z,
+// s1 = 1 - t^2:  d phi/ds = s1 z/s;  for L phi = 2 |w|^2 t s1 (|w|^2 = s^2 |w_hat|^2)
+// d/ds = 2 L phi / s + 2 |w|^2 s1 (1 - 3 t^2) z/s;  the diffusion rows subtract
+// d/ds [(grad a . w) s1] = (grad a . w) s1 (1/s - 2 t z/s);  F phi = (w . n) s1
+// gives d/ds = (w . n) s1 (1/s - 2 t z/s).  The derivative rows go to the value
+// rows' offsets + dshift of the subdomain (the scale tables' layout).
+__global__ void __launch_bounds__(256) interior_rows_ds_kernel(const SubDev *__restrict__ subs, int sub0,
+                                                               double *__restrict__ db, long long o_w,
+                                                               long long o_fc, long long o_exp2, long long o_xint,
+                                                               long long o_aint, long long o_gaint, int op,
+                                                               double inv_s) {
+  __shared__ double s_exp2[256];
+  const SubDev d = subs[sub0 + blockIdx.y];
+  const int r0 = blockIdx.x * 8;
+  if (r0 >= d.nI) return;
+  load_exp2tab(s_exp2, db + o_exp2);
+  const double *w = db + o_w + 2 * d.w_off;
+  const double4 *fc = reinterpret_cast<const double4 *>(db + o_fc) + d.w_off;
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = r0 + rr;
+    if (r >= d.nI) break;
+    const long long pi = d.int_off + r;
+    const double x = db[o_xint + 2 * pi], y = db[o_xint + 2 * pi + 1];
+    double a = 1.0, ax = 0.0, ay = 0.0;
+    if (op == DDELM_OP_DIFFUSION) {
+      a = db[o_aint + pi];
+      ax = db[o_gaint + 2 * pi];
+      ay = db[o_gaint + 2 * pi + 1];
+    }
+    double *o0 = db + d.oK + d.dshift + (long long)r * d.M;
+    double *o1 = db + d.oKb + d.dshift + (long long)r * d.M;
+    for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+      const double4 c = fc[j];  // 2 w_x, 2 w_y, 2 b, 2 |w|^2
+      const double u = fma(c.x, x, fma(c.y, y, c.z));
+      const double t = tanh_half(u, s_exp2);
+      const double s1 = fma(-t, t, 1.0);
+      const double zs = 0.5 * u * inv_s;       // z / s
+      const double lp = (c.w * t) * s1;        // L phi (Poisson)
+      double v = fma(2.0 * inv_s, lp, c.w * s1 * fma(-3.0 * t, t, 1.0) * zs);
+      if (op == DDELM_OP_DIFFUSION) {
+        const double ga = ax * w[2 * j] + ay * w[2 * j + 1];
+        v = a * v - ga * s1 * fma(-2.0 * t, zs, inv_s);
+      }
+      o0[j] = v;
+      o1[j] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) special_rows_ds_kernel(const SpecialRow *__restrict__ rows,
+                                                              const SubDev *__restrict__ subs,
+                                                              double *__restrict__ db, long long o_w,
+                                                              long long o_fc, long long o_exp2, double inv_s) {
+  __shared__ double s_exp2[256];
+  const SpecialRow rw = rows[blockIdx.x];
+  if (rw.kind == ROW_AM) return;
+  load_exp2tab(s_exp2, db + o_exp2);
+  const SubDev d = subs[rw.sub];
+  const double *w = db + o_w + 2 * d.w_off;
+  const double4 *fc = reinterpret_cast<const double4 *>(db + o_fc) + d.w_off;
+  const long long sh = d.dshift;
+  double *o0 = db + rw.out0 + sh;
+  double *o1 = rw.out1 >= 0 ? db + rw.out1 + sh : nullptr;
+  const bool delta = rw.kind == ROW_DELTA;
+  for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+    const double4 c = fc[j];
+    const double u = fma(c.x, rw.x, fma(c.y, rw.y, c.z));
+    const double t = tanh_half(u, s_exp2);
+    const double s1 = fma(-t, t, 1.0);
+    const double zs = 0.5 * u * inv_s;
+    const double dp = s1 * zs;
+    o0[j] = dp;
+    if (o1) o1[j] = dp;
+    if (delta) {
+      const double f = (rw.nx * w[2 * j] + rw.ny * w[2 * j + 1]) * s1 * fma(-2.0 * t, zs, inv_s);
+      db[rw.out2 + sh + j] = f;
+      db[rw.out3 + sh + j] = f;
+    }
+  }
+}
+
+// Second pass on the derivative rows: the change-of-variables rows are the same
+// combination of derivative rows; the A_m corner row's corner flux
+// (w . n)(1 - t_c^2) has the derivative (w . n)(s1_c / s - 2 t_c dt_c/ds), with
+// t_c from the value block and dt_c/ds from the derivative block.
+__global__ void __launch_bounds__(256) special_combine_ds_kernel(const SpecialRow *__restrict__ rows,
+                                                                 const SubDev *__restrict__ subs,
+                                                                 double *__restrict__ db, long long o_w,
+                                                                 double inv_s) {
+  const SpecialRow rw = rows[blockIdx.x];
+  const bool tinv = rw.kind == ROW_DELTA && (rw.ca >= 0 || rw.cb >= 0);
+  if (!tinv && rw.kind != ROW_AM) return;
+  const SubDev d = subs[rw.sub];
+  const double *w = db + o_w + 2 * d.w_off;
+  const long long M = d.M, sh = d.dshift;
+  for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
+    if (tinv) {
+      double v = db[rw.out0 + sh + j];
+      if (rw.ca >= 0) v -= rw.alpha * db[rw.ca + sh + j];
+      if (rw.cb >= 0) v -= rw.beta * db[rw.cb + sh + j];
+      db[rw.out0 + sh + j] = v;
+      db[rw.out1 + sh + j] = v;
+    } else {
+      const double wx = w[2 * j], wy = w[2 * j + 1];
+      const double tc = db[rw.ca + j], dtc = db[rw.ca + sh + j];
+      const double sc = 1.0 - tc * tc;
+      double v = 0.0;
+      for (int e = 0; e < 2; ++e) {
+        const int ne = rw.am_e[e];
+        double acc = (rw.am_n[e][0] * wx + rw.am_n[e][1] * wy) * fma(sc, inv_s, -2.0 * tc * dtc);
+        for (int k = 0; k < ne; ++k) acc += db[rw.am_f[e] + sh + k * M + j];
+        v += acc / double(ne + 1);
+      }
+      db[rw.out0 + sh + j] = v;
+    }
+  }
+}
+
 }  // namespace
+
+// The scale gradient's local matrices of wave w: K_c, K-bar, A_m, A-bar and the
+// evaluation matrix re-assembled into the scale buffers, then their s-derivatives.
+cudaError_t launch_scale_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_ssubs);
+  const SpecialRow *rows = reinterpret_cast<const SpecialRow *>(base + p.off_srows);
+  double *db = reinterpret_cast<double *>(base + p.off_dbl);
+  const int s0 = wave * p.wave, s1 = std::min(p.n_sub, s0 + p.wave);
+  int max_nI = 0;
+  for (int i = s0; i < s1; ++i) max_nI = std::max(max_nI, p.subs[i].nI);
+  const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
+  const int e0 = p.wave_erow0[wave], e1 = p.wave_erow0[wave + 1];
+  const dim3 grid((max_nI + 7) / 8, s1 - s0);
+  if (max_nI > 0) { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
+  if (r1 > r0) {
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w); DDELM_COUNT_LAUNCH(); }
+  }
+  if (e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
+  if (max_nI > 0) { interior_rows_ds_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.inv_scale); DDELM_COUNT_LAUNCH(); }
+  if (r1 > r0) {
+    { special_rows_ds_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.inv_scale); DDELM_COUNT_LAUNCH(); }
+    { special_combine_ds_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.inv_scale); DDELM_COUNT_LAUNCH(); }
+  }
+  if (e1 > e0) { special_rows_ds_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.inv_scale); DDELM_COUNT_LAUNCH(); }
+  return cudaGetLastError();
+}
 
 // Features of the subdomains of one setup wave (their special rows included);
 // wave 0 also writes the evaluation rows.

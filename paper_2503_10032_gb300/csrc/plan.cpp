@@ -75,8 +75,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_CQR2_SERIES || o.setup_passes < 0 ||
       o.setup_passes > 8)
     return fail("bad setup scheme");
+  if (o.barrier_timeout_ms < 0 || o.inject_barrier_stall < 0 || o.inject_barrier_stall > 1)
+    return fail("bad barrier options");
+  if (o.plain_flux_corners < 0 || o.plain_flux_corners > 1) return fail("bad plain_flux_corners");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
+  P.inv_scale = pr.scale != 0.0 ? 1.0 / pr.scale : 0.0;
   const int nx = pr.nx, ny = pr.ny, n_sub = nx * ny;
   Geo g{nx, ny, pr.x0, pr.x1, pr.y0, pr.y1, (pr.x1 - pr.x0) / nx, (pr.y1 - pr.y0) / ny, pr.edge_pts};
   const int n_edges = g.n_edges();
@@ -244,6 +248,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     d.oA = take(nG * M);
     d.oEval = take(d.nE * M);
     d.oV = take(M * M);
+    d.oVb = take(M * M);  // R^{-1} of K-bar (kept: the scale gradient reuses it)
     d.oV3 = take(M * M);
     d.oQG = take(nG * M);
     d.oKpE = take(M * nG);
@@ -427,8 +432,10 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       v.Tb = take(M * M);
       v.W32 = take(M * M);  // 2 M^2 floats
       v.V3 = t == 0 ? -1 : take(M * M);
-      v.V = t == 0 ? -1 : take(M * M);
+      v.V = -1;  // R^{-1} of both variants is persistent
     }
+    P.slot_begin.push_back(c.Kb);
+    P.slot_end.push_back(cur);
   }
   std::vector<Scr> scr(n_sub);
   for (int i = 0; i < n_sub; ++i) {
@@ -440,7 +447,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     d.oY1 = scr[i].Y1;
     d.oY1b = scr[i].Y1b;
     d.oAbar = scr[i].Abar;
-    d.oVb = scr[i].v[1].V;
+    scr[i].v[1].V = d.oVb;
     // the Q updates alternate between the feature buffer and the other one;
     // the features go where the last update lands in oX
     d.oK = (P.n_pass % 2 == 0) ? d.oX : d.oY1;
@@ -518,7 +525,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         const EdgeRef &e = s.am_edges[k][t];
         a.am_n[t][0] = e.n[0];
         a.am_n[t][1] = e.n[1];
-        a.am_e[t] = pr.edge_pts[e.id];
+        // plain flux rows: the corner's own flux only (no edge points, weight 1)
+        a.am_e[t] = o.plain_flux_corners ? 0 : pr.edge_pts[e.id];
         // an edge meeting a cross point is an interface edge: its Delta points are
         // the e points the mean runs over
         a.am_f[t] = d.oA + (long long)(d.nPi + s.dstart.at(e.id)) * M;
@@ -1164,6 +1172,11 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       return fail(e.c_str());
     }
   }
+  // ---- scale gradient: tables and buffers (inside the free setup scratch)
+  if (build_scale(P, cur) != DDELM_OK) {
+    const std::string e = P.err.empty() ? std::string("scale plan") : P.err;
+    return fail(e.c_str());
+  }
   P.n_dbl = cur;
 
   // ---- bounds of every access the kernels make (an error here, not a fault there)
@@ -1181,10 +1194,25 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
     for (const auto &t : P.gtile)
       if (t.desc < 0 || t.desc >= (int)P.gdesc.size()) return fail("internal: GEMM tile");
-    for (const auto &ph : P.setup_gemm)  // a phase's tiles use only its own descriptors
+    auto phase_ok = [&](const GemmPhase &ph) {  // a phase's tiles use only its own descriptors
       for (int q = ph.tile0; q < ph.tile0 + ph.ntile; ++q)
-        if (P.gtile[q].desc < ph.desc0 || P.gtile[q].desc >= ph.desc0 + ph.ndesc)
-          return fail("internal: GEMM phase tiles");
+        if (q < 0 || q >= (int)P.gtile.size() || P.gtile[q].desc < ph.desc0 || P.gtile[q].desc >= ph.desc0 + ph.ndesc)
+          return false;
+      return true;
+    };
+    for (const auto &ph : P.setup_gemm)
+      if (!phase_ok(ph)) return fail("internal: GEMM phase tiles");
+    for (const auto &ph : P.sc_coarse)
+      if (!phase_ok(ph)) return fail("internal: GEMM phase tiles");
+    for (const auto &w : P.sc_wave)
+      for (const auto &ph : w)
+        if (!phase_ok(ph)) return fail("internal: GEMM phase tiles");
+    for (const auto &dd : P.dots) {
+      const long long al = dd.rows > 0 ? (long long)(dd.rows - 1) * dd.lda + dd.cols : 0;
+      const long long bl = dd.rows > 0 ? (long long)(dd.rows - 1) * dd.ldb + dd.cols : 0;
+      if (!in(dd.a, al) || !in(dd.b, bl) || dd.sub < 0 || dd.sub >= n_sub || dd.lda < dd.cols || dd.ldb < dd.cols)
+        return fail("internal: dot product bounds");
+    }
     for (const auto &c : P.cdesc) {
       const long long mm = (long long)c.M * c.M;
       if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm)) || (c.prec == 1 && !in(c.w, mm)))
@@ -1318,6 +1346,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   off = al(off + std::max<size_t>(P.otile.size(), 1) * sizeof(OzTile));
   P.off_tmaps = off;
   off = al(off + std::max<size_t>(P.sdesc.size(), 1) * 128);
+  P.off_ssubs = off;
+  off = al(off + std::max<size_t>(P.ssubs.size(), 1) * sizeof(SubDev));
+  P.off_srows = off;
+  off = al(off + std::max<size_t>(P.srows.size(), 1) * sizeof(SpecialRow));
+  P.off_scsub = off;
+  off = al(off + std::max<size_t>(P.scsub.size(), 1) * sizeof(ScaleSub));
+  P.off_dots = off;
+  off = al(off + std::max<size_t>(P.dots.size(), 1) * sizeof(DotDesc));
   P.bytes_tables = off;
   P.off_dbl = off;
   off = al(off + (size_t)P.n_dbl * sizeof(double));

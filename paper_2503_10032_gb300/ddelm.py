@@ -37,7 +37,8 @@ class ddelm_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("keep_matrices", ctypes.c_int), ("setup_wave", ctypes.c_int),
                 ("setup_scheme", ctypes.c_int), ("setup_passes", ctypes.c_int),
-                ("disable_graphs", ctypes.c_int)]
+                ("disable_graphs", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
+                ("inject_barrier_stall", ctypes.c_int), ("plain_flux_corners", ctypes.c_int)]
 
 
 class ddelm_problem(ctypes.Structure):
@@ -93,7 +94,7 @@ def load_library(path: str = LIB_PATH):
                                 ctypes.c_void_p]
     lib.ddelm_solve.restype = ctypes.c_int
     lib.ddelm_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                   ctypes.c_void_p, ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
+                                   ctypes.c_void_p, _dp, ctypes.POINTER(ddelm_solve_info), ctypes.c_void_p]
     lib.ddelm_backward.restype = ctypes.c_int
     lib.ddelm_interface_residual.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]
     lib.ddelm_interface_residual.restype = ctypes.c_int
@@ -133,10 +134,12 @@ def ddelm_status_string(status: int) -> str:
 
 def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change_of_vars=True,
                  precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False, setup_wave=0,
-                 setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0, graphs=True):
+                 setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0, graphs=True, barrier_timeout_ms=0,
+                 inject_barrier_stall=False, use_Am=True):
     return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
                          max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
-                         int(setup_passes), int(not graphs))
+                         int(setup_passes), int(not graphs), int(barrier_timeout_ms),
+                         int(inject_barrier_stall), int(not use_Am))
 
 
 class ProblemArgs:
@@ -211,12 +214,15 @@ def ddelm_solve(h, f_ptr, g_ptr, c_ptr, mu_ptr, u_ptr, stream):
     return rc, info
 
 
-def ddelm_backward(h, grad_c_ptr, grad_u_ptr, grad_f_ptr, grad_g_ptr, stream):
+def ddelm_backward(h, grad_c_ptr, grad_u_ptr, grad_f_ptr, grad_g_ptr, stream, want_scale=False):
+    """(status, info, dL/ds or None)."""
     info = ddelm_solve_info()
+    gs = ctypes.c_double(0.0)
     rc = _lib.ddelm_backward(h, ctypes.c_void_p(grad_c_ptr), ctypes.c_void_p(grad_u_ptr),
-                             ctypes.c_void_p(grad_f_ptr), ctypes.c_void_p(grad_g_ptr), ctypes.byref(info),
+                             ctypes.c_void_p(grad_f_ptr), ctypes.c_void_p(grad_g_ptr),
+                             ctypes.byref(gs) if want_scale else None, ctypes.byref(info),
                              ctypes.c_void_p(stream))
-    return rc, info
+    return rc, info, (gs.value if want_scale else None)
 
 
 def ddelm_interface_residual(h, f_ptr, g_ptr, mu_ptr, r_ptr, c_ptr, u_ptr, stream):
@@ -322,8 +328,10 @@ class Solver:
             raise DDELMError(rc, "ddelm_interface_solve")
         return mu[:self.sizes.n_delta], info
 
-    def backward(self, grad_c=None, grad_u=None):
-        """(dL/df [sum n_int, R], dL/dg [n_bnd, R], info) for cotangents of c and/or u."""
+    def backward(self, grad_c=None, grad_u=None, scale=False):
+        """(dL/df [sum n_int, R], dL/dg [n_bnd, R], info) for cotangents of c and/or u;
+        with scale=True also dL/ds for the hidden-layer scale at the last solve
+        (a float, the fourth element)."""
         torch = self.torch
         R = self.prob.n_rhs
         sz = self.sizes
@@ -331,11 +339,13 @@ class Solver:
         gg = torch.empty((max(sz.n_bnd, 1), R), dtype=torch.float64, device=self.device)
         gc = grad_c.contiguous() if grad_c is not None else None
         gu = grad_u.contiguous() if grad_u is not None else None
-        rc, info = ddelm_backward(self.h, gc.data_ptr() if gc is not None else 0,
-                                  gu.data_ptr() if gu is not None else 0, gf.data_ptr(), gg.data_ptr(),
-                                  self.stream.cuda_stream)
+        rc, info, gs = ddelm_backward(self.h, gc.data_ptr() if gc is not None else 0,
+                                      gu.data_ptr() if gu is not None else 0, gf.data_ptr(), gg.data_ptr(),
+                                      self.stream.cuda_stream, want_scale=scale)
         if rc not in (DDELM_OK, DDELM_ERR_NOT_CONVERGED):
             raise DDELMError(rc, "ddelm_backward")
+        if scale:
+            return gf[:sz.sum_int], gg[:sz.n_bnd], info, gs
         return gf[:sz.sum_int], gg[:sz.n_bnd], info
 
     def inspect(self, sub, which):

@@ -151,7 +151,7 @@ def coef_a(x, y):
 
 def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
                  op=OP_POISSON, box=(0.0, 1.0, 0.0, 1.0), n_eval=32,
-                 forcing=None, coef=None, exact_known=True, name=""):
+                 forcing=None, coef=None, exact_known=True, points="random", name=""):
     """Draw one problem.
 
     M, n_int: int or per-subdomain arrays.  edge_pts: int or per-edge array.
@@ -162,6 +162,8 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
     forcing (optional): list of f(x, y) callables overriding -L u, with g = u on
     the boundary all the same.  coef (optional, diffusion): (x, y) -> (a, a_x, a_y)
     in place of coef_a.  exact_known = False: u_eval_exact is NaN (no closed form).
+    points = "grid": the interior points of a subdomain are the centres of a
+    uniform n x n grid of cells (n_int = n^2) instead of uniform random points.
     """
     rng = np.random.default_rng(seed)
     n_sub = nx * ny
@@ -185,7 +187,16 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
         w_hat.append(wh)
         b_hat.append(bh)
         nI = int(nIs[i])
-        x_int.append(np.stack([rng.uniform(xa, xb, nI), rng.uniform(ya, yb, nI)], 1))
+        if points == "grid":
+            n = int(round(np.sqrt(nI)))
+            if n * n != nI:
+                raise ValueError("grid points need a square n_int")
+            cx = xa + (np.arange(n) + 0.5) * (xb - xa) / n
+            cy = ya + (np.arange(n) + 0.5) * (yb - ya) / n
+            gx, gy = np.meshgrid(cx, cy)
+            x_int.append(np.stack([gx.ravel(), gy.ravel()], 1))
+        else:
+            x_int.append(np.stack([rng.uniform(xa, xb, nI), rng.uniform(ya, yb, nI)], 1))
         x_ev.append(np.stack([rng.uniform(xa, xb, n_eval), rng.uniform(ya, yb, n_eval)], 1))
     x_int = np.concatenate(x_int)
     x_ev = np.concatenate(x_ev)
@@ -359,6 +370,18 @@ def fourier_basis(x):
 def fourier_coefficients():
     """The 16 coefficients a_pq of the poisson_8x8_fourier forcing (row p-1, column q-1 flattened)."""
     return np.random.default_rng(10040).standard_normal(16)
+
+
+def paper_scale(n, seed=2001, max_neurons=1024):
+    """The paper's ablation setting (Sec. 4.1, Sec. 4.2): n x n subdomains of the
+    unit square, 2^16 neurons in total (2^16 / n^2 per subdomain, capped at
+    max_neurons, the library's per-subdomain limit), a (320 / n) x (320 / n)
+    uniform grid per subdomain (cell centres inside, 320 / n points on every
+    edge), the paper's initialisation with l = 32, u = sin(pi x) sin(pi y)."""
+    g = 320 // n
+    M = min(2 ** 16 // (n * n), max_neurons)
+    return make_problem(n, n, M, g * g, g, scale=32.0, init="paper", seed=seed, solutions=[_sin_sin(1, 1)],
+                        points="grid", name=f"paper_{n}x{n}")
 
 
 def small_uneven_problem(nx=4, ny=3, M_range=(20, 90), seed=13, n_rhs=1, init="paper", scale=8.0):

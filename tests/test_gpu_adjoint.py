@@ -5,6 +5,7 @@ import pytest
 
 from oracle import ddelm as odd
 from paper_2503_10032_gb300 import inputs
+from parity_util import close
 
 pytestmark = pytest.mark.gpu
 
@@ -24,9 +25,6 @@ def _t(a):
     import torch
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -56,7 +54,7 @@ def test_adjoint_is_transpose_of_solve(D, prec):
     g_ref = Jc.T @ cbar + Ju.T @ ubar        # [n, 1]
     g_gpu = np.vstack([gf.cpu().numpy(), gg.cpu().numpy()])
     assert g_gpu.shape == (n, 1)
-    assert _rel(g_gpu, g_ref) < (1e-6 if prec == "fp64" else 1e-5)
+    assert close(g_gpu, g_ref, (1e-6 if prec == "fp64" else 1e-5), "g_gpu vs g_ref")
 
 
 def test_fourier_coefficient_gradient(D):
@@ -93,7 +91,7 @@ def test_fourier_coefficient_gradient(D):
             e = torch.zeros(16, dtype=torch.float64, device="cuda")
             e[k] = h
             fd[k] = (float(loss_of(a + e)) - float(loss_of(a - e))) / (2 * h)
-    assert _rel(grad, fd) < 1e-6
+    assert close(grad, fd, 1e-6, "grad vs fd")
     # oracle: u is linear in a; du/da_pq = solve(basis column pq, g = 0)
     q = inputs.make_problem(3, 3, 40, 120, 4, scale=8.0, init="paper", seed=41,
                             solutions=[inputs.fourier_forcing(a0)], n_eval=16)
@@ -103,14 +101,17 @@ def test_fourier_coefficient_gradient(D):
     U = ref["u_eval"]                          # [n_eval, 16]
     u_now = U @ a0
     grad_ref = 2.0 / len(u_now) * U.T @ (u_now - np.sin(np.pi * p.x_eval[:, 0]) * np.sin(np.pi * p.x_eval[:, 1]))
-    assert _rel(grad, grad_ref) < 1e-6
+    assert close(grad, grad_ref, 1e-6, "grad vs grad_ref")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_scale_gradient(D, prec):
-    """dL/ds for the hidden-layer scale s (w = s w_hat, b = s b_hat), with
-    L = mean (u - sin(pi x) sin(pi y))^2: the tangent path against central
-    differences of the FP64 oracle's solution."""
+    """dL/ds for the hidden-layer scale s (w = s w_hat, b = s b_hat) from one
+    ddelm_backward call (the library's reverse mode at the solve, no further
+    setup), against a fourth-order central difference of the FP64 oracle's
+    solution, for three losses: the squared error of u against
+    sin(pi x) sin(pi y) (through torch.autograd), a seeded linear functional of
+    u, and a seeded linear functional of the coefficients c."""
     import dataclasses
     import torch
     from paper_2503_10032_gb300.autograd import solve_u_scaled
@@ -121,24 +122,34 @@ def test_scale_gradient(D, prec):
     f = _t(p.f_int)
     g = _t(p.g_bnd)
     target = np.sin(np.pi * p.x_eval[:, 0]) * np.sin(np.pi * p.x_eval[:, 1])
-    ut = _t(target)[:, None]
+    wu = inputs.interface_vectors(len(target), 1, 1, 11)[0]
+    wc = inputs.interface_vectors(int(p.M.sum()), 1, 1, 12)[0]
+    # L1 through torch.autograd (DDELMSolveScaled -> ddelm_backward with the scale output)
     sc = torch.tensor(p.scale, dtype=torch.float64, device="cuda", requires_grad=True)
     u = solve_u_scaled(s, f, g, sc)
-    L = ((u - ut) ** 2).mean()
-    L.backward()
-    grad = float(sc.grad)
+    ((u - _t(target)[:, None]) ** 2).mean().backward()
+    got = [float(sc.grad)]
+    # L2 = w . u and L3 = w . c through the binding
+    _, _, _, gs2 = s.backward(grad_u=_t(wu), scale=True)
+    _, _, _, gs3 = s.backward(grad_c=_t(wc), scale=True)
+    got += [gs2, gs3]
 
-    def loss_oracle(scale):
-        q = dataclasses.replace(p, scale=scale)
-        uo = odd.solve(q, odd.Options(eps_rel=1e-6))["u_eval"][:, 0]
-        return float(np.mean((uo - target) ** 2))
+    def losses(scale):
+        r = odd.solve(dataclasses.replace(p, scale=scale), odd.Options(eps_rel=1e-6))
+        ue, ce = r["u_eval"][:, 0], np.concatenate(r["c"])[:, 0]
+        return np.array([np.mean((ue - target) ** 2), wu[:, 0] @ ue, wc[:, 0] @ ce])
 
-    h = 1e-4 * p.scale
-    fd = (loss_oracle(p.scale + h) - loss_oracle(p.scale - h)) / (2 * h)
-    assert abs(grad - fd) <= 1e-5 * abs(fd), (grad, fd)
-    # the tangent of u itself against the oracle's central difference
-    from paper_2503_10032_gb300.tangent import scale_tangent
-    _, du = scale_tangent(s, f, g)
-    up = odd.solve(dataclasses.replace(p, scale=p.scale + h), odd.Options(eps_rel=1e-6))["u_eval"]
-    um = odd.solve(dataclasses.replace(p, scale=p.scale - h), odd.Options(eps_rel=1e-6))["u_eval"]
-    assert _rel(du.cpu().numpy(), (up - um) / (2 * h)) < 1e-5
+    def fd4(h):
+        Lp2, Lp1, Lm1, Lm2 = (losses(p.scale + j * h) for j in (2, 1, -1, -2))
+        return (-Lp2 + 8 * Lp1 - 8 * Lm1 + Lm2) / (12 * h)
+
+    h = 2e-3 * p.scale
+    ref_h, ref = fd4(h), fd4(h / 2)
+    for k in range(3):
+        # halving the step moves the fourth-order difference by about 15x its
+        # remaining truncation error; the bound adds that movement to 1e-6
+        assert abs(ref_h[k] - ref[k]) <= 1e-5 * abs(ref[k]), (k, ref_h[k], ref[k])
+        tol = 1e-6 * abs(ref[k]) + abs(ref_h[k] - ref[k])
+        print(f"scale gradient 3x3 {prec} loss {k + 1}: {got[k]:.12e} vs oracle {ref[k]:.12e} "
+              f"rel {abs(got[k] - ref[k]) / abs(ref[k]):.2e}")
+        assert abs(got[k] - ref[k]) <= tol, (k, got[k], ref[k], tol)

@@ -111,3 +111,18 @@ def test_feature_rows_to_rounding(D, case):
             scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1e-300)
             worst = max(worst, float((np.abs(got - ref) / scale).max()))
     assert worst < 2e-14, worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cov,use_Am", [(True, True), (True, False), (False, True), (False, False)])
+def test_ablation_variants_match_oracle(D, cov, use_Am, prec):
+    """The coarse-space variants of the paper's ablation: K or K_c (change of
+    variables, Sec. 3.2) with the plain flux rows A or the modified A_m."""
+    p = inputs.small_problem(3, 3, M=24, n_int=70, edge_pts=4, n_rhs=1, seed=19)
+    ref = odd.solve(p, odd.Options(eps_rel=1e-6, theta=0.999, use_change_of_vars=cov, use_Am=use_Am))
+    s, c, mu, u, info, rc = _run(D, p, theta=0.999, eps_rel=1e-6, tol=1e-12, use_change_of_vars=cov,
+                                 use_Am=use_Am, precision=D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED)
+    assert rc == D.DDELM_OK
+    n_pi = ref["oracle"].n_pi
+    assert close(mu[n_pi:], ref["mu_delta"], 1e-9, f"ablation cov={cov} Am={use_Am} {prec} mu")
+    assert close(u, ref["u_eval"], 1e-9, f"ablation cov={cov} Am={use_Am} {prec} u")
