@@ -73,6 +73,24 @@ def measured_peaks():
         return {}
 
 
+def method_setup_flops(sub_sizes):
+    """The method's algorithmic setup work per step (what DDELM-NN has to compute,
+    not what this implementation executes).  Per subdomain with m rows, M neurons,
+    nG interface and nDl Delta points: the Gram of the m - nG interior and
+    boundary rows shared by K_c and K-bar ((m - nG) M^2, symmetric), the Grams of
+    the two interface blocks (2 nG M^2), the three local operators Lambda, Psi,
+    Phi (triangular solves and products: 2 nG M^2 + 3 nG^2 M + 2 nDl M^2 +
+    2 nDl^2 M) and two Cholesky factorisations (2 M^3 / 3).  Returns (GEMM flops,
+    Cholesky flops)."""
+    gemm = chol = 0.0
+    for d in sub_sizes:
+        m, M, nG, nDl = (float(d[k]) for k in ("m", "M", "nG", "nDl"))
+        gemm += (m - nG) * M * M + 2 * nG * M * M + 2 * nG * M * M + 3 * nG * nG * M + 2 * nDl * M * M \
+            + 2 * nDl * nDl * M
+        chol += 2.0 * M ** 3 / 3.0
+    return gemm, chol
+
+
 def workload_config(name, prob, sizes=None):
     cfg = {"workload": name, "subdomains": f"{prob.nx}x{prob.ny}",
            "neurons_per_subdomain": int(prob.M[0]) if len(set(prob.M.tolist())) == 1 else "uneven",
@@ -137,21 +155,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(prob, n_sample, budget_s=None):
-    """Times the oracle's per-subdomain setup on a bounded sample of subdomains.
-
-    Returns (seconds per full-problem setup estimate, description).  The
-    oracle's coarse problem and CG are left out of the sample (they are a
-    minority of its time on these workloads), so the estimate favours the
-    oracle."""
+def oracle_complete_solve(prob):
+    """Times one complete FP64 oracle solve of the workload: every local ridge
+    pseudo-inverse by Householder QR, the coarse problem (S_Pi assembled and
+    factored), plain CG on Eq. (nn-mixed) from mu = 0 to the relative residual
+    TOL, and the reconstruction of Eq. (coarse_sol_2) with u at the evaluation
+    points.  Returns (seconds, CG iterations)."""
     from oracle import ddelm as odd
-    n = prob.n_sub
-    n_sample = max(1, min(n, n_sample))
-    only = set(np.linspace(0, n - 1, n_sample).round().astype(int).tolist())
     t0 = time.perf_counter()
-    odd.DDELMOracle(prob, odd.Options(eps_rel=EPS_REL, theta=THETA, tol=TOL), only=only)
-    dt = time.perf_counter() - t0
-    return dt * n / len(only), dt, len(only)
+    r = odd.solve(prob, odd.Options(eps_rel=EPS_REL, theta=THETA, tol=TOL), method="cg")
+    return time.perf_counter() - t0, int(r["iters"])
+
+
+def oracle_threads():
+    """Threads the oracle's BLAS runs with (its parallelism is BLAS-level)."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count() or 1
 
 
 def max_over_ranks(x, dist, device):
@@ -166,33 +187,37 @@ def max_over_ranks(x, dist, device):
 
 
 def run_reference(args):
+    """The oracle on the host cores: every timed step is one complete oracle solve
+    of the workload (see oracle_complete_solve); the warm-up steps solve the 2x2,
+    M = 100 workload completely (imports, BLAS threads and caches warmed at a
+    fraction of the cost)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from paper_2503_10032_gb300 import inputs
     prob = inputs.config(args.workload)
-    cores = os.cpu_count() or 1
-    n_sample = max(1, prob.n_sub // 8)
+    small = inputs.config("poisson_2x2_m100")
     for _ in range(args.warmup):
-        oracle_sample(prob, n_sample)
-    per = []
-    t_total = 0.0
+        oracle_complete_solve(small)
+    per, its = [], []
     for _ in range(args.steps):
-        est, dt, ns = oracle_sample(prob, n_sample)
-        per.append(est)
-        t_total += dt
+        dt, it = oracle_complete_solve(prob)
+        per.append(dt)
+        its.append(it)
     sec = float(np.mean(per))
     value = 1.0 / sec
+    cores = oracle_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, prob),
+            "cg_iterations": int(np.median(its)),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"per step the FP64 oracle's local setup (features, two ridge "
-                                       f"pseudo-inverses by Householder QR, local blocks) of {n_sample} of "
-                                       f"{prob.n_sub} subdomains, scaled by {prob.n_sub}/{n_sample}; coarse "
-                                       f"problem and CG not included (favours the oracle)"},
+                             "sample": f"each step one complete FP64 oracle solve of the whole workload "
+                                       f"({prob.n_sub} local ridge pseudo-inverses by Householder QR, coarse "
+                                       f"problem, CG to relative residual {TOL}, reconstruction); warm-up "
+                                       f"steps solve the 2x2, M=100 workload"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -268,29 +293,46 @@ def main():
     for _ in range(args.warmup):
         out = step()
     torch.cuda.synchronize(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    plan6 = D.ddelm_inspect(solver.h, 0, 9, 6)
+    graphs = {"setup": bool(plan6[4]), "solve": bool(plan6[5])}
+
+    def timed_steps(n):
+        """n steps between CUDA events on the library's stream, L2 flushed before
+        each (outside the events); returns (per-step ms, solve infos)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        res = []
+        for k in range(n):
+            with torch.cuda.stream(stream):
+                flush.zero_()                         # L2 flush, outside the timed events
+                ev[k][0].record(stream)
+            o = step()
+            ev[k][1].record(stream)
+            res.append((o[3].iterations, o[3].rel_residual, o[4], o))
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in ev], res
+
+    # timed region: the production configuration (setup and solve replayed from
+    # their captured CUDA graphs, no per-launch events)
     clocks = ClockSampler(local)
-    solver.profile(enable=True, reset=True)
     barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
-    infos = []
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                         # L2 flush, outside the timed events
-            ev[k][0].record(stream)
-        out = step()
-        ev[k][1].record(stream)
-        infos.append((out[3].iterations, out[3].rel_residual, out[4]))
-    torch.cuda.synchronize(dev)
+    step_ms, res = timed_steps(args.steps)
     barrier()
     clk = clocks.stop()
-    prof_ms, prof_n = solver.profile(enable=False, reset=True)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    infos = [r[:3] for r in res]
+    out = res[-1][3]
     total_ms = float(sum(step_ms))
     total_ms = max_over_ranks(total_ms, dist, dev)
     value = world * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
+
+    # profiled pass: the same number of steps again with CUDA events around every
+    # launch (graphs are not replayed while profiling), for the per-kernel-class
+    # times, launch counts and the roofline of the dominant class
+    solver.profile(enable=True, reset=True)
+    prof_step_ms, _ = timed_steps(args.steps)
+    prof_ms, prof_n = solver.profile(enable=False, reset=True)
 
     # secondary metric: repeated solves with the reused handle (right-hand side,
     # CG and reconstruction only), L2 flushed between solves
@@ -385,40 +427,55 @@ def main():
     h2d = int(sizes.upload_bytes) + f_h.numel() * 8 + g_h.numel() * 8
     d2h = c_h.numel() * 8 + mu_h.numel() * 8 + u_h.numel() * 8
 
-    # roofline of the dominant kernel class (time measured live over the timed region)
+    # roofline of the dominant kernel class: the method's algorithmic work per
+    # step over the class's time per step in the profiled pass
     names = D.PROF_CLASS_NAMES
     n_cls = len(names)
     k_dom = int(np.argmax(prof_ms[:n_cls]))
     launches_total = int(prof_n.sum())
-    per_launch_ms = prof_ms[k_dom] / max(prof_n[k_dom], 1)
     peaks = measured_peaks()
+    alg_gemm, alg_chol = method_setup_flops(sub_sizes)
+    # the method's GEMM work is split between the tensor-core and FP64 engines in
+    # the proportion of the implementation's own (FP64-equivalent) setup products
+    tc_share = (flops[0] - flops[4]) / flops[0] if (prec == D.DDELM_PREC_MIXED and flops[0] > 0) else 0.0
+    bf16_peak = 1000.0 * float(peaks.get("bf16_tflops_sustained", 1700.0))
+    bf16_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
+    alg_work = {"tc_gemm": alg_gemm * tc_share, "gemm_f64": alg_gemm * (1.0 - tc_share) + flops[2],
+                "chol_inv": alg_chol}
+    dom = names[k_dom]
+    per_launch_ms = prof_ms[k_dom] / max(prof_n[k_dom], 1)
+    work_per_launch = alg_work.get(dom, float("nan")) * args.steps / max(prof_n[k_dom], 1)
     bound, unit, peak, peak_src = "alu", "GFLOP/s", FP64_PEAK_GFLOPS, \
         "nominal FP64 of the recipe table (no FP64 entry in the measured peaks)"
-    if names[k_dom] == "gemm_f64":
-        work = (flops[4] + flops[2]) * args.steps / max(prof_n[k_dom], 1)
-    elif names[k_dom] == "chol_inv":
-        work = flops[1] * args.steps / max(prof_n[k_dom], 1)
-        if flops[5] > 0.5 * flops[1]:
-            peak, peak_src = FP32_PEAK_GFLOPS, ("nominal FP32 CUDA-core rate (152 SMs x 128 lanes x 2 x 2.07 GHz); "
-                                                "the Cholesky passes run in FP32")
-    elif names[k_dom] == "tc_gemm":
-        work = flops[3] * args.steps / max(prof_n[k_dom], 1)
-        bound, unit = "tensor", "GFLOP/s"
-        peak = 1000.0 * float(peaks.get("bf16_tflops_sustained", 1700.0))
-        peak_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
-    else:
-        work = float("nan")
-    achieved = work / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
+    if dom == "tc_gemm":
+        bound, peak, peak_src = "tensor", bf16_peak, bf16_src
+    elif dom == "chol_inv" and flops[5] > 0.5 * flops[1]:
+        peak, peak_src = FP32_PEAK_GFLOPS, ("nominal FP32 CUDA-core rate (152 SMs x 128 lanes x 2 x 2.07 GHz); "
+                                            "the Cholesky passes run in FP32")
+    achieved = work_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
     traffic = None
-    if (names[k_dom] == "tc_gemm" and args.workload == TC_TRAFFIC["workload"] and prec == D.DDELM_PREC_MIXED
+    if (dom == "tc_gemm" and args.workload == TC_TRAFFIC["workload"] and prec == D.DDELM_PREC_MIXED
             and args.scheme == "auto" and kernel_sources_sha256() == TC_TRAFFIC["sources_sha256"]):
         traffic = TC_TRAFFIC["dram_bytes_per_step"] / TC_TRAFFIC["launches_per_step"]
-    roofline = {"kernel": names[k_dom], "bound": bound, "achieved": achieved, "peak": peak,
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak if math.isfinite(achieved) else None,
                 "traffic": traffic, "traffic_source": TC_TRAFFIC["source"] if traffic is not None else None,
                 "peak_source": peak_src,
+                "work": ("the method's algorithmic setup flops per step (per subdomain: shared Gram, two "
+                         "interface updates, three local operators; two Cholesky factorisations for chol_inv)"
+                         f" = {alg_gemm:.4g} GEMM + {alg_chol:.4g} Cholesky flops, times the class's share; "
+                         "per launch = per step x steps / launches"),
                 "time_share": {n: float(prof_ms[i] / max(prof_ms[:n_cls].sum(), 1e-12)) for i, n in enumerate(names)},
-                "launches": {n: int(prof_n[i]) for i, n in enumerate(names)}}
+                "launches": {n: int(prof_n[i]) for i, n in enumerate(names)},
+                "profiled_ms_per_step": float(np.mean(prof_step_ms))}
+    if dom == "tc_gemm":
+        # what the tensor cores execute: the BF16 slice-pair products of the exact
+        # FP64 emulation (far more than the method's flops)
+        emu = flops[3] * args.steps / (prof_ms[k_dom] * 1e-3) / 1e9
+        roofline["emulated"] = {"achieved": emu, "peak": bf16_peak, "unit": "GFLOP/s", "frac": emu / bf16_peak,
+                                "work": "BF16 slice-pair flops executed per step", "flops_per_step": flops[3]}
+        roofline["vs_fp64_nominal"] = {"peak": FP64_PEAK_GFLOPS, "frac": achieved / FP64_PEAK_GFLOPS,
+                                       "note": "the same algorithmic rate against the nominal FP64 rate"}
 
     # every kernel class against its own roof (algorithmic work over live time)
     n_it = float(np.median([i for i, _, _ in infos]))
@@ -427,13 +484,13 @@ def main():
     feat_bytes = 8.0 * sum((2 * s_["m"] + s_["nG"] + s_["nDl"]) * s_["M"] for s_ in sub_sizes)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofs = {"features": (feat_bytes, "GB/s", hbm, "hbm (matrix bytes written; the tanh arithmetic is FP64)"),
-             "gemm_f64": (flops[4] + flops[2], "GFLOP/s", FP64_PEAK_GFLOPS, "alu (FP64 nominal)"),
-             "chol_inv": (flops[1], "GFLOP/s", FP32_PEAK_GFLOPS if flops[5] > 0.5 * flops[1] else FP64_PEAK_GFLOPS,
+             "gemm_f64": (alg_work["gemm_f64"], "GFLOP/s", FP64_PEAK_GFLOPS, "alu (FP64 nominal)"),
+             "chol_inv": (alg_chol, "GFLOP/s", FP32_PEAK_GFLOPS if flops[5] > 0.5 * flops[1] else FP64_PEAK_GFLOPS,
                           "alu (FP32 nominal)" if flops[5] > 0.5 * flops[1] else "alu (FP64 nominal)"),
              "cg_persistent": (cg_bytes, "GB/s", hbm, "hbm (local operators read per iteration)"),
              "slicing": (flops[6], "GB/s", hbm, "hbm"),
-             "tc_gemm": (flops[3], "GFLOP/s", 1000.0 * float(peaks.get("bf16_tflops_sustained", 1700.0)),
-                         "tensor (BF16 sustained, measured)")}
+             "tc_gemm": (alg_work["tc_gemm"], "GFLOP/s", bf16_peak,
+                         "tensor (BF16 sustained, measured); the method's flops")}
     kernels = {}
     for i, n in enumerate(names):
         if n not in roofs or prof_ms[i] <= 0:
@@ -461,12 +518,24 @@ def main():
     if fp64_cmp is not None:
         line["fp64"] = fp64_cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, dt, ns = oracle_sample(prob, prob.n_sub)  # the whole local setup: ~10-20 s of host work
-        line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count() or 1,
-                                "kind": "oracle",
-                                "sample": f"FP64 oracle local setup of {ns} of {prob.n_sub} subdomains "
-                                          f"({dt:.1f} s), scaled by {prob.n_sub}/{ns}; coarse problem and CG "
-                                          f"left out (favours the oracle)"}
+        # one complete oracle solve of the workload when its dense local
+        # pseudo-inverses fit comfortably in host memory (the 8x8, M = 400
+        # workload: about 30 s on 16 cores); larger workloads are not sampled
+        oracle_bytes = 8.0 * sum(4.0 * d["m"] * d["M"] for d in sub_sizes)
+        if oracle_bytes < 8e9:
+            dt, it = oracle_complete_solve(prob)
+            line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle_threads(),
+                                    "kind": "oracle", "cg_iterations": it,
+                                    "sample": f"one complete FP64 oracle solve of the whole workload ({dt:.1f} s): "
+                                              f"{prob.n_sub} local ridge pseudo-inverses by Householder QR, coarse "
+                                              f"problem, CG to relative residual {TOL}, reconstruction"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
+                                    "sample": f"not run: the oracle's dense local pseudo-inverses need "
+                                              f"{oracle_bytes / 1e9:.0f} GB"}
+    line["gpu_launches_source"] = ("kernel launches of the library counted in the profiled pass (the same "
+                                   f"{args.steps} steps as the timed region, whose captured graphs replay them)")
+    line["graphs"] = graphs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
