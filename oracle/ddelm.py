@@ -28,7 +28,12 @@ Readings where the paper is silent:
   diffusion operator the flux is the normal derivative as well;
 * A-bar^i uses the same rows as the Delta rows of K_c^i (the (T^i)^{-1} C phi
   rows) when the change of variables is on;
-* R_f^i is the plain restriction (no sign), as for R^i.
+* R_f^i is the plain restriction (no sign), as for R^i;
+* biharmonic (op 2, the coupled system of Sec. 2.1): L phi = Lap^2 phi, the
+  boundary rows are phi and Lap phi, and every interface point carries the
+  continuity rows phi and Lap phi and the flux rows d phi/dn and d Lap phi/dn
+  (two interface components, `layout.Layout(n_comp=2)`); the change of
+  variables and A_m act on each component separately.
 """
 from __future__ import annotations
 
@@ -64,11 +69,13 @@ def phi(w, b, xy):
 
 
 def L_phi(w, b, xy, op, a=None, grad_a=None):
-    """L phi for -Lap (op 0) or -div(a grad) (op 1).
+    """L phi for -Lap (op 0), -div(a grad) (op 1) or Lap^2 (op 2).
 
     With t = tanh(z): grad phi = w (1 - t^2), Lap phi = |w|^2 (-2 t (1 - t^2)).
     -div(a grad phi) = -a Lap phi - grad a . grad phi.
     """
+    if op == 2:
+        return bilap_phi(w, b, xy)
     t = np.tanh(_z(w, b, xy))
     s1 = 1.0 - t * t
     w2 = (w * w).sum(1)[None, :]
@@ -78,10 +85,54 @@ def L_phi(w, b, xy, op, a=None, grad_a=None):
     return -a[:, None] * lap - (grad_a @ w.T) * s1
 
 
+# Derivatives of tanh as polynomials in t = tanh z (d^k/dz^k tanh, k = 1..4):
+#   1 - t^2,  -2 t (1 - t^2),  -2 (1 - t^2)(1 - 3 t^2),  8 t (1 - t^2)(2 - 3 t^2).
+# For phi_j(x) = tanh(w_j . x + b_j): Lap phi = |w|^2 times the second,
+# grad Lap phi = |w|^2 w times the third, Lap^2 phi = |w|^4 times the fourth.
+
+def lap_phi(w, b, xy):
+    """Lap phi (the second derivative of tanh times |w|^2)."""
+    t = np.tanh(_z(w, b, xy))
+    w2 = (w * w).sum(1)[None, :]
+    return -2.0 * w2 * t * (1.0 - t * t)
+
+
+def F_lap_phi(w, b, xy, normals):
+    """d(Lap phi)/dn (the third derivative of tanh times |w|^2 (w . n))."""
+    t = np.tanh(_z(w, b, xy))
+    w2 = (w * w).sum(1)[None, :]
+    return -2.0 * w2 * (1.0 - t * t) * (1.0 - 3.0 * t * t) * (normals @ w.T)
+
+
+def bilap_phi(w, b, xy):
+    """Lap^2 phi (the fourth derivative of tanh times |w|^4)."""
+    t = np.tanh(_z(w, b, xy))
+    w2 = (w * w).sum(1)[None, :]
+    return 8.0 * w2 * w2 * t * (1.0 - t * t) * (2.0 - 3.0 * t * t)
+
+
 def F_phi(w, b, xy, normals):
     """F phi = d phi / dn = (w . n)(1 - t^2)."""
     t = np.tanh(_z(w, b, xy))
     return (normals @ w.T) * (1.0 - t * t)
+
+
+def C_rows(w, b, xy, comp):
+    """Continuity / boundary rows: phi for component 0, Lap phi for component 1."""
+    out = phi(w, b, xy)
+    one = np.asarray(comp) == 1
+    if one.any():
+        out[one] = lap_phi(w, b, xy[one])
+    return out
+
+
+def F_rows(w, b, xy, normals, comp):
+    """Flux rows: d phi/dn for component 0, d Lap phi/dn for component 1."""
+    out = F_phi(w, b, xy, normals)
+    one = np.asarray(comp) == 1
+    if one.any():
+        out[one] = F_lap_phi(w, b, xy[one], normals[one])
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -111,7 +162,8 @@ class DDELMOracle:
         skips the coarse problem (used to time a bounded sample of the setup)."""
         self.p = prob
         self.o = opts or Options()
-        self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts, use_Am=self.o.use_Am)
+        self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts, use_Am=self.o.use_Am,
+                          n_comp=2 if prob.op == 2 else 1)
         self.n_pi, self.n_dl = self.lay.n_pi, self.lay.n_delta
         self._build_local(only)
         if only is None:
@@ -135,9 +187,9 @@ class DDELMOracle:
             aI = p.a_int[Ioff[i]:Ioff[i + 1]]
             gI = p.grad_a_int[Ioff[i]:Ioff[i + 1]]
             rows_I = L_phi(w, b, xI, p.op, aI, gI)
-            rows_B = phi(w, b, sl.bnd_xy)
-            C_pi = phi(w, b, sl.pi_xy)
-            C_dl = phi(w, b, sl.dl_xy)
+            rows_B = C_rows(w, b, sl.bnd_xy, sl.bnd_comp)
+            C_pi = C_rows(w, b, sl.pi_xy, sl.pi_comp)
+            C_dl = C_rows(w, b, sl.dl_xy, sl.dl_comp)
             if o.use_change_of_vars:
                 # (T^i)^{-1} C phi: Delta row minus its weights on the corner rows
                 Tinv_dl = C_dl.copy()
@@ -153,11 +205,11 @@ class DDELMOracle:
             L.K = np.vstack([rows_I, rows_B, C_pi, Tinv_dl])
             L.m = L.K.shape[0]
             # A_m^i: Delta rows are point fluxes, Pi rows the mean edge fluxes
-            F_dl = F_phi(w, b, sl.dl_xy, sl.dl_normal)
+            F_dl = F_rows(w, b, sl.dl_xy, sl.dl_normal, sl.dl_comp)
             A_pi = np.zeros((L.nPi, len(w)))
             for k, terms in enumerate(sl.am_terms):
                 for wgt, xy, nrm in terms:
-                    A_pi[k] += wgt * F_phi(w, b, xy[None, :], np.array([nrm]))[0]
+                    A_pi[k] += wgt * F_rows(w, b, xy[None, :], np.array([nrm]), [sl.pi_comp[k]])[0]
             L.Ahat = np.vstack([A_pi, F_dl])
             L.Kbar = np.vstack([rows_I, rows_B, C_pi, F_dl])
             L.Abar = Tinv_dl

@@ -40,15 +40,30 @@ class SubLayout:
         self.dl_beta = None       # [nDl] T weight on the end vertex
         self.dl_beta_pi = None    # [nDl] local Pi index of the end vertex or -1
         self.am_terms = None      # per local Pi: list of (weight, xy, normal)
+        # interface / boundary component of every row: 0 the value and the normal
+        # derivative of u; 1 (biharmonic) those of Lap u
+        self.bnd_comp = None
+        self.pi_comp = None
+        self.dl_comp = None
 
 
 class Layout:
-    def __init__(self, nx, ny, box, edge_pts, use_Am=True):
+    def __init__(self, nx, ny, box, edge_pts, use_Am=True, n_comp=1):
         """use_Am: the corner rows of A_m (Sec. 3.2); False: the plain flux rows
         of Eq. (ddelm), whose corner row (the corner normal is undefined) is the
         sum over the two edges of the subdomain meeting the corner of the flux
-        there with that edge's normal."""
+        there with that edge's normal.
+
+        n_comp = 2 (the biharmonic coupled system of Sec. 2.1: u and Lap u are
+        both continuous across the interface, and both normal derivatives
+        balance): every boundary, Pi and Delta point carries two rows.  Global
+        numbering: the Dirichlet list holds the u data, then the Lap u data;
+        Gamma = Pi (component 0, then 1), then Delta (component 0, then 1); in a
+        subdomain the rows of component 1 follow those of component 0 in each
+        block, and its change of variables and A_m rows combine rows of the
+        same component."""
         self.use_Am = use_Am
+        self.n_comp = n_comp
         self.nx, self.ny, self.box = nx, ny, box
         self.edge_pts = np.asarray(edge_pts, np.int64)
         x0, x1, y0, y1 = box
@@ -82,6 +97,34 @@ class Layout:
         self.subs = []
         for i in range(nx * ny):
             self.subs.append(self._sub(i, bnd_off, vtx_bnd, dl_off))
+        if n_comp == 2:
+            self._second_component()
+        elif n_comp != 1:
+            raise ValueError("n_comp must be 1 or 2")
+
+    def _second_component(self):
+        nb, npi, nd = self.n_bnd, self.n_pi, self.n_delta
+        for s in self.subs:
+            kb, kp, kd = len(s.bnd_xy), len(s.pi_xy), len(s.dl_xy)
+            s.bnd_xy = np.vstack([s.bnd_xy, s.bnd_xy])
+            s.bnd_gidx = np.concatenate([s.bnd_gidx, s.bnd_gidx + nb])
+            s.bnd_comp = np.repeat([0, 1], kb)
+            s.pi_xy = np.vstack([s.pi_xy, s.pi_xy])
+            s.pi_gidx = np.concatenate([s.pi_gidx, s.pi_gidx + npi])
+            s.pi_vertex = s.pi_vertex + s.pi_vertex
+            s.pi_comp = np.repeat([0, 1], kp)
+            d0 = s.dl_gidx - npi                      # Delta position of component 0
+            s.dl_xy = np.vstack([s.dl_xy, s.dl_xy])
+            s.dl_gidx = np.concatenate([2 * npi + d0, 2 * npi + nd + d0])
+            s.dl_normal = np.vstack([s.dl_normal, s.dl_normal])
+            s.dl_comp = np.repeat([0, 1], kd)
+            s.dl_alpha = np.concatenate([s.dl_alpha, s.dl_alpha])
+            s.dl_beta = np.concatenate([s.dl_beta, s.dl_beta])
+            s.dl_alpha_pi = np.concatenate([s.dl_alpha_pi, np.where(s.dl_alpha_pi >= 0, s.dl_alpha_pi + kp, -1)])
+            s.dl_beta_pi = np.concatenate([s.dl_beta_pi, np.where(s.dl_beta_pi >= 0, s.dl_beta_pi + kp, -1)])
+            s.am_terms = s.am_terms + s.am_terms
+        self.n_bnd, self.n_pi, self.n_delta = 2 * nb, 2 * npi, 2 * nd
+        self.n_gamma = self.n_pi + self.n_delta
 
     # ------------------------------------------------------------------
     def edge_on_boundary(self, eid):
@@ -170,4 +213,7 @@ class Layout:
                     t.append((wgt, pa + k / (e + 1) * (pb - pa), nrm))
             terms.append(t)
         s.am_terms = terms
+        s.bnd_comp = np.zeros(len(s.bnd_xy), np.int64)
+        s.pi_comp = np.zeros(len(s.pi_xy), np.int64)
+        s.dl_comp = np.zeros(len(s.dl_xy), np.int64)
         return s

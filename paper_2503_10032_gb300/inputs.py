@@ -32,6 +32,7 @@ import numpy as np
 
 OP_POISSON = 0
 OP_DIFFUSION = 1
+OP_BIHARMONIC = 2
 
 
 @dataclasses.dataclass
@@ -51,6 +52,7 @@ class Problem:
     edge_pts: np.ndarray     # [n_edges] points strictly inside every grid edge
     f_int: np.ndarray        # [sum n_int, R] forcing at interior points
     g_bnd: np.ndarray        # [n_bnd, R] Dirichlet data at the global boundary points
+                             # (biharmonic: [2 n_bnd, R], the values of u, then of Lap u)
     n_eval: np.ndarray       # [n_sub]
     x_eval: np.ndarray       # [sum n_eval, 2]
     u_eval_exact: np.ndarray  # [sum n_eval, R] exact solution where known (else NaN)
@@ -108,10 +110,13 @@ def boundary_points(nx, ny, box, edge_pts):
 
 
 # ----------------------------------------------------------------------------
-# manufactured solutions: (u, -L u) as functions of (x, y) arrays
+# manufactured solutions: (u, grad u, Lap u[, Lap^2 u]) as functions of (x, y)
+# arrays; the eigenfunctions below have Lap u = -k^2 u, so Lap^2 u = k^4 u
 # ----------------------------------------------------------------------------
 
 def _sin_sin(p, q):
+    k2 = (p * p + q * q) * np.pi ** 2
+
     def u(x, y):
         return np.sin(p * np.pi * x) * np.sin(q * np.pi * y)
 
@@ -120,8 +125,11 @@ def _sin_sin(p, q):
                 q * np.pi * np.sin(p * np.pi * x) * np.cos(q * np.pi * y))
 
     def lap(x, y):
-        return -(p * p + q * q) * np.pi ** 2 * u(x, y)
-    return u, grad, lap
+        return -k2 * u(x, y)
+
+    def bilap(x, y):
+        return k2 * k2 * u(x, y)
+    return u, grad, lap, bilap
 
 
 def _sin2pix_cos3piy():
@@ -134,7 +142,10 @@ def _sin2pix_cos3piy():
 
     def lap(x, y):
         return -13 * np.pi ** 2 * u(x, y)
-    return u, grad, lap
+
+    def bilap(x, y):
+        return 169 * np.pi ** 4 * u(x, y)
+    return u, grad, lap, bilap
 
 
 def coef_a(x, y):
@@ -158,9 +169,10 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
     init: "uniform" (w_hat, b_hat ~ U[-1, 1]) or "paper" (w_hat ~ U[-1,1]^2,
     b_hat = -w_hat . xi with xi uniform in the subdomain's box enlarged by
     r = diam/2 on every side, so that b = -w . xi as in Sec. 4.1).
-    solutions: list of (u, grad u, lap u) triples, one per right-hand side;
-    forcing (optional): list of f(x, y) callables overriding -L u, with g = u on
-    the boundary all the same.  coef (optional, diffusion): (x, y) -> (a, a_x, a_y)
+    solutions: list of (u, grad u, lap u[, bilap u]) tuples, one per right-hand
+    side (the biharmonic operator, op 2, needs bilap: f = Lap^2 u, and the
+    boundary data are u, then Lap u); forcing (optional): list of f(x, y)
+    callables overriding L u, with the boundary data of u all the same.  coef (optional, diffusion): (x, y) -> (a, a_x, a_y)
     in place of coef_a.  exact_known = False: u_eval_exact is NaN (no closed form).
     points = "grid": the interior points of a subdomain are the centres of a
     uniform n x n grid of cells (n_int = n^2) instead of uniform random points.
@@ -207,17 +219,23 @@ def make_problem(nx, ny, M, n_int, edge_pts, *, scale, init, seed, solutions,
     else:
         a, grad_a = np.ones(len(x_int)), np.zeros((len(x_int), 2))
     f_cols, g_cols, u_cols = [], [], []
-    for k, (u, gu, lu) in enumerate(solutions):
+    for k, sol in enumerate(solutions):
+        u, gu, lu = sol[:3]
         X, Y = x_int[:, 0], x_int[:, 1]
         if forcing is not None:
             f = forcing[k](X, Y)
+        elif op == OP_BIHARMONIC:
+            f = sol[3](X, Y)
         elif op == OP_DIFFUSION:
             ux, uy = gu(X, Y)
             f = -a * lu(X, Y) - grad_a[:, 0] * ux - grad_a[:, 1] * uy
         else:
             f = -lu(X, Y)
         f_cols.append(f)
-        g_cols.append(u(xb_pts[:, 0], xb_pts[:, 1]))
+        g = u(xb_pts[:, 0], xb_pts[:, 1])
+        if op == OP_BIHARMONIC:
+            g = np.concatenate([g, lu(xb_pts[:, 0], xb_pts[:, 1])])
+        g_cols.append(g)
         u_cols.append(u(x_ev[:, 0], x_ev[:, 1]) if exact_known else np.full(len(x_ev), np.nan))
     return Problem(nx=nx, ny=ny, box=tuple(float(v) for v in box), op=op, M=Ms,
                    w_hat=np.concatenate(w_hat), b_hat=np.concatenate(b_hat),
@@ -372,16 +390,19 @@ def fourier_coefficients():
     return np.random.default_rng(10040).standard_normal(16)
 
 
-def paper_scale(n, seed=2001, max_neurons=1024):
-    """The paper's ablation setting (Sec. 4.1, Sec. 4.2): n x n subdomains of the
-    unit square, 2^16 neurons in total (2^16 / n^2 per subdomain, capped at
+def paper_scale(n, seed=2001, max_neurons=1024, op=OP_POISSON):
+    """The paper's setting (Sec. 4.1, Sec. 4.2, Sec. 4.5): n x n subdomains of
+    the unit square, 2^16 neurons in total (2^16 / n^2 per subdomain, capped at
     max_neurons, the library's per-subdomain limit), a (320 / n) x (320 / n)
     uniform grid per subdomain (cell centres inside, 320 / n points on every
-    edge), the paper's initialisation with l = 32, u = sin(pi x) sin(pi y)."""
+    edge), the paper's initialisation with l = 32 (Poisson) or l = 64
+    (biharmonic), u = sin(pi x) sin(pi y)."""
     g = 320 // n
     M = min(2 ** 16 // (n * n), max_neurons)
-    return make_problem(n, n, M, g * g, g, scale=32.0, init="paper", seed=seed, solutions=[_sin_sin(1, 1)],
-                        points="grid", name=f"paper_{n}x{n}")
+    scale = 64.0 if op == OP_BIHARMONIC else 32.0
+    tag = "biharmonic" if op == OP_BIHARMONIC else "paper"
+    return make_problem(n, n, M, g * g, g, scale=scale, init="paper", seed=seed, solutions=[_sin_sin(1, 1)],
+                        points="grid", op=op, name=f"{tag}_{n}x{n}")
 
 
 def small_uneven_problem(nx=4, ny=3, M_range=(20, 90), seed=13, n_rhs=1, init="paper", scale=8.0):
