@@ -29,11 +29,19 @@ Readings where the paper is silent:
 * A-bar^i uses the same rows as the Delta rows of K_c^i (the (T^i)^{-1} C phi
   rows) when the change of variables is on;
 * R_f^i is the plain restriction (no sign), as for R^i;
-* biharmonic (op 2, the coupled system of Sec. 2.1): L phi = Lap^2 phi, the
-  boundary rows are phi and Lap phi, and every interface point carries the
-  continuity rows phi and Lap phi and the flux rows d phi/dn and d Lap phi/dn
-  (two interface components, `layout.Layout(n_comp=2)`); the change of
-  variables and A_m act on each component separately.
+* biharmonic (op 2, the coupled system of Sec. 2.1): every boundary and
+  interface point carries two components (`layout.Layout(n_comp=2)`), u and
+  v = Lap u / s^2 (s the hidden-layer scale): the loss terms are reweighted
+  (Sec. 1 announces a reweighting and never gives it) by writing the system
+  for u and v, i.e. every Laplacian divided by s^2: interior rows
+  Lap^2 phi / s^4 with data f / s^4, boundary rows phi and Lap phi / s^2 with
+  data g_1 and g_2 / s^2, continuity rows phi and Lap phi / s^2, flux rows
+  d phi/dn and (d Lap phi/dn) / s^2; mu of component 1 is v.  The change of
+  variables and A_m act on each component separately;
+* vanilla DDELM (`Options.use_coarse = False`, Sec. 2.2.1): no coarse space;
+  every cross point is an interface unknown of the Delta set shared by its
+  four subdomains, with the plain corner flux row (the sum of the fluxes
+  with the two edge normals of the subdomain there).
 """
 from __future__ import annotations
 
@@ -51,6 +59,7 @@ class Options:
     eps_rel: float = 1e-8          # ridge reading (module docstring)
     use_change_of_vars: bool = True  # K_c instead of K (Sec. 3.2)
     use_Am: bool = True             # A_m instead of the plain flux rows A (Sec. 3.2)
+    use_coarse: bool = True         # False: vanilla DDELM (Sec. 2.2.1), cross points in Delta, Pi empty
     tol: float = 1e-9              # CG relative residual (Sec. 4)
     max_iters: int = 20000
 
@@ -117,21 +126,21 @@ def F_phi(w, b, xy, normals):
     return (normals @ w.T) * (1.0 - t * t)
 
 
-def C_rows(w, b, xy, comp):
-    """Continuity / boundary rows: phi for component 0, Lap phi for component 1."""
+def C_rows(w, b, xy, comp, w_c1=1.0):
+    """Continuity / boundary rows: phi for component 0, w_c1 Lap phi for component 1."""
     out = phi(w, b, xy)
     one = np.asarray(comp) == 1
     if one.any():
-        out[one] = lap_phi(w, b, xy[one])
+        out[one] = w_c1 * lap_phi(w, b, xy[one])
     return out
 
 
-def F_rows(w, b, xy, normals, comp):
-    """Flux rows: d phi/dn for component 0, d Lap phi/dn for component 1."""
+def F_rows(w, b, xy, normals, comp, w_c1=1.0):
+    """Flux rows: d phi/dn for component 0, w_c1 d Lap phi/dn for component 1."""
     out = F_phi(w, b, xy, normals)
     one = np.asarray(comp) == 1
     if one.any():
-        out[one] = F_lap_phi(w, b, xy[one], normals[one])
+        out[one] = w_c1 * F_lap_phi(w, b, xy[one], normals[one])
     return out
 
 
@@ -163,7 +172,7 @@ class DDELMOracle:
         self.p = prob
         self.o = opts or Options()
         self.lay = Layout(prob.nx, prob.ny, prob.box, prob.edge_pts, use_Am=self.o.use_Am,
-                          n_comp=2 if prob.op == 2 else 1)
+                          n_comp=2 if prob.op == 2 else 1, use_coarse=self.o.use_coarse)
         self.n_pi, self.n_dl = self.lay.n_pi, self.lay.n_delta
         self._build_local(only)
         if only is None:
@@ -186,10 +195,13 @@ class DDELMOracle:
             xI = p.x_int[Ioff[i]:Ioff[i + 1]]
             aI = p.a_int[Ioff[i]:Ioff[i + 1]]
             gI = p.grad_a_int[Ioff[i]:Ioff[i + 1]]
-            rows_I = L_phi(w, b, xI, p.op, aI, gI)
-            rows_B = C_rows(w, b, sl.bnd_xy, sl.bnd_comp)
-            C_pi = C_rows(w, b, sl.pi_xy, sl.pi_comp)
-            C_dl = C_rows(w, b, sl.dl_xy, sl.dl_comp)
+            # biharmonic: the system in u and v = Lap u / s^2 (module docstring)
+            w_int = p.scale ** -4 if p.op == 2 else 1.0
+            w_c1 = p.scale ** -2 if p.op == 2 else 1.0
+            rows_I = w_int * L_phi(w, b, xI, p.op, aI, gI)
+            rows_B = C_rows(w, b, sl.bnd_xy, sl.bnd_comp, w_c1)
+            C_pi = C_rows(w, b, sl.pi_xy, sl.pi_comp, w_c1)
+            C_dl = C_rows(w, b, sl.dl_xy, sl.dl_comp, w_c1)
             if o.use_change_of_vars:
                 # (T^i)^{-1} C phi: Delta row minus its weights on the corner rows
                 Tinv_dl = C_dl.copy()
@@ -205,15 +217,16 @@ class DDELMOracle:
             L.K = np.vstack([rows_I, rows_B, C_pi, Tinv_dl])
             L.m = L.K.shape[0]
             # A_m^i: Delta rows are point fluxes, Pi rows the mean edge fluxes
-            F_dl = F_rows(w, b, sl.dl_xy, sl.dl_normal, sl.dl_comp)
+            F_dl = F_rows(w, b, sl.dl_xy, sl.dl_normal, sl.dl_comp, w_c1)
             A_pi = np.zeros((L.nPi, len(w)))
             for k, terms in enumerate(sl.am_terms):
                 for wgt, xy, nrm in terms:
-                    A_pi[k] += wgt * F_rows(w, b, xy[None, :], np.array([nrm]), [sl.pi_comp[k]])[0]
+                    A_pi[k] += wgt * F_rows(w, b, xy[None, :], np.array([nrm]), [sl.pi_comp[k]], w_c1)[0]
             L.Ahat = np.vstack([A_pi, F_dl])
             L.Kbar = np.vstack([rows_I, rows_B, C_pi, F_dl])
             L.Abar = Tinv_dl
-            L.f = np.vstack([p.f_int[Ioff[i]:Ioff[i + 1]], p.g_bnd[sl.bnd_gidx],
+            g_w = np.where(np.asarray(sl.bnd_comp) == 1, w_c1, 1.0)[:, None]
+            L.f = np.vstack([w_int * p.f_int[Ioff[i]:Ioff[i + 1]], g_w * p.g_bnd[sl.bnd_gidx],
                              np.zeros((L.nG, p.n_rhs))])
             L.gpi = sl.pi_gidx                       # R_Pi^i as an index map
             L.gdl = sl.dl_gidx - self.n_pi           # R_Delta^i (= R_f^i) as an index map

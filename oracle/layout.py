@@ -48,7 +48,7 @@ class SubLayout:
 
 
 class Layout:
-    def __init__(self, nx, ny, box, edge_pts, use_Am=True, n_comp=1):
+    def __init__(self, nx, ny, box, edge_pts, use_Am=True, n_comp=1, use_coarse=True):
         """use_Am: the corner rows of A_m (Sec. 3.2); False: the plain flux rows
         of Eq. (ddelm), whose corner row (the corner normal is undefined) is the
         sum over the two edges of the subdomain meeting the corner of the flux
@@ -61,9 +61,18 @@ class Layout:
         Gamma = Pi (component 0, then 1), then Delta (component 0, then 1); in a
         subdomain the rows of component 1 follow those of component 0 in each
         block, and its change of variables and A_m rows combine rows of the
-        same component."""
+        same component.
+
+        use_coarse = False: vanilla DDELM (Sec. 2.2.1, Eq. (schur)), no coarse
+        space: Pi is empty and every cross point is an interface point of the
+        Delta set shared by its four subdomains, numbered before the edge
+        points (in cross-point order).  Its flux row in subdomain i is the plain
+        one of Eq. (ddelm) with the undefined corner normal resolved as in the
+        plain-A reading above: the sum of the outward normals of the two edges
+        of subdomain i that meet there (the flux is linear in the normal)."""
         self.use_Am = use_Am
         self.n_comp = n_comp
+        self.use_coarse = use_coarse
         self.nx, self.ny, self.box = nx, ny, box
         self.edge_pts = np.asarray(edge_pts, np.int64)
         x0, x1, y0, y1 = box
@@ -85,9 +94,10 @@ class Layout:
                     nb += 1
         self.n_bnd = nb
         # global Gamma
-        self.n_pi = (nx - 1) * (ny - 1)
+        n_cross = (nx - 1) * (ny - 1)
+        self.n_pi = n_cross if use_coarse else 0
         dl_off = {}
-        nd = 0
+        nd = 0 if use_coarse else n_cross      # vanilla: the cross points open the Delta list
         for eid in range(self.n_edges):
             if not self.edge_on_boundary(eid):
                 dl_off[eid] = self.n_pi + nd
@@ -170,12 +180,26 @@ class Layout:
                 bg.append(vtx_bnd[v])
         s.bnd_xy = np.array(bxy).reshape(-1, 2)
         s.bnd_gidx = np.array(bg, np.int64)
-        pis = [v for v in (BL, BR, TL, TR) if self.is_cross(v)]
+        crosses = [v for v in (BL, BR, TL, TR) if self.is_cross(v)]
+        pis = crosses if self.use_coarse else []
         s.pi_vertex = pis
         s.pi_xy = np.array([self.vxy(v) for v in pis]).reshape(-1, 2)
         s.pi_gidx = np.array([self.pi_index(v) for v in pis], np.int64)
         loc_pi = {v: k for k, v in enumerate(pis)}
         dxy, dg, dn, al, alp, be, bep = [], [], [], [], [], [], []
+        if not self.use_coarse:
+            for v in crosses:
+                nsum = np.zeros(2)
+                for eid, a, b, nrm in edges:
+                    if v in (a, b):
+                        nsum += nrm
+                dxy.append(self.vxy(v))
+                dg.append(self.pi_index(v))          # Delta index = cross-point order
+                dn.append(nsum)
+                al.append(0.0)
+                alp.append(-1)
+                be.append(0.0)
+                bep.append(-1)
         for eid, a, b, nrm in edges:
             if self.edge_on_boundary(eid):
                 continue

@@ -13,6 +13,9 @@ assembled by applying the operator to unit vectors and solved by Cholesky
   diffusion_4x4_m1000_r16   the same (the 32x32 workload's per-subdomain shape)
   poisson_8x8_grf           the same (g = 0, f a GRF with alpha = 32, Sec. 4.3)
   varcoef_8x8_grf           the same (-div(rho grad u) = 1, rho = tanh(GRF) + 1.1, Sec. 4.4)
+  biharmonic_16x16          the same (Lap^2 u = f, u = Lap u = 0 on the boundary, Sec. 4.5:
+                            256 subdomains, M = 256, a 20 x 20 grid, l = 64; the
+                            system in u and v = Lap u / s^2)
   poisson_8x8_fourier       U = du/da (u at the evaluation points for each of the
                             16 Fourier modes as forcing, g = 0: u is linear in a),
                             and dL/ds for two losses by a fourth-order central
@@ -41,7 +44,7 @@ OPTS = dict(theta=0.999, eps_rel=1e-8)
 MU_SEED = 7001
 SCALE_STEP = 1e-3          # relative step of the scale difference
 SOLUTION_SETS = ("poisson_8x8_m400", "poisson_16x16_uneven", "diffusion_4x4_m1000_r16", "poisson_8x8_grf",
-                 "varcoef_8x8_grf")
+                 "varcoef_8x8_grf", "biharmonic_16x16")
 
 
 def _save(name, what, arr, head):

@@ -97,7 +97,8 @@ def test_biharmonic_structured_equals_dense_bruteforce(case):
 
 def test_biharmonic_plain_flux_rows():
     """Plain A (Eq. (ddelm)) for the second component: a corner row is d Lap phi/dn
-    at the corner with each of the two edges' outward normals, summed."""
+    at the corner with each of the two edges' outward normals, summed (divided
+    by s^2: the second component is Lap u / s^2)."""
     p = inputs.small_problem(3, 3, M=12, n_int=40, edge_pts=3, n_rhs=1, seed=9, op=inputs.OP_BIHARMONIC)
     o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6, use_Am=False))
     L, sl = o.loc[4], o.lay.subs[4]
@@ -107,8 +108,8 @@ def test_biharmonic_plain_flux_rows():
         xy = o.lay.vxy(v)[None, :]
         nx_ = 1.0 if v[0] == 2 else -1.0
         ny_ = 1.0 if v[1] == 2 else -1.0
-        want = ddelm.F_lap_phi(L.w, L.b, xy, np.array([[nx_, 0.0]])) + \
-            ddelm.F_lap_phi(L.w, L.b, xy, np.array([[0.0, ny_]]))
+        want = (ddelm.F_lap_phi(L.w, L.b, xy, np.array([[nx_, 0.0]])) +
+                ddelm.F_lap_phi(L.w, L.b, xy, np.array([[0.0, ny_]]))) / p.scale ** 2
         np.testing.assert_allclose(L.Ahat[k], want[0], rtol=1e-13, atol=1e-13 * np.abs(want).max())
 
 
@@ -159,3 +160,41 @@ def test_biharmonic_manufactured_solution_converges():
         errs.append(np.linalg.norm(r["u_eval"] - p.u_eval_exact, axis=0) / np.linalg.norm(p.u_eval_exact, axis=0))
     assert errs[1][0] < 1e-3 and errs[1][1] < 0.1
     assert np.all(errs[1] < 0.05 * errs[0])
+
+
+def test_biharmonic_reweighting():
+    """The biharmonic system is written for u and v = Lap u / s^2: interior rows
+    Lap^2 phi / s^4 with data f / s^4; the second component's boundary,
+    continuity and flux rows Lap phi / s^2 and (d Lap phi/dn) / s^2, with the
+    boundary data Lap u / s^2; the first component's rows unscaled."""
+    p = inputs.small_problem(3, 3, M=14, n_int=50, edge_pts=2, n_rhs=1, seed=4, op=inputs.OP_BIHARMONIC)
+    o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6))
+    s = p.scale
+    L, sl = o.loc[4], o.lay.subs[4]
+    i0 = int(p.n_int[:4].sum())
+    xI = p.x_int[i0:i0 + L.nI]
+    np.testing.assert_allclose(L.K[:L.nI], ddelm.bilap_phi(L.w, L.b, xI) / s ** 4, rtol=1e-14, atol=0)
+    kb = L.nB // 2
+    np.testing.assert_allclose(L.K[L.nI:L.nI + kb], ddelm.phi(L.w, L.b, sl.bnd_xy[:kb]), rtol=1e-14, atol=0)
+    np.testing.assert_allclose(L.K[L.nI + kb:L.nI + L.nB], ddelm.lap_phi(L.w, L.b, sl.bnd_xy[kb:]) / s ** 2,
+                               rtol=1e-14, atol=0)
+    kd = L.nDl // 2
+    F1 = ddelm.F_lap_phi(L.w, L.b, sl.dl_xy[kd:], sl.dl_normal[kd:]) / s ** 2
+    np.testing.assert_allclose(L.Ahat[L.nPi + kd:], F1, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(L.Kbar[L.m - kd:], F1, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(L.f[:L.nI, 0], p.f_int[i0:i0 + L.nI, 0] / s ** 4, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(L.f[L.nI + kb:L.nI + L.nB, 0], p.g_bnd[sl.bnd_gidx[kb:], 0] / s ** 2, rtol=1e-15,
+                               atol=0)
+
+
+def test_biharmonic_paper_scale_subdomains():
+    """Subdomains of side 1/16 with the paper's l = 64 and 256 neurons (the
+    16x16 case of Sec. 4.5), on a 4x4 patch: the reweighted system reaches a
+    small error where unit weights do not (the Lap^2 phi rows are ~1e8 larger
+    than the point values and, with the ridge, bury the continuity of u)."""
+    p = inputs.make_problem(4, 4, 256, 400, 20, scale=64.0, init="paper", seed=2001,
+                            solutions=[inputs._sin_sin(1, 1)], op=inputs.OP_BIHARMONIC, points="grid",
+                            box=(0.0, 0.25, 0.0, 0.25))
+    r = ddelm.solve(p, ddelm.Options(eps_rel=1e-8, theta=0.999))
+    err = np.linalg.norm(r["u_eval"] - p.u_eval_exact) / np.linalg.norm(p.u_eval_exact)
+    assert err < 1e-5, err

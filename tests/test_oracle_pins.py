@@ -253,6 +253,71 @@ def test_no_cross_points_is_vanilla_ddelm():
     assert _rel(np.concatenate(cs), c_ref) < 1e-9
 
 
+@pytest.mark.parametrize("op", [0, 2])
+def test_vanilla_ddelm_with_cross_points(op):
+    """use_coarse = False (vanilla DDELM, Sec. 2.2.1): every cross point is an
+    interface unknown of its four subdomains, with the plain corner flux rows;
+    the structured system equals the literal Eq. (schur) Schur complement."""
+    p = inputs.small_problem(3, 3, M=30, n_int=90, edge_pts=3, seed=5, op=op)
+    o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6, theta=0.0, use_coarse=False))
+    nc = 2 if op == 2 else 1
+    assert o.n_pi == 0 and o.n_dl == nc * (4 + 12 * 3)
+    cnt = np.zeros(o.n_dl, np.int64)
+    for L in o.loc:
+        np.add.at(cnt, L.gdl, 1)
+    assert sorted(set(cnt.tolist())) == [2, 4] and (cnt == 4).sum() == 4 * nc
+    # the centre subdomain's corner rows: the flux with each edge's outward normal, summed
+    L, sl = o.loc[4], o.lay.subs[4]
+    for k in range(4):
+        xy = sl.dl_xy[k:k + 1]
+        nrm = sl.dl_normal[k]
+        assert abs(nrm[0]) == 1.0 and abs(nrm[1]) == 1.0
+        want = ddelm.F_phi(L.w, L.b, xy, np.array([[nrm[0], 0.0]])) + \
+            ddelm.F_phi(L.w, L.b, xy, np.array([[0.0, nrm[1]]]))
+        np.testing.assert_allclose(L.Ahat[k], want[0], rtol=1e-12, atol=1e-13 * np.abs(want).max())
+    g = dense.global_system(o)
+    K, B, A, f = g["K"], g["B"], g["A"], g["f"]
+    Kp = np.linalg.pinv(K)
+    D, dd = -A @ Kp @ B, -A @ Kp @ f
+    S = B.T @ B + D.T @ D - B.T @ K @ Kp @ B
+    rhs = (B.T - B.T @ K @ Kp) @ f + D.T @ dd
+    mu, S_o, b_o = o.solve_direct()
+    assert _rel(S_o, S) < 1e-10 and _rel(b_o, rhs) < 1e-10
+    cs, _ = o.reconstruct(mu)
+    assert _rel(np.concatenate(cs), Kp @ (f - B @ mu)) < 1e-8
+
+
+def test_vanilla_consistent_system_exact_recovery():
+    """A consistent Eq. (ddelm) on a grid with cross points is solved exactly by
+    vanilla DDELM (ridge off)."""
+    p = inputs.small_problem(3, 2, M=16, n_int=60, edge_pts=3, scale=4.0, seed=5)
+    o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=0.0, theta=0.0, use_coarse=False))
+    g = dense.global_system(o)
+    nc, nG = g["K"].shape[1], g["B"].shape[1]
+    rows, r0 = [], 0
+    for L in o.loc:
+        M = L.K.shape[1]
+        sel = np.zeros((L.nG, g["K"].shape[0]))
+        sel[np.arange(L.nG), r0 + L.m - L.nG + np.arange(L.nG)] = 1.0
+        rows.append(sel)
+        r0 += L.m + M
+    SelG = np.vstack(rows)
+    C = np.vstack([np.hstack([SelG @ g["K"], SelG @ g["B"]]), np.hstack([g["A"], np.zeros((nG, nG))])])
+    N = sla.null_space(C)
+    z = N @ np.random.default_rng(3).standard_normal(N.shape[1])
+    c_star, mu_star = z[:nc], z[nc:]
+    off_c = 0
+    for L in o.loc:
+        M = L.K.shape[1]
+        nIB = L.m - L.nG
+        L.f = np.zeros((L.m, 1))
+        L.f[:nIB, 0] = L.K[:nIB] @ c_star[off_c:off_c + M]
+        off_c += M
+    o._build_coarse()
+    mu, _, _ = o.solve_direct()
+    assert _rel(mu[:, 0], mu_star) < 1e-8
+
+
 def test_symmetric_positive_definite():
     p = inputs.small_problem(3, 3, M=12, n_int=50, edge_pts=3, seed=9)
     o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-8))
