@@ -71,8 +71,20 @@ extern "C" {
 #define DDELM_ERR_TIMEOUT (-5)        /* a device-side grid barrier gave up waiting */
 #define DDELM_ERR_UNSUPPORTED (-6)    /* an option or size this build does not support */
 
-#define DDELM_OP_POISSON 0   /* L = -Laplacian */
-#define DDELM_OP_DIFFUSION 1 /* L = -div(a grad), a and grad a given at x_int */
+#define DDELM_OP_POISSON 0    /* L = -Laplacian */
+#define DDELM_OP_DIFFUSION 1  /* L = -div(a grad), a and grad a given at x_int */
+#define DDELM_OP_BIHARMONIC 2 /* L = Laplacian^2, the coupled system of Sec. 2.1: u and Lap u given on
+                                 the boundary; u and Lap u continuous across the interface and both
+                                 normal derivatives balanced, so every boundary and interface point
+                                 carries two unknowns (component 0: u, component 1: Lap u). The
+                                 Dirichlet list and the interface are numbered component 0 first:
+                                 g = [u on the n_bnd/2 points; Lap u on the same points],
+                                 Gamma = [Pi u; Pi Lap u; Delta u; Delta Lap u]. The change of
+                                 variables and A_m (Sec. 3.2) act on each component separately.
+                                 The loss terms are reweighted by writing the system for u and
+                                 v = Lap u / s^2 (s = scale > 0 required): interior rows and f
+                                 times s^-4, every row of the second component and its boundary
+                                 data times s^-2; mu of the second component is v. */
 
 #define DDELM_PREC_FP64 0  /* every step in FP64 */
 #define DDELM_PREC_MIXED 1 /* FP32 inner CG with FP64 true-residual refinement */
@@ -119,12 +131,18 @@ typedef struct ddelm_options {
                              the two edges); 1: the plain flux rows A of Eq. (ddelm), the corner
                              row being the sum, over the two edges of the subdomain that meet the
                              corner, of the flux at the corner with that edge's normal */
+  int vanilla;            /* 1: vanilla DDELM (Sec. 2.2.1, Eq. (schur)), no coarse space: Pi is empty
+                             and every cross point is an interface unknown of its four subdomains,
+                             numbered first in Delta (in the order (vy-1)(nx-1) + vx-1), with the
+                             plain corner flux row above; requires theta = 0 (the NN map of
+                             Sec. 3.1 belongs to the coarse-space method). 0: the coarse space
+                             of Sec. 3 */
 } ddelm_options;
 
 typedef struct ddelm_problem {
   int nx, ny;               /* subdomains per direction (>= 1 each) */
   double x0, x1, y0, y1;    /* the rectangle */
-  int op;                   /* DDELM_OP_POISSON or DDELM_OP_DIFFUSION */
+  int op;                   /* DDELM_OP_POISSON, DDELM_OP_DIFFUSION or DDELM_OP_BIHARMONIC */
   int n_rhs;                /* right-hand sides solved together (>= 1) */
   const int *M;             /* [n_sub] neurons per subdomain (1..1024) */
   const double *w_hat;      /* [sum M][2] hidden weights before scaling */
@@ -142,8 +160,8 @@ typedef struct ddelm_problem {
 
 typedef struct ddelm_sizes {
   int n_sub, n_edges;
-  int n_bnd;           /* length of the global Dirichlet list */
-  int n_pi, n_delta;   /* |Pi|, |Delta| */
+  int n_bnd;           /* length of the global Dirichlet list (biharmonic: both components) */
+  int n_pi, n_delta;   /* |Pi|, |Delta| (biharmonic: both components) */
   long long sum_M, sum_int, sum_eval;
   size_t workspace_bytes; /* device workspace ddelm_setup needs */
   size_t upload_bytes;    /* host-to-device bytes ddelm_setup copies (tables + problem data) */
@@ -209,7 +227,8 @@ int ddelm_solve(ddelm_handle *h, const double *d_f_int, const double *d_g_bnd, d
  * derivative of the ridge pseudo-inverse, low-rank cotangents of K_c^i, K-bar^i,
  * A_m^i, A-bar^i and the evaluation matrix, contracted with their analytic
  * s-derivatives (the ridge eps^2 = eps_rel^2 |K|_F^2 / M included).  It uses
- * the setup scratch of the workspace.
+ * the setup scratch of the workspace.  Not available for DDELM_OP_BIHARMONIC
+ * (DDELM_ERR_UNSUPPORTED when h_grad_scale is given).
  *
  * info as in ddelm_solve (iterations of the adjoint CG; rel_residual is not
  * computed and reads 0). */

@@ -7,8 +7,13 @@ on the paper's problem u = sin(pi x) sin(pi y) at the paper's scale
 subdomain).  CG runs to the paper's relative residual 1e-9.
 
     python -m paper_2503_10032_gb300.ablation [--grids 2,4,8,16] [--precision fp64|mixed]
+    python -m paper_2503_10032_gb300.ablation --table6 [--grids 2,4,8,16]
 
-Prints one JSON line per solve and the two tables in markdown.
+Prints one JSON line per solve and the two tables in markdown.  --table6: the
+biharmonic problem of Sec. 4.5 (Lap^2 u = f, u = Lap u = 0 on the boundary,
+u = sin(pi x) sin(pi y), l = 64) solved by vanilla DDELM (no coarse space),
+DDELM-CS (theta = 0) and DDELM-NN (theta = 0.999, K_c and A_m), with the GPU
+time of one setup + solve.
 """
 from __future__ import annotations
 
@@ -22,18 +27,51 @@ VARIANTS = [("K, A", False, False), ("K_c, A", True, False), ("K, A_m", False, T
 THETAS = [0.0, 0.5, 0.9, 0.99, 0.999, 0.9999, 1.0]
 
 
-def run_one(D, prob, torch, **kw):
+def run_one(D, prob, torch, timed=False, **kw):
     s = D.Solver(prob, **kw)
     f = torch.tensor(prob.f_int, dtype=torch.float64, device="cuda")
     g = torch.tensor(prob.g_bnd, dtype=torch.float64, device="cuda")
     c, mu, u, info, rc = s.solve(f, g)
     torch.cuda.synchronize()
+    out = {}
+    if timed:
+        # one more setup + solve on the same handle, timed with events on the current stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.refactor()
+        c, mu, u, info, rc = s.solve(f, g)
+        e1.record()
+        torch.cuda.synchronize()
+        out["setup_solve_ms"] = float(e0.elapsed_time(e1))
     u = u.cpu().numpy()[:, 0]
     ex = prob.u_eval_exact[:, 0]
     err = float(np.linalg.norm(u - ex) / np.linalg.norm(ex))
     s.close()
     return dict(iterations=int(info.iterations), rel_residual=float(info.rel_residual), status=int(rc),
-                rel_l2_error=err)
+                rel_l2_error=err, **out)
+
+
+def table6(D, torch, grids, prec, args):
+    """Sec. 4.5: DDELM, DDELM-CS and DDELM-NN on the biharmonic problem."""
+    from . import inputs
+    rows = {}
+    for n in grids:
+        prob = inputs.paper_scale(n, op=inputs.OP_BIHARMONIC)
+        nG = 2 * (4 * (320 // n) + 4)
+        p = prec if nG <= 256 else D.DDELM_PREC_FP64   # MIXED holds at most 256 interface rows per subdomain
+        for name, kw in (("DDELM", dict(theta=0.0, use_coarse=False)), ("DDELM-CS", dict(theta=0.0)),
+                         ("DDELM-NN", dict(theta=0.999))):
+            r = run_one(D, prob, torch, timed=True, eps_rel=args.eps_rel, tol=1e-9, max_iters=args.max_iters,
+                        precision=p, **kw)
+            r["precision"] = "fp64" if p == D.DDELM_PREC_FP64 else "mixed"
+            rows[(name, n)] = r
+            print(json.dumps(dict(table=6, grid=f"{n}x{n}", M=int(prob.M[0]), method=name, **r)), flush=True)
+    print("\nTable 6 (biharmonic, u = sin(pi x) sin(pi y))\n")
+    print("| method | grid | M | rel. L2 error | iterations | setup + solve (ms) | precision |")
+    print("|---|---|---|---|---|---|---|")
+    for (name, n), r in sorted(rows.items(), key=lambda kv: (kv[0][0], kv[0][1])):
+        print(f"| {name} | {n}x{n} | {min(2 ** 16 // (n * n), 1024)} | {r['rel_l2_error']:.2e} | {r['iterations']} | "
+              f"{r['setup_solve_ms']:.1f} | {r['precision']} |")
 
 
 def main(argv=None):
@@ -42,6 +80,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--eps-rel", type=float, default=1e-8)
     ap.add_argument("--max-iters", type=int, default=60000)
+    ap.add_argument("--table6", action="store_true")
     args = ap.parse_args(argv)
     import torch
     from . import build
@@ -50,6 +89,9 @@ def main(argv=None):
     from . import inputs
     prec = D.DDELM_PREC_FP64 if args.precision == "fp64" else D.DDELM_PREC_MIXED
     grids = [int(x) for x in args.grids.split(",")]
+    if args.table6:
+        table6(D, torch, grids, prec, args)
+        return 0
     t1, t2 = {}, {}
     for n in grids:
         prob = inputs.paper_scale(n)

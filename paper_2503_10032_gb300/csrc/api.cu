@@ -578,6 +578,7 @@ int ddelm_backward(ddelm_handle *h, const double *d_grad_c, const double *d_grad
                    double *d_grad_g, double *h_grad_scale, ddelm_solve_info *info, void *stream) {
   if (!h) return DDELM_ERR_INVALID_ARG;
   Plan &p = h->plan;
+  if (h_grad_scale && p.op == DDELM_OP_BIHARMONIC) return DDELM_ERR_UNSUPPORTED;
   if (h_grad_scale && (!h->fwd_valid || p.inv_scale == 0.0)) return DDELM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double *db = dbase(h);

@@ -287,20 +287,24 @@ __device__ void ph_dl_first(const Ctx &c, const double *piv, const double *x, co
   }
 }
 
-// Δ gather: out[δ] = s * (slab[A] + slab[B]) + t * add[δ]
+// sum of a slab column over the owners of Δ point p: two, or four for the
+// cross points of vanilla DDELM (rows -1 past the owners)
+__device__ __forceinline__ double dl_owner_sum(const Ctx &c, const double *slab, int p, int k) {
+  const int4 rw = *reinterpret_cast<const int4 *>(c.ints + c.o_dl_rows + 4 * p);
+  double v = ldg_cg(slab + (long long)rw.x * c.R + k) + ldg_cg(slab + (long long)rw.y * c.R + k);
+  if (rw.z >= 0) v += ldg_cg(slab + (long long)rw.z * c.R + k) + ldg_cg(slab + (long long)rw.w * c.R + k);
+  return v;
+}
+
+// Δ gather: out[δ] = s * (sum of slab over the owners) + t * add[δ]
 __device__ void ph_dl_gather(const Ctx &c, int sl, double s, double *out, const double *add, double t,
                              int sl2, double *out2) {
   for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
     const int p = e / c.R, k = e % c.R;
-    const int sa = c.ints[c.o_dl_own + 4 * p], la = c.ints[c.o_dl_own + 4 * p + 1];
-    const int sb = c.ints[c.o_dl_own + 4 * p + 2], lb = c.ints[c.o_dl_own + 4 * p + 3];
-    const SubDev &da = c.subs[sa];
-    const SubDev &dB = c.subs[sb];
-    const double v = ldg_cg(slab_row(c, sl, da, da.nPi + la) + k) + ldg_cg(slab_row(c, sl, dB, dB.nPi + lb) + k);
-    double r = s * v;
+    double r = s * dl_owner_sum(c, c.slab[sl], p, k);
     if (add) r = fma(t, ldg_cg(add + e), r);
     out[e] = r;
-    if (out2) out2[e] = ldg_cg(slab_row(c, sl2, da, da.nPi + la) + k) + ldg_cg(slab_row(c, sl2, dB, dB.nPi + lb) + k);
+    if (out2) out2[e] = dl_owner_sum(c, c.slab[sl2], p, k);
   }
 }
 
@@ -643,11 +647,13 @@ __device__ __forceinline__ int n_chunks(const Ctx &c) {
   return ch < 1 ? 1 : (ch > 8 ? 8 : ch);
 }
 
-// gathered slab sum at the Delta point of local interface row (d, a): the two
-// owners' rows (column k)
+// gathered slab sum at the Delta point of local interface row (d, a): its
+// owners' rows (two, or four for a cross point of vanilla DDELM), column k
 __device__ __forceinline__ float gam_pair(const Ctx &c, int sl, const SubDev &d, int a, int k) {
-  const int2 rw = *reinterpret_cast<const int2 *>(c.ints + c.o_gam_rows + 2 * (d.loc_off + a));
-  return __ldcg(c.fslab[sl] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[sl] + (long long)rw.y * c.R + k);
+  const int4 rw = *reinterpret_cast<const int4 *>(c.ints + c.o_gam_rows + 4 * (d.loc_off + a));
+  float v = __ldcg(c.fslab[sl] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[sl] + (long long)rw.y * c.R + k);
+  if (rw.z >= 0) v += __ldcg(c.fslab[sl] + (long long)rw.z * c.R + k) + __ldcg(c.fslab[sl] + (long long)rw.w * c.R + k);
+  return v;
 }
 
 // The vector S is applied to: x itself (xp == nullptr), or the CG direction
@@ -962,13 +968,21 @@ __device__ bool f_apply_S(const Ctx &c, const DirIn &x, float *q) {
   // q[delta] = sum_owners (YL + BL)
   for (int e = gthread(); e < c.n_dl * c.R; e += nthreads()) {
     const int gd = e / c.R, k = e % c.R;
-    const int sa = c.ints[c.o_dl_own + 4 * gd], la = c.ints[c.o_dl_own + 4 * gd + 1];
-    const int sb = c.ints[c.o_dl_own + 4 * gd + 2], lb = c.ints[c.o_dl_own + 4 * gd + 3];
-    const SubDev &da = c.subs[sa];
-    const SubDev &dB = c.subs[sb];
-    const int2 rw = *reinterpret_cast<const int2 *>(c.ints + c.o_dl_rows + 2 * gd);
-    q[e] = f_yl(c, da, da.nPi + la, k, nu, dnu) + f_yl(c, dB, dB.nPi + lb, k, nu, dnu) +
-           __ldcg(c.fslab[FS_BL] + (long long)rw.x * c.R + k) + __ldcg(c.fslab[FS_BL] + (long long)rw.y * c.R + k);
+    const int *own = c.ints + c.o_dl_own + 8 * gd;
+    const SubDev &da = c.subs[own[0]];
+    const SubDev &dB = c.subs[own[2]];
+    const int4 rw = *reinterpret_cast<const int4 *>(c.ints + c.o_dl_rows + 4 * gd);
+    float v = f_yl(c, da, da.nPi + own[1], k, nu, dnu) + f_yl(c, dB, dB.nPi + own[3], k, nu, dnu);
+    if (rw.z >= 0) {  // a cross point of vanilla DDELM: four owners
+      const SubDev &dc = c.subs[own[4]];
+      const SubDev &dd = c.subs[own[6]];
+      v += f_yl(c, dc, dc.nPi + own[5], k, nu, dnu) + f_yl(c, dd, dd.nPi + own[7], k, nu, dnu);
+    }
+    v = v + __ldcg(c.fslab[FS_BL] + (long long)rw.x * c.R + k);
+    v = v + __ldcg(c.fslab[FS_BL] + (long long)rw.y * c.R + k);
+    if (rw.z >= 0)
+      v += __ldcg(c.fslab[FS_BL] + (long long)rw.z * c.R + k) + __ldcg(c.fslab[FS_BL] + (long long)rw.w * c.R + k);
+    q[e] = v;
   }
   return true;
 }

@@ -359,16 +359,22 @@ __global__ void fill_identity_kernel(double *dst, int n, double diag) {
     dst[e] = (e / n == e % n) ? diag : 0.0;
 }
 
-// F^i = [f(x_I); g(x_B)] per subdomain ([nI + nB] x R)
+// F^i = [w_int f(x_I); g(x_B)] per subdomain ([nI + nB] x R); the Dirichlet data
+// of the second biharmonic component (global index >= nb0) times w_c1
 __global__ void gather_rhs_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
                                   double *__restrict__ db, const double *__restrict__ f_int,
-                                  const double *__restrict__ g_bnd, int R) {
+                                  const double *__restrict__ g_bnd, int R, double w_int, double w_c1, int nb0) {
   const SubDev d = subs[blockIdx.x];
   const int rows = d.nI + d.nB;
   double *F = db + d.oF;
   for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
     const int r = e / R, c = e % R;
-    F[e] = r < d.nI ? f_int[(d.int_off + r) * R + c] : g_bnd[(long long)ints[d.bnd_off + r - d.nI] * R + c];
+    if (r < d.nI) {
+      F[e] = w_int * f_int[(d.int_off + r) * R + c];
+    } else {
+      const int gb = ints[d.bnd_off + r - d.nI];
+      F[e] = (gb >= nb0 ? w_c1 : 1.0) * g_bnd[(long long)gb * R + c];
+    }
   }
 }
 
@@ -387,14 +393,14 @@ __global__ void copy_c_to_y_kernel(const SubDev *__restrict__ subs, double *__re
 
 // dL/df = interior rows of F-bar; dL/dg = sum over the owners of each Dirichlet point
 __global__ void adjoint_scatter_f_kernel(const SubDev *__restrict__ subs, const double *__restrict__ db,
-                                         double *__restrict__ grad_f, int R) {
+                                         double *__restrict__ grad_f, int R, double w_int) {
   const SubDev d = subs[blockIdx.x];
-  for (int e = threadIdx.x; e < d.nI * R; e += blockDim.x) grad_f[d.int_off * R + e] = db[d.oF + e];
+  for (int e = threadIdx.x; e < d.nI * R; e += blockDim.x) grad_f[d.int_off * R + e] = w_int * db[d.oF + e];
 }
 
 __global__ void adjoint_scatter_g_kernel(const SubDev *__restrict__ subs, const int *__restrict__ ints,
                                          const double *__restrict__ db, double *__restrict__ grad_g, int n_bnd,
-                                         int o_own, int R) {
+                                         int o_own, int R, double w_c1, int nb0) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_bnd * R; e += gridDim.x * blockDim.x) {
     const int b = e / R, k = e % R;
     double v = 0.0;
@@ -405,7 +411,7 @@ __global__ void adjoint_scatter_g_kernel(const SubDev *__restrict__ subs, const 
       const SubDev &d = subs[s];
       v += db[d.oF + (long long)(d.nI + r) * R + k];
     }
-    grad_g[e] = v;
+    grad_g[e] = (b >= nb0 ? w_c1 : 1.0) * v;
   }
 }
 
@@ -429,12 +435,12 @@ cudaError_t launch_adjoint_scatter(const Plan &p, void *ws, double *grad_f, doub
   char *base = static_cast<char *>(ws);
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const double *db = reinterpret_cast<const double *>(base + p.off_dbl);
-  if (grad_f && p.sz.sum_int > 0) { adjoint_scatter_f_kernel<<<p.n_sub, 256, 0, s>>>(subs, db, grad_f, p.n_rhs); DDELM_COUNT_LAUNCH(); }
+  if (grad_f && p.sz.sum_int > 0) { adjoint_scatter_f_kernel<<<p.n_sub, 256, 0, s>>>(subs, db, grad_f, p.n_rhs, p.w_int); DDELM_COUNT_LAUNCH(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (grad_g && p.sz.n_bnd > 0)
     { adjoint_scatter_g_kernel<<<64, 256, 0, s>>>(subs, reinterpret_cast<const int *>(base + p.off_ints), db, grad_g,
-                                                p.sz.n_bnd, p.o_bnd_own, p.n_rhs); DDELM_COUNT_LAUNCH(); }
+                                                p.sz.n_bnd, p.o_bnd_own, p.n_rhs, p.w_c1, p.nb0); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -514,7 +520,8 @@ cudaError_t launch_gather_rhs(const Plan &p, void *ws, const double *f_int, cons
   const SubDev *subs = reinterpret_cast<const SubDev *>(base + p.off_subs);
   const int *ints = reinterpret_cast<const int *>(base + p.off_ints);
   double *db = reinterpret_cast<double *>(base + p.off_dbl);
-  { gather_rhs_kernel<<<p.n_sub, 256, 0, s>>>(subs, ints, db, f_int, g_bnd, p.n_rhs); DDELM_COUNT_LAUNCH(); }
+  { gather_rhs_kernel<<<p.n_sub, 256, 0, s>>>(subs, ints, db, f_int, g_bnd, p.n_rhs, p.w_int, p.w_c1, p.nb0);
+    DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ enum RowKind : int {
 
 struct SpecialRow {
   int kind, sub;
+  int comp, pad_;        // 0: phi and d phi/dn; 1 (biharmonic): (Lap phi and d Lap phi/dn) w_c1
   long long out0, out1;  // row starts in dbase (out1 < 0: single output)
   long long out2, out3;  // ROW_DELTA: K-bar Delta row and A_m Delta row (flux)
   long long ca, cb;      // rows holding phi(x_a), phi(x_b) (ROW_DELTA; < 0: none) or phi(corner) (ROW_AM)
@@ -205,12 +206,13 @@ struct Plan {
   double chol_flops = 0.0;             // all Cholesky + inverse passes of one setup
   // named ranges into ints
   int o_pi_own = 0;   // per Pi point: 4 x (sub, local) pairs, -1 padded
-  int o_dl_own = 0;   // per Delta point: 2 x (sub, local)
+  int o_dl_own = 0;   // per Delta point: 4 x (sub, local), -1 past its owners (2, or 4 for the
+                      // cross points of vanilla DDELM)
   int o_tasks_pi = 0, n_tasks_pi = 0;  // (sub, local Pi row)
   int o_tasks_dl = 0, n_tasks_dl = 0;  // (sub, local Delta row)
   int o_tasks_g = 0, n_tasks_g = 0;    // (sub, local Gamma row)
   int o_tasks_c = 0, n_tasks_c = 0;    // (sub, coefficient row j < M)
-  int o_dl_rows = 0;                    // per Delta point: the 2 owners' slab rows
+  int o_dl_rows = 0;                    // per Delta point: its owners' slab rows (4, -1 past the owners)
   int o_gam_rows = 0;                   // per local interface row: those rows of its Delta point (-1 on Pi)
   int o_bnd_map = 0;                    // local boundary -> global Dirichlet index
   int o_bnd_own = 0;                    // per global Dirichlet point: 2 x (sub, local row)
@@ -273,6 +275,11 @@ struct Plan {
   double slice_bytes = 0.0;       // HBM bytes of the slicing kernels of one setup
   // scale gradient (ddelm_backward with a scale output)
   double inv_scale = 0.0;                 // 1 / s
+  // row weights of the biharmonic system written for u and v = Lap u / s^2:
+  // interior rows (and f) times w_int = s^-4, every row of the second component
+  // (and its boundary data) times w_c1 = s^-2; 1 for the other operators
+  double w_int = 1.0, w_c1 = 1.0;
+  int nb0 = 0;                            // Dirichlet points of the first component
   std::vector<long long> slot_begin, slot_end;  // contiguous setup-scratch extent of each wave slot
   std::vector<SubDev> ssubs;              // feature tables writing into the scale buffers
   std::vector<SpecialRow> srows;

@@ -69,7 +69,8 @@ __device__ __forceinline__ void load_exp2tab(double *s, const double *__restrict
 __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__restrict__ subs, int sub0,
                                                             double *__restrict__ db, long long o_w,
                                                             long long o_fc, long long o_exp2, long long o_xint,
-                                                            long long o_aint, long long o_gaint, int op) {
+                                                            long long o_aint, long long o_gaint, int op,
+                                                            double w_int) {
   __shared__ double s_exp2[256];
   const SubDev d = subs[sub0 + blockIdx.y];
   const int r0 = blockIdx.x * 8;
@@ -96,6 +97,9 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
       const double s1 = fma(-t, t, 1.0);
       double v = (c.w * t) * s1;  // 2 |w|^2 t (1 - t^2)
       if (op == DDELM_OP_DIFFUSION) v = a * v - (ax * w[2 * j] + ay * w[2 * j + 1]) * s1;
+      // Lap^2 phi = |w|^4 tanh''''(z) = 8 |w|^4 t (1 - t^2)(2 - 3 t^2), with c.w = 2 |w|^2,
+      // weighted by w_int = s^-4
+      if (op == DDELM_OP_BIHARMONIC) v = w_int * (2.0 * (c.w * c.w) * (t * s1) * fma(-3.0 * t, t, 2.0));
       o0[j] = v;
       o1[j] = v;
     }
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
 __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__restrict__ rows,
                                                            const SubDev *__restrict__ subs,
                                                            double *__restrict__ db, long long o_w,
-                                                           long long o_fc, long long o_exp2) {
+                                                           long long o_fc, long long o_exp2, double w_c1) {
   __shared__ double s_exp2[256];
   const SpecialRow rw = rows[blockIdx.x];
   if (rw.kind == ROW_AM) return;
@@ -117,13 +121,20 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
   double *o0 = db + rw.out0;
   double *o1 = rw.out1 >= 0 ? db + rw.out1 : nullptr;
   const bool delta = rw.kind == ROW_DELTA;
+  const bool lap = rw.comp == 1;  // biharmonic second component: (Lap phi and d Lap phi/dn) w_c1
   for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
     const double4 c = fc[j];
     const double t = tanh_half(fma(c.x, rw.x, fma(c.y, rw.y, c.z)), s_exp2);
-    o0[j] = t;
-    if (o1) o1[j] = t;
+    const double s1 = fma(-t, t, 1.0);
+    // Lap phi = |w|^2 tanh''(z) = -2 |w|^2 t (1 - t^2)  (c.w = 2 |w|^2)
+    const double v = lap ? w_c1 * (-(c.w * t) * s1) : t;
+    o0[j] = v;
+    if (o1) o1[j] = v;
     if (delta) {
-      const double f = (rw.nx * w[2 * j] + rw.ny * w[2 * j + 1]) * fma(-t, t, 1.0);
+      // d phi/dn = (w . n) tanh'(z); d Lap phi/dn = |w|^2 (w . n) tanh'''(z),
+      // tanh''' = -2 (1 - t^2)(1 - 3 t^2)
+      const double wn = rw.nx * w[2 * j] + rw.ny * w[2 * j + 1];
+      const double f = lap ? w_c1 * (-(c.w * wn) * s1 * fma(-3.0 * t, t, 1.0)) : wn * s1;
       db[rw.out2 + j] = f;
       db[rw.out3 + j] = f;
     }
@@ -136,7 +147,8 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
 //   and the e edge points (the corner's flux from its point value)
 __global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *__restrict__ rows,
                                                               const SubDev *__restrict__ subs,
-                                                              double *__restrict__ db, long long o_w) {
+                                                              double *__restrict__ db, long long o_w,
+                                                              double w_c1) {
   const SpecialRow rw = rows[blockIdx.x];
   const bool tinv = rw.kind == ROW_DELTA && (rw.ca >= 0 || rw.cb >= 0);
   if (!tinv && rw.kind != ROW_AM) return;
@@ -152,8 +164,11 @@ __global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *
       db[rw.out1 + j] = v;
     } else {
       const double wx = w[2 * j], wy = w[2 * j + 1];
-      const double tc = db[rw.ca + j];
-      const double sc = 1.0 - tc * tc;
+      const double tc = db[rw.ca + j];  // phi at the corner
+      double sc = 1.0 - tc * tc;
+      // biharmonic second component: the corner flux is w_c1 d Lap phi/dn,
+      // |w|^2 (w . n) tanh''' with tanh''' = -2 (1 - t^2)(1 - 3 t^2)
+      if (rw.comp == 1) sc = w_c1 * (-2.0 * fma(wx, wx, wy * wy) * sc * fma(-3.0 * tc, tc, 1.0));
       double v = 0.0;
       for (int e = 0; e < 2; ++e) {
         const int ne = rw.am_e[e];
@@ -300,12 +315,12 @@ cudaError_t launch_scale_features(const Plan &p, void *ws, int wave, cudaStream_
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
   const int e0 = p.wave_erow0[wave], e1 = p.wave_erow0[wave + 1];
   const dim3 grid((max_nI + 7) / 8, s1 - s0);
-  if (max_nI > 0) { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
+  if (max_nI > 0) { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.w_int); DDELM_COUNT_LAUNCH(); }
   if (r1 > r0) {
-    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
-    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w); DDELM_COUNT_LAUNCH(); }
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_c1); DDELM_COUNT_LAUNCH(); }
   }
-  if (e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
+  if (e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
   if (max_nI > 0) { interior_rows_ds_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.inv_scale); DDELM_COUNT_LAUNCH(); }
   if (r1 > r0) {
     { special_rows_ds_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.inv_scale); DDELM_COUNT_LAUNCH(); }
@@ -327,15 +342,15 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
   for (int i = s0; i < s1; ++i) max_nI = std::max(max_nI, p.subs[i].nI);
   if (max_nI > 0) {
     dim3 grid((max_nI + 7) / 8, s1 - s0);
-    { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op); DDELM_COUNT_LAUNCH(); }
+    { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.w_int); DDELM_COUNT_LAUNCH(); }
   }
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
   if (r1 > r0) {
-    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
-    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w); DDELM_COUNT_LAUNCH(); }
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_c1); DDELM_COUNT_LAUNCH(); }
   }
   const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
-  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2); DDELM_COUNT_LAUNCH(); }
+  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

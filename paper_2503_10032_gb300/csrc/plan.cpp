@@ -65,7 +65,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (pr.nx < 1 || pr.ny < 1 || (long long)pr.nx * pr.ny > 65535) return fail("bad nx/ny");
   if (!(pr.x1 > pr.x0) || !(pr.y1 > pr.y0)) return fail("bad rectangle");
   if (pr.n_rhs < 1 || pr.n_rhs > 16) return fail("n_rhs must be in 1..16");
-  if (pr.op != DDELM_OP_POISSON && pr.op != DDELM_OP_DIFFUSION) return fail("bad op");
+  if (pr.op != DDELM_OP_POISSON && pr.op != DDELM_OP_DIFFUSION && pr.op != DDELM_OP_BIHARMONIC)
+    return fail("bad op");
   if (!pr.M || !pr.w_hat || !pr.b_hat || !pr.n_int || !pr.edge_pts) return fail("null input");
   if (pr.op == DDELM_OP_DIFFUSION && (!pr.a_int || !pr.grad_a_int)) return fail("diffusion needs a");
   const ddelm_options &o = pr.opt;
@@ -78,9 +79,17 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.barrier_timeout_ms < 0 || o.inject_barrier_stall < 0 || o.inject_barrier_stall > 1)
     return fail("bad barrier options");
   if (o.plain_flux_corners < 0 || o.plain_flux_corners > 1) return fail("bad plain_flux_corners");
+  if (o.vanilla < 0 || o.vanilla > 1) return fail("bad vanilla");
+  if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
   P.inv_scale = pr.scale != 0.0 ? 1.0 / pr.scale : 0.0;
+  if (pr.op == DDELM_OP_BIHARMONIC) {
+    if (!(pr.scale > 0.0)) return fail("biharmonic needs scale > 0");
+    // the system in u and v = Lap u / s^2 (the reweighting of the loss terms)
+    P.w_c1 = P.inv_scale * P.inv_scale;
+    P.w_int = P.w_c1 * P.w_c1;
+  }
   const int nx = pr.nx, ny = pr.ny, n_sub = nx * ny;
   Geo g{nx, ny, pr.x0, pr.x1, pr.y0, pr.y1, (pr.x1 - pr.x0) / nx, (pr.y1 - pr.y0) / ny, pr.edge_pts};
   const int n_edges = g.n_edges();
@@ -114,8 +123,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   for (int vy = 0; vy <= ny; ++vy)
     for (int vx = 0; vx <= nx; ++vx)
       if (vx == 0 || vx == nx || vy == 0 || vy == ny) vtx_bnd[vy * (nx + 1) + vx] = nb++;
-  const int n_pi = (nx - 1) * (ny - 1);
-  int nd = 0;
+  // vanilla DDELM (Sec. 2.2.1, no coarse space): Pi is empty and the cross
+  // points open the Delta list (in cross-point order), each shared by four subdomains
+  const bool vanilla = o.vanilla != 0;
+  const int n_cross = (nx - 1) * (ny - 1);
+  int n_pi = vanilla ? 0 : n_cross;
+  int nd = vanilla ? n_cross : 0;
   for (int e = 0; e < n_edges; ++e)
     if (!g.edge_on_boundary(e)) {
       dl_off[e] = nd;
@@ -145,6 +158,9 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     std::vector<int> alp, bep;
     std::vector<std::vector<EdgeRef>> am_edges;  // per local Pi: the two edges meeting it
     std::map<int, int> dstart;                    // edge id -> index of its first Delta point
+    // interface / boundary component of every point (biharmonic: 0 u, 1 Lap u)
+    std::vector<int> bcomp, pcomp, dcomp;
+    int np0 = 0, nd0 = 0;                         // Pi and Delta points of component 0
   };
   std::vector<SubGeo> sg(n_sub);
   const int H = g.H();
@@ -172,7 +188,24 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       }
     std::map<std::pair<int, int>, int> locpi;
     for (auto v : verts)
-      if (g.is_cross(v)) {
+      if (g.is_cross(v) && vanilla) {
+        // an interface point of the Delta set; its flux row is the plain one of
+        // Eq. (ddelm) with the corner normal resolved as the sum of the outward
+        // normals of the two edges of this subdomain that meet there
+        V2 nsum{0.0, 0.0};
+        for (auto &e : edges)
+          if ((e.sv[0] == v[0] && e.sv[1] == v[1]) || (e.ev[0] == v[0] && e.ev[1] == v[1])) {
+            nsum.x += e.n[0];
+            nsum.y += e.n[1];
+          }
+        s.dxy.push_back(g.vxy(v));
+        s.dnrm.push_back(nsum);
+        s.dg.push_back(g.pi_index(v));
+        s.al.push_back(0.0);
+        s.alp.push_back(-1);
+        s.be.push_back(0.0);
+        s.bep.push_back(-1);
+      } else if (g.is_cross(v)) {
         locpi[{v[0], v[1]}] = int(s.pxy.size());
         s.pxy.push_back(g.vxy(v));
         s.pg.push_back(g.pi_index(v));
@@ -203,6 +236,62 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         if (at_s || at_e) s.am_edges[k].push_back(e);
       }
   }
+
+  // ---- biharmonic (the coupled system of Sec. 2.1): u and Lap u are both
+  // interface unknowns, so every boundary, Pi and Delta point gets a second
+  // row of component 1, numbered after all of component 0 (globally and within
+  // each block of a subdomain); its change of variables refers to the
+  // component-1 corner rows
+  const int n_comp = pr.op == DDELM_OP_BIHARMONIC ? 2 : 1;
+  P.nb0 = nb;
+  for (auto &s : sg) {
+    const int kb = int(s.bxy.size()), kp = int(s.pxy.size()), kd = int(s.dxy.size());
+    s.np0 = kp;
+    s.nd0 = kd;
+    s.bcomp.assign(kb, 0);
+    s.pcomp.assign(kp, 0);
+    s.dcomp.assign(kd, 0);
+    if (n_comp == 1) continue;
+    for (int k = 0; k < kb; ++k) {
+      const V2 xy = s.bxy[k];
+      s.bxy.push_back(xy);
+      s.bg.push_back(s.bg[k] + nb);
+      s.bcomp.push_back(1);
+    }
+    for (int k = 0; k < kp; ++k) {
+      const V2 xy = s.pxy[k];
+      const std::pair<int, int> v = s.pv[k];
+      const std::vector<EdgeRef> ae = s.am_edges[k];
+      s.pxy.push_back(xy);
+      s.pg.push_back(s.pg[k] + n_pi);
+      s.pv.push_back(v);
+      s.am_edges.push_back(ae);
+      s.pcomp.push_back(1);
+    }
+    for (int k = 0; k < kd; ++k) {
+      const V2 xy = s.dxy[k], nrm = s.dnrm[k];
+      const double al = s.al[k], be = s.be[k];
+      const int alp = s.alp[k], bep = s.bep[k];
+      s.dxy.push_back(xy);
+      s.dnrm.push_back(nrm);
+      s.dg.push_back(s.dg[k] + nd);
+      s.al.push_back(al);
+      s.be.push_back(be);
+      s.alp.push_back(alp >= 0 ? alp + kp : -1);
+      s.bep.push_back(bep >= 0 ? bep + kp : -1);
+      s.dcomp.push_back(1);
+    }
+  }
+  if (n_comp == 2) {
+    nb *= 2;
+    n_pi *= 2;
+    nd *= 2;
+  }
+  P.n_pi = n_pi;
+  P.n_dl = nd;
+  P.sz.n_bnd = nb;
+  P.sz.n_pi = n_pi;
+  P.sz.n_delta = nd;
 
   // ---- workspace layout
   P.subs.resize(n_sub);
@@ -476,6 +565,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     };
     for (int k = 0; k < d.nB; ++k) {  // boundary rows of K_c and K-bar
       SpecialRow r = base(ROW_POINT);
+      r.comp = s.bcomp[k];
       r.x = s.bxy[k].x;
       r.y = s.bxy[k].y;
       r.out0 = d.oK + (long long)(d.nI + k) * M;
@@ -486,6 +576,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     auto pi_row = [&](int k) { return d.oK + (long long)(g0 + k) * M; };  // phi at local Pi point k
     for (int k = 0; k < d.nPi; ++k) {  // Pi rows: point values in K_c and K-bar
       SpecialRow r = base(ROW_POINT);
+      r.comp = s.pcomp[k];
       r.x = s.pxy[k].x;
       r.y = s.pxy[k].y;
       r.out0 = pi_row(k);
@@ -496,6 +587,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       // K_c Delta row (also A-bar row): (T^i)^{-1} C phi, or C phi without the
       // change of variables; K-bar Delta row (also A_m Delta row): F phi
       SpecialRow r = base(ROW_DELTA);
+      r.comp = s.dcomp[k];
       r.x = s.dxy[k].x;
       r.y = s.dxy[k].y;
       r.nx = s.dnrm[k].x;
@@ -519,8 +611,9 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
     for (int k = 0; k < d.nPi; ++k) {  // A_m corner rows from the flux rows of the two edges
       SpecialRow a = base(ROW_AM);
+      a.comp = s.pcomp[k];
       a.out0 = d.oA + (long long)k * M;
-      a.ca = pi_row(k);
+      a.ca = pi_row(a.comp ? k - s.np0 : k);  // phi at the corner (component 0's row)
       for (int t = 0; t < 2; ++t) {
         const EdgeRef &e = s.am_edges[k][t];
         a.am_n[t][0] = e.n[0];
@@ -529,7 +622,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         a.am_e[t] = o.plain_flux_corners ? 0 : pr.edge_pts[e.id];
         // an edge meeting a cross point is an interface edge: its Delta points are
         // the e points the mean runs over
-        a.am_f[t] = d.oA + (long long)(d.nPi + s.dstart.at(e.id)) * M;
+        a.am_f[t] = d.oA + (long long)(d.nPi + s.dstart.at(e.id) + a.comp * s.nd0) * M;
       }
       P.rows.push_back(a);
     }
@@ -570,7 +663,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.o_pi_own = int(I.size());
   I.resize(I.size() + 8 * (size_t)n_pi, -1);
   P.o_dl_own = int(I.size());
-  I.resize(I.size() + 4 * (size_t)nd, -1);
+  I.resize(I.size() + 8 * (size_t)nd, -1);
   {
     std::vector<int> cnt(n_pi, 0), cntd(nd, 0);
     for (int i = 0; i < n_sub; ++i) {
@@ -584,13 +677,17 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       for (size_t k = 0; k < sg[i].dg.size(); ++k) {
         int gi = sg[i].dg[k];
         int c = cntd[gi]++;
-        if (c >= 2) return fail("internal: Delta point with more than two subdomains");
-        I[P.o_dl_own + 4 * gi + 2 * c] = i;
-        I[P.o_dl_own + 4 * gi + 2 * c + 1] = int(k);
+        if (c >= 4) return fail("internal: Delta point with more than four subdomains");
+        I[P.o_dl_own + 8 * gi + 2 * c] = i;
+        I[P.o_dl_own + 8 * gi + 2 * c + 1] = int(k);
       }
     }
-    for (int v : cntd)
-      if (v != 2) return fail("internal: Delta point not shared by two subdomains");
+    // four owners exactly at the cross points of vanilla DDELM (the first n_cross
+    // Delta points of each component)
+    const int nd1 = nd / n_comp;
+    for (int gd = 0; gd < nd; ++gd)
+      if (cntd[gd] != ((vanilla && gd % nd1 < n_cross) ? 4 : 2))
+        return fail("internal: Delta point with the wrong number of subdomains");
   }
   // per global Dirichlet point: up to 2 (sub, local boundary row) owners (adjoint scatter)
   P.o_bnd_own = int(I.size());
@@ -634,23 +731,24 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       I.push_back(k);
     }
   P.n_tasks_c = (int(I.size()) - P.o_tasks_c) / 2;
-  // slab rows of the two owners of every Delta point, by global point and by
-  // local interface row (-1 on Pi rows): the gathers read slabs in one step
-  if (I.size() % 2) I.push_back(-1);  // int2 reads
+  // slab rows of the owners of every Delta point (4 per point, -1 past the
+  // owners), by global point and by local interface row (-1 on Pi rows): the
+  // gathers read slabs in one step
+  while (I.size() % 4) I.push_back(-1);  // int4 reads
   P.o_dl_rows = int(I.size());
   for (int gd = 0; gd < nd; ++gd)
-    for (int o = 0; o < 2; ++o) {
-      const int s = I[P.o_dl_own + 4 * gd + 2 * o], l = I[P.o_dl_own + 4 * gd + 2 * o + 1];
-      I.push_back(P.subs[s].loc_off + P.subs[s].nPi + l);
+    for (int o = 0; o < 4; ++o) {
+      const int s = I[P.o_dl_own + 8 * gd + 2 * o], l = I[P.o_dl_own + 8 * gd + 2 * o + 1];
+      I.push_back(s >= 0 ? P.subs[s].loc_off + P.subs[s].nPi + l : -1);
     }
   P.o_gam_rows = int(I.size());
-  I.resize(I.size() + 2 * (size_t)sum_nG, -1);
+  I.resize(I.size() + 4 * (size_t)sum_nG, -1);
   for (int i = 0; i < n_sub; ++i) {
     const SubDev &d = P.subs[i];
     for (int b = 0; b < d.nDl; ++b) {
       const int gd = sg[i].dg[b];
-      I[P.o_gam_rows + 2 * (d.loc_off + d.nPi + b)] = I[P.o_dl_rows + 2 * gd];
-      I[P.o_gam_rows + 2 * (d.loc_off + d.nPi + b) + 1] = I[P.o_dl_rows + 2 * gd + 1];
+      for (int o = 0; o < 4; ++o)
+        I[P.o_gam_rows + 4 * (d.loc_off + d.nPi + b) + o] = I[P.o_dl_rows + 4 * gd + o];
     }
   }
 
@@ -1272,10 +1370,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         if (s >= 0 && (s >= n_sub || a < 0 || a >= P.subs[s].nPi)) return fail("internal: Pi owner map");
       }
     for (int p = 0; p < nd; ++p)
-      for (int o = 0; o < 2; ++o) {
-        const int s = I[P.o_dl_own + 4 * p + 2 * o], a = I[P.o_dl_own + 4 * p + 2 * o + 1];
-        if (s < 0 || s >= n_sub || a < 0 || a >= P.subs[s].nDl) return fail("internal: Delta owner map");
+      for (int o = 0; o < 4; ++o) {
+        const int s = I[P.o_dl_own + 8 * p + 2 * o], a = I[P.o_dl_own + 8 * p + 2 * o + 1];
+        if (o < 2 && s < 0) return fail("internal: Delta point without two owners");
+        if (s >= 0 && (s >= n_sub || a < 0 || a >= P.subs[s].nDl)) return fail("internal: Delta owner map");
+        const int r = I[P.o_dl_rows + 4 * p + o];
+        if ((s < 0) != (r < 0) || r >= P.sum_nG) return fail("internal: Delta slab rows");
       }
+    if (P.o_dl_rows % 4 || P.o_gam_rows % 4) return fail("internal: int4 table alignment");
     for (int b = 0; b < nb; ++b) {
       const int s0 = I[P.o_bnd_own + 4 * b];
       if (s0 < 0) return fail("internal: boundary point without owner");

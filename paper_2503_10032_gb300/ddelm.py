@@ -24,6 +24,7 @@ DDELM_ERR_TIMEOUT = -5
 DDELM_ERR_UNSUPPORTED = -6
 DDELM_OP_POISSON = 0
 DDELM_OP_DIFFUSION = 1
+DDELM_OP_BIHARMONIC = 2
 DDELM_PREC_FP64 = 0
 DDELM_PREC_MIXED = 1
 
@@ -38,7 +39,8 @@ class ddelm_options(ctypes.Structure):
                 ("keep_matrices", ctypes.c_int), ("setup_wave", ctypes.c_int),
                 ("setup_scheme", ctypes.c_int), ("setup_passes", ctypes.c_int),
                 ("disable_graphs", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
-                ("inject_barrier_stall", ctypes.c_int), ("plain_flux_corners", ctypes.c_int)]
+                ("inject_barrier_stall", ctypes.c_int), ("plain_flux_corners", ctypes.c_int),
+                ("vanilla", ctypes.c_int)]
 
 
 class ddelm_problem(ctypes.Structure):
@@ -135,11 +137,11 @@ def ddelm_status_string(status: int) -> str:
 def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change_of_vars=True,
                  precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False, setup_wave=0,
                  setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0, graphs=True, barrier_timeout_ms=0,
-                 inject_barrier_stall=False, use_Am=True):
+                 inject_barrier_stall=False, use_Am=True, use_coarse=True):
     return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
                          max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
                          int(setup_passes), int(not graphs), int(barrier_timeout_ms),
-                         int(inject_barrier_stall), int(not use_Am))
+                         int(inject_barrier_stall), int(not use_Am), int(not use_coarse))
 
 
 class ProblemArgs:
