@@ -62,7 +62,7 @@ def kernel_sources_sha256():
             h.update(fh.read())
     return h.hexdigest()
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz
-SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2, "cqr2series": 3}
+SCHEMES = {"auto": 0, "fp64cqr3": 1, "fp32": 2, "cqr2series": 3, "cqr2series-dw": 4}
 
 
 def measured_peaks():
@@ -283,7 +283,7 @@ def main():
         sub_sizes.append({"m": m_, "M": M_, "nG": nG_, "nDl": nDl_})
     flops = D.ddelm_inspect(solver.h, 0, 8, 7)
     plan = D.ddelm_inspect(solver.h, 0, 9, 4)
-    scheme_desc = {1: "fp64-cholesky-cqr3", 3: "fp64-cholesky x2 + series"}.get(
+    scheme_desc = {1: "fp64-cholesky-cqr3", 3: "fp64-cholesky x2 + series", 4: "double-fp32-cholesky x2 + series"}.get(
         int(plan[0]), f"fp32-cholesky x{int(plan[1])} shifted + 1 polished")
 
     def step():

@@ -81,10 +81,11 @@ extern "C" {
                                  g = [u on the n_bnd/2 points; Lap u on the same points],
                                  Gamma = [Pi u; Pi Lap u; Delta u; Delta Lap u]. The change of
                                  variables and A_m (Sec. 3.2) act on each component separately.
-                                 The loss terms are reweighted by writing the system for u and
-                                 v = Lap u / s^2 (s = scale > 0 required): interior rows and f
-                                 times s^-4, every row of the second component and its boundary
-                                 data times s^-2; mu of the second component is v. */
+                                 The loss terms are reweighted: every derivative of order k times
+                                 H^k, H = sqrt(hx hy) the subdomain size (interior rows and f
+                                 times H^4, the second component's point rows and boundary data
+                                 times H^2, flux rows times H and H^3); mu of the second
+                                 component is v = H^2 Lap u. */
 
 #define DDELM_PREC_FP64 0  /* every step in FP64 */
 #define DDELM_PREC_MIXED 1 /* FP32 inner CG with FP64 true-residual refinement */
@@ -106,6 +107,12 @@ extern "C" {
 #define DDELM_SCHEME_FP64CQR3 1
 #define DDELM_SCHEME_FP32 2
 #define DDELM_SCHEME_CQR2_SERIES 3
+/* CQR2_SERIES_DW: as CQR2_SERIES, the two Cholesky factors computed in
+ * double-FP32 arithmetic (pairs of FP32 numbers, about 46 significant bits) on
+ * the FP32 pipe instead of FP64; they are preconditioners only (every product
+ * with them is FP64-exact and the series polish is checked), and the first
+ * pass's shift covers the 2^-46 rounding. */
+#define DDELM_SCHEME_CQR2_SERIES_DW 4
 
 typedef struct ddelm_options {
   double theta;           /* Eq. (nn-mixed) mixing weight; the paper uses 0.999 */

@@ -31,13 +31,13 @@ Readings where the paper is silent:
 * R_f^i is the plain restriction (no sign), as for R^i;
 * biharmonic (op 2, the coupled system of Sec. 2.1): every boundary and
   interface point carries two components (`layout.Layout(n_comp=2)`), u and
-  v = Lap u / s^2 (s the hidden-layer scale): the loss terms are reweighted
-  (Sec. 1 announces a reweighting and never gives it) by writing the system
-  for u and v, i.e. every Laplacian divided by s^2: interior rows
-  Lap^2 phi / s^4 with data f / s^4, boundary rows phi and Lap phi / s^2 with
-  data g_1 and g_2 / s^2, continuity rows phi and Lap phi / s^2, flux rows
-  d phi/dn and (d Lap phi/dn) / s^2; mu of component 1 is v.  The change of
-  variables and A_m act on each component separately;
+  v = H^2 Lap u.  The loss terms are reweighted (Sec. 1 announces a
+  reweighting and never gives it) by writing every derivative of order k
+  times H^k, H = sqrt(hx hy) the subdomain size: interior rows H^4 Lap^2 phi
+  with data H^4 f, boundary rows phi and H^2 Lap phi with data g_1 and
+  H^2 g_2, continuity rows phi and H^2 Lap phi, flux rows H d phi/dn and
+  H^3 d Lap phi/dn; mu of component 1 is v.  The change of variables and A_m
+  act on each component separately;
 * vanilla DDELM (`Options.use_coarse = False`, Sec. 2.2.1): no coarse space;
   every cross point is an interface unknown of the Delta set shared by its
   four subdomains, with the plain corner flux row (the sum of the fluxes
@@ -135,12 +135,12 @@ def C_rows(w, b, xy, comp, w_c1=1.0):
     return out
 
 
-def F_rows(w, b, xy, normals, comp, w_c1=1.0):
-    """Flux rows: d phi/dn for component 0, w_c1 d Lap phi/dn for component 1."""
-    out = F_phi(w, b, xy, normals)
+def F_rows(w, b, xy, normals, comp, w_f=(1.0, 1.0)):
+    """Flux rows: w_f[0] d phi/dn for component 0, w_f[1] d Lap phi/dn for component 1."""
+    out = w_f[0] * F_phi(w, b, xy, normals)
     one = np.asarray(comp) == 1
     if one.any():
-        out[one] = w_c1 * F_lap_phi(w, b, xy[one], normals[one])
+        out[one] = w_f[1] * F_lap_phi(w, b, xy[one], normals[one])
     return out
 
 
@@ -195,9 +195,12 @@ class DDELMOracle:
             xI = p.x_int[Ioff[i]:Ioff[i + 1]]
             aI = p.a_int[Ioff[i]:Ioff[i + 1]]
             gI = p.grad_a_int[Ioff[i]:Ioff[i + 1]]
-            # biharmonic: the system in u and v = Lap u / s^2 (module docstring)
-            w_int = p.scale ** -4 if p.op == 2 else 1.0
-            w_c1 = p.scale ** -2 if p.op == 2 else 1.0
+            # biharmonic: every derivative of order k times H^k (module docstring)
+            H = np.sqrt(self.lay.hx * self.lay.hy)
+            bih = p.op == 2
+            w_int = H ** 4 if bih else 1.0
+            w_c1 = H ** 2 if bih else 1.0
+            w_f = (H, H ** 3) if bih else (1.0, 1.0)
             rows_I = w_int * L_phi(w, b, xI, p.op, aI, gI)
             rows_B = C_rows(w, b, sl.bnd_xy, sl.bnd_comp, w_c1)
             C_pi = C_rows(w, b, sl.pi_xy, sl.pi_comp, w_c1)
@@ -217,11 +220,11 @@ class DDELMOracle:
             L.K = np.vstack([rows_I, rows_B, C_pi, Tinv_dl])
             L.m = L.K.shape[0]
             # A_m^i: Delta rows are point fluxes, Pi rows the mean edge fluxes
-            F_dl = F_rows(w, b, sl.dl_xy, sl.dl_normal, sl.dl_comp, w_c1)
+            F_dl = F_rows(w, b, sl.dl_xy, sl.dl_normal, sl.dl_comp, w_f)
             A_pi = np.zeros((L.nPi, len(w)))
             for k, terms in enumerate(sl.am_terms):
                 for wgt, xy, nrm in terms:
-                    A_pi[k] += wgt * F_rows(w, b, xy[None, :], np.array([nrm]), [sl.pi_comp[k]], w_c1)[0]
+                    A_pi[k] += wgt * F_rows(w, b, xy[None, :], np.array([nrm]), [sl.pi_comp[k]], w_f)[0]
             L.Ahat = np.vstack([A_pi, F_dl])
             L.Kbar = np.vstack([rows_I, rows_B, C_pi, F_dl])
             L.Abar = Tinv_dl

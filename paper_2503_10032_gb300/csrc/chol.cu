@@ -25,6 +25,89 @@ namespace {
 constexpr int CT = 512;
 constexpr int NB = 16;   // panel rows
 
+__device__ __forceinline__ double shfl_xor(unsigned m, double v, int o) { return __shfl_xor_sync(m, v, o); }
+__device__ __forceinline__ float shfl_xor(unsigned m, float v, int o) { return __shfl_xor_sync(m, v, o); }
+
+}  // namespace
+
+// Double-FP32 numbers x = hi + lo with |lo| <= ulp(hi)/2: about 46 significant
+// bits carried by the FP32 pipe, which this GPU runs at 64 times its FP64 rate.
+// Built from Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based exact
+// product (a b = p + e with e = fma(a, b, -p)); additions renormalise once, so
+// a sum is accurate to about 2^-47 of |x| + |y| (backward stable, like an FP64
+// addition at that unit roundoff), which is all a Cholesky factorisation needs.
+// The functions live in their own namespace and are found by argument-dependent
+// lookup, so the FP64 and FP32 instances of the factorisation are unchanged.
+namespace dw {
+
+struct __align__(8) ff {
+  float hi, lo;
+  ff() = default;
+  __device__ __forceinline__ ff(float h) : hi(h), lo(0.0f) {}
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return ff(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = a + b;
+  return ff(s, b - (s - a));
+}
+__device__ __forceinline__ ff operator+(ff x, ff y) {
+  const ff s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ff operator-(ff x) { return ff(-x.hi, -x.lo); }
+__device__ __forceinline__ ff operator-(ff x, ff y) { return x + (-y); }
+__device__ __forceinline__ ff &operator+=(ff &x, ff y) { return x = x + y; }
+__device__ __forceinline__ ff &operator-=(ff &x, ff y) { return x = x - y; }
+// product: exact product of the high parts plus the cross terms (lo lo dropped)
+__device__ __forceinline__ ff operator*(ff x, ff y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+// a b + c with one renormalisation
+__device__ __forceinline__ ff fma(ff a, ff b, ff c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const ff s = two_sum(p, c.hi);
+  return fast_two_sum(s.hi, s.lo + (e + c.lo));
+}
+// 1 / x: the FP32 reciprocal and one Newton step r + r (1 - x r)
+__device__ __forceinline__ ff recip(ff x) {
+  const ff r(1.0f / x.hi);
+  return fma(r, fma(-x, r, ff(1.0f)), r);
+}
+__device__ __forceinline__ ff operator/(ff a, ff b) { return a * recip(b); }
+// sqrt(a): the FP32 root y and one correction (a - y^2) / (2 y), y^2 exact by FMA
+__device__ __forceinline__ ff sqrt(ff a) {
+  const float y = sqrtf(a.hi);
+  if (!(y > 0.0f)) return ff(y);
+  return fast_two_sum(y, (fmaf(-y, y, a.hi) + a.lo) / (2.0f * y));
+}
+__device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool isfinite(ff a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
+__device__ __forceinline__ ff shfl_xor(unsigned m, ff v, int o) {
+  return ff(__shfl_xor_sync(m, v.hi, o), __shfl_xor_sync(m, v.lo, o));
+}
+__device__ __forceinline__ ff from_double(double d) {
+  const float h = float(d);
+  return ff(h, float(d - double(h)));
+}
+__device__ __forceinline__ double to_double(ff x) { return double(x.hi) + double(x.lo); }
+
+}  // namespace dw
+
+namespace {
+
 // Blocked right-looking upper Cholesky A = R^T R in place (upper triangle), then
 // V = R^{-1} by blocked back substitution, in precision T.  The panel (NB rows
 // of the trailing matrix) lives in shared memory; the trailing update is a
@@ -151,7 +234,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
         __syncwarp(gmask);
         for (int o = 1; o < tpc; o <<= 1)
 #pragma unroll
-          for (int r = 0; r < NB; ++r) acc[r] += __shfl_xor_sync(gmask, acc[r], o);
+          for (int r = 0; r < NB; ++r) acc[r] += shfl_xor(gmask, acc[r], o);
       }
       if (part == 0) {
       T x[NB];
@@ -275,6 +358,43 @@ __global__ void __launch_bounds__(CT) chol_inv32_kernel(const CholDesc *__restri
   const double ez = sqrt(eps2);
   for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
     const double v = double(V32[e]);
+    V[e] = v;
+    if (cd.z >= 0) db[cd.z + e] = ez * v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_bad) status[cd.status] = 1;
+}
+
+// Double-FP32 pass (a preconditioning factor of shifted CholeskyQR, as the FP32
+// pass, in about 46-bit arithmetic so that two passes suffice): G + (eps^2 + s) I
+// is converted in place to double-FP32 numbers (8 bytes, like the FP64 entries
+// they replace), factored, and R (upper triangle of G) and V = R^{-1} are
+// converted back to FP64 in place.
+__global__ void __launch_bounds__(CT) chol_inv_dw_kernel(const CholDesc *__restrict__ descs,
+                                                         double *__restrict__ db, int *__restrict__ status) {
+  extern __shared__ dw::ff Pw[];
+  const CholDesc cd = descs[blockIdx.x];
+  const int M = cd.M;
+  double *G = db + cd.g;
+  double *V = db + cd.v;
+  dw::ff *A = reinterpret_cast<dw::ff *>(G);
+  dw::ff *Vw = reinterpret_cast<dw::ff *>(V);
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  double eps2 = 0.0, add = 0.0;
+  diag_additions(cd, G, &eps2, &add);
+  for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
+    const long long i = e / M, j = e % M;
+    A[e] = dw::from_double(G[e] + (i == j ? add : 0.0));  // each thread rewrites its own entries
+  }
+  __syncthreads();
+  if (cd.epsout >= 0 && threadIdx.x == 0) db[cd.epsout] = sqrt(eps2);
+  chol_inv_core<dw::ff>(A, Vw, M, cd.band, Pw, &s_bad, cd.inv_block);
+  __syncthreads();
+  const double ez = sqrt(eps2);
+  for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
+    G[e] = dw::to_double(A[e]);
+    const double v = dw::to_double(Vw[e]);
     V[e] = v;
     if (cd.z >= 0) db[cd.z + e] = ez * v;
   }
@@ -452,15 +572,19 @@ cudaError_t launch_chol_phase(const Plan &p, const CholPhase &ph, void *ws, cuda
   int *status = reinterpret_cast<int *>(db + p.o_status);
   int maxM = 0;
   for (int k = 0; k < ph.ndesc; ++k) maxM = p.cdesc[ph.desc0 + k].M > maxM ? p.cdesc[ph.desc0 + k].M : maxM;
-  const bool f32 = p.cdesc[ph.desc0].prec == 1;
-  const size_t smem = (f32 ? sizeof(float) : sizeof(double)) * (size_t)NB * (size_t)maxM;
+  const int prec = p.cdesc[ph.desc0].prec;  // one precision per phase
+  const bool f32 = prec == 1, fdw = prec == 2;
+  const size_t smem = (f32 ? sizeof(float) : sizeof(double)) * (size_t)NB * (size_t)maxM;  // double-FP32: 8 B
   if (smem > 48 * 1024) {
-    cudaError_t e = f32 ? cudaFuncSetAttribute(chol_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                        : cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = f32   ? cudaFuncSetAttribute(chol_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                    : fdw ? cudaFuncSetAttribute(chol_inv_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   if (f32)
     { chol_inv32_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
+  else if (fdw)
+    { chol_inv_dw_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
   else
     { chol_inv_kernel<<<ph.ndesc, CT, smem, s>>>(descs, db, status); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();

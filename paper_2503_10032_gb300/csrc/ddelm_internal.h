@@ -111,7 +111,7 @@ struct CholDesc {
   int M, m;     // order, rows of the matrix whose Gram g is (for the shift)
   int ridge;    // 1: add eps^2 = eps_rel^2 tr(G)/M (the ridge of the local problem)
   int shift_kind;  // 0 none, 1 shift_rel * tr(G + eps^2 I), 2 shift_rel * max diag(G + eps^2 I)
-  int prec;     // 0 FP64, 1 FP32
+  int prec;     // 0 FP64, 1 FP32, 2 double-FP32
   int band;     // > 0: G and R vanish beyond this many superdiagonals
   int status;   // index into the status array
   int inv_block; // > 0: only the inv_block x inv_block diagonal blocks of R^{-1} (the rest by GEMMs)
@@ -275,10 +275,12 @@ struct Plan {
   double slice_bytes = 0.0;       // HBM bytes of the slicing kernels of one setup
   // scale gradient (ddelm_backward with a scale output)
   double inv_scale = 0.0;                 // 1 / s
-  // row weights of the biharmonic system written for u and v = Lap u / s^2:
-  // interior rows (and f) times w_int = s^-4, every row of the second component
-  // (and its boundary data) times w_c1 = s^-2; 1 for the other operators
-  double w_int = 1.0, w_c1 = 1.0;
+  // row weights of the biharmonic system (every derivative of order k times H^k,
+  // H the subdomain size): interior rows (and f) times w_int = H^4, the second
+  // component's point rows (and its boundary data) times w_c1 = H^2, flux rows
+  // times w_f0 = H (first component) and w_f1 = H^3 (second); 1 for the other
+  // operators
+  double w_int = 1.0, w_c1 = 1.0, w_f0 = 1.0, w_f1 = 1.0;
   int nb0 = 0;                            // Dirichlet points of the first component
   std::vector<long long> slot_begin, slot_end;  // contiguous setup-scratch extent of each wave slot
   std::vector<SubDev> ssubs;              // feature tables writing into the scale buffers

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
       double v = (c.w * t) * s1;  // 2 |w|^2 t (1 - t^2)
       if (op == DDELM_OP_DIFFUSION) v = a * v - (ax * w[2 * j] + ay * w[2 * j + 1]) * s1;
       // Lap^2 phi = |w|^4 tanh''''(z) = 8 |w|^4 t (1 - t^2)(2 - 3 t^2), with c.w = 2 |w|^2,
-      // weighted by w_int = s^-4
+      // weighted by w_int = H^4
       if (op == DDELM_OP_BIHARMONIC) v = w_int * (2.0 * (c.w * c.w) * (t * s1) * fma(-3.0 * t, t, 2.0));
       o0[j] = v;
       o1[j] = v;
@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256) interior_rows_kernel(const SubDev *__rest
 __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__restrict__ rows,
                                                            const SubDev *__restrict__ subs,
                                                            double *__restrict__ db, long long o_w,
-                                                           long long o_fc, long long o_exp2, double w_c1) {
+                                                           long long o_fc, long long o_exp2, double w_c1,
+                                                           double w_f0, double w_f1) {
   __shared__ double s_exp2[256];
   const SpecialRow rw = rows[blockIdx.x];
   if (rw.kind == ROW_AM) return;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
   double *o0 = db + rw.out0;
   double *o1 = rw.out1 >= 0 ? db + rw.out1 : nullptr;
   const bool delta = rw.kind == ROW_DELTA;
-  const bool lap = rw.comp == 1;  // biharmonic second component: (Lap phi and d Lap phi/dn) w_c1
+  const bool lap = rw.comp == 1;  // biharmonic second component: w_c1 Lap phi and w_f1 d Lap phi/dn
   for (int j = threadIdx.x; j < d.M; j += blockDim.x) {
     const double4 c = fc[j];
     const double t = tanh_half(fma(c.x, rw.x, fma(c.y, rw.y, c.z)), s_exp2);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
       // d phi/dn = (w . n) tanh'(z); d Lap phi/dn = |w|^2 (w . n) tanh'''(z),
       // tanh''' = -2 (1 - t^2)(1 - 3 t^2)
       const double wn = rw.nx * w[2 * j] + rw.ny * w[2 * j + 1];
-      const double f = lap ? w_c1 * (-(c.w * wn) * s1 * fma(-3.0 * t, t, 1.0)) : wn * s1;
+      const double f = lap ? w_f1 * (-(c.w * wn) * s1 * fma(-3.0 * t, t, 1.0)) : w_f0 * (wn * s1);
       db[rw.out2 + j] = f;
       db[rw.out3 + j] = f;
     }
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) special_rows_kernel(const SpecialRow *__r
 __global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *__restrict__ rows,
                                                               const SubDev *__restrict__ subs,
                                                               double *__restrict__ db, long long o_w,
-                                                              double w_c1) {
+                                                              double w_f0, double w_f1) {
   const SpecialRow rw = rows[blockIdx.x];
   const bool tinv = rw.kind == ROW_DELTA && (rw.ca >= 0 || rw.cb >= 0);
   if (!tinv && rw.kind != ROW_AM) return;
@@ -166,9 +167,9 @@ __global__ void __launch_bounds__(256) special_combine_kernel(const SpecialRow *
       const double wx = w[2 * j], wy = w[2 * j + 1];
       const double tc = db[rw.ca + j];  // phi at the corner
       double sc = 1.0 - tc * tc;
-      // biharmonic second component: the corner flux is w_c1 d Lap phi/dn,
-      // |w|^2 (w . n) tanh''' with tanh''' = -2 (1 - t^2)(1 - 3 t^2)
-      if (rw.comp == 1) sc = w_c1 * (-2.0 * fma(wx, wx, wy * wy) * sc * fma(-3.0 * tc, tc, 1.0));
+      // the corner flux w_f0 d phi/dn or, for the biharmonic second component,
+      // w_f1 d Lap phi/dn = w_f1 |w|^2 (w . n) tanh''', tanh''' = -2 (1 - t^2)(1 - 3 t^2)
+      sc = rw.comp == 1 ? w_f1 * (-2.0 * fma(wx, wx, wy * wy) * sc * fma(-3.0 * tc, tc, 1.0)) : w_f0 * sc;
       double v = 0.0;
       for (int e = 0; e < 2; ++e) {
         const int ne = rw.am_e[e];
@@ -317,10 +318,10 @@ cudaError_t launch_scale_features(const Plan &p, void *ws, int wave, cudaStream_
   const dim3 grid((max_nI + 7) / 8, s1 - s0);
   if (max_nI > 0) { interior_rows_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.w_int); DDELM_COUNT_LAUNCH(); }
   if (r1 > r0) {
-    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
-    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_c1); DDELM_COUNT_LAUNCH(); }
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
   }
-  if (e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
+  if (e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
   if (max_nI > 0) { interior_rows_ds_kernel<<<grid, 256, 0, s>>>(subs, s0, db, p.o_w, p.o_fc, p.o_exp2, p.o_xint, p.o_aint, p.o_gaint, p.op, p.inv_scale); DDELM_COUNT_LAUNCH(); }
   if (r1 > r0) {
     { special_rows_ds_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.inv_scale); DDELM_COUNT_LAUNCH(); }
@@ -346,11 +347,11 @@ cudaError_t launch_features(const Plan &p, void *ws, int wave, cudaStream_t s) {
   }
   const int r0 = p.wave_row0[wave], r1 = p.wave_row0[wave + 1];
   if (r1 > r0) {
-    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
-    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_c1); DDELM_COUNT_LAUNCH(); }
+    { special_rows_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
+    { special_combine_kernel<<<(unsigned)(r1 - r0), 256, 0, s>>>(rows + r0, subs, db, p.o_w, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
   }
   const int e0 = p.wave_row0[p.n_waves], e1 = int(p.rows.size());
-  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1); DDELM_COUNT_LAUNCH(); }
+  if (wave == 0 && e1 > e0) { special_rows_kernel<<<(unsigned)(e1 - e0), 256, 0, s>>>(rows + e0, subs, db, p.o_w, p.o_fc, p.o_exp2, p.w_c1, p.w_f0, p.w_f1); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 

@@ -73,7 +73,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail("theta must be in [0,1]");
   if (!(o.eps_rel >= 0.0) || !(o.tol > 0.0) || o.max_iters < 1) return fail("bad options");
   if (o.precision != DDELM_PREC_FP64 && o.precision != DDELM_PREC_MIXED) return fail("bad precision");
-  if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_CQR2_SERIES || o.setup_passes < 0 ||
+  if (o.setup_scheme < DDELM_SCHEME_AUTO || o.setup_scheme > DDELM_SCHEME_CQR2_SERIES_DW || o.setup_passes < 0 ||
       o.setup_passes > 8)
     return fail("bad setup scheme");
   if (o.barrier_timeout_ms < 0 || o.inject_barrier_stall < 0 || o.inject_barrier_stall > 1)
@@ -85,9 +85,11 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.keep = o.keep_matrices != 0;
   P.inv_scale = pr.scale != 0.0 ? 1.0 / pr.scale : 0.0;
   if (pr.op == DDELM_OP_BIHARMONIC) {
-    if (!(pr.scale > 0.0)) return fail("biharmonic needs scale > 0");
-    // the system in u and v = Lap u / s^2 (the reweighting of the loss terms)
-    P.w_c1 = P.inv_scale * P.inv_scale;
+    // the reweighting of the loss terms: every derivative of order k times H^k
+    const double H = std::sqrt((pr.x1 - pr.x0) / pr.nx * ((pr.y1 - pr.y0) / pr.ny));
+    P.w_f0 = H;
+    P.w_c1 = H * H;
+    P.w_f1 = H * H * H;
     P.w_int = P.w_c1 * P.w_c1;
   }
   const int nx = pr.nx, ny = pr.ny, n_sub = nx * ny;
@@ -444,7 +446,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       P.n_pass = 2;
       P.polish = false;
       P.tri_v = true;
-    } else if (sch == DDELM_SCHEME_CQR2_SERIES) {
+    } else if (sch == DDELM_SCHEME_CQR2_SERIES || sch == DDELM_SCHEME_CQR2_SERIES_DW) {
       P.n_pass = 2;
       P.polish = true;
       P.tri_v = false;
@@ -815,7 +817,8 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // [K; eps I] and [K-bar; eps-bar I] by shifted CholeskyQR with every O(m M^2)
   // and O(M^3) product a GEMM phase, then the local operators.
   const bool fp32 = P.scheme == DDELM_SCHEME_FP32;
-  const bool series = P.scheme == DDELM_SCHEME_CQR2_SERIES;
+  const bool series = P.scheme == DDELM_SCHEME_CQR2_SERIES || P.scheme == DDELM_SCHEME_CQR2_SERIES_DW;
+  const bool dw = P.scheme == DDELM_SCHEME_CQR2_SERIES_DW;  // double-FP32 Cholesky factors
   fp64_tiles = o.precision != DDELM_PREC_MIXED;
   // MIXED, FP64 passes: the Cholesky kernel (FP64 on CUDA cores, one SM per
   // matrix) inverts only the 128 x 128 diagonal blocks of R
@@ -911,6 +914,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             c.shift_rel = 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) * u;
             if (o.precision == DDELM_PREC_MIXED)
               c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -lv_first64));
+            if (dw) {
+              // double-FP32 factor: the same bound with u = 2^-46
+              c.prec = 2;
+              c.shift_rel = std::max(c.shift_rel, 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) *
+                                                      std::ldexp(1.0, -46));
+            }
           } else {
             // FP32 factor: the shift keeps the FP32 Cholesky away from breakdown and
             // limits the condition number each pass removes to about 1/shift

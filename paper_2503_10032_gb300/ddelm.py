@@ -73,6 +73,7 @@ EXPORTS = ("ddelm_query", "ddelm_setup", "ddelm_refactor", "ddelm_solve", "ddelm
            "ddelm_status_string", "ddelm_last_error")
 DDELM_STATIC_SCRATCH_DOUBLES = 1048576
 DDELM_SCHEME_AUTO, DDELM_SCHEME_FP64CQR3, DDELM_SCHEME_FP32, DDELM_SCHEME_CQR2_SERIES = 0, 1, 2, 3
+DDELM_SCHEME_CQR2_SERIES_DW = 4
 DDELM_PROF_CLASSES = 8
 PROF_CLASS_NAMES = ("features", "gemm_f64", "chol_inv", "cg_persistent", "other", "slicing", "tc_gemm")
 

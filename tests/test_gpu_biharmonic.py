@@ -1,12 +1,12 @@
 """Biharmonic operator (the coupled system of Sec. 2.1) on the GPU against the
 FP64 oracle, through the C ABI: fourth-order interior rows, two boundary and
 two interface components per point, the per-component change of variables
-and A_m rows, the reweighted system in u and v = Lap u / s^2, the solution in
+and A_m rows, the reweighted system (derivatives of order k times H^k), the solution in
 both precisions.
 
 Tolerances: the spread of two backward-stable FP64 factorisations of the same
 ridge problems (oracle with Householder-QR vs SVD pseudo-inverses), measured
-on these cases, is at most 9.9e-11 (mu) and 1.7e-9 (u, the 3x3 two-RHS
+on these cases, is at most 5.8e-11 (mu) and 1.8e-9 (u, the 3x3 two-RHS
 case); the bounds below are 1e-9 (mu) and 5e-9 (u)."""
 import numpy as np
 import pytest
@@ -58,10 +58,10 @@ def _problem(case):
 
 @pytest.mark.parametrize("case", [BIH[1], BIH[2], BIH[5]])
 def test_biharmonic_rows_to_rounding(D, case):
-    """Every row of K_c, K-bar and A_m (Lap^2 phi / s^4, phi and Lap phi / s^2 at
-    boundary and interface points, both fluxes, both components' change of
-    variables and corner rows) within a few units of rounding of the oracle's,
-    relative to the row's largest entry."""
+    """Every row of K_c, K-bar and A_m (H^4 Lap^2 phi, phi and H^2 Lap phi at
+    boundary and interface points, both weighted fluxes, both components'
+    change of variables and corner rows) within a few units of rounding of the
+    oracle's, relative to the row's largest entry."""
     nx, ny, M, nI, e, eps, th, R, seed = case
     p = _problem(case)
     o = odd.DDELMOracle(p, odd.Options(eps_rel=eps, theta=th))

@@ -75,16 +75,19 @@ def test_too_few_fp32_passes_is_reported(D):
                  setup_scheme=D.DDELM_SCHEME_FP32, setup_passes=2)
 
 
+@pytest.mark.parametrize("scheme", ["fp64 factors", "double-fp32 factors"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", SCHEME_CASES[:3])
-def test_cqr2_series_scheme(D, case, prec):
-    """Two Cholesky passes, the third replaced by the series of (I + E)^{-1/2}."""
+def test_cqr2_series_scheme(D, case, prec, scheme):
+    """Two Cholesky passes, the third replaced by the series of (I + E)^{-1/2};
+    the two factors in FP64 or in double-FP32 arithmetic."""
     nx, ny, M, nI, e, eps, R, seed, _ = case
     p = inputs.small_problem(nx, ny, M=M, n_int=nI, edge_pts=e, n_rhs=R, seed=seed)
     o = odd.DDELMOracle(p, odd.Options(eps_rel=eps))
     pr = D.DDELM_PREC_FP64 if prec == "fp64" else D.DDELM_PREC_MIXED
     s, mu, u, info, rc = _solve(D, p, eps_rel=eps, tol=1e-11, precision=pr,
-                                setup_scheme=D.DDELM_SCHEME_CQR2_SERIES)
+                                setup_scheme=D.DDELM_SCHEME_CQR2_SERIES if scheme == "fp64 factors"
+                                else D.DDELM_SCHEME_CQR2_SERIES_DW)
     assert rc == D.DDELM_OK
     tol_op = 1e-9 if eps >= 1e-6 else 1e-6
     for i in range(p.n_sub):
@@ -110,7 +113,7 @@ def test_fp32_scheme_uneven(D):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("scheme", [1, 2, 3])
+@pytest.mark.parametrize("scheme", [1, 2, 3, 4])
 def test_variable_coefficient_operator(D, prec, scheme):
     """-div(a grad u) = f with a = 1 + 0.5 sin(2 pi x) sin(2 pi y): local operators and solution."""
     p = inputs.small_problem(3, 3, M=80, n_int=200, edge_pts=6, n_rhs=2, seed=21, op=inputs.OP_DIFFUSION)

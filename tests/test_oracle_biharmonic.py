@@ -97,8 +97,8 @@ def test_biharmonic_structured_equals_dense_bruteforce(case):
 
 def test_biharmonic_plain_flux_rows():
     """Plain A (Eq. (ddelm)) for the second component: a corner row is d Lap phi/dn
-    at the corner with each of the two edges' outward normals, summed (divided
-    by s^2: the second component is Lap u / s^2)."""
+    at the corner with each of the two edges' outward normals, summed (times
+    H^3, the weight of a third derivative)."""
     p = inputs.small_problem(3, 3, M=12, n_int=40, edge_pts=3, n_rhs=1, seed=9, op=inputs.OP_BIHARMONIC)
     o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6, use_Am=False))
     L, sl = o.loc[4], o.lay.subs[4]
@@ -108,8 +108,9 @@ def test_biharmonic_plain_flux_rows():
         xy = o.lay.vxy(v)[None, :]
         nx_ = 1.0 if v[0] == 2 else -1.0
         ny_ = 1.0 if v[1] == 2 else -1.0
+        H3 = (o.lay.hx * o.lay.hy) ** 1.5
         want = (ddelm.F_lap_phi(L.w, L.b, xy, np.array([[nx_, 0.0]])) +
-                ddelm.F_lap_phi(L.w, L.b, xy, np.array([[0.0, ny_]]))) / p.scale ** 2
+                ddelm.F_lap_phi(L.w, L.b, xy, np.array([[0.0, ny_]]))) * H3
         np.testing.assert_allclose(L.Ahat[k], want[0], rtol=1e-13, atol=1e-13 * np.abs(want).max())
 
 
@@ -163,13 +164,15 @@ def test_biharmonic_manufactured_solution_converges():
 
 
 def test_biharmonic_reweighting():
-    """The biharmonic system is written for u and v = Lap u / s^2: interior rows
-    Lap^2 phi / s^4 with data f / s^4; the second component's boundary,
-    continuity and flux rows Lap phi / s^2 and (d Lap phi/dn) / s^2, with the
-    boundary data Lap u / s^2; the first component's rows unscaled."""
-    p = inputs.small_problem(3, 3, M=14, n_int=50, edge_pts=2, n_rhs=1, seed=4, op=inputs.OP_BIHARMONIC)
+    """Every derivative of order k times H^k (H the subdomain size): interior
+    rows H^4 Lap^2 phi with data H^4 f; the second component's boundary and
+    continuity rows H^2 Lap phi with boundary data H^2 Lap u; flux rows
+    H d phi/dn and H^3 d Lap phi/dn; point values unscaled.  A 3x2 grid on
+    [0, 1.5] x [0, 1] has square subdomains of side H = 0.5."""
+    p = inputs.make_problem(3, 2, 14, 50, 2, scale=3.0, init="uniform", seed=4, solutions=[inputs._sin_sin(1, 1)],
+                            op=inputs.OP_BIHARMONIC, box=(0.0, 1.5, 0.0, 1.0), n_eval=8)
     o = ddelm.DDELMOracle(p, ddelm.Options(eps_rel=1e-6))
-    s = p.scale
+    s = 2.0   # 1 / H
     L, sl = o.loc[4], o.lay.subs[4]
     i0 = int(p.n_int[:4].sum())
     xI = p.x_int[i0:i0 + L.nI]
@@ -179,7 +182,9 @@ def test_biharmonic_reweighting():
     np.testing.assert_allclose(L.K[L.nI + kb:L.nI + L.nB], ddelm.lap_phi(L.w, L.b, sl.bnd_xy[kb:]) / s ** 2,
                                rtol=1e-14, atol=0)
     kd = L.nDl // 2
-    F1 = ddelm.F_lap_phi(L.w, L.b, sl.dl_xy[kd:], sl.dl_normal[kd:]) / s ** 2
+    F0 = ddelm.F_phi(L.w, L.b, sl.dl_xy[:kd], sl.dl_normal[:kd]) / s
+    F1 = ddelm.F_lap_phi(L.w, L.b, sl.dl_xy[kd:], sl.dl_normal[kd:]) / s ** 3
+    np.testing.assert_allclose(L.Ahat[L.nPi:L.nPi + kd], F0, rtol=1e-14, atol=0)
     np.testing.assert_allclose(L.Ahat[L.nPi + kd:], F1, rtol=1e-14, atol=0)
     np.testing.assert_allclose(L.Kbar[L.m - kd:], F1, rtol=1e-14, atol=0)
     np.testing.assert_allclose(L.f[:L.nI, 0], p.f_int[i0:i0 + L.nI, 0] / s ** 4, rtol=1e-15, atol=0)
