@@ -107,11 +107,12 @@ extern "C" {
 #define DDELM_SCHEME_FP64CQR3 1
 #define DDELM_SCHEME_FP32 2
 #define DDELM_SCHEME_CQR2_SERIES 3
-/* CQR2_SERIES_DW: as CQR2_SERIES, the two Cholesky factors computed in
- * double-FP32 arithmetic (pairs of FP32 numbers, about 46 significant bits) on
- * the FP32 pipe instead of FP64; they are preconditioners only (every product
- * with them is FP64-exact and the series polish is checked), and the first
- * pass's shift covers the 2^-46 rounding. */
+/* CQR2_SERIES_DW: as CQR2_SERIES, the factor of the shifted first pass computed
+ * in double-FP32 arithmetic (pairs of FP32 numbers, about 46 significant bits)
+ * on the FP32 pipe instead of FP64: it is a preconditioner only (every product
+ * with it is FP64-exact) and the pass's shift covers the 2^-46 rounding.  The
+ * unshifted second pass stays FP64 (its factor sets the |E| the series must
+ * remove). */
 #define DDELM_SCHEME_CQR2_SERIES_DW 4
 
 typedef struct ddelm_options {

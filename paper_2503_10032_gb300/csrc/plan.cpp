@@ -914,8 +914,10 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             c.shift_rel = 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) * u;
             if (o.precision == DDELM_PREC_MIXED)
               c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -lv_first64));
-            if (dw) {
-              // double-FP32 factor: the same bound with u = 2^-46
+            if (dw && k == 0) {
+              // double-FP32 factor of the shifted first pass: the same bound with u = 2^-46.
+              // The unshifted second pass stays FP64: its factor leaves |E| ~ M u cond(G1)
+              // for the series, about 4e-7 in FP64 but near the 1e-4 limit at u = 2^-46.
               c.prec = 2;
               c.shift_rel = std::max(c.shift_rel, 11.0 * (double(d.m + d.M) * d.M + double(d.M) * (d.M + 1)) *
                                                       std::ldexp(1.0, -46));
