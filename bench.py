@@ -536,6 +536,10 @@ def main():
     line["gpu_launches_source"] = ("kernel launches of the library counted in the profiled pass (the same "
                                    f"{args.steps} steps as the timed region, whose captured graphs replay them)")
     line["graphs"] = graphs
+    tune = D.ddelm_inspect(solver.h, 0, 11, 4)
+    line["autotune"] = {"phases_timed": int(tune[0]), "switched": int(tune[1]),
+                        "ms_rule_widths": float(tune[2]), "ms_chosen_widths": float(tune[3]),
+                        "note": "tensor-core tile width per GEMM phase, timed on the handle's first setup"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

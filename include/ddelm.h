@@ -102,7 +102,7 @@ extern "C" {
  * The series are checked: max |E| > 1e-4 fails the setup (RANK_DEFICIENT).
  * Automatic: FP64CQR3 in FP64 precision; in MIXED, FP32 once some subdomain has
  * M >= 512 (where the O(M^3) FP64 Cholesky of one SM per matrix dominates),
- * else CQR2_SERIES. */
+ * else CQR2_SERIES_DW (defined below). */
 #define DDELM_SCHEME_AUTO 0
 #define DDELM_SCHEME_FP64CQR3 1
 #define DDELM_SCHEME_FP32 2
@@ -145,6 +145,12 @@ typedef struct ddelm_options {
                              plain corner flux row above; requires theta = 0 (the NN map of
                              Sec. 3.1 belongs to the coarse-space method). 0: the coarse space
                              of Sec. 3 */
+  int autotune;           /* MIXED: 1 = the first setup of a handle (ddelm_setup) times both tile
+                             shapes of every tensor-core GEMM phase whose products overwrite their
+                             output (128 x 64 tiles with four slice levels per group, 128 x 128
+                             with two) and keeps the faster for every later setup; phases that
+                             accumulate keep the fixed rule (128 wide when every contraction is
+                             longer than 1024).  Results are FP64-exact either way.  0: the rule */
 } ddelm_options;
 
 typedef struct ddelm_problem {
@@ -272,7 +278,9 @@ int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta
  * {scheme, Cholesky passes before the last, setup waves, subdomains per wave,
  * setup graph captured, solve graph captured} (sub ignored, out_len >= 4; the
  * last two when out_len >= 6), 10 V = R^{-1} of the ridge factorisation of
- * [K_c^i; eps I] [M x M].  Blocks 0-2 are
+ * [K_c^i; eps I] [M x M], 11 the tile-shape autotuner's outcome {phases timed,
+ * phases switched to the other width, their time in ms with the rule's widths,
+ * with the chosen widths} (sub ignored, out_len >= 4).  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */

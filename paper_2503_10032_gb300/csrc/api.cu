@@ -41,6 +41,10 @@ struct ddelm_handle {
   long long solves = 0;
   bool fwd_valid = false;  // the solve staging holds the data and solution of the last ddelm_solve
   bool graph_off = false;  // capture unavailable (or disabled by the options)
+  // tile-shape autotuner: pending until the first setup has run; its outcome
+  bool tune_pending = false, capturing = false;
+  int tune_phases = 0, tune_switched = 0;
+  double tune_ms_rule = 0.0, tune_ms_chosen = 0.0;
   // profiling: event pairs around launches, reduced on ddelm_profile
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -262,9 +266,12 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub, bool capture) 
   Plan &p = h->plan;
   double *db = dbase(h);
   {
+    h->capturing = capture;
     const int rc = capture ? run_graph(h, s, &h->setup_exec, [&] { return enqueue_setup(h, s); })
                            : enqueue_setup(h, s);
+    h->capturing = false;
     if (rc != DDELM_OK) return rc;
+    if (!capture) h->tune_pending = false;  // the first direct setup has tuned every phase it could
   }
   CK(cudaStreamSynchronize(s));
   int oz_err = 0;
@@ -292,8 +299,45 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
   // a setup GEMM phase runs on the tensor cores (BF16 slices) in MIXED precision
   auto gemm = [&](int q) -> int {
     if (p.mixed && q < (int)p.oz_phase.size() && p.oz_phase[q].ntile > 0) {
-      LAUNCH(PC_SLICE, launch_slices(p, p.oz_phase[q], h->ws, s));
-      LAUNCH(PC_TC, launch_oz_gemm(p, p.oz_phase[q], h->ws, s));
+      OzPhase &ph = p.oz_phase[q];
+      LAUNCH(PC_SLICE, launch_slices(p, ph, h->ws, s));
+      if (h->tune_pending && !h->capturing && ph.overwrite && ph.ntile_alt > 0) {
+        // autotuner: the other tile width, then the rule's (whose output stays);
+        // the faster is kept for every later setup (and the captured graph)
+        OzPhase alt = ph;
+        alt.tile0 = ph.tile0_alt;
+        alt.ntile = ph.ntile_alt;
+        alt.bn = ph.bn_alt;
+        cudaEvent_t ev[4] = {};
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(ev[0], s));
+        LAUNCH(PC_TC, launch_oz_gemm(p, alt, h->ws, s));
+        CK(cudaEventRecord(ev[1], s));
+        CK(cudaEventRecord(ev[2], s));
+        LAUNCH(PC_TC, launch_oz_gemm(p, ph, h->ws, s));
+        CK(cudaEventRecord(ev[3], s));
+        CK(cudaEventSynchronize(ev[3]));
+        float t_alt = 0.f, t_rule = 0.f;
+        CK(cudaEventElapsedTime(&t_alt, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&t_rule, ev[2], ev[3]));
+        for (auto &e : ev) CK(cudaEventDestroy(e));
+        h->tune_phases++;
+        h->tune_ms_rule += t_rule;
+        if (t_alt < 0.97f * t_rule) {  // a clear gain only: timings of one run carry noise
+          std::swap(ph.tile0, ph.tile0_alt);
+          std::swap(ph.ntile, ph.ntile_alt);
+          std::swap(ph.bn, ph.bn_alt);
+          std::swap(ph.flops, ph.flops_alt);
+          p.oz_flops += ph.flops - ph.flops_alt;
+          h->tune_switched++;
+          h->tune_ms_chosen += t_alt;
+          LAUNCH(PC_TC, launch_oz_gemm(p, ph, h->ws, s));  // the kept width's output
+        } else {
+          h->tune_ms_chosen += t_rule;
+        }
+        return DDELM_OK;
+      }
+      LAUNCH(PC_TC, launch_oz_gemm(p, ph, h->ws, s));
     } else {
       LAUNCH(PC_GEMM, launch_gemm_phase(p, G[q], h->ws, s));
     }
@@ -381,6 +425,7 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
     return rc;
   }
   h->graph_off = prob->opt.disable_graphs != 0;
+  h->tune_pending = prob->opt.autotune != 0 && prob->opt.precision == DDELM_PREC_MIXED;
   if (workspace_bytes < h->plan.bytes_total) {
     delete h;
     return DDELM_ERR_INVALID_ARG;
@@ -725,6 +770,14 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       host_out[4] = p.mixed ? fleft : fs;
       if (out_len >= 6) host_out[5] = p.chol_flops32;
       if (out_len >= 7) host_out[6] = p.slice_bytes;
+      return DDELM_OK;
+    }
+    case 11: {  // tile-shape autotuner: phases timed, phases switched, their ms by the rule / as chosen
+      if (out_len < 4) return DDELM_ERR_INVALID_ARG;
+      host_out[0] = h->tune_phases;
+      host_out[1] = h->tune_switched;
+      host_out[2] = h->tune_ms_rule;
+      host_out[3] = h->tune_ms_chosen;
       return DDELM_OK;
     }
     case 9: {

@@ -43,6 +43,11 @@ struct OzPhase {
   int tile0, ntile;      // OzTile range
   int max_rpad, max_kpad;
   int bn;                // tile width: 64 (four levels per group) or 128 (two)
+  // the other tile width's tile list (ntile_alt = 0: none, the contraction is too
+  // long for the four-level integer sums), for the autotuner
+  int tile0_alt, ntile_alt, bn_alt;
+  int overwrite;         // every product has beta = 0: the phase may run twice
+  double flops, flops_alt;  // slice-pair flops of the two tile lists
 };
 
 cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);

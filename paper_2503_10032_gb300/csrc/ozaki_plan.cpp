@@ -59,14 +59,15 @@ int build_mixed(Plan &P, long long &cur) {
     }
     P.odesc.reserve(nd);
     P.sdesc.reserve(2 * nd);
-    P.otile.reserve(nt);
+    P.otile.reserve(nt + nt / 2 + 16);  // both tile widths
   }
   std::vector<std::pair<int, long long>> scale_fix;  // (slice desc, relative scale offset)
   long long scale_base = 0;
   std::vector<int> phase_slices_begin;
   for (size_t q = 0; q < n_setup && q < P.setup_gemm.size(); ++q) {
     const GemmPhase &gp = P.setup_gemm[q];
-    OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0, 64};
+    OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0, 64, 0, 0, 64, 0, 0.0,
+               0.0};
     if (gp.ndesc == 0) {
       P.oz_phase[q] = op;
       continue;
@@ -84,7 +85,7 @@ int build_mixed(Plan &P, long long &cur) {
     // the 96-bit integer sum of the four-level tiles holds up to 16 k-chunks
     // (|X| < 2^(43 + 48 + 4)); longer contractions take the FP64 combination
     wide = wide || long_k;
-    const int OZ_BN = wide ? 128 : 64;
+    const int OZ_BN = wide ? 128 : 64;  // the rule; the autotuner may switch to the other width
     op.bn = OZ_BN;
     std::unordered_map<Key, int, KeyHash> seen;
     seen.reserve(2 * (size_t)gp.ndesc);
@@ -116,8 +117,10 @@ int build_mixed(Plan &P, long long &cur) {
       op.max_kpad = std::max(op.max_kpad, s.Kpad);
       return idx;
     };
+    op.overwrite = 1;
     for (int t = 0; t < gp.ndesc; ++t) {
       const GemmDesc &d = P.gdesc[gp.desc0 + t];
+      if (d.beta != 0.0) op.overwrite = 0;
       const int sa = slice_of(d.a, d.lda, d.ta, d.m, d.k);
       const int sb = slice_of(d.b, d.ldb, d.tb ? 0 : 1, d.n, d.k);
       OzDesc o;
@@ -137,27 +140,37 @@ int build_mixed(Plan &P, long long &cur) {
       o.scaleB = P.sdesc[sb].scale;
       o.alpha = d.alpha;
       o.beta = d.beta;
-      const int di = int(P.odesc.size());
       P.odesc.push_back(o);
       op.ndesc++;
-      const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + OZ_BN - 1) / OZ_BN;
-      const int nkb = o.Kpad / OZ_BK;
-      // tensor-core work: every level's pairs over the k blocks a tile needs
-      double pairs = 0;
-      for (int l = 0; l < S; ++l) pairs += l + 1;
-      for (int x = 0; x < tm; ++x)
-        for (int y = 0; y < tn; ++y) {
-          if (d.syrk && x * OZ_BM >= (y + 1) * OZ_BN) continue;  // strictly below the diagonal
-          int kb0 = 0, kb1 = nkb;
-          // op(B)[k][j] = 0 for k > j ; op(A)[i][k] = 0 for k < i
-          if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (OZ_BN / OZ_BK));
-          if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / OZ_BK));
-          if (kb1 < kb0) kb1 = kb0;
-          P.otile.push_back({di, x, y, kb0, kb1, 0, 0, 0});
-          op.ntile++;
-          P.oz_flops += 2.0 * OZ_BM * OZ_BN * (double)(kb1 - kb0) * OZ_BK * pairs;
-        }
     }
+    // tile lists: the rule's width, then (for the autotuner) the other one
+    double pairs = 0;  // tensor-core work: every level's pairs over the k blocks a tile needs
+    for (int l = 0; l < S; ++l) pairs += l + 1;
+    auto emit_tiles = [&](int BN, int &ntile, double &flops) {
+      for (int t = 0; t < gp.ndesc; ++t) {
+        const GemmDesc &d = P.gdesc[gp.desc0 + t];
+        const int di = op.desc0 + t;
+        const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + BN - 1) / BN;
+        const int nkb = P.odesc[di].Kpad / OZ_BK;
+        for (int x = 0; x < tm; ++x)
+          for (int y = 0; y < tn; ++y) {
+            if (d.syrk && x * OZ_BM >= (y + 1) * BN) continue;  // strictly below the diagonal
+            int kb0 = 0, kb1 = nkb;
+            // op(B)[k][j] = 0 for k > j ; op(A)[i][k] = 0 for k < i
+            if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (BN / OZ_BK));
+            if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / OZ_BK));
+            if (kb1 < kb0) kb1 = kb0;
+            P.otile.push_back({di, x, y, kb0, kb1, 0, 0, 0});
+            ntile++;
+            flops += 2.0 * OZ_BM * BN * (double)(kb1 - kb0) * OZ_BK * pairs;
+          }
+      }
+    };
+    emit_tiles(OZ_BN, op.ntile, op.flops);
+    P.oz_flops += op.flops;
+    op.bn_alt = OZ_BN == 64 ? 128 : 64;
+    op.tile0_alt = int(P.otile.size());
+    if (!long_k) emit_tiles(op.bn_alt, op.ntile_alt, op.flops_alt);
     op.nslice = int(P.sdesc.size()) - op.slice0;
     for (int t = op.slice0; t < op.slice0 + op.nslice; ++t)
       if (P.sdesc[t].S != S) {  // the slicing launch takes one level count

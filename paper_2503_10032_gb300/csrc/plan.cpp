@@ -80,6 +80,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     return fail("bad barrier options");
   if (o.plain_flux_corners < 0 || o.plain_flux_corners > 1) return fail("bad plain_flux_corners");
   if (o.vanilla < 0 || o.vanilla > 1) return fail("bad vanilla");
+  if (o.autotune < 0 || o.autotune > 1) return fail("bad autotune");
   if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
@@ -440,7 +441,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     int sch = o.setup_scheme;
     if (sch == DDELM_SCHEME_AUTO)
       sch = o.precision != DDELM_PREC_MIXED ? DDELM_SCHEME_FP64CQR3
-                                            : (max_M >= 512 ? DDELM_SCHEME_FP32 : DDELM_SCHEME_CQR2_SERIES);
+                                            : (max_M >= 512 ? DDELM_SCHEME_FP32 : DDELM_SCHEME_CQR2_SERIES_DW);
     P.scheme = sch;
     if (sch == DDELM_SCHEME_FP64CQR3) {
       P.n_pass = 2;
@@ -1415,13 +1416,20 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
     }
     for (const auto &ph : P.oz_phase) {
       if (ph.bn != 64 && ph.bn != 128) return fail("internal: tensor-core tile width");
-      for (int q = ph.tile0; q < ph.tile0 + ph.ntile; ++q) {
-        const OzTile &t = P.otile[q];
-        if (t.desc < ph.desc0 || t.desc >= ph.desc0 + ph.ndesc) return fail("internal: tensor-core tile");
-        const OzDesc &od = P.odesc[t.desc];
-        if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * ph.bn > od.RpadB)
-          return fail("internal: tensor-core tile box");
-        if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
+      if (ph.ntile_alt > 0 && ph.bn_alt + ph.bn != 192) return fail("internal: tensor-core alternative width");
+      // both tile lists (the rule's and the autotuner's alternative)
+      for (int which = 0; which < 2; ++which) {
+        const int t0 = which ? ph.tile0_alt : ph.tile0, nt = which ? ph.ntile_alt : ph.ntile;
+        const int bn = which ? ph.bn_alt : ph.bn;
+        if (t0 < 0 || (size_t)t0 + nt > P.otile.size()) return fail("internal: tensor-core tile list");
+        for (int q = t0; q < t0 + nt; ++q) {
+          const OzTile &t = P.otile[q];
+          if (t.desc < ph.desc0 || t.desc >= ph.desc0 + ph.ndesc) return fail("internal: tensor-core tile");
+          const OzDesc &od = P.odesc[t.desc];
+          if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * bn > od.RpadB)
+            return fail("internal: tensor-core tile box");
+          if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
+        }
       }
     }
     const long long cg_need = 12LL * std::max(nd, 1) * R + 14LL * std::max(n_pi, 1) * R + 2048 * 32;

@@ -1,6 +1,8 @@
 """Factorisation schemes and the variable-coefficient operator against the FP64
 oracle: the FP32-Cholesky scheme (shifted FP32 passes, exact updates, series
-polish of the last factor) in both precisions, and -div(a grad u) problems."""
+polish of the last factor) in both precisions, the CQR2 + series scheme with
+FP64 or double-FP32 first factors, the tensor-core tile autotuner, and
+-div(a grad u) problems."""
 import numpy as np
 import pytest
 
@@ -21,6 +23,12 @@ def D():
     from paper_2503_10032_gb300 import ddelm
     return ddelm
 
+
+
+def _data(p):
+    import torch
+    return (torch.tensor(p.f_int, dtype=torch.float64, device="cuda"),
+            torch.tensor(p.g_bnd, dtype=torch.float64, device="cuda"))
 
 
 def _solve(D, p, **kw):
@@ -131,3 +139,27 @@ def test_variable_coefficient_operator(D, prec, scheme):
     ref = odd.solve(p, odd.Options(eps_rel=1e-6))
     assert close(mu[o.n_pi:], ref["mu_delta"], 1e-8, "mu[o.n_pi:] vs ref['mu_delta']")
     assert close(u, ref["u_eval"], 1e-8, "u vs ref['u_eval']")
+
+
+def test_tile_autotuner(D):
+    """The first setup times both tensor-core tile shapes of every phase whose
+    products overwrite their output and keeps the faster: the solution is the
+    same as with the fixed rule (both shapes are exact slice expansions) and
+    the tuner reports what it timed."""
+    p = inputs.small_problem(3, 3, M=130, n_int=300, edge_pts=7, n_rhs=1, seed=6)
+    ref = odd.solve(p, odd.Options(eps_rel=1e-6))
+    sols = {}
+    for tune in (False, True):
+        s, mu, u, info, rc = _solve(D, p, eps_rel=1e-6, tol=1e-12, precision=D.DDELM_PREC_MIXED, autotune=tune)
+        assert rc == D.DDELM_OK
+        rep = D.ddelm_inspect(s.h, 0, 11, 4)
+        if tune:
+            assert rep[0] > 0 and 0 <= rep[1] <= rep[0] and rep[2] > 0 and rep[3] <= rep[2] * 1.0001
+        else:
+            assert rep[0] == 0
+        s.refactor()                                # a second setup with the kept widths
+        c2, mu2, u2, info2, rc2 = s.solve(*_data(p))
+        assert rc2 == D.DDELM_OK
+        sols[tune] = u2.cpu().numpy()
+        assert close(u, ref["u_eval"], 1e-9, f"autotune={tune} u")
+    assert close(sols[True], sols[False], 1e-10, "autotuned vs rule widths")
