@@ -102,7 +102,8 @@ extern "C" {
  * The series are checked: max |E| > 1e-4 fails the setup (RANK_DEFICIENT).
  * Automatic: FP64CQR3 in FP64 precision; in MIXED, FP32 once some subdomain has
  * M >= 512 (where the O(M^3) FP64 Cholesky of one SM per matrix dominates),
- * else CQR2_SERIES_DW (defined below). */
+ * else CQR2_SERIES_DW (defined below), and ddelm_setup falls back to
+ * CQR2_SERIES when that setup reports a failed factorisation. */
 #define DDELM_SCHEME_AUTO 0
 #define DDELM_SCHEME_FP64CQR3 1
 #define DDELM_SCHEME_FP32 2
@@ -150,7 +151,9 @@ typedef struct ddelm_options {
                              output (128 x 64 tiles with four slice levels per group, 128 x 128
                              with two) and keeps the faster for every later setup; phases that
                              accumulate keep the fixed rule (128 wide when every contraction is
-                             longer than 1024).  Results are FP64-exact either way.  0: the rule */
+                             longer than 1024).  The choices are cached for the process by phase
+                             shape, so later handles of the same problem reuse them without
+                             timing.  Results are FP64-exact either way.  0: the rule */
 } ddelm_options;
 
 typedef struct ddelm_problem {

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ddelm_internal.h"
@@ -287,6 +288,35 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub, bool capture) 
   return DDELM_OK;
 }
 
+// Choices of the tile-shape autotuner, kept for the life of the process and
+// shared by every handle: the key is the phase's shape (its products' sizes,
+// levels and triangular flags, and both tile counts), so a later handle with
+// the same phases (a new setup of the same problem) reuses the choice instead
+// of timing again.
+std::mutex g_tune_mutex;
+std::unordered_map<unsigned long long, int> g_tune_bn;
+
+unsigned long long tune_key(const Plan &p, const OzPhase &ph) {
+  unsigned long long k = 1469598103934665603ull;  // FNV-1a over the shape
+  auto mix = [&](long long v) {
+    for (int b = 0; b < 8; ++b) {
+      k ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+      k *= 1099511628211ull;
+    }
+  };
+  mix(ph.ntile);
+  mix(ph.ntile_alt);
+  mix(ph.bn);
+  for (int t = ph.desc0; t < ph.desc0 + ph.ndesc; ++t) {
+    const OzDesc &o = p.odesc[t];
+    mix(o.m);
+    mix(o.n);
+    mix(o.Kpad);
+    mix(o.S);
+  }
+  return k;
+}
+
 // Every launch and copy of the setup, in stream order (no host synchronisation).
 int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
   Plan &p = h->plan;
@@ -304,6 +334,26 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
       if (h->tune_pending && !h->capturing && ph.overwrite && ph.ntile_alt > 0) {
         // autotuner: the other tile width, then the rule's (whose output stays);
         // the faster is kept for every later setup (and the captured graph)
+        const unsigned long long key = tune_key(p, ph);
+        int known = 0;
+        {
+          std::lock_guard<std::mutex> lk(g_tune_mutex);
+          auto it = g_tune_bn.find(key);
+          if (it != g_tune_bn.end()) known = it->second;
+        }
+        if (known) {  // timed before in this process: apply the choice
+          if (known != ph.bn) {
+            std::swap(ph.tile0, ph.tile0_alt);
+            std::swap(ph.ntile, ph.ntile_alt);
+            std::swap(ph.bn, ph.bn_alt);
+            std::swap(ph.flops, ph.flops_alt);
+            p.oz_flops += ph.flops - ph.flops_alt;
+            h->tune_switched++;
+          }
+          h->tune_phases++;
+          LAUNCH(PC_TC, launch_oz_gemm(p, ph, h->ws, s));
+          return DDELM_OK;
+        }
         OzPhase alt = ph;
         alt.tile0 = ph.tile0_alt;
         alt.ntile = ph.ntile_alt;
@@ -323,7 +373,12 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
         for (auto &e : ev) CK(cudaEventDestroy(e));
         h->tune_phases++;
         h->tune_ms_rule += t_rule;
-        if (t_alt < 0.97f * t_rule) {  // a clear gain only: timings of one run carry noise
+        const bool take_alt = t_alt < 0.97f * t_rule;  // a clear gain only: one run's timings carry noise
+        {
+          std::lock_guard<std::mutex> lk(g_tune_mutex);
+          g_tune_bn[key] = take_alt ? alt.bn : ph.bn;
+        }
+        if (take_alt) {
           std::swap(ph.tile0, ph.tile0_alt);
           std::swap(ph.ntile, ph.ntile_alt);
           std::swap(ph.bn, ph.bn_alt);
@@ -434,6 +489,26 @@ int ddelm_setup(const ddelm_problem *prob, void *d_workspace, size_t workspace_b
   h->ws_bytes = workspace_bytes;
   rc = upload(h, prob, static_cast<cudaStream_t>(stream));
   if (rc == DDELM_OK) rc = compute_setup(h, static_cast<cudaStream_t>(stream), info_sub, false);
+  if (rc == DDELM_ERR_RANK_DEFICIENT && h->plan.dw_auto) {
+    // the automatic double-FP32 first factors were not accurate enough for this
+    // problem: FP64 factors (the CQR2_SERIES scheme) and the setup again
+    Plan &p = h->plan;
+    for (const auto &fb : p.dw_fallback) {
+      p.cdesc[fb.first].prec = 0;
+      p.cdesc[fb.first].shift_rel = fb.second;
+    }
+    p.scheme = DDELM_SCHEME_CQR2_SERIES;
+    p.dw_auto = false;
+    const cudaError_t e = cudaMemcpy(h->ws + p.off_cdesc, p.cdesc.data(), p.cdesc.size() * sizeof(CholDesc),
+                                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      record_cuda_error(e, "cudaMemcpy(cdesc)", __FILE__, __LINE__);
+      rc = DDELM_ERR_CUDA;
+    } else {
+      if (info_sub) *info_sub = -1;
+      rc = compute_setup(h, static_cast<cudaStream_t>(stream), info_sub, false);
+    }
+  }
   if (rc != DDELM_OK && rc != DDELM_ERR_RANK_DEFICIENT) {
     ddelm_destroy(h);
     return rc;

@@ -281,6 +281,11 @@ struct Plan {
   // times w_f0 = H (first component) and w_f1 = H^3 (second); 1 for the other
   // operators
   double w_int = 1.0, w_c1 = 1.0, w_f0 = 1.0, w_f1 = 1.0;
+  // automatic double-FP32 first factors: the Cholesky descriptors that take
+  // them and their FP64 shifts, for the fallback to FP64 factors when such a
+  // setup fails (a hard problem where the first factor's accuracy is marginal)
+  bool dw_auto = false;
+  std::vector<std::pair<int, double>> dw_fallback;
   int nb0 = 0;                            // Dirichlet points of the first component
   std::vector<long long> slot_begin, slot_end;  // contiguous setup-scratch extent of each wave slot
   std::vector<SubDev> ssubs;              // feature tables writing into the scale buffers

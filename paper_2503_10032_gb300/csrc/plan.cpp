@@ -443,6 +443,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       sch = o.precision != DDELM_PREC_MIXED ? DDELM_SCHEME_FP64CQR3
                                             : (max_M >= 512 ? DDELM_SCHEME_FP32 : DDELM_SCHEME_CQR2_SERIES_DW);
     P.scheme = sch;
+    P.dw_auto = o.setup_scheme == DDELM_SCHEME_AUTO && sch == DDELM_SCHEME_CQR2_SERIES_DW;
     if (sch == DDELM_SCHEME_FP64CQR3) {
       P.n_pass = 2;
       P.polish = false;
@@ -916,6 +917,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             if (o.precision == DDELM_PREC_MIXED)
               c.shift_rel = std::max(c.shift_rel, 4.0 * d.m * std::pow(64.0, -lv_first64));
             if (dw && k == 0) {
+              P.dw_fallback.push_back({int(P.cdesc.size()), c.shift_rel});
               // double-FP32 factor of the shifted first pass: the same bound with u = 2^-46.
               // The unshifted second pass stays FP64: its factor leaves |E| ~ M u cond(G1)
               // for the series, about 4e-7 in FP64 but near the 1e-4 limit at u = 2^-46.
