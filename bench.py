@@ -432,7 +432,6 @@ def main():
     # step over the class's time per step in the profiled pass
     names = D.PROF_CLASS_NAMES
     n_cls = len(names)
-    k_dom = int(np.argmax(prof_ms[:n_cls]))
     launches_total = int(prof_n.sum())
     peaks = measured_peaks()
     alg_gemm, alg_chol = method_setup_flops(sub_sizes)
@@ -443,6 +442,9 @@ def main():
     bf16_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
     alg_work = {"tc_gemm": alg_gemm * tc_share, "gemm_f64": alg_gemm * (1.0 - tc_share) + flops[2],
                 "chol_inv": alg_chol}
+    # the roofline is the method's algorithmic work over the time of the class
+    # that does it: the largest of the classes that carry that work
+    k_dom = max((i for i, n in enumerate(names) if n in alg_work), key=lambda i: prof_ms[i])
     dom = names[k_dom]
     per_launch_ms = prof_ms[k_dom] / max(prof_n[k_dom], 1)
     work_per_launch = alg_work.get(dom, float("nan")) * args.steps / max(prof_n[k_dom], 1)

@@ -154,6 +154,12 @@ typedef struct ddelm_options {
                              longer than 1024).  The choices are cached for the process by phase
                              shape, so later handles of the same problem reuse them without
                              timing.  Results are FP64-exact either way.  0: the rule */
+  int trim_levels;        /* experiments only (MIXED): slice levels taken off the tensor-core
+                             products of the classes in trim_mask (at least 3 remain), to measure
+                             what each class's level count buys; 0 in normal use */
+  int trim_mask;          /* 1 Grams after the first pass, 2 Q and ridge-block updates, 4 products
+                             of triangular factors, 8 local operators and their inputs, 16 the
+                             first Gram */
 } ddelm_options;
 
 typedef struct ddelm_problem {

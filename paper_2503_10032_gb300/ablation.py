@@ -8,6 +8,15 @@ subdomain).  CG runs to the paper's relative residual 1e-9.
 
     python -m paper_2503_10032_gb300.ablation [--grids 2,4,8,16] [--precision fp64|mixed]
     python -m paper_2503_10032_gb300.ablation --table6 [--grids 2,4,8,16]
+    python -m paper_2503_10032_gb300.ablation --levels
+
+--levels: what the BF16-slice level counts of the MIXED setup buy.  On the
+8x8 / M = 400 workload each class of tensor-core products (Grams after the
+first pass, Q and ridge-block updates, products of triangular factors, local
+operators and their inputs, the first Gram) loses 1, 2 or 3 slice levels in
+turn; each run reports whether the setup succeeds, the relative L2 distance of
+u from the FP64 path (the oracle parity of u on this workload is 3.4e-8, its
+tolerance 1e-7) and the GPU time of one setup + solve.
 
 Prints one JSON line per solve and the two tables in markdown.  --table6: the
 biharmonic problem of Sec. 4.5 (Lap^2 u = f, u = Lap u = 0 on the boundary,
@@ -51,6 +60,50 @@ def run_one(D, prob, torch, timed=False, **kw):
                 rel_l2_error=err, **out)
 
 
+LEVEL_CLASSES = [(16, "first Gram"), (1, "Grams after the first pass"), (2, "Q and ridge-block updates"),
+                 (4, "products of triangular factors"), (8, "local operators and their inputs")]
+
+
+def levels(D, torch, args):
+    from . import inputs
+    prob = inputs.config("poisson_8x8_m400")
+    common = dict(eps_rel=1e-8, tol=1e-8, theta=0.999)
+    f = torch.tensor(prob.f_int, dtype=torch.float64, device="cuda")
+    g = torch.tensor(prob.g_bnd, dtype=torch.float64, device="cuda")
+
+    def run(**kw):
+        s = None
+        try:
+            s = D.Solver(prob, **common, **kw)
+            s.solve(f, g)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.refactor()
+            c, mu, u, info, rc = s.solve(f, g)
+            e1.record()
+            torch.cuda.synchronize()
+            return u.cpu().numpy(), float(e0.elapsed_time(e1)), "ok" if rc == D.DDELM_OK else "not converged"
+        except D.DDELMError as e:
+            return None, None, str(e).split(":")[1].strip()
+        finally:
+            if s is not None:
+                s.close()
+    u64, _, _ = run(precision=D.DDELM_PREC_FP64)
+    base, base_ms, _ = run(precision=D.DDELM_PREC_MIXED)
+    rows = [("none", 0, float(np.linalg.norm(base - u64) / np.linalg.norm(u64)), base_ms, "ok")]
+    for mask, name in LEVEL_CLASSES:
+        for trim in (1, 2, 3):
+            u, ms, st = run(precision=D.DDELM_PREC_MIXED, trim_levels=trim, trim_mask=mask)
+            d = float(np.linalg.norm(u - u64) / np.linalg.norm(u64)) if u is not None else float("nan")
+            rows.append((name, trim, d, ms, st))
+            print(json.dumps(dict(levels=name, trim=trim, rel_l2_u_vs_fp64=d, setup_solve_ms=ms, status=st)),
+                  flush=True)
+    print("\n| class | levels removed | u vs FP64 path | setup + solve (ms) | status |")
+    print("|---|---|---|---|---|")
+    for name, trim, d, ms, st in rows:
+        print(f"| {name} | {trim} | {d:.1e} | {ms if ms is not None else float('nan'):.1f} | {st} |")
+
+
 def table6(D, torch, grids, prec, args):
     """Sec. 4.5: DDELM, DDELM-CS and DDELM-NN on the biharmonic problem."""
     from . import inputs
@@ -81,6 +134,7 @@ def main(argv=None):
     ap.add_argument("--eps-rel", type=float, default=1e-8)
     ap.add_argument("--max-iters", type=int, default=60000)
     ap.add_argument("--table6", action="store_true")
+    ap.add_argument("--levels", action="store_true")
     args = ap.parse_args(argv)
     import torch
     from . import build
@@ -91,6 +145,9 @@ def main(argv=None):
     grids = [int(x) for x in args.grids.split(",")]
     if args.table6:
         table6(D, torch, grids, prec, args)
+        return 0
+    if args.levels:
+        levels(D, torch, args)
         return 0
     t1, t2 = {}, {}
     for n in grids:

@@ -81,6 +81,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.plain_flux_corners < 0 || o.plain_flux_corners > 1) return fail("bad plain_flux_corners");
   if (o.vanilla < 0 || o.vanilla > 1) return fail("bad vanilla");
   if (o.autotune < 0 || o.autotune > 1) return fail("bad autotune");
+  if (o.trim_levels < 0 || o.trim_levels > 6) return fail("bad trim_levels");
   if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
@@ -833,7 +834,11 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // many orders of magnitude inside a row, and the slice truncation is
   // relative to the row maximum: they keep 60 bits.
   const int lv_exact = 9, lv_factor = 10, lv_first64 = 6, lv_shifted32 = 5, lv_small = 4, lv_tiny = 3;
-  auto gemm_step = [&](GemmPhase &ph, int levels) {
+  // cls: the phase's class for the level-trim experiment option (1 Grams after
+  // the first pass, 2 Q and Z updates, 4 products of triangular factors,
+  // 8 local operators and their inputs, 16 the first Gram; 0 the series terms)
+  auto gemm_step = [&](GemmPhase &ph, int levels, int cls) {
+    if (o.trim_levels > 0 && (o.trim_mask & cls)) levels = std::max(3, levels - o.trim_levels);
     P.steps.push_back({STEP_GEMM, int(P.setup_gemm.size())});
     P.setup_gemm.push_back(ph);
     P.setup_levels.push_back(levels);
@@ -872,7 +877,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         add(ph, qk(i, 0, 0), qk(i, 0, 0), scr[i].v[0].G, d.M, d.M, d.nI + d.nB, d.M, d.M, d.M, 1, 0, 0, 1.0, 0.0,
             true);
       }
-      gemm_step(ph, lv0);
+      gemm_step(ph, lv0, 16);
       const int m0 = int(P.mdesc.size());
       for (int i = w0; i < w1; ++i)
         P.mdesc.push_back(MatopDesc{scr[i].v[0].G, 0, scr[i].v[1].G, P.subs[i].M, 3, 2 * i + 1, -1});
@@ -884,7 +889,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           const long long rows = qk(i, t, 0) + (long long)(d.nI + d.nB) * d.M;  // the nG interface rows
           add(ph2, rows, rows, scr[i].v[t].G, d.M, d.M, d.nG, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0, true);
         }
-      gemm_step(ph2, lv0);
+      gemm_step(ph2, lv0, 16);
     }
     for (int k = 0; k <= N; ++k) {
       const bool last = k == N;
@@ -970,7 +975,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
                   add(ph, V + r0 * M + r0, Tb, V + r0 * M + r1, INVB, int(n1), INVB, d.M, int(n1), d.M, 0, 0,
                       GEMM_A_UPPER, -1.0, 0.0);
               }
-            gemm_step(ph, lv_factor);
+            gemm_step(ph, lv_factor, 4);
           }
         }
         if (k == 0) {
@@ -995,7 +1000,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
               add(ph, zk(i, t, k - 1), vk(i, t, k), zk(i, t, k), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
                   GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
           }
-        gemm_step(ph, lv_exact);
+        gemm_step(ph, lv_exact, 2);
       }
       if (k > 0) {
         GemmPhase ph = phase_begin();
@@ -1005,7 +1010,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             add(ph, tk(i, t, k - 1), vk(i, t, k), tk(i, t, k), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
                 GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
           }
-        gemm_step(ph, lv_factor);
+        gemm_step(ph, lv_factor, 4);
       }
       // the Gram of pass k+1: G = Q^T Q, then G += Z^T Z (Z upper triangular)
       const int lv = (fp32 && k + 1 < N) ? lv_shifted32 : lv_exact;
@@ -1017,7 +1022,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             add(ph, qk(i, t, k + 1), qk(i, t, k + 1), scr[i].v[t].G, d.M, d.M, d.m, d.M, d.M, d.M, 1, 0, 0, 1.0,
                 0.0, true);
           }
-        gemm_step(ph, lv);
+        gemm_step(ph, lv, 1);
         GemmPhase ph2 = phase_begin();
         for (int i = w0; i < w1; ++i)
           for (int t = 0; t < 2; ++t) {
@@ -1025,7 +1030,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             add(ph2, zk(i, t, k), zk(i, t, k), scr[i].v[t].G, d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, GEMM_B_UPPER,
                 1.0, 1.0, true);
           }
-        gemm_step(ph2, lv);
+        gemm_step(ph2, lv, 1);
       }
     }
     if (P.polish) {
@@ -1059,14 +1064,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             const SubDev &d = P.subs[i];
             add(ph, scr[i].v[t].G, vk(i, t, N), H(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_B_UPPER, 1.0, 0.0);
           }
-        gemm_step(ph, lv_exact);
+        gemm_step(ph, lv_exact, 4);
         GemmPhase ph2 = phase_begin();
         for (int i = w0; i < w1; ++i)
           for (int t = 0; t < 2; ++t) {
             const SubDev &d = P.subs[i];
             add(ph2, vk(i, t, N), H(i, t), E(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 1, 0, 0, 1.0, 1.0);
           }
-        gemm_step(ph2, lv_exact);
+        gemm_step(ph2, lv_exact, 1);
       }
       GemmPhase ph3 = phase_begin();
       for (int i = w0; i < w1; ++i)
@@ -1074,14 +1079,14 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           const SubDev &d = P.subs[i];
           add(ph3, E(i, t), E(i, t), E2(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, 0, 1.0, 0.0);
         }
-      gemm_step(ph3, lv_small);
+      gemm_step(ph3, lv_small, 0);
       GemmPhase ph5 = phase_begin();
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t) {
           const SubDev &d = P.subs[i];
           add(ph5, E2(i, t), E(i, t), E3(i, t), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, 0, 1.0, 0.0);
         }
-      gemm_step(ph5, lv_tiny);
+      gemm_step(ph5, lv_tiny, 0);
       m0 = int(P.mdesc.size());
       for (int i = w0; i < w1; ++i)
         for (int t = 0; t < 2; ++t)
@@ -1096,7 +1101,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
             add(ph4, vk(i, t, N), E2(i, t), scr[i].v[t].V3, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0, GEMM_A_UPPER, 1.0,
                 0.0);
           }
-        gemm_step(ph4, lv_exact);
+        gemm_step(ph4, lv_exact, 4);
       }
     }
     // R^{-1} = T_{N-1} V3
@@ -1108,7 +1113,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           add(ph, tk(i, t, N - 1), scr[i].v[t].V3, scr[i].v[t].V, d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
               GEMM_A_UPPER | TU, 1.0, 0.0);
         }
-      gemm_step(ph, lv_factor);
+      gemm_step(ph, lv_factor, 4);
     }
     // Q_Gamma = Q_N[Gamma rows] V3 ; Q-bar_Delta = Q-bar_N[Delta rows] V3-bar ; A_m V ; A-bar V-bar
     {
@@ -1123,7 +1128,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         add(ph, d.oA, d.oV, scr[i].AV, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
         add(ph, d.oAbar, scr[i].v[1].V, scr[i].AbV, d.nDl, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
       }
-      gemm_step(ph, lv_exact);
+      gemm_step(ph, lv_exact, 8);
     }
     // Lambda, Lambda^T, Psi, K^+ E_Gamma, Phi, Phi^T
     {
@@ -1137,7 +1142,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         add(ph, scr[i].AbV, scr[i].QbD, d.oPhi, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
         add(ph, scr[i].QbD, scr[i].AbV, d.oPhiT, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
       }
-      gemm_step(ph, lv_exact);
+      gemm_step(ph, lv_exact, 8);
     }
   }
   P.ph_coarse = int(P.setup_gemm.size());
