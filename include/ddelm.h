@@ -160,6 +160,10 @@ typedef struct ddelm_options {
   int trim_mask;          /* 1 Grams after the first pass, 2 Q and ridge-block updates, 4 products
                              of triangular factors, 8 local operators and their inputs, 16 the
                              first Gram */
+  int chol_unblocked;     /* MIXED: 0 = the FP64 Cholesky passes of subdomains with M > 128 are
+                             blocked (the FP64 kernel factors and inverts the 128-wide diagonal
+                             blocks, tensor-core GEMMs form the panels and the trailing updates);
+                             1 = one CTA factors a whole matrix */
 } ddelm_options;
 
 typedef struct ddelm_problem {

@@ -116,7 +116,8 @@ namespace {
 // in-band entries are touched.  A non-positive pivot sets *bad and continues
 // with a unit pivot.
 template <typename T>
-__device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int invb = 0) {
+__device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int invb = 0, int ld = 0) {
+  if (ld <= 0) ld = M;  // A and V: M x M blocks with leading dimension ld
   __shared__ T s_piv, s_rinv;
   __shared__ T rinv[NB];
   const int tid = threadIdx.x;
@@ -126,7 +127,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
     const int W = min(M, k0 + nb + BW) - k0;  // panel columns k0 .. k0+W
     for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      P[r * W + c] = A[(long long)(k0 + r) * M + k0 + c];
+      P[r * W + c] = A[(long long)(k0 + r) * ld + k0 + c];
     }
     __syncthreads();
     for (int t = 0; t < nb; ++t) {  // unblocked elimination inside the panel
@@ -151,7 +152,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
     }
     for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      if (c >= r) A[(long long)(k0 + r) * M + k0 + c] = P[r * W + c];
+      if (c >= r) A[(long long)(k0 + r) * ld + k0 + c] = P[r * W + c];
     }
     // trailing update of the upper triangle: A[i][j] -= sum_t P[t][i] P[t][j], i <= j
     const int T0 = k0 + nb, T1 = k0 + W, nt = T1 - T0;  // only columns the panel reaches
@@ -189,7 +190,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int j = j0 + b;
-            if (j < T1 && j >= i) A[(long long)i * M + j] -= acc[a][b];
+            if (j < T1 && j >= i) A[(long long)i * ld + j] -= acc[a][b];
           }
         }
       }
@@ -198,7 +199,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
   }
   // V = R^{-1}: block rows from the bottom;
   // V[i][j] = (delta_ij - sum_{k>i} R[i][k] V[k][j]) / R[i][i], j >= i
-  for (long long e = tid; e < (long long)M * M; e += CT) V[e] = T(0);
+  for (long long e = tid; e < (long long)M * M; e += CT) V[(e / M) * ld + e % M] = T(0);
   __syncthreads();
   const int nblk = (M + NB - 1) / NB;
   for (int b = nblk - 1; b >= 0; --b) {
@@ -206,9 +207,9 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
     const int W = min(M, i0 + nb + BW) - i0;  // R[i0..i1][i0 .. i0+W] holds the block's nonzeros
     for (int e = tid; e < nb * W; e += CT) {
       const int r = e / W, c = e % W;
-      P[r * W + c] = A[(long long)(i0 + r) * M + i0 + c];
+      P[r * W + c] = A[(long long)(i0 + r) * ld + i0 + c];
     }
-    if (tid < nb) rinv[tid] = T(1) / A[(long long)(i0 + tid) * M + i0 + tid];
+    if (tid < nb) rinv[tid] = T(1) / A[(long long)(i0 + tid) * ld + i0 + tid];
     __syncthreads();
     // tpc consecutive lanes share a column (strided k), so that the short block
     // rows near the bottom still keep every warp busy.  invb > 0: columns only
@@ -224,7 +225,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
       for (int r = 0; r < NB; ++r) acc[r] = T(0);
       const int kend = min(j, i0 + W - 1);
       for (int k = i1 + part; k <= kend; k += tpc) {
-        const T vk = V[(long long)k * M + j];
+        const T vk = V[(long long)k * ld + j];
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k - i0)], vk, acc[r]);
       }
@@ -253,7 +254,7 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
       }
 #pragma unroll
       for (int r = 0; r < NB; ++r)
-        if (r < nb && j >= i0 + r) V[(long long)(i0 + r) * M + j] = x[r];
+        if (r < nb && j >= i0 + r) V[(long long)(i0 + r) * ld + j] = x[r];
       }
     }
     __syncthreads();
@@ -305,24 +306,32 @@ __device__ void diag_additions(const CholDesc &cd, const double *G, double *eps2
   *add_out = eps2 + shift;
 }
 
-// FP64 pass: factor in place in G, V = R^{-1}
+// FP64 pass: factor in place in G, V = R^{-1}.  mode 1 (the first step of a
+// blocked factorisation, whose diagonal blocks are then factored by mode 0
+// with a leading dimension and its panels and trailing updates are
+// tensor-core GEMMs): only the diagonal additions, eps, and V zeroed.
 __global__ void __launch_bounds__(CT) chol_inv_kernel(const CholDesc *__restrict__ descs,
                                                       double *__restrict__ db, int *__restrict__ status) {
   extern __shared__ double P[];
   const CholDesc cd = descs[blockIdx.x];
   const int M = cd.M;
+  const int ld = cd.ld > 0 ? cd.ld : M;
   double *G = db + cd.g;
   double *V = db + cd.v;
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
   double eps2 = 0.0, add = 0.0;
-  diag_additions(cd, G, &eps2, &add);
+  if (cd.mode == 1 || cd.ridge || cd.shift_kind) diag_additions(cd, G, &eps2, &add);
   if (add != 0.0) {
-    for (int j = threadIdx.x; j < M; j += CT) G[(long long)j * M + j] += add;
+    for (int j = threadIdx.x; j < M; j += CT) G[(long long)j * ld + j] += add;
     __syncthreads();
   }
   if (cd.epsout >= 0 && threadIdx.x == 0) db[cd.epsout] = sqrt(eps2);
-  chol_inv_core<double>(G, V, M, cd.band, P, &s_bad, cd.inv_block);
+  if (cd.mode == 1) {
+    for (long long e = threadIdx.x; e < (long long)M * M; e += CT) V[e] = 0.0;
+    return;
+  }
+  chol_inv_core<double>(G, V, M, cd.band, P, &s_bad, cd.inv_block, ld);
   if (cd.z >= 0) {
     double *Z = db + cd.z;
     const double e = sqrt(eps2);
@@ -383,9 +392,11 @@ __global__ void __launch_bounds__(CT) chol_inv_dw_kernel(const CholDesc *__restr
   if (threadIdx.x == 0) s_bad = 0;
   double eps2 = 0.0, add = 0.0;
   diag_additions(cd, G, &eps2, &add);
+  // the factorisation reads the upper triangle only: convert that (the FP64
+  // conversions run on this GPU's slow FP64 pipe) and zero the rest
   for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
     const long long i = e / M, j = e % M;
-    A[e] = dw::from_double(G[e] + (i == j ? add : 0.0));  // each thread rewrites its own entries
+    A[e] = j >= i ? dw::from_double(G[e] + (i == j ? add : 0.0)) : dw::ff(0.0f);  // own entries only
   }
   __syncthreads();
   if (cd.epsout >= 0 && threadIdx.x == 0) db[cd.epsout] = sqrt(eps2);
@@ -393,8 +404,9 @@ __global__ void __launch_bounds__(CT) chol_inv_dw_kernel(const CholDesc *__restr
   __syncthreads();
   const double ez = sqrt(eps2);
   for (long long e = threadIdx.x; e < (long long)M * M; e += CT) {
-    G[e] = dw::to_double(A[e]);
-    const double v = dw::to_double(Vw[e]);
+    const bool up = e % M >= e / M;  // R and V are upper triangular
+    G[e] = up ? dw::to_double(A[e]) : 0.0;
+    const double v = up ? dw::to_double(Vw[e]) : 0.0;
     V[e] = v;
     if (cd.z >= 0) db[cd.z + e] = ez * v;
   }

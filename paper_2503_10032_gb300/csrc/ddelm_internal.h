@@ -115,6 +115,9 @@ struct CholDesc {
   int band;     // > 0: G and R vanish beyond this many superdiagonals
   int status;   // index into the status array
   int inv_block; // > 0: only the inv_block x inv_block diagonal blocks of R^{-1} (the rest by GEMMs)
+  int ld;       // leading dimension of g and v (0: M); a diagonal block of a larger matrix
+  int mode;     // 0 factor (and invert); 1 blocked factorisation's first step: add the ridge and
+                // shift to the diagonal of the whole matrix, write eps, zero v (M x M, leading dim M)
   double eps_rel;
   double shift_rel;
   long long epsout;  // >= 0: dbase offset receiving eps = sqrt(eps^2) (the ridge block is formed later)

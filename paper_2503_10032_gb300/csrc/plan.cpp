@@ -82,6 +82,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.vanilla < 0 || o.vanilla > 1) return fail("bad vanilla");
   if (o.autotune < 0 || o.autotune > 1) return fail("bad autotune");
   if (o.trim_levels < 0 || o.trim_levels > 6) return fail("bad trim_levels");
+  if (o.chol_unblocked < 0 || o.chol_unblocked > 1) return fail("bad chol_unblocked");
   if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
@@ -827,13 +828,22 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // matrix) inverts only the 128 x 128 diagonal blocks of R
   constexpr int INVB = 128;
   const bool blocked_inv = !fp32 && o.precision == DDELM_PREC_MIXED;
+  const bool blocked_fact = blocked_inv && !o.chol_unblocked;
   const int N = P.n_pass;
   // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
-  // accurate well below the shift; every other product keeps 54 bits.
-  // Products of the triangular factors (R^{-1} accumulated pass by pass) span
-  // many orders of magnitude inside a row, and the slice truncation is
-  // relative to the row maximum: they keep 60 bits.
+  // accurate well below the shift; the later Grams, whose residual the series
+  // must remove, keep 54 bits.  Products of the triangular factors (R^{-1}
+  // accumulated pass by pass) span many orders of magnitude inside a row, and
+  // the slice truncation is relative to the row maximum: they keep 60 bits.
+  // The Q and ridge-block updates and the local-operator products keep 54 bits
+  // as well.  Measured by removing levels one class at a time: one level fewer
+  // on the updates moves the local operator Lambda by 8e-8 (8x8, M = 400),
+  // beyond the ~1e-8 spread of two FP64 factorisations of the same problems;
+  // one fewer on the local-operator products leaves the 8x8 case unchanged but
+  // moves Phi (3e-9) and u (4e-7) of smaller test cases past their parity
+  // bounds; one fewer on the later Grams fails the series check.
   const int lv_exact = 9, lv_factor = 10, lv_first64 = 6, lv_shifted32 = 5, lv_small = 4, lv_tiny = 3;
+  const int lv_update = lv_exact, lv_ops = lv_exact;
   // cls: the phase's class for the level-trim experiment option (1 Grams after
   // the first pass, 2 Q and Z updates, 4 products of triangular factors,
   // 8 local operators and their inputs, 16 the first Gram; 0 the series terms)
@@ -949,7 +959,68 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           }
           P.cdesc.push_back(c);
         }
-      chol_step(c0);
+      // blocked factorisation (FP64 passes in MIXED, M > INVB): the diagonal
+      // additions of the whole matrix, then per INVB-wide diagonal block r:
+      // the FP64 kernel factors and inverts the block (R_rr, V_rr = R_rr^{-1});
+      // the panel R[r, r+1:] = V_rr^T A[r, r+1:] (in place) and the trailing
+      // update A[r+1:, r+1:] -= R[r, r+1:]^T R[r, r+1:] (upper tiles) are
+      // tensor-core GEMMs; the back substitution below completes V = R^{-1}.
+      // The FP64 pipe keeps only the diagonal blocks' work.
+      const bool block_this = blocked_fact && P.cdesc[c0].prec == 0;
+      if (block_this) {
+        int maxnb = 0;
+        for (int q = c0; q < int(P.cdesc.size()); ++q) {
+          CholDesc &c = P.cdesc[q];
+          if (c.M > INVB) {
+            c.mode = 1;
+            c.inv_block = 0;
+            maxnb = std::max(maxnb, (c.M + INVB - 1) / INVB);
+          }
+        }
+        chol_step(c0);
+        for (int jb = 0; jb < maxnb; ++jb) {
+          const int cb0 = int(P.cdesc.size());
+          for (int i = w0; i < w1; ++i)
+            for (int t = 0; t < 2; ++t) {
+              const SubDev &d = P.subs[i];
+              const long long M = d.M, r0 = (long long)jb * INVB;
+              if (d.M <= INVB || r0 >= M) continue;
+              CholDesc b = P.cdesc[c0 + 2 * (i - w0) + t];
+              b.g += r0 * M + r0;
+              b.v += r0 * M + r0;
+              b.M = int(std::min<long long>(INVB, M - r0));
+              b.ld = d.M;
+              b.mode = 0;
+              b.ridge = 0;
+              b.shift_kind = 0;
+              b.inv_block = 0;
+              b.epsout = -1;
+              b.z = -1;
+              P.cdesc.push_back(b);
+            }
+          chol_step(cb0);
+          for (int part = 0; part < 2; ++part) {
+            GemmPhase ph = phase_begin();
+            for (int i = w0; i < w1; ++i)
+              for (int t = 0; t < 2; ++t) {
+                const SubDev &d = P.subs[i];
+                const long long M = d.M, r0 = (long long)jb * INVB, r1 = r0 + INVB, rest = M - r1;
+                if (d.M <= INVB || rest <= 0) continue;
+                const CholDesc &c = P.cdesc[c0 + 2 * (i - w0) + t];
+                const int bj = INVB;
+                if (part == 0)  // panel: V_rr^T A[r, r+1:]
+                  add(ph, c.v + r0 * M + r0, c.g + r0 * M + r1, c.g + r0 * M + r1, bj, int(rest), bj, d.M, d.M,
+                      d.M, 1, 0, 0, 1.0, 0.0);
+                else            // trailing update of the upper triangle
+                  add(ph, c.g + r0 * M + r1, c.g + r0 * M + r1, c.g + r1 * M + r1, int(rest), int(rest), bj, d.M,
+                      d.M, d.M, 1, 0, 0, -1.0, 1.0, true);
+              }
+            gemm_step(ph, lv_factor, 4);
+          }
+        }
+      } else {
+        chol_step(c0);
+      }
       if (blocked_inv) {
         // block back substitution, block rows from the bottom:
         //   T = R[r, r+1:] V[r+1:, r+1:] ;  V[r, r+1:] = -V_rr T
@@ -1000,7 +1071,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
               add(ph, zk(i, t, k - 1), vk(i, t, k), zk(i, t, k), d.M, d.M, d.M, d.M, d.M, d.M, 0, 0,
                   GEMM_A_UPPER | GEMM_B_UPPER, 1.0, 0.0);
           }
-        gemm_step(ph, lv_exact, 2);
+        gemm_step(ph, lv_update, 2);
       }
       if (k > 0) {
         GemmPhase ph = phase_begin();
@@ -1128,7 +1199,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         add(ph, d.oA, d.oV, scr[i].AV, d.nG, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
         add(ph, d.oAbar, scr[i].v[1].V, scr[i].AbV, d.nDl, d.M, d.M, d.M, d.M, d.M, 0, 0, TU, 1.0, 0.0);
       }
-      gemm_step(ph, lv_exact, 8);
+      gemm_step(ph, lv_ops, 8);
     }
     // Lambda, Lambda^T, Psi, K^+ E_Gamma, Phi, Phi^T
     {
@@ -1142,7 +1213,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         add(ph, scr[i].AbV, scr[i].QbD, d.oPhi, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
         add(ph, scr[i].QbD, scr[i].AbV, d.oPhiT, d.nDl, d.nDl, d.M, d.M, d.M, d.nDl, 0, 1, 0, 1.0, 0.0);
       }
-      gemm_step(ph, lv_exact, 8);
+      gemm_step(ph, lv_ops, 8);
     }
   }
   P.ph_coarse = int(P.setup_gemm.size());
@@ -1269,6 +1340,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   }
   P.chol_coarse.ndesc = int(P.cdesc.size()) - P.chol_coarse.desc0;
   for (const auto &c : P.cdesc) {
+    if (c.mode == 1) continue;  // diagonal additions only
     double f = 2.0 * c.M * (double)c.M * c.M / 3.0;  // factor + inverse
     if (c.inv_block > 0) {  // factor + the diagonal blocks of the inverse
       f = c.M * (double)c.M * c.M / 3.0;
@@ -1331,7 +1403,10 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         return fail("internal: dot product bounds");
     }
     for (const auto &c : P.cdesc) {
-      const long long mm = (long long)c.M * c.M;
+      // a diagonal block with leading dimension ld spans (M - 1) ld + M entries
+      const long long mm = c.ld > 0 ? (long long)(c.M - 1) * c.ld + c.M : (long long)c.M * c.M;
+      if (c.ld > 0 && (c.ld < c.M || c.mode != 0 || c.ridge || c.shift_kind || c.prec != 0))
+        return fail("internal: Cholesky block");
       if (!in(c.g, mm) || !in(c.v, mm) || (c.z >= 0 && !in(c.z, mm)) || (c.prec == 1 && !in(c.w, mm)))
         return fail("internal: Cholesky bounds");
       if (c.prec == 1 && c.band != 0) return fail("internal: banded FP32 Cholesky");

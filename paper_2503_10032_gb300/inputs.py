@@ -360,6 +360,9 @@ def config(name: str) -> Problem:
         return make_problem(8, 8, 400, 1600, 40, scale=32.0, init="paper", seed=1008,
                             solutions=[_zero_solution()], forcing=[lambda x, y: np.ones(np.shape(x))],
                             op=OP_DIFFUSION, coef=grf_coefficient(32.0, 1009), exact_known=False, name=name)
+    if name == "poisson_4x4_m400":          # the 8x8 M=400 workload's per-subdomain shape on a 4x4 grid (profiling)
+        return make_problem(4, 4, 400, 1600, 40, scale=32.0, init="paper", seed=1010,
+                            solutions=[_sin2pix_cos3piy()], name=name)
     if name == "biharmonic_16x16":          # Sec. 4.5 at 16x16: M=256, 20x20 grid, 20 per edge, l=64
         return paper_scale(16, op=OP_BIHARMONIC)
     if name == "diffusion_4x4_m1000_r16":   # the 32x32 workload's per-subdomain shape on a 4x4 grid
