@@ -163,7 +163,12 @@ typedef struct ddelm_options {
   int chol_unblocked;     /* MIXED: 0 = the FP64 Cholesky passes of subdomains with M > 128 are
                              blocked (the FP64 kernel factors and inverts the 128-wide diagonal
                              blocks, tensor-core GEMMs form the panels and the trailing updates);
-                             1 = one CTA factors a whole matrix */
+                             1 = one CTA factors a whole matrix.  The blocked panels multiply by
+                             the explicit inverse of the diagonal block, which is not backward
+                             stable: with eps_rel = 1e-8 the second pass's Gram (condition ~1e11)
+                             fails the series check; use it for well-conditioned problems
+                             (eps_rel >= 1e-4, where it matches the unblocked factor to 1e-12).
+                             The Python binding passes 1 unless chol_blocked=True */
 } ddelm_options;
 
 typedef struct ddelm_problem {

@@ -140,7 +140,7 @@ def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change
                  precision=DDELM_PREC_FP64, max_refine=8, keep_matrices=False, setup_wave=0,
                  setup_scheme=DDELM_SCHEME_AUTO, setup_passes=0, graphs=True, barrier_timeout_ms=0,
                  inject_barrier_stall=False, use_Am=True, use_coarse=True, autotune=True, trim_levels=0,
-                 trim_mask=0, chol_blocked=True):
+                 trim_mask=0, chol_blocked=False):
     return ddelm_options(theta, eps_rel, tol, max_iters, int(use_change_of_vars), precision,
                          max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
                          int(setup_passes), int(not graphs), int(barrier_timeout_ms),

@@ -141,6 +141,22 @@ def test_variable_coefficient_operator(D, prec, scheme):
     assert close(u, ref["u_eval"], 1e-8, "u vs ref['u_eval']")
 
 
+def test_blocked_cholesky_matches_unblocked(D):
+    """The blocked FP64 Cholesky (diagonal blocks on the FP64 pipe, panels and
+    trailing updates as tensor-core GEMMs) on well-conditioned local problems
+    (eps_rel = 1e-4): the same factor and solution as one CTA per matrix."""
+    p = inputs.make_problem(2, 2, 300, 1000, 20, scale=32.0, init="paper", seed=5, solutions=[inputs._sin_sin(1, 1)])
+    out = {}
+    for blocked in (False, True):
+        s, mu, u, info, rc = _solve(D, p, eps_rel=1e-4, tol=1e-12, precision=D.DDELM_PREC_MIXED,
+                                    setup_scheme=D.DDELM_SCHEME_CQR2_SERIES, chol_blocked=blocked)
+        assert rc == D.DDELM_OK
+        out[blocked] = (u, s.inspect(0, 10))
+        s.close()
+    assert close(out[True][0], out[False][0], 1e-11, "blocked Cholesky u")
+    assert close(out[True][1], out[False][1], 1e-10, "blocked Cholesky V = R^{-1}")
+
+
 def test_tile_autotuner(D):
     """The first setup times both tensor-core tile shapes of every phase whose
     products overwrite their output and keeps the faster: the solution is the
