@@ -237,6 +237,9 @@ def main():
     ap.add_argument("--scheme", default="auto", choices=list(SCHEMES))
     ap.add_argument("--passes", type=int, default=0, help="FP32 scheme: shifted passes (0: automatic)")
     ap.add_argument("--solve-steps", type=int, default=5, help="timed solves with the reused handle")
+    ap.add_argument("--tc-tiles", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="MIXED tensor-core tile shapes: 0 all-levels by rule + autotuner, "
+                         "1 level-group shapes only, 2 all-levels only, 3 128x64 level groups only")
     ap.add_argument("--theta", type=float, default=THETA,
                     help="NN weight of Eq. (nn-mixed); 0 gives the coarse-space method without the NN term")
     args = ap.parse_args()
@@ -269,7 +272,7 @@ def main():
     prob = inputs.config(args.workload)
     prec = D.DDELM_PREC_FP64 if args.precision == "fp64" else D.DDELM_PREC_MIXED
     opt_kw = dict(theta=THETA, eps_rel=EPS_REL, tol=TOL, max_iters=20000, precision=prec,
-                  setup_scheme=SCHEMES[args.scheme], setup_passes=args.passes)
+                  setup_scheme=SCHEMES[args.scheme], setup_passes=args.passes, tc_tiles=args.tc_tiles)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         solver = D.Solver(prob, device=dev, stream=stream, **opt_kw)
@@ -395,7 +398,7 @@ def main():
     e2e_ms = []
     ws_ptr, ws_bytes = solver.ws_ptr, int(sizes.workspace_bytes)
     pa = D.ProblemArgs(prob, D.make_options(**opt_kw))
-    tune = D.ddelm_inspect(solver.h, 0, 11, 4)   # the tile-shape autotuner's outcome
+    tune = D.ddelm_inspect(solver.h, 0, 11, 4 + 5 * 128)   # the tile-shape autotuner's outcome
     solver.close()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
@@ -511,6 +514,9 @@ def main():
             "data": "synthetic",
             "config": dict(workload_config(args.workload, prob, sizes), precision=args.precision,
                            factorisation=scheme_desc, setup_waves=int(plan[2]),
+                           tc_tiles=["all-levels 128x48 by rule, autotuned against level groups",
+                                     "level groups 128x64 / 128x128", "all-levels 128x48",
+                                     "level groups 128x64"][args.tc_tiles],
                            parallelism=f"replicas{world}", l2="flushed between steps (512 MB write)"),
             "cg_iterations": int(np.median(iters)), "rel_residual_max": resid,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -541,7 +547,11 @@ def main():
     line["graphs"] = graphs
     line["autotune"] = {"phases_timed": int(tune[0]), "switched": int(tune[1]),
                         "ms_rule_widths": float(tune[2]), "ms_chosen_widths": float(tune[3]),
-                        "note": "tensor-core tile width per GEMM phase, timed on the handle's first setup"}
+                        "phases": [[int(tune[4 + 5 * k]), int(tune[5 + 5 * k]), round(float(tune[6 + 5 * k]), 4),
+                                    int(tune[7 + 5 * k]), round(float(tune[8 + 5 * k]), 4)]
+                                   for k in range(min(int(tune[0]), 128)) if tune[5 + 5 * k] > 0],
+                        "note": "tensor-core tile width per GEMM phase, timed on the handle's first setup; "
+                                "phases: [index, rule width, ms, alternative width, ms]"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -169,6 +169,15 @@ typedef struct ddelm_options {
                              fails the series check; use it for well-conditioned problems
                              (eps_rel >= 1e-4, where it matches the unblocked factor to 1e-12).
                              The Python binding passes 1 unless chol_blocked=True */
+  int tc_tiles;           /* MIXED tensor-core tile shapes: 0 = the all-levels shape (128 x 48
+                             tiles, every slice level of a 32-wide k block in one shared-memory
+                             stage) by rule, with the level-group shape (128 x 64 or 128 x 128,
+                             see autotune) as the autotuner's alternative; 1 = the level-group
+                             shapes only (the rule and the other width); 2 = the all-levels shape
+                             only; 3 = the 128 x 64 level-group shape only (its exact integer
+                             level combination, for every contraction length).  Contractions
+                             longer than 16384 always take the 128-wide level-group shape.
+                             FP64-exact either way */
 } ddelm_options;
 
 typedef struct ddelm_problem {
@@ -298,7 +307,9 @@ int ddelm_interface_solve(ddelm_handle *h, const double *d_b, double *d_mu_delta
  * last two when out_len >= 6), 10 V = R^{-1} of the ridge factorisation of
  * [K_c^i; eps I] [M x M], 11 the tile-shape autotuner's outcome {phases timed,
  * phases switched to the other width, their time in ms with the rule's widths,
- * with the chosen widths} (sub ignored, out_len >= 4).  Blocks 0-2 are
+ * with the chosen widths}, then as far as out_len allows five numbers per phase
+ * timed by this handle {phase index, rule's tile width, its ms, alternative
+ * width, its ms} (sub ignored, out_len >= 4).  Blocks 0-2 are
  * only kept when the problem was set up with opt.keep_matrices = 1 (which adds
  * their size to the workspace).  out_len is the capacity of host_out in
  * doubles; a block that does not fit returns DDELM_ERR_INVALID_ARG. */

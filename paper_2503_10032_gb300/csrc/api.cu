@@ -46,6 +46,7 @@ struct ddelm_handle {
   bool tune_pending = false, capturing = false;
   int tune_phases = 0, tune_switched = 0;
   double tune_ms_rule = 0.0, tune_ms_chosen = 0.0;
+  std::vector<double> tune_log;  // per timed phase: index, rule width, its ms, alternative width, its ms
   // profiling: event pairs around launches, reduced on ddelm_profile
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -373,6 +374,7 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
         for (auto &e : ev) CK(cudaEventDestroy(e));
         h->tune_phases++;
         h->tune_ms_rule += t_rule;
+        for (double v : {(double)q, (double)ph.bn, (double)t_rule, (double)alt.bn, (double)t_alt}) h->tune_log.push_back(v);
         const bool take_alt = t_alt < 0.97f * t_rule;  // a clear gain only: one run's timings carry noise
         {
           std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -853,6 +855,7 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
       host_out[1] = h->tune_switched;
       host_out[2] = h->tune_ms_rule;
       host_out[3] = h->tune_ms_chosen;
+      for (size_t k = 0; k < h->tune_log.size() && 4 + k < out_len; ++k) host_out[4 + k] = h->tune_log[k];
       return DDELM_OK;
     }
     case 9: {

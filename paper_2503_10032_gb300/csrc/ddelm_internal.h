@@ -268,6 +268,7 @@ struct Plan {
   size_t off_mdesc = 0;
   // tensor-core emulation of the setup GEMMs (precision MIXED)
   bool mixed = false;
+  int tc_tiles = 0;               // tensor-core tile shapes allowed (the tc_tiles option)
   std::vector<SliceDesc> sdesc;
   std::vector<OzDesc> odesc;
   std::vector<OzTile> otile;

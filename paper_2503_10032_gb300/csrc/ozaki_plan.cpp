@@ -13,6 +13,8 @@ namespace ddelm {
 
 namespace {
 constexpr int OZ_BM = 128, OZ_BK = 64, OZ_KC = 1024;
+// the all-levels shape: 128 x 48 tiles over 32-wide k blocks
+constexpr int OZ_AL_BN = 48, OZ_AL_BK = 32;
 // tile width of a phase: 128 (two levels per group) when every product has a
 // contraction longer than one k-chunk, where A traffic dominates; else 64
 // (four levels per group, combined exactly in integers)
@@ -59,7 +61,7 @@ int build_mixed(Plan &P, long long &cur) {
     }
     P.odesc.reserve(nd);
     P.sdesc.reserve(2 * nd);
-    P.otile.reserve(nt + nt / 2 + 16);  // both tile widths
+    P.otile.reserve(3 * nt + 16);  // two tile lists, the 48-wide one up to 4/3 nt
   }
   std::vector<std::pair<int, long long>> scale_fix;  // (slice desc, relative scale offset)
   long long scale_base = 0;
@@ -85,7 +87,13 @@ int build_mixed(Plan &P, long long &cur) {
     // the 96-bit integer sum of the four-level tiles holds up to 16 k-chunks
     // (|X| < 2^(43 + 48 + 4)); longer contractions take the FP64 combination
     wide = wide || long_k;
-    const int OZ_BN = wide ? 128 : 64;  // the rule; the autotuner may switch to the other width
+    // the rule: the all-levels shape (48 wide) unless the options ask for the
+    // level-group shapes only or the contraction needs the FP64 combination;
+    // the autotuner may switch to the alternative (the level-group rule's
+    // width, or with tc_tiles = 1 the other level-group width; tc_tiles = 3
+    // keeps the 64-wide level-group shape alone)
+    const int grp_bn = (long_k || (wide && P.tc_tiles != 3)) ? 128 : 64;
+    const int OZ_BN = (P.tc_tiles != 1 && P.tc_tiles != 3 && !long_k) ? OZ_AL_BN : grp_bn;
     op.bn = OZ_BN;
     std::unordered_map<Key, int, KeyHash> seen;
     seen.reserve(2 * (size_t)gp.ndesc);
@@ -146,31 +154,33 @@ int build_mixed(Plan &P, long long &cur) {
     // tile lists: the rule's width, then (for the autotuner) the other one
     double pairs = 0;  // tensor-core work: every level's pairs over the k blocks a tile needs
     for (int l = 0; l < S; ++l) pairs += l + 1;
+    // k blocks are 64 wide for the level-group shapes, 32 for the all-levels one
     auto emit_tiles = [&](int BN, int &ntile, double &flops) {
+      const int BK = BN == OZ_AL_BN ? OZ_AL_BK : OZ_BK;
       for (int t = 0; t < gp.ndesc; ++t) {
         const GemmDesc &d = P.gdesc[gp.desc0 + t];
         const int di = op.desc0 + t;
         const int tm = (d.m + OZ_BM - 1) / OZ_BM, tn = (d.n + BN - 1) / BN;
-        const int nkb = P.odesc[di].Kpad / OZ_BK;
+        const int nkb = (d.k + BK - 1) / BK;  // blocks wholly past k would load only zeros
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) {
             if (d.syrk && x * OZ_BM >= (y + 1) * BN) continue;  // strictly below the diagonal
             int kb0 = 0, kb1 = nkb;
             // op(B)[k][j] = 0 for k > j ; op(A)[i][k] = 0 for k < i
-            if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, (y + 1) * (BN / OZ_BK));
-            if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / OZ_BK));
+            if (d.flags & GEMM_B_UPPER) kb1 = std::min(kb1, ((y + 1) * BN + BK - 1) / BK);
+            if (d.flags & GEMM_A_UPPER) kb0 = std::max(kb0, x * (OZ_BM / BK));
             if (kb1 < kb0) kb1 = kb0;
             P.otile.push_back({di, x, y, kb0, kb1, 0, 0, 0});
             ntile++;
-            flops += 2.0 * OZ_BM * BN * (double)(kb1 - kb0) * OZ_BK * pairs;
+            flops += 2.0 * OZ_BM * BN * (double)(kb1 - kb0) * BK * pairs;
           }
       }
     };
     emit_tiles(OZ_BN, op.ntile, op.flops);
     P.oz_flops += op.flops;
-    op.bn_alt = OZ_BN == 64 ? 128 : 64;
+    op.bn_alt = OZ_BN == OZ_AL_BN ? grp_bn : (OZ_BN == 64 ? 128 : 64);
     op.tile0_alt = int(P.otile.size());
-    if (!long_k) emit_tiles(op.bn_alt, op.ntile_alt, op.flops_alt);
+    if (!long_k && P.tc_tiles < 2) emit_tiles(op.bn_alt, op.ntile_alt, op.flops_alt);
     op.nslice = int(P.sdesc.size()) - op.slice0;
     for (int t = op.slice0; t < op.slice0 + op.nslice; ++t)
       if (P.sdesc[t].S != S) {  // the slicing launch takes one level count
@@ -191,12 +201,15 @@ int build_mixed(Plan &P, long long &cur) {
   return DDELM_OK;
 }
 
-// One 3-D tensor map per slice buffer: S levels of R rows of K BF16 (row
-// stride Kpad, level stride Rpad Kpad), box 64 x 64 x 1, 128-byte swizzle
-// (the canonical K-major layout tcgen05 reads).  Boxes reaching past R or K
-// are zero-filled by the copy, so the slicing writes no padding.
+// Three 3-D tensor maps per slice buffer i, each over S levels of R rows of K
+// BF16 (row stride Kpad, level stride Rpad Kpad): map i with box 64 x 64 x 1
+// and the 128-byte swizzle (the level-group shapes), maps n + 2 i and
+// n + 2 i + 1 (n slice buffers) with boxes 32 x 128 x S and 32 x 48 x S and
+// the 64-byte swizzle (the all-levels shape's A and B sides); all are the
+// canonical K-major layouts tcgen05 reads.  Boxes reaching past R or K are
+// zero-filled by the copy, so the slicing writes no padding.
 int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps) {
-  maps.assign(std::max<size_t>(P.sdesc.size(), 1) * 128, 0);
+  maps.assign(std::max<size_t>(P.sdesc.size(), 1) * 3 * 128, 0);
   if (P.sdesc.empty()) return DDELM_OK;
   typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -218,14 +231,19 @@ int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps
     if ((reinterpret_cast<uintptr_t>(gaddr) & 15u) != 0) return DDELM_ERR_INVALID_ARG;
     cuuint64_t dims[3] = {(cuuint64_t)s.K, (cuuint64_t)s.R, (cuuint64_t)s.S};
     cuuint64_t strides[2] = {(cuuint64_t)s.Kpad * 2, (cuuint64_t)s.Rpad * (cuuint64_t)s.Kpad * 2};
-    cuuint32_t box[3] = {64, 64, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUtensorMap m;
-    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, gaddr, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return DDELM_ERR_CUDA;
-    std::memcpy(maps.data() + i * 128, &m, 128);
+    const size_t slot[3] = {i, P.sdesc.size() + 2 * i, P.sdesc.size() + 2 * i + 1};
+    const cuuint32_t boxes[3][3] = {{64, 64, 1},
+                                    {(cuuint32_t)OZ_AL_BK, (cuuint32_t)OZ_BM, (cuuint32_t)s.S},
+                                    {(cuuint32_t)OZ_AL_BK, (cuuint32_t)OZ_AL_BN, (cuuint32_t)s.S}};
+    for (int v = 0; v < 3; ++v) {
+      CUtensorMap m;
+      CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, gaddr, dims, strides, boxes[v], estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, v == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return DDELM_ERR_CUDA;
+      std::memcpy(maps.data() + slot[v] * 128, &m, 128);
+    }
   }
   return DDELM_OK;
 }

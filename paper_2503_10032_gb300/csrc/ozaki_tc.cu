@@ -569,6 +569,282 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- all levels per stage
+// The second tile shape: 128 x 48 output tiles whose shared-memory stage holds
+// every level of both operands for one 32-wide k block (A_0 .. A_{S-1} of 128
+// rows and B_0 .. B_{S-1} of 48 rows, 64-byte swizzle, one 3-D copy each), so
+// a tile brings each slice in once per k block and every pair p + q < S is
+// multiplied out of shared memory: S (S + 1) MMAs per stage against 2 S
+// boxes, where the level groups of the first shape reload A_p for every group
+// and B_q for every (p, group).  The S level accumulators (48 TMEM columns
+// each, S <= 10) form one set: a k-chunk's epilogue runs between its last MMA
+// and the next chunk's first while the producer keeps loading.  The level sums
+// are the same integers as in the first shape, combined by the same 96-bit
+// arithmetic.
+constexpr int AL_BN = 48, AL_BK = 32;
+constexpr int AL_A_BYTES = BM * AL_BK * 2;       // one level of A: 8 KB
+constexpr int AL_B_BYTES = AL_BN * AL_BK * 2;    // one level of B: 3 KB
+constexpr int AL_MAX_STAGES = 8;
+constexpr int AL_RING_BYTES = 2 * 10 * (AL_A_BYTES + AL_B_BYTES);  // two stages of ten levels
+constexpr int AL_CW = AL_BN / (EPI_WARPS / 4);  // 12 columns per epilogue thread
+constexpr int AL_MAX_S = 10;
+
+__host__ __device__ constexpr int al_stages(int S) {
+  return AL_RING_BYTES / (S * (AL_A_BYTES + AL_B_BYTES)) < AL_MAX_STAGES
+             ? AL_RING_BYTES / (S * (AL_A_BYTES + AL_B_BYTES))
+             : AL_MAX_STAGES;
+}
+
+// K-major operand of 32-element (64 B) BF16 rows with the 64-byte swizzle:
+// 8-row atoms of 512 B, SBO = 512 B, LBO unused (1), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;              // LBO (ignored for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;     // SBO
+  d |= (uint64_t)1u << 46;              // descriptor version
+  d |= (uint64_t)4u << 61;              // SWIZZLE_64B
+  return d;
+}
+
+// Persistent like the first shape; maps[map0 + 2 s] and maps[map0 + 2 s + 1]
+// are slice buffer s's A-side (32 x 128 x S) and B-side (32 x 48 x S) boxes.
+// S is a template parameter: the S (S + 1) MMAs of a stage unroll into
+// constant descriptor offsets, so the single issuing thread keeps ahead of
+// the 128 x 48 x 16 MMAs (about 24 tensor cycles each).
+template <int S>
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    ozaki_gemm_all_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles, int ntile,
+                          int map0, const CUtensorMap *__restrict__ maps, double *__restrict__ db,
+                          int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_full[AL_MAX_STAGES], bar_empty[AL_MAX_STAGES], bar_acc_full, bar_acc_empty,
+      bar_drain;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ double s_scale[BM + AL_BN];  // row scales, then column scales
+  constexpr int NST = al_stages(S);
+  constexpr uint32_t stage_bytes = (uint32_t)S * (AL_A_BYTES + AL_B_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc_full), 1);
+    mbar_init(smem_u32(&bar_acc_empty), 32 * EPI_WARPS);
+    mbar_init(smem_u32(&bar_drain), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: one stage per (tile, k block)
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
+        const OzTile tl = tiles[ti];
+        const OzDesc d = descs[tl.desc];
+        const CUtensorMap *ma = maps + map0 + 2 * d.tmapA;
+        const CUtensorMap *mb = maps + map0 + 2 * d.tmapB + 1;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
+        for (int kb = tl.kb0; kb < tl.kb1; ++kb) {
+          if (issued >= NST && !mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1u, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = smem_u32(smem + st * stage_bytes);
+          const uint32_t fb = smem_u32(&bar_full[st]);
+          mbar_expect_tx(fb, stage_bytes);
+          tma_load_3d(sa, ma, kb * AL_BK, tl.tm * BM, 0, fb);
+          tma_load_3d(sa + (uint32_t)S * AL_A_BYTES, mb, kb * AL_BK, tl.tn * AL_BN, 0, fb);
+          ++issued;
+          if (++st == NST) {
+            st = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // drain: every stage issued must have landed before the CTA may exit
+      for (int q = 0; q < NST && q < issued; ++q) {
+        if (--st < 0) {
+          st = NST - 1;
+          ph ^= 1u;
+        }
+        const unsigned long long t0 = gtimer();
+        while (!mbar_test(smem_u32(&bar_full[st]), ph)) {
+          if (gtimer() - t0 > 2000000000ull) {
+            atomicExch(err, 4);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: per k-chunk of a tile, every pair into its level
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      long long G = 0;  // k-chunks across tiles
+      for (int ti = blockIdx.x; ti < ntile && ok; ti += gridDim.x) {
+        const OzTile tl = tiles[ti];
+        const int kcb = descs[tl.desc].kc / AL_BK;
+        for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += kcb, ++G) {
+          const int c1 = min(tl.kb1, c0 + kcb);
+          if (G >= 1 && !mbar_wait(smem_u32(&bar_acc_empty), (uint32_t)((G - 1) & 1), err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int kb = c0; kb < c1; ++kb) {
+            if (!mbar_wait(smem_u32(&bar_full[st]), ph, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * stage_bytes);
+            // level p of A at +p 8 KB, level q of B at +S 8 KB + q 3 KB; a
+            // 16-element k step is +32 B: offsets of 16 B in the descriptor's
+            // address field (no carry: shared addresses stay below 256 KB)
+            const uint64_t a0 = smem_desc_sw64(sa), b0 = smem_desc_sw64(sa + (uint32_t)S * AL_A_BYTES);
+            const uint32_t later = kb != c0 ? 1u : 0u;  // the chunk's first MMA into a level starts it
+#pragma unroll
+            for (int kk = 0; kk < AL_BK / 16; ++kk)
+#pragma unroll
+              for (int p = 0; p < S; ++p)
+#pragma unroll
+                for (int q = 0; q < S - p; ++q)
+                  mma_bf16<AL_BN>(tmem + (uint32_t)((p + q) * AL_BN),
+                                  a0 + (uint64_t)(p * (AL_A_BYTES >> 4) + 2 * kk),
+                                  b0 + (uint64_t)(q * (AL_B_BYTES >> 4) + 2 * kk), (kk > 0 || p > 0) ? 1u : later);
+            mma_commit(smem_u32(&bar_empty[st]));
+            if (++st == NST) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+          if (ok) mma_commit(smem_u32(&bar_acc_full));  // the chunk's level sums to the epilogue
+        }
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(smem_u32(&bar_drain));
+      const unsigned long long t0 = gtimer();
+      while (!mbar_test(smem_u32(&bar_drain), 0)) {
+        if (gtimer() - t0 > 2000000000ull) {
+          atomicExch(err, 5);
+          break;
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2 .. 2 + EPI_WARPS - 1
+    // Level l is read as t = S - 1 - l (least significant first); the groups
+    // of four, t = 4 g .. 4 g + 3, become exact 43-bit integers added at bit
+    // 24 g of a 96-bit integer per element, as in the first shape.
+    // After a failed wait every thread still walks the same tiles and named
+    // barriers (skipping the work), so the barriers cannot deadlock.
+    const int ew = warp - 2;
+    const int quad = warp & 3;   // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;    // column part of the tile
+    const int row = quad * 32 + lane;
+    const int et = threadIdx.x - 64;
+    bool ok = true;
+    long long G = 0;
+    for (int ti = blockIdx.x; ti < ntile; ti += gridDim.x) {
+      const OzTile tl = tiles[ti];
+      const OzDesc d = descs[tl.desc];
+      const int kcb = d.kc / AL_BK;
+      const int nchunk = tl.kb1 > tl.kb0 ? (tl.kb1 - tl.kb0 + kcb - 1) / kcb : 0;
+      epi_sync();  // the previous tile's stores no longer read the scales
+      if (et < BM) {
+        const int gi = tl.tm * BM + et;
+        s_scale[et] = gi < d.m ? db[d.scaleA + gi] : 0.0;
+      } else if (et < BM + AL_BN) {
+        const int gj = tl.tn * AL_BN + et - BM;
+        s_scale[et] = gj < d.n ? db[d.scaleB + gj] : 0.0;
+      }
+      epi_sync();
+      uint32_t w0[AL_CW], w1[AL_CW], w2[AL_CW];
+#pragma unroll
+      for (int j = 0; j < AL_CW; ++j) w0[j] = w1[j] = w2[j] = 0u;
+      for (int g = 0; g < nchunk; ++g, ++G) {
+        if (ok && !mbar_wait(smem_u32(&bar_acc_full), (uint32_t)(G & 1), err)) ok = false;
+        if (!ok) continue;
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * AL_CW);
+#pragma unroll
+        for (int c0 = 0; c0 < AL_CW; c0 += 4) {
+          uint32_t r[AL_MAX_S][4];
+#pragma unroll
+          for (int t = 0; t < AL_MAX_S; ++t) {
+            if (t < S) {
+              tmem_ld4_nowait(base + (uint32_t)((S - 1 - t) * AL_BN) + c0, r[t]);
+            } else {
+              r[t][0] = r[t][1] = r[t][2] = r[t][3] = 0u;
+            }
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const int x01 = f32_exact_int(r[4 * q][j]) + 64 * f32_exact_int(r[4 * q + 1][j]);
+              const int x23 = 4 * q + 2 < AL_MAX_S
+                                  ? f32_exact_int(r[4 * q + 2][j]) + 64 * f32_exact_int(r[4 * q + 3][j])
+                                  : 0;
+              add96(w0[c0 + j], w1[c0 + j], w2[c0 + j], x01, x23, q);
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bar_acc_empty));
+      }
+      if (ok) {
+        const int gi = tl.tm * BM + row;
+        if (gi < d.m) {
+          double *crow = db + d.c + (long long)gi * d.ldc;
+          const int j0 = tl.tn * AL_BN + half * AL_CW;
+          const int ei = (int)((__double2hiint(s_scale[row]) >> 20) & 0x7FF) - 1023 - 6 * (S + 1);
+#pragma unroll
+          for (int j = 0; j < AL_CW; ++j) {
+            const int gj = j0 + j;
+            if (gj < d.n) {
+              const int ej = (int)((__double2hiint(s_scale[BM + half * AL_CW + j]) >> 20) & 0x7FF) - 1023;
+              double v = i96_ldexp(w0[j], w1[j], w2[j], ei + ej);
+              if (d.alpha != 1.0) v *= d.alpha;
+              if (d.beta != 0.0) v = fma(d.beta, crow[gj], v);
+              crow[gj] = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- slicing
 // Integer arithmetic only (the FP64 pipe is the scarce unit of this GPU):
 // sigma_r = 2^(E_max - 1022) from the largest biased exponent E_max of the
@@ -729,11 +1005,17 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
   const OzDesc *od = reinterpret_cast<const OzDesc *>(base + p.off_odesc);
   const OzTile *ot = reinterpret_cast<const OzTile *>(base + p.off_otile) + ph.tile0;
   const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(base + p.off_tmaps);
-  const size_t smem = STAGES * STAGE_BYTES + 1024;
-  if (ph.bn != 64 && ph.bn != 128) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(ph.bn == 64 ? ozaki_gemm_kernel<64> : ozaki_gemm_kernel<128>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (ph.bn != 64 && ph.bn != 128 && ph.bn != AL_BN) return cudaErrorInvalidValue;
+  const int S = p.sdesc[ph.slice0].S;  // one level count per phase
+  if (ph.bn == AL_BN && (S < 1 || S > AL_MAX_S)) return cudaErrorInvalidValue;
+  const size_t smem = ph.bn == AL_BN ? (size_t)al_stages(S) * S * (AL_A_BYTES + AL_B_BYTES) + 1024
+                                     : (size_t)STAGES * STAGE_BYTES + 1024;
+  cudaError_t e = cudaSuccess;
+  if (ph.bn != AL_BN) {
+    e = cudaFuncSetAttribute(ph.bn == 64 ? ozaki_gemm_kernel<64> : ozaki_gemm_kernel<128>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   static int nsm = 0;  // one persistent CTA per SM
   if (nsm == 0) {
     int dev = 0;
@@ -745,7 +1027,23 @@ cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStrea
     }
   }
   const int grid = ph.ntile < nsm ? ph.ntile : nsm;
-  if (ph.bn == 64) { ozaki_gemm_kernel<64><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
+  if (ph.bn == AL_BN) {
+    const int map0 = (int)p.sdesc.size();
+    switch (S) {
+#define DDELM_AL_CASE(n)                                                                        \
+  case n:                                                                                       \
+    e = cudaFuncSetAttribute(ozaki_gemm_all_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             AL_RING_BYTES + 1024);                                             \
+    if (e != cudaSuccess) return e;                                                             \
+    ozaki_gemm_all_kernel<n><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, map0, maps, db, err); \
+    DDELM_COUNT_LAUNCH();                                                                       \
+    break;
+      DDELM_AL_CASE(1) DDELM_AL_CASE(2) DDELM_AL_CASE(3) DDELM_AL_CASE(4) DDELM_AL_CASE(5)
+      DDELM_AL_CASE(6) DDELM_AL_CASE(7) DDELM_AL_CASE(8) DDELM_AL_CASE(9) DDELM_AL_CASE(10)
+#undef DDELM_AL_CASE
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (ph.bn == 64) { ozaki_gemm_kernel<64><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
   else { ozaki_gemm_kernel<128><<<grid, OZ_THREADS, smem, s>>>(od, ot, ph.ntile, maps, db, err); DDELM_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }

@@ -81,6 +81,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.plain_flux_corners < 0 || o.plain_flux_corners > 1) return fail("bad plain_flux_corners");
   if (o.vanilla < 0 || o.vanilla > 1) return fail("bad vanilla");
   if (o.autotune < 0 || o.autotune > 1) return fail("bad autotune");
+  if (o.tc_tiles < 0 || o.tc_tiles > 3) return fail("bad tc_tiles");
   if (o.trim_levels < 0 || o.trim_levels > 6) return fail("bad trim_levels");
   if (o.chol_unblocked < 0 || o.chol_unblocked > 1) return fail("bad chol_unblocked");
   if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
@@ -1356,6 +1357,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // ---- tensor-core emulation tables (precision MIXED)
   if (o.precision == DDELM_PREC_MIXED) {
     P.mixed = true;
+    P.tc_tiles = o.tc_tiles;
     if (build_mixed(P, cur) != DDELM_OK) {
       const std::string e = P.err.empty() ? std::string("mixed plan") : P.err;
       return fail(e.c_str());
@@ -1497,8 +1499,13 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
         return fail("internal: tensor-core GEMM shape");
     }
     for (const auto &ph : P.oz_phase) {
-      if (ph.bn != 64 && ph.bn != 128) return fail("internal: tensor-core tile width");
-      if (ph.ntile_alt > 0 && ph.bn_alt + ph.bn != 192) return fail("internal: tensor-core alternative width");
+      auto width_ok = [](int bn) { return bn == 48 || bn == 64 || bn == 128; };
+      if (!width_ok(ph.bn)) return fail("internal: tensor-core tile width");
+      if (ph.ntile_alt > 0 && (!width_ok(ph.bn_alt) || ph.bn_alt == ph.bn))
+        return fail("internal: tensor-core alternative width");
+      if (ph.ntile > 0 && (ph.bn == 48 || (ph.ntile_alt > 0 && ph.bn_alt == 48)) &&
+          (P.sdesc[ph.slice0].S < 1 || P.sdesc[ph.slice0].S > 10))
+        return fail("internal: all-levels tile levels");
       // both tile lists (the rule's and the autotuner's alternative)
       for (int which = 0; which < 2; ++which) {
         const int t0 = which ? ph.tile0_alt : ph.tile0, nt = which ? ph.ntile_alt : ph.ntile;
@@ -1508,9 +1515,12 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           const OzTile &t = P.otile[q];
           if (t.desc < ph.desc0 || t.desc >= ph.desc0 + ph.ndesc) return fail("internal: tensor-core tile");
           const OzDesc &od = P.odesc[t.desc];
-          if ((t.tm + 1) * 128 > od.RpadA || (t.tn + 1) * bn > od.RpadB)
+          // 48-wide tiles may reach past the padded rows of B: the copy's
+          // bounds are the tensor map's R rows, past which it fills zeros
+          if ((t.tm + 1) * 128 > od.RpadA || (bn == 48 ? t.tn * bn >= od.n : (t.tn + 1) * bn > od.RpadB))
             return fail("internal: tensor-core tile box");
-          if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * 64 > od.Kpad) return fail("internal: tensor-core tile k range");
+          const int bk = bn == 48 ? 32 : 64;
+          if (t.kb0 < 0 || t.kb1 < t.kb0 || t.kb1 * bk > od.Kpad) return fail("internal: tensor-core tile k range");
         }
       }
     }
@@ -1548,7 +1558,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   P.off_otile = off;
   off = al(off + std::max<size_t>(P.otile.size(), 1) * sizeof(OzTile));
   P.off_tmaps = off;
-  off = al(off + std::max<size_t>(P.sdesc.size(), 1) * 128);
+  off = al(off + std::max<size_t>(P.sdesc.size(), 1) * 3 * 128);  // three tensor maps per slice buffer
   P.off_ssubs = off;
   off = al(off + std::max<size_t>(P.ssubs.size(), 1) * sizeof(SubDev));
   P.off_srows = off;
