@@ -355,6 +355,7 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
           LAUNCH(PC_TC, launch_oz_gemm(p, ph, h->ws, s));
           return DDELM_OK;
         }
+        CK(preload_oz_kernels());  // no lazy module load inside the timed launches
         OzPhase alt = ph;
         alt.tile0 = ph.tile0_alt;
         alt.ntile = ph.ntile_alt;

@@ -52,5 +52,6 @@ struct OzPhase {
 
 cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
+cudaError_t preload_oz_kernels();
 
 }  // namespace ddelm
