@@ -126,9 +126,22 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 }
 
 // kind::f16 instruction descriptor: D F32, A/B BF16, K-major, M=128, N=BN
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 template <int BN>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  return idesc_n(BN);
+}
+
+// the same with the instruction descriptor as an operand (N chosen per call)
+__device__ __forceinline__ void mma_bf16_id(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(id), "r"(accum)
+      : "memory");
 }
 
 template <int BN>
@@ -574,10 +587,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // every level of both operands for one 32-wide k block (A_0 .. A_{S-1} of 128
 // rows and B_0 .. B_{S-1} of 48 rows, 64-byte swizzle, one 3-D copy each), so
 // a tile brings each slice in once per k block and every pair p + q < S is
-// multiplied out of shared memory: S (S + 1) MMAs per stage against 2 S
-// boxes, where the level groups of the first shape reload A_p for every group
-// and B_q for every (p, group).  The S level accumulators (48 TMEM columns
-// each, S <= 10) form one set: a k-chunk's epilogue runs between its last MMA
+// multiplied out of shared memory (S (S + 1) / 2 level pairs per 16-wide k
+// step, issued as about a fifth as many MMAs of up to five B levels each)
+// against 2 S boxes, where the level groups of the first shape reload A_p for
+// every group and B_q for every (p, group).  The S level accumulators (48
+// TMEM columns each, S <= 10) form one set: a k-chunk's epilogue runs between its last MMA
 // and the next chunk's first while the producer keeps loading.  The level sums
 // are the same integers as in the first shape, combined by the same 96-bit
 // arithmetic.
@@ -660,9 +674,9 @@ __device__ __forceinline__ void al_combine_pair(const uint32_t (&r)[S][2], uint3
 
 // Persistent like the first shape; maps[map0 + 2 s] and maps[map0 + 2 s + 1]
 // are slice buffer s's A-side (32 x 128 x S) and B-side (32 x 48 x S) boxes.
-// S is a template parameter: the S (S + 1) MMAs of a stage unroll into
-// constant descriptor offsets, so the single issuing thread keeps ahead of
-// the 128 x 48 x 16 MMAs (about 24 tensor cycles each).
+// S is a template parameter: the MMAs of a stage unroll into constant
+// descriptor offsets and instruction descriptors, so the single issuing
+// thread stays ahead of the tensor pipe.
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozaki_gemm_all_kernel(const OzDesc *__restrict__ descs, const OzTile *__restrict__ tiles, int ntile,
@@ -775,15 +789,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // address field (no carry: shared addresses stay below 256 KB)
             const uint64_t a0 = smem_desc_sw64(sa), b0 = smem_desc_sw64(sa + (uint32_t)S * AL_A_BYTES);
             const uint32_t later = kb != c0 ? 1u : 0u;  // the chunk's first MMA into a level starts it
+            // B_0 .. B_{S-1} are consecutive 48-row blocks of one K-major
+            // operand, so A_p times [B_0; ..; B_{S-1-p}] is one MMA of
+            // N = 48 (S - p) into the accumulators of levels p .. S-1 (adjacent
+            // TMEM columns), split at five levels (N <= 256): about S(S+1)/10
+            // instructions per k step, each reading A once from shared memory
 #pragma unroll
             for (int kk = 0; kk < AL_BK / 16; ++kk)
 #pragma unroll
               for (int p = 0; p < S; ++p)
 #pragma unroll
-                for (int q = 0; q < S - p; ++q)
-                  mma_bf16<AL_BN>(tmem + (uint32_t)((p + q) * AL_BN),
-                                  a0 + (uint64_t)(p * (AL_A_BYTES >> 4) + 2 * kk),
-                                  b0 + (uint64_t)(q * (AL_B_BYTES >> 4) + 2 * kk), (kk > 0 || p > 0) ? 1u : later);
+                for (int q0 = 0; q0 < S - p; q0 += 5) {
+                  const int nq = S - p - q0 < 5 ? S - p - q0 : 5;
+                  mma_bf16_id(tmem + (uint32_t)((p + q0) * AL_BN), a0 + (uint64_t)(p * (AL_A_BYTES >> 4) + 2 * kk),
+                              b0 + (uint64_t)(q0 * (AL_B_BYTES >> 4) + 2 * kk), idesc_n(nq * AL_BN),
+                              (kk > 0 || p > 0) ? 1u : later);
+                }
             mma_commit(smem_u32(&bar_empty[st]));
             if (++st == NST) {
               st = 0;
