@@ -889,16 +889,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int sgn = a_pow2 ? (int)((unsigned long long)ab >> 32) & (int)0x80000000 : 0;
           const bool has_beta = (__double_as_longlong(d.beta) << 1) != 0;
           const int ei = (int)((__double2hiint(s_scale[row]) >> 20) & 0x7FF) - 1023 - 6 * (S + 1) + ea;
+          // two store loops under one uniform test: a short conditional
+          // multiply or FMA inside the loop would be predicated, putting a
+          // DMUL, a DFMA and a read of C on every element
+          if (a_pow2 && !has_beta) {
 #pragma unroll
-          for (int j = 0; j < AL_CW; ++j) {
-            const int gj = j0 + j;
-            if (gj < d.n) {
-              const int ej = (int)((__double2hiint(s_scale[BM + half * AL_CW + j]) >> 20) & 0x7FF) - 1023;
-              double v = i96_ldexp(w0[j], w1[j], w2[j], ei + ej);
-              if (a_pow2) v = __hiloint2double(__double2hiint(v) ^ sgn, __double2loint(v));
-              else v *= d.alpha;
-              if (has_beta) v = fma(d.beta, crow[gj], v);
-              crow[gj] = v;
+            for (int j = 0; j < AL_CW; ++j) {
+              const int gj = j0 + j;
+              if (gj < d.n) {
+                const int ej = (int)((__double2hiint(s_scale[BM + half * AL_CW + j]) >> 20) & 0x7FF) - 1023;
+                const double v = i96_ldexp(w0[j], w1[j], w2[j], ei + ej);
+                crow[gj] = __hiloint2double(__double2hiint(v) ^ sgn, __double2loint(v));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < AL_CW; ++j) {
+              const int gj = j0 + j;
+              if (gj < d.n) {
+                const int ej = (int)((__double2hiint(s_scale[BM + half * AL_CW + j]) >> 20) & 0x7FF) - 1023;
+                double v = i96_ldexp(w0[j], w1[j], w2[j], ei + ej);
+                if (a_pow2) v = __hiloint2double(__double2hiint(v) ^ sgn, __double2loint(v));
+                else v *= d.alpha;
+                if (has_beta) v = fma(d.beta, crow[gj], v);
+                crow[gj] = v;
+              }
             }
           }
         }
