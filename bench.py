@@ -42,11 +42,11 @@ THETA = 0.999
 # bench reports it (per launch, like "achieved") only when their hash matches.
 TC_TRAFFIC = {
     "workload": "poisson_8x8_m400",
-    "dram_bytes_per_step": 24852646912,
+    "dram_bytes_per_step": 15820302336 + 2951762432,
     "launches_per_step": 26,
-    "sources_sha256": "5d7e898ba774b73d690de76bba78f6afd7bf359ae7f5a2541fcda52822a70bf9",
+    "sources_sha256": "cc1f8b4ee28b95cdeb5a1cffcd257f436310e5d14e8ed47563ece715e31d3a95",
     "source": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-               "--clock-control none -k regex:ozaki_gemm -s 26 -c 26 python bench.py --steps 1 --warmup 3 "
+               "--clock-control none -k regex:ozaki_gemm_all -s 26 -c 26 python bench.py --steps 1 --warmup 3 "
                "--no-cpu-baseline --no-fp64-compare --solve-steps 0 (second setup; per launch = step / 26)"),
 }
 TC_SOURCES = ("paper_2503_10032_gb300/csrc/ozaki_tc.cu", "paper_2503_10032_gb300/csrc/ozaki_plan.cpp",
@@ -461,7 +461,8 @@ def main():
     achieved = work_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else float("nan")
     traffic = None
     if (dom == "tc_gemm" and args.workload == TC_TRAFFIC["workload"] and prec == D.DDELM_PREC_MIXED
-            and args.scheme == "auto" and kernel_sources_sha256() == TC_TRAFFIC["sources_sha256"]):
+            and args.scheme == "auto" and args.tc_tiles == 0
+            and kernel_sources_sha256() == TC_TRAFFIC["sources_sha256"]):
         traffic = TC_TRAFFIC["dram_bytes_per_step"] / TC_TRAFFIC["launches_per_step"]
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak if math.isfinite(achieved) else None,
