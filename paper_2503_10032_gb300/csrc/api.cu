@@ -291,32 +291,21 @@ int compute_setup(ddelm_handle *h, cudaStream_t s, int *info_sub, bool capture) 
 
 // Choices of the tile-shape autotuner, kept for the life of the process and
 // shared by every handle: the key is the phase's shape (its products' sizes,
-// levels and triangular flags, and both tile counts), so a later handle with
-// the same phases (a new setup of the same problem) reuses the choice instead
-// of timing again.
+// levels and triangular flags, and the tile options), so a later handle with
+// the same phases (a new setup of the same problem) plans the chosen tile list
+// alone instead of timing again.
 std::mutex g_tune_mutex;
 std::unordered_map<unsigned long long, int> g_tune_bn;
 
-unsigned long long tune_key(const Plan &p, const OzPhase &ph) {
-  unsigned long long k = 1469598103934665603ull;  // FNV-1a over the shape
-  auto mix = [&](long long v) {
-    for (int b = 0; b < 8; ++b) {
-      k ^= (unsigned long long)((v >> (8 * b)) & 0xff);
-      k *= 1099511628211ull;
-    }
-  };
-  mix(ph.ntile);
-  mix(ph.ntile_alt);
-  mix(ph.bn);
-  for (int t = ph.desc0; t < ph.desc0 + ph.ndesc; ++t) {
-    const OzDesc &o = p.odesc[t];
-    mix(o.m);
-    mix(o.n);
-    mix(o.Kpad);
-    mix(o.S);
-  }
-  return k;
+}  // namespace
+
+int ddelm::tuned_tile_width(unsigned long long key) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  auto it = g_tune_bn.find(key);
+  return it == g_tune_bn.end() ? 0 : it->second;
 }
+
+namespace {
 
 // Every launch and copy of the setup, in stream order (no host synchronisation).
 int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
@@ -335,13 +324,8 @@ int enqueue_setup(ddelm_handle *h, cudaStream_t s) {
       if (h->tune_pending && !h->capturing && ph.overwrite && ph.ntile_alt > 0) {
         // autotuner: the other tile width, then the rule's (whose output stays);
         // the faster is kept for every later setup (and the captured graph)
-        const unsigned long long key = tune_key(p, ph);
-        int known = 0;
-        {
-          std::lock_guard<std::mutex> lk(g_tune_mutex);
-          auto it = g_tune_bn.find(key);
-          if (it != g_tune_bn.end()) known = it->second;
-        }
+        const unsigned long long key = ph.key;
+        const int known = tuned_tile_width(key);
         if (known) {  // timed before in this process: apply the choice
           if (known != ph.bn) {
             std::swap(ph.tile0, ph.tile0_alt);
@@ -852,7 +836,7 @@ int ddelm_inspect(ddelm_handle *h, int sub, int which, double *host_out, size_t 
     }
     case 11: {  // tile-shape autotuner: phases timed, phases switched, their ms by the rule / as chosen
       if (out_len < 4) return DDELM_ERR_INVALID_ARG;
-      host_out[0] = h->tune_phases;
+      host_out[0] = h->tune_phases + h->plan.tune_from_cache;
       host_out[1] = h->tune_switched;
       host_out[2] = h->tune_ms_rule;
       host_out[3] = h->tune_ms_chosen;

@@ -269,6 +269,9 @@ struct Plan {
   // tensor-core emulation of the setup GEMMs (precision MIXED)
   bool mixed = false;
   int tc_tiles = 0;               // tensor-core tile shapes allowed (the tc_tiles option)
+  bool autotune = false;          // the autotuner's alternative lists are planned
+  int tune_from_cache = 0;        // phases whose width an earlier handle's autotuner chose
+  bool maps_grp = false, maps_al = false;  // tensor-map families some tile list uses
   std::vector<SliceDesc> sdesc;
   std::vector<OzDesc> odesc;
   std::vector<OzTile> otile;

@@ -48,10 +48,15 @@ struct OzPhase {
   int tile0_alt, ntile_alt, bn_alt;
   int overwrite;         // every product has beta = 0: the phase may run twice
   double flops, flops_alt;  // slice-pair flops of the two tile lists
+  unsigned long long key;   // the phase's shape, the autotuner's cache key
 };
 
 cudaError_t launch_slices(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
 cudaError_t launch_oz_gemm(const Plan &p, const OzPhase &ph, void *ws, cudaStream_t s);
 cudaError_t preload_oz_kernels();
+
+// the tile width the autotuner chose earlier in this process for a phase of
+// this shape (0: none yet); defined with the autotuner
+int tuned_tile_width(unsigned long long key);
 
 }  // namespace ddelm

@@ -69,7 +69,7 @@ int build_mixed(Plan &P, long long &cur) {
   for (size_t q = 0; q < n_setup && q < P.setup_gemm.size(); ++q) {
     const GemmPhase &gp = P.setup_gemm[q];
     OzPhase op{int(P.sdesc.size()), 0, int(P.odesc.size()), 0, int(P.otile.size()), 0, 0, 0, 64, 0, 0, 64, 0, 0.0,
-               0.0};
+               0.0, 0ull};
     if (gp.ndesc == 0) {
       P.oz_phase[q] = op;
       continue;
@@ -94,7 +94,6 @@ int build_mixed(Plan &P, long long &cur) {
     // keeps the 64-wide level-group shape alone)
     const int grp_bn = (long_k || (wide && P.tc_tiles != 3)) ? 128 : 64;
     const int OZ_BN = (P.tc_tiles != 1 && P.tc_tiles != 3 && !long_k) ? OZ_AL_BN : grp_bn;
-    op.bn = OZ_BN;
     std::unordered_map<Key, int, KeyHash> seen;
     seen.reserve(2 * (size_t)gp.ndesc);
     long long elem = 0, scl = 0;
@@ -176,11 +175,49 @@ int build_mixed(Plan &P, long long &cur) {
           }
       }
     };
-    emit_tiles(OZ_BN, op.ntile, op.flops);
+    // the autotuner's key: the phase's product shapes and tile options
+    {
+      unsigned long long k = 1469598103934665603ull;  // FNV-1a
+      auto mix = [&](long long v) {
+        for (int b = 0; b < 8; ++b) {
+          k ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+          k *= 1099511628211ull;
+        }
+      };
+      mix(P.tc_tiles);
+      mix(S);
+      mix(gp.ndesc);
+      for (int t = 0; t < gp.ndesc; ++t) {
+        const GemmDesc &d = P.gdesc[gp.desc0 + t];
+        mix(d.m);
+        mix(d.n);
+        mix(d.k);
+        mix(d.flags | (d.syrk ? 1 << 20 : 0));
+      }
+      op.key = k;
+    }
+    int bn_rule = OZ_BN, bn_alt = OZ_BN == OZ_AL_BN ? grp_bn : (OZ_BN == 64 ? 128 : 64);
+    bool with_alt = P.autotune && op.overwrite && !long_k && P.tc_tiles < 2;
+    if (with_alt) {
+      // a width chosen for this shape by an earlier handle's autotuner: that
+      // list alone (nothing left to time)
+      const int known = tuned_tile_width(op.key);
+      if (known == bn_alt) std::swap(bn_rule, bn_alt);
+      if (known == bn_rule) {
+        with_alt = false;
+        P.tune_from_cache++;
+      }
+    }
+    op.bn = bn_rule;
+    emit_tiles(bn_rule, op.ntile, op.flops);
     P.oz_flops += op.flops;
-    op.bn_alt = OZ_BN == OZ_AL_BN ? grp_bn : (OZ_BN == 64 ? 128 : 64);
+    op.bn_alt = bn_alt;
     op.tile0_alt = int(P.otile.size());
-    if (!long_k && P.tc_tiles < 2) emit_tiles(op.bn_alt, op.ntile_alt, op.flops_alt);
+    if (with_alt) emit_tiles(op.bn_alt, op.ntile_alt, op.flops_alt);
+    for (const int bn : {op.bn, op.ntile_alt > 0 ? op.bn_alt : op.bn}) {
+      if (bn == OZ_AL_BN) P.maps_al = true;
+      else P.maps_grp = true;
+    }
     op.nslice = int(P.sdesc.size()) - op.slice0;
     for (int t = op.slice0; t < op.slice0 + op.nslice; ++t)
       if (P.sdesc[t].S != S) {  // the slicing launch takes one level count
@@ -237,6 +274,7 @@ int encode_tensor_maps(const Plan &P, void *ws, std::vector<unsigned char> &maps
                                     {(cuuint32_t)OZ_AL_BK, (cuuint32_t)OZ_BM, (cuuint32_t)s.S},
                                     {(cuuint32_t)OZ_AL_BK, (cuuint32_t)OZ_AL_BN, (cuuint32_t)s.S}};
     for (int v = 0; v < 3; ++v) {
+      if (v == 0 ? !P.maps_grp : !P.maps_al) continue;  // no tile list reads through this family
       CUtensorMap m;
       CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, gaddr, dims, strides, boxes[v], estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, v == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,

@@ -1358,6 +1358,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.precision == DDELM_PREC_MIXED) {
     P.mixed = true;
     P.tc_tiles = o.tc_tiles;
+    P.autotune = o.autotune != 0;
     if (build_mixed(P, cur) != DDELM_OK) {
       const std::string e = P.err.empty() ? std::string("mixed plan") : P.err;
       return fail(e.c_str());
