@@ -657,19 +657,20 @@ __device__ __forceinline__ float gam_pair(const Ctx &c, int sl, const SubDev &d,
 }
 
 // The vector S is applied to: x itself (xp == nullptr), or the CG direction
-// p' = r + beta p formed on the fly from the residual x and the previous
-// direction xp (columns with alpha == 0 keep p), bit for bit what the update
-// loop stores, so that no grid barrier has to separate that loop from the
+// The direction p_i = (r_{i-1} - a q_{i-1}) + b p_{i-1} formed on the fly from
+// vectors completed before the previous reduction (a = alpha_{i-1}, b =
+// beta_{i-1} per column; absent terms: null), bit for bit what the owners'
+// update stores, so that no grid barrier separates that update from the
 // next application.
 struct DirIn {
-  const float *x, *xp;
-  const float *alpha, *beta;  // per column, shared memory
+  const float *r, *q, *p;
+  const float *a, *b;  // per column, shared memory
 };
 __device__ __forceinline__ float dir_at(const DirIn &v, long long idx, int k) {
-  const float r = __ldcg(v.x + idx);
-  if (!v.xp) return r;
-  const float p = __ldcg(v.xp + idx);
-  return v.alpha[k] != 0.f ? fmaf(v.beta[k], p, r) : p;
+  float x = __ldcg(v.r + idx);
+  if (v.q) x = fmaf(-v.a[k], __ldcg(v.q + idx), x);
+  if (v.p) x = fmaf(v.b[k], __ldcg(v.p + idx), x);
+  return x;
 }
 
 // P1: H1 = Lambda_{Pi,Delta} x^, H2 = Psi_{Pi,Delta} x^ (the few Pi rows)
@@ -1016,74 +1017,145 @@ __device__ void f_partial_dot(const Ctx &c, const float *x, const float *y, int 
   __syncthreads();
 }
 
+// The owners' step after an application q_i = S32 p_i, over the element walk
+// of that application's last phase (no barrier between): r_i = r_{i-1} -
+// a q_{i-1}, p_i = r_i + b p_{i-1} (the values the application formed),
+// d += a p_{i-1}, and partial sums of (p_i, q_i), (r_i, q_i), then (q_i, q_i),
+// (r_i, r_i) for one reduction: pair h, sum j at red[h grid 32 + blk 32 +
+// j 16 + k].
+template <int RC>
+__device__ void f_dots2(const Ctx &c, const double (&acc)[2][RC], int pair) {
+  __shared__ double sred[CG_WARPS][2][16];
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < RC; ++k) sred[threadIdx.x >> 5][j][k] = acc[j][k];
+  __syncthreads();
+  if (threadIdx.x < 2 * RC) {
+    const int j = threadIdx.x / RC, k = threadIdx.x % RC;
+    double sm = 0.0;
+    for (int w = 0; w < CG_WARPS; ++w) sm += sred[w][j][k];
+    c.red[(long long)pair * gridDim.x * 32 + (long long)blockIdx.x * 32 + j * 16 + k] = sm;
+  }
+  __syncthreads();
+}
+
+template <int RC>
+__device__ void f_step_dots(const Ctx &c, float *Rv, float *Pv, float *Dv, const float *Qo, const float *Qn,
+                            const float *a, const float *b) {
+  const int R = c.R;
+  double acc[2][RC];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[j][k] = 0.0;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
+    const int col = e % R;
+    const float pold = Pv[e];
+    const float r = fmaf(-a[col], __ldcg(Qo + e), Rv[e]);
+    const float pn = fmaf(b[col], pold, r);
+    Dv[e] = fmaf(a[col], pold, Dv[e]);
+    Rv[e] = r;
+    Pv[e] = pn;
+    const double q = (double)__ldcg(Qn + e);
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k == col) {
+        acc[0][k] += (double)pn * q;
+        acc[1][k] += (double)r * q;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) warp_sum<RC>(acc[j]);
+  f_dots2<RC>(c, acc, 0);
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[j][k] = 0.0;
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {  // this thread's own r_i, just stored
+    const int col = e % R;
+    const double q = (double)__ldcg(Qn + e), r = (double)Rv[e];
+#pragma unroll
+    for (int k = 0; k < RC; ++k)
+      if (k == col) {
+        acc[0][k] += q * q;
+        acc[1][k] += r * r;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) warp_sum<RC>(acc[j]);
+  f_dots2<RC>(c, acc, 1);
+}
+
 // FP32 CG on S32 d = r (r already in F_R, d accumulates in F_D from 0), per
 // column until |r_k| <= tol_in |r_k(0)|; returns iterations or -1 (timeout).
+// One grid-wide reduction per iteration (the application's own barriers
+// aside): after q_i = S32 p_i the owners update r, p, d and reduce
+// (p_i, q_i), (r_i, q_i), (q_i, q_i), (r_i, r_i) together; alpha_i =
+// (r_i, r_i) / (p_i, q_i), and |r_{i+1}|^2 = (r_i, r_i) - 2 alpha_i (r_i, q_i) +
+// alpha_i^2 (q_i, q_i) gives beta_i and the stopping test before r_{i+1} is
+// formed (by the next iteration's owners, from the vectors of this one).
 template <int RC>
 __device__ int f_cg(const Ctx &c, const double *tol_in, int max_it) {
-  __shared__ double s_r0[16], s_rr[16], s_pq[16], s_rn[16];
-  __shared__ float s_alpha[16], s_beta[16];
+  __shared__ double s_r0[16], s_rn[16], s_d[4][16];
+  __shared__ float s_a[16], s_b[16];
   __shared__ int s_done;
-  float *Rv = c.fdl[F_R], *Dv = c.fdl[F_D], *Qv = c.fdl[F_Q];
-  float *P[2] = {c.fdl[F_P0], c.fdl[F_P1]};
+  float *Rv = c.fdl[F_R], *Dv = c.fdl[F_D], *Pv = c.fdl[F_P0];
+  float *Qb[2] = {c.fdl[F_Q], c.fdl[F_P1]};
   const int R = c.R;
   for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
-    P[0][e] = Rv[e];
+    Pv[e] = 0.f;
+    Qb[0][e] = 0.f;
     Dv[e] = 0.f;
   }
   f_partial_dot<RC>(c, Rv, Rv, 1);
   if (!grid_sync(c)) return -1;
-  finish_dot<RC>(c, 1, s_rr);
-  if (threadIdx.x < RC) s_r0[threadIdx.x] = s_rr[threadIdx.x];
+  finish_dot<RC>(c, 1, s_rn);
+  if (threadIdx.x < 16) {
+    s_r0[threadIdx.x] = threadIdx.x < RC ? s_rn[threadIdx.x] : 0.0;
+    s_a[threadIdx.x] = 0.f;  // p_0 = r_0: no previous direction
+    s_b[threadIdx.x] = 0.f;
+  }
   __syncthreads();
   int it = 0, cur = 0;
   while (true) {
     if (threadIdx.x == 0) {
       int done = 1;
       for (int k = 0; k < R && k < RC; ++k)
-        if (s_r0[k] > 0.0 && s_rr[k] > tol_in[k] * tol_in[k] * s_r0[k]) done = 0;
+        if (s_r0[k] > 0.0 && s_rn[k] > tol_in[k] * tol_in[k] * s_r0[k]) done = 0;
       s_done = done || it >= max_it;
     }
     __syncthreads();
     if (s_done) break;
-    // the direction of this iteration: P[cur], stored by the previous
-    // iteration's update without a barrier after it, so formed here from the
-    // residual and the previous direction
-    const DirIn dir = it == 0 ? DirIn{P[cur], nullptr, nullptr, nullptr} : DirIn{Rv, P[cur ^ 1], s_alpha, s_beta};
-    if (!f_apply_S<RC>(c, dir, Qv)) return -1;
-    f_partial_dot<RC>(c, P[cur], Qv, 0);
+    const DirIn dir{Rv, Qb[cur], Pv, s_a, s_b};
+    if (!f_apply_S<RC>(c, dir, Qb[cur ^ 1])) return -1;
+    f_step_dots<RC>(c, Rv, Pv, Dv, Qb[cur], Qb[cur ^ 1], s_a, s_b);
     if (!grid_sync(c)) return -1;
-    finish_dot<RC>(c, 0, s_pq);
-    if (threadIdx.x < RC) {
-      const int k = threadIdx.x;
-      const bool live = k < R && s_r0[k] > 0.0 && s_rr[k] > tol_in[k] * tol_in[k] * s_r0[k] && s_pq[k] != 0.0;
-      s_alpha[k] = live ? (float)(s_rr[k] / s_pq[k]) : 0.f;
+    if (threadIdx.x < 4 * RC) {
+      const int j = threadIdx.x / RC, k = threadIdx.x % RC;
+      const long long base = (long long)(j >> 1) * gridDim.x * 32;
+      double sm = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) sm += ldg_cg(c.red + base + (long long)b * 32 + (j & 1) * 16 + k);
+      s_d[j][k] = sm;
     }
     __syncthreads();
-    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
-      const float al = s_alpha[e % R];
-      Dv[e] = fmaf(al, P[cur][e], Dv[e]);
-      Rv[e] = fmaf(-al, __ldcg(Qv + e), Rv[e]);
-    }
-    f_partial_dot<RC>(c, Rv, Rv, 1);
-    if (!grid_sync(c)) return -1;
-    finish_dot<RC>(c, 1, s_rn);
     if (threadIdx.x < RC) {
       const int k = threadIdx.x;
-      s_beta[k] = (s_alpha[k] != 0.f && s_rr[k] > 0.0) ? (float)(s_rn[k] / s_rr[k]) : 0.f;
-      if (s_alpha[k] != 0.f) s_rr[k] = s_rn[k];
+      const double pq = s_d[0][k], rq = s_d[1][k], qq = s_d[2][k], rr = s_d[3][k];
+      const bool live = k < R && s_r0[k] > 0.0 && rr > tol_in[k] * tol_in[k] * s_r0[k] && pq != 0.0;
+      const double al = live ? rr / pq : 0.0;
+      const double rn = live ? fmax(rr - 2.0 * al * rq + al * al * qq, 0.0) : rr;
+      s_a[k] = (float)al;
+      s_b[k] = (live && rr > 0.0) ? (float)(rn / rr) : 0.f;
+      s_rn[k] = rn;
     }
     __syncthreads();
-    // the next direction goes to the other buffer, which this iteration's
-    // application read (before the barriers above); its next readers (the dot
-    // and the update of the next iteration) come after the next application's
-    // barriers, and that application forms the values itself
-    for (int e = gthread(); e < c.n_dl * R; e += nthreads()) {
-      const int k = e % R;
-      P[cur ^ 1][e] = s_alpha[k] != 0.f ? fmaf(s_beta[k], P[cur][e], Rv[e]) : P[cur][e];
-    }
     cur ^= 1;
     ++it;
   }
+  // the pending step d += alpha_i p_i of the last reduction
+  for (int e = gthread(); e < c.n_dl * R; e += nthreads()) Dv[e] = fmaf(s_a[e % R], Pv[e], Dv[e]);
   return it;
 }
 
@@ -1660,7 +1732,9 @@ cudaError_t launch_cg(const Plan &p, void *ws, const CgArgs &a, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int grid = nsm < 2048 ? nsm : 2048;
+  // at most 1022 CTAs: the inner CG's four per-CTA partial sums use twice
+  // the 32 entries per CTA of the 2048 x 32 reduction area (its last 64: info)
+  const int grid = nsm < 1022 ? nsm : 1022;
   void *args[] = {&c};
   DDELM_COUNT_LAUNCH();
   if (p.n_rhs == 1) return cudaLaunchCooperativeKernel((const void *)cg_kernel<1>, grid, CG_THREADS, args, 0, s);
