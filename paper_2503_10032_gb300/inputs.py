@@ -363,6 +363,9 @@ def config(name: str) -> Problem:
     if name == "poisson_4x4_m400":          # the 8x8 M=400 workload's per-subdomain shape on a 4x4 grid (profiling)
         return make_problem(4, 4, 400, 1600, 40, scale=32.0, init="paper", seed=1010,
                             solutions=[_sin2pix_cos3piy()], name=name)
+    if name == "poisson_8x8_m100":          # the 8x8 M=400 workload's interface (40 per edge) with M=100, 400 interior (profiling the CG)
+        return make_problem(8, 8, 100, 400, 40, scale=32.0, init="paper", seed=1011,
+                            solutions=[_sin2pix_cos3piy()], name=name)
     if name == "biharmonic_16x16":          # Sec. 4.5 at 16x16: M=256, 20x20 grid, 20 per edge, l=64
         return paper_scale(16, op=OP_BIHARMONIC)
     if name == "diffusion_4x4_m1000_r16":   # the 32x32 workload's per-subdomain shape on a 4x4 grid
