@@ -224,7 +224,19 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
 #pragma unroll
       for (int r = 0; r < NB; ++r) acc[r] = T(0);
       const int kend = min(j, i0 + W - 1);
-      for (int k = i1 + part; k <= kend; k += tpc) {
+      // eight loads of V in flight per thread before their FMAs (one at a time
+      // the loop waited an L2 round trip per k); the same accumulation order
+      int k = i1 + part;
+      for (; k + 7 * tpc <= kend; k += 8 * tpc) {
+        T vk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vk[u] = V[(long long)(k + u * tpc) * ld + j];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k + u * tpc - i0)], vk[u], acc[r]);
+      }
+      for (; k <= kend; k += tpc) {
         const T vk = V[(long long)k * ld + j];
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[r] = fma(P[r * W + (k - i0)], vk, acc[r]);
