@@ -160,11 +160,15 @@ __device__ void chol_inv_core(T *A, T *V, int M, int band, T *P, int *bad, int i
       const int nbt = (nt + 3) / 4;
       const int ntiles = nbt * (nbt + 1) / 2;
       for (int q = tid; q < ntiles; q += CT) {
-        int bi = 0, rem = q;
-        while (rem >= nbt - bi) {
-          rem -= nbt - bi;
-          ++bi;
-        }
+        // tile row bi: the largest b with S(b) = b nbt - b (b - 1) / 2 <= q (the
+        // tiles before row b), from the root of the quadratic, corrected to the
+        // exact integer (a linear search cost as much as the tile at M = 1000)
+        const int tw = 2 * nbt + 1;
+        int bi = (int)(0.5f * ((float)tw - sqrtf((float)(tw * tw - 8 * q))));
+        bi = max(0, min(bi, nbt - 1));
+        while (bi > 0 && bi * nbt - bi * (bi - 1) / 2 > q) --bi;
+        while (bi + 1 < nbt && (bi + 1) * nbt - (bi + 1) * bi / 2 <= q) ++bi;
+        const int rem = q - (bi * nbt - bi * (bi - 1) / 2);
         const int bj = bi + rem;
         const int i0 = T0 + 4 * bi, j0 = T0 + 4 * bj;
         T acc[4][4];
