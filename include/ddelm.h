@@ -160,15 +160,15 @@ typedef struct ddelm_options {
   int trim_mask;          /* 1 Grams after the first pass, 2 Q and ridge-block updates, 4 products
                              of triangular factors, 8 local operators and their inputs, 16 the
                              first Gram */
-  int chol_unblocked;     /* MIXED: 0 = the FP64 Cholesky passes of subdomains with M > 128 are
-                             blocked (the FP64 kernel factors and inverts the 128-wide diagonal
-                             blocks, tensor-core GEMMs form the panels and the trailing updates);
-                             1 = one CTA factors a whole matrix.  The blocked panels multiply by
-                             the explicit inverse of the diagonal block, which is not backward
-                             stable: with eps_rel = 1e-8 the second pass's Gram (condition ~1e11)
-                             fails the series check; use it for well-conditioned problems
-                             (eps_rel >= 1e-4, where it matches the unblocked factor to 1e-12).
-                             The Python binding passes 1 unless chol_blocked=True */
+  int chol_blocked;       /* MIXED, experimental: 1 = the FP64 Cholesky passes of subdomains with
+                             M > 128 are blocked (the FP64 kernel factors and inverts the 128-wide
+                             diagonal blocks, tensor-core GEMMs form the panels and the trailing
+                             updates); 0 (the default) = one CTA factors a whole matrix.  The
+                             blocked panels multiply by the explicit inverse of the diagonal
+                             block, which is not backward stable: with eps_rel = 1e-8 the second
+                             pass's Gram (condition ~1e11) fails the series check; use it for
+                             well-conditioned problems (eps_rel >= 1e-4, where it matches the
+                             unblocked factor to 1e-12 and saves ~1.8 ms per setup at 8x8/M=400) */
   int tc_tiles;           /* MIXED tensor-core tile shapes: 0 = the all-levels shape (128 x 48
                              tiles, every slice level of a 32-wide k block in one shared-memory
                              stage) by rule, with the level-group shape (128 x 64 or 128 x 128,

@@ -83,7 +83,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   if (o.autotune < 0 || o.autotune > 1) return fail("bad autotune");
   if (o.tc_tiles < 0 || o.tc_tiles > 3) return fail("bad tc_tiles");
   if (o.trim_levels < 0 || o.trim_levels > 6) return fail("bad trim_levels");
-  if (o.chol_unblocked < 0 || o.chol_unblocked > 1) return fail("bad chol_unblocked");
+  if (o.chol_blocked < 0 || o.chol_blocked > 1) return fail("bad chol_blocked");
   if (o.vanilla && o.theta != 0.0) return fail("vanilla DDELM takes theta = 0");
   P.opt = o;
   P.keep = o.keep_matrices != 0;
@@ -829,7 +829,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // matrix) inverts only the 128 x 128 diagonal blocks of R
   constexpr int INVB = 128;
   const bool blocked_inv = !fp32 && o.precision == DDELM_PREC_MIXED;
-  const bool blocked_fact = blocked_inv && !o.chol_unblocked;
+  const bool blocked_fact = blocked_inv && o.chol_blocked;
   const int N = P.n_pass;
   // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
   // accurate well below the shift; the later Grams, whose residual the series

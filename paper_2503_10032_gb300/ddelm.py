@@ -41,7 +41,7 @@ class ddelm_options(ctypes.Structure):
                 ("disable_graphs", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
                 ("inject_barrier_stall", ctypes.c_int), ("plain_flux_corners", ctypes.c_int),
                 ("vanilla", ctypes.c_int), ("autotune", ctypes.c_int), ("trim_levels", ctypes.c_int),
-                ("trim_mask", ctypes.c_int), ("chol_unblocked", ctypes.c_int), ("tc_tiles", ctypes.c_int)]
+                ("trim_mask", ctypes.c_int), ("chol_blocked", ctypes.c_int), ("tc_tiles", ctypes.c_int)]
 
 
 class ddelm_problem(ctypes.Structure):
@@ -145,7 +145,7 @@ def make_options(theta=0.999, eps_rel=1e-8, tol=1e-8, max_iters=5000, use_change
                          max_refine, int(keep_matrices), int(setup_wave), int(setup_scheme),
                          int(setup_passes), int(not graphs), int(barrier_timeout_ms),
                          int(inject_barrier_stall), int(not use_Am), int(not use_coarse), int(autotune),
-                         int(trim_levels), int(trim_mask), int(not chol_blocked), int(tc_tiles))
+                         int(trim_levels), int(trim_mask), int(chol_blocked), int(tc_tiles))
 
 
 class ProblemArgs:
