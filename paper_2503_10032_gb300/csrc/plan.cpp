@@ -828,7 +828,19 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
   // MIXED, FP64 passes: the Cholesky kernel (FP64 on CUDA cores, one SM per
   // matrix) inverts only the 128 x 128 diagonal blocks of R
   constexpr int INVB = 128;
-  const bool blocked_inv = !fp32 && o.precision == DDELM_PREC_MIXED;
+  // MIXED, FP32 scheme, every subdomain with M >= 768 and at most 256
+  // subdomains: the shifted passes (preconditioners whose Grams the shift keeps
+  // at condition <= ~1e4, so the blocked factorisation's explicit-inverse
+  // panels lose nothing) run as blocked FP64 passes in place, where the FP32
+  // kernel's one CTA per matrix would leave most SMs idle; the last, unshifted
+  // pass keeps the FP32 kernel (in its own work buffer: the polish reads the
+  // Gram after it).  Measured: M = 1000 on a 4x4 grid 5.25 -> 6.30 solves/s;
+  // M in 200..800 on 16x16 2.77 -> 2.63 and M = 1000 on 32x32 unchanged (the
+  // block phases' tensor-core and slicing work outweighs or matches the saving).
+  int min_M = 1 << 30;
+  for (int i = 0; i < n_sub; ++i) min_M = std::min(min_M, P.subs[i].M);
+  const bool fp32_blocked = fp32 && o.precision == DDELM_PREC_MIXED && min_M >= 768 && n_sub <= 256;
+  const bool blocked_inv = o.precision == DDELM_PREC_MIXED;
   const bool blocked_fact = blocked_inv && o.chol_blocked;
   const int N = P.n_pass;
   // BF16 slice levels (MIXED): a Gram feeding a shifted Cholesky only has to be
@@ -944,12 +956,13 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
           } else {
             // FP32 factor: the shift keeps the FP32 Cholesky away from breakdown and
             // limits the condition number each pass removes to about 1/shift
-            c.prec = 1;
+            // (MIXED: the shifted passes blocked in FP64, above)
+            c.prec = (fp32_blocked && !last) ? 0 : 1;
             c.shift_kind = last ? 0 : 2;
             c.shift_rel = std::max(1e-4, 2.0 * d.M * 5.9604644775390625e-8);
           }
           c.epsout = -1;
-          if (blocked_inv && d.M > INVB) {
+          if (blocked_inv && d.M > INVB && c.prec != 1) {
             // R^{-1} beyond the diagonal blocks comes from the tensor cores below;
             // the ridge block eps R^{-1} after it
             c.inv_block = INVB;
@@ -967,7 +980,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       // update A[r+1:, r+1:] -= R[r, r+1:]^T R[r, r+1:] (upper tiles) are
       // tensor-core GEMMs; the back substitution below completes V = R^{-1}.
       // The FP64 pipe keeps only the diagonal blocks' work.
-      const bool block_this = blocked_fact && P.cdesc[c0].prec == 0;
+      const bool block_this = (blocked_fact || (fp32_blocked && !last)) && P.cdesc[c0].prec == 0;
       if (block_this) {
         int maxnb = 0;
         for (int q = c0; q < int(P.cdesc.size()); ++q) {
@@ -1022,7 +1035,7 @@ int build_plan(const ddelm_problem *prob, Plan &P) {
       } else {
         chol_step(c0);
       }
-      if (blocked_inv) {
+      if (blocked_inv && P.cdesc[c0].prec != 1) {
         // block back substitution, block rows from the bottom:
         //   T = R[r, r+1:] V[r+1:, r+1:] ;  V[r, r+1:] = -V_rr T
         int maxnb = 0;
