@@ -3,9 +3,12 @@ word for word and checked against exact rational arithmetic (CPU): the
 balanced base-64 slice digits in offset form (slice_write_kernel), the FP32
 level sums read by bit extraction, four levels and three level groups summed
 exactly on 32-bit words and converted once with round-to-nearest-even
-(f32_exact_int, add96, i96_ldexp of ozaki_tc.cu), and the table-driven tanh
-of the feature kernels (tanh_half of features.cu: Tang's exponential with a
-Cody-Waite split of ln2/256), whose absolute error must stay below 2e-16."""
+(f32_exact_int, add96, i96_ldexp of ozaki_tc.cu), the all-levels kernel's
+FP32 fast readout of small level sums and its stacked-B MMA schedule, the
+Cholesky trailing update's closed-form tile row (chol.cu), and the
+table-driven tanh of the feature kernels (tanh_half of features.cu: Tang's
+exponential with a Cody-Waite split of ln2/256), whose absolute error must
+stay below 2e-16."""
 import math
 import random
 import struct
@@ -164,3 +167,88 @@ def test_table_driven_tanh_absolute_error():
         ref = mpmath.tanh(mpmath.mpf(u) / 2)
         worst = max(worst, float(abs(mpmath.mpf(_tanh_half(u, tab)) - ref)))
     assert worst < 2e-16, worst
+
+
+def _f32_magic_int(x):
+    """The all-levels epilogue's fast readout of an integer-valued FP32 sum:
+    the bits of x + 1.5 2^23 less those of 1.5 2^23."""
+    y = np.float32(x) + np.float32(12582912.0)
+    return int(np.array(y, dtype=np.float32).view(np.int32)) - 0x4B400000
+
+
+def test_fp32_fast_integer_readout():
+    # exact for every integer below 2^22 in magnitude (the kernel takes this
+    # path only when the warp's sums all are); sampled plus the edges
+    rng = random.Random(7)
+    vals = [0, 1, -1, 2 ** 22 - 1, -(2 ** 22 - 1), 2 ** 21, -(2 ** 21), 12345, -54321]
+    vals += [rng.randrange(-(2 ** 22) + 1, 2 ** 22) for _ in range(20000)]
+    for v in vals:
+        assert float(np.float32(v)) == v
+        assert _f32_magic_int(v) == v, v
+    # the guard is needed: beyond 2^22 the readout is wrong for some sums
+    bad = [v for v in (2 ** 22 + 1, 2 ** 23 - 3, -(2 ** 22) - 5) if _f32_magic_int(v) != v]
+    assert bad
+    # the guard's threshold: |x| < 2^22 exactly when the FP32 bits of |x| are below those of 2^22
+    two22 = int(np.array(np.float32(2.0 ** 22)).view(np.int32))
+    assert two22 == 0x4A800000
+
+
+def test_syrk_tile_row_closed_form():
+    """The Cholesky trailing update's tile row from the inverse of the
+    triangular count S(b) = b nbt - b (b - 1) / 2 (FP32 root, corrected to
+    the integer) equals the linear search for every tile, up to M = 1024."""
+    for nbt in list(range(1, 64)) + [100, 128, 200, 250, 256]:
+        ntiles = nbt * (nbt + 1) // 2
+        for q in range(ntiles):
+            bi, rem = 0, q
+            while rem >= nbt - bi:
+                rem -= nbt - bi
+                bi += 1
+            tw = 2 * nbt + 1
+            root = np.float32(math.sqrt(np.float32(tw * tw - 8 * q)))
+            b = int(np.float32(0.5) * (np.float32(tw) - root))
+            b = max(0, min(b, nbt - 1))
+            while b > 0 and b * nbt - b * (b - 1) // 2 > q:
+                b -= 1
+            while b + 1 < nbt and (b + 1) * nbt - (b + 1) * b // 2 <= q:
+                b += 1
+            assert (b, q - (b * nbt - b * (b - 1) // 2)) == (bi, rem), (nbt, q)
+
+
+@pytest.mark.parametrize("S", range(1, 11))
+def test_stacked_b_mma_schedule(S):
+    """The all-levels kernel's MMA schedule: per A level p, B levels q0 ..
+    q0 + n - 1 (n <= 5) stacked into one MMA of N = 48 n columns written at
+    TMEM column 48 (p + q0).  Every pair p + q < S lands once in the
+    accumulator of level p + q, N is a valid kind::f16 width for M = 128 (a
+    multiple of 16, at most 256) and the S accumulators fit 512 columns; the
+    first MMA into each level of a chunk (the one that starts it) is issued
+    before any other MMA into that level."""
+    BN = 48
+    hits = {}
+    first_seen = {}
+    order = 0
+    for kk in range(2):
+        for p in range(S):
+            q0 = 0
+            while q0 < S - p:
+                n = min(5, S - p - q0)
+                N = BN * n
+                assert N % 16 == 0 and 16 <= N <= 256
+                col0 = BN * (p + q0)
+                assert col0 + N <= BN * S <= 512
+                starts = not (kk > 0 or p > 0)  # accumulate flag 0 only for kk = 0, p = 0
+                for j in range(n):
+                    lvl = (col0 + BN * j) // BN
+                    assert lvl == p + q0 + j
+                    hits[(kk, p, q0 + j)] = hits.get((kk, p, q0 + j), 0) + 1
+                    if lvl not in first_seen:
+                        first_seen[lvl] = (order, starts)
+                order += 1
+                q0 += 5
+    for kk in range(2):
+        for p in range(S):
+            for q in range(S - p):
+                assert hits[(kk, p, q)] == 1
+    assert len(hits) == 2 * S * (S + 1) // 2
+    assert sorted(first_seen) == list(range(S)) and all(st for _, st in first_seen.values())
