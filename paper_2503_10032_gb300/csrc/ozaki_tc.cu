@@ -1007,30 +1007,32 @@ __global__ void __launch_bounds__(256) slice_write_kernel(const SliceDesc *__res
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   if (r0 >= s.R || k0 >= s.K) return;
   const double *X = db + s.x;
-  if (s.trans) {  // coalesced along r, transposed through shared memory
-    const int rr = threadIdx.x & 31;
-    for (int kk = threadIdx.x >> 5; kk < 64; kk += 8) {
-      const int r = r0 + rr, k = k0 + kk;
-      tile[rr][kk] = (r < s.R && k < s.K) ? X[(long long)k * s.ld + r] : 0.0;
-    }
-  } else {
-    const int kk = threadIdx.x & 63;
-    for (int rr = threadIdx.x >> 6; rr < 32; rr += 4) {
-      const int r = r0 + rr, k = k0 + kk;
-      tile[rr][kk] = (r < s.R && k < s.K) ? X[(long long)r * s.ld + k] : 0.0;
-    }
-  }
-  __syncthreads();
-  const int rr = threadIdx.x >> 3, kq = (threadIdx.x & 7) * 8;
+  const int rr = threadIdx.x >> 3, kq = (threadIdx.x & 7) * 8;  // this thread's row and 8 columns
   const int r = r0 + rr;
-  if (r >= s.R || k0 + kq >= s.K) return;
+  double xv[8];
+  if (s.trans) {  // coalesced along r, transposed through shared memory (uniform per block)
+    const int tr = threadIdx.x & 31;
+    for (int kk = threadIdx.x >> 5; kk < 64; kk += 8) {
+      const int rt = r0 + tr, k = k0 + kk;
+      tile[tr][kk] = (rt < s.R && k < s.K) ? X[(long long)k * s.ld + rt] : 0.0;
+    }
+    __syncthreads();
+    if (r >= s.R || k0 + kq >= s.K) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xv[j] = tile[rr][kq + j];
+  } else {  // row-contiguous: the 8 entries straight from global memory (a warp covers 4 rows x 512 B)
+    if (r >= s.R || k0 + kq >= s.K) return;
+    const double *xr = X + (long long)r * s.ld + k0 + kq;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xv[j] = k0 + kq + j < s.K ? xr[j] : 0.0;
+  }
   const long long sb = __double_as_longlong(db[s.scale + r]);
   const int e = int((sb >> 52) & 0x7FF) - 1023;
   constexpr unsigned long long off = ((1ull << (6 * S)) - 1ull) / 63ull * 32ull;
   unsigned wlo[8], whi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const unsigned long long w = fixed_offset(tile[rr][kq + j], 6 * S - 1075 - e, off);
+    const unsigned long long w = fixed_offset(xv[j], 6 * S - 1075 - e, off);
     wlo[j] = (unsigned)w;
     whi[j] = (unsigned)(w >> 32);
   }
