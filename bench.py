@@ -42,9 +42,9 @@ THETA = 0.999
 # bench reports it (per launch, like "achieved") only when their hash matches.
 TC_TRAFFIC = {
     "workload": "poisson_8x8_m400",
-    "dram_bytes_per_step": 15824409088 + 2950628096,
+    "dram_bytes_per_step": 15824769536 + 2952566528,
     "launches_per_step": 26,
-    "sources_sha256": "a4e29b9bdfb1a57f823bb40f49e725ca5e7795907370c18dd0f5d74eecb7cbe3",
+    "sources_sha256": "f6b4696adf81ef5ccc5333a6f58a9b7cd09c228739554440fbea621e862accf3",
     "source": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                "--clock-control none -k regex:ozaki_gemm_all -s 26 -c 26 python bench.py --steps 1 --warmup 3 "
                "--no-cpu-baseline --no-fp64-compare --solve-steps 0 (second setup; per launch = step / 26)"),
